@@ -1,0 +1,133 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds only input definitions: the counter-based random stream,
+initial wave functions and the workload parameter sets.  It contains none
+of the split-step arithmetic (no FFT, phase, normalisation of a step,
+reduction or cavity update); both the oracle and the CUDA path receive the
+same arrays from here.
+
+Random numbers: SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) gives 64-bit words from a
+counter; the top 53 bits make a double in [0, 1); Box-Muller turns pairs
+of uniforms into standard normals.
+
+Workloads follow the paper's physical setups (Sec. 4.1 timing benchmark:
+harmonic trap, imaginary time, grids N = 2^n; Sec. 5.1 trapped interacting
+BEC; Sec. 5.2 lattice pulse; Sec. 5.3 cavity self-organisation) in
+oscillator units (Sec. 3.2: hbar = m = omega = 1).  There is no dataset:
+these synthetic states stand in for the paper's experiments.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_MASK = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Words offset..offset+n-1 of the SplitMix64 stream for `seed`."""
+    with np.errstate(over="ignore"):
+        gamma = np.uint64(0x9E3779B97F4A7C15)
+        idx = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * gamma
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n doubles in [0, 1) from the top 53 bits of SplitMix64 words."""
+    w = splitmix64(seed, n, offset)
+    return (w >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """n standard normals by Box-Muller on consecutive uniform pairs."""
+    m = (n + 1) // 2
+    u = uniform(seed, 2 * m)
+    u1 = 1.0 - u[0::2]                      # (0, 1]: log is finite
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * m)
+    z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return z[:n]
+
+
+def grid_axis(n: int, L: float) -> np.ndarray:
+    """x_j = -L/2 + j L/n, j = 0..n-1: the periodic box without its right end."""
+    return -0.5 * L + np.arange(n) * (L / n)
+
+
+def gaussian_state(nx: int, ny: int, Lx: float, Ly: float, width: float = 1.5,
+                   noise: float = 1e-3, seed: int = 0, x0: float = 0.0,
+                   y0: float = 0.0, kx0: float = 0.0) -> np.ndarray:
+    """Initial wave function, complex128 [ny][nx], unit norm on the grid.
+
+    psi ~ exp(-((x-x0)^2 + (y-y0)^2) / (2 width^2)) e^{i kx0 x}, plus
+    noise * max|G| * (xi_r + i xi_i) with xi ~ N(0,1) per point from the
+    seeded stream, then scaled so that sum |psi|^2 dx dy = 1.
+    """
+    x = grid_axis(nx, Lx)[None, :]
+    y = grid_axis(ny, Ly)[:, None]
+    g = np.exp(-((x - x0) ** 2 + (y - y0) ** 2) / (2.0 * width ** 2)) * np.exp(1j * kx0 * x)
+    if noise:
+        xi = normal(seed, 2 * nx * ny).reshape(2, ny, nx)
+        g = g + noise * np.abs(g).max() * (xi[0] + 1j * xi[1])
+    s = np.sum(np.abs(g) ** 2) * (Lx / nx) * (Ly / ny)
+    return (g / np.sqrt(s)).astype(np.complex128)
+
+
+def uniform_state(nx: int, ny: int, Lx: float, Ly: float) -> np.ndarray:
+    """Constant wave function of unit norm (used for lattice pins)."""
+    return np.full((ny, nx), 1.0 / np.sqrt(Lx * Ly), dtype=np.complex128)
+
+
+def control_points(seed: int, n: int, T: float, lo: float, hi: float):
+    """n piecewise-linear control points at t_i = i T/(n-1), values uniform in [lo, hi]."""
+    t = np.linspace(0.0, T, n)
+    v = lo + (hi - lo) * uniform(seed, n)
+    return t, v
+
+
+# ---------------------------------------------------------------------------
+# Workloads.  Keys are the physical parameters of both implementations.
+# ---------------------------------------------------------------------------
+def potential_defaults() -> dict:
+    return dict(wx=0.0, wy=0.0, lat_V0x=0.0, lat_V0y=0.0, lat_kx=0.0, lat_ky=0.0,
+                Varr=None, V_scale=1.0, cavity=0, eta=0.0, U0=0.0, dc=0.0,
+                kappa=0.0, kc=0.0, Nat=1.0, pump_lattice=1, ctrl_target=0,
+                ctrl_t=None, ctrl_v=None)
+
+
+def harmonic_trap(n: int = 128, L: float = 20.0, g: float = 0.0, seed: int = 0) -> dict:
+    """Trapped BEC, V = r^2/2, imaginary time (Secs. 4.1 and 5.1): 128^2, box 20."""
+    p = potential_defaults()
+    p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=g, wx=1.0, wy=1.0)
+    return dict(params=p, dt=1e-3, imag=True, steps=2000,
+                psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed))
+
+
+def lattice_real_time(n: int = 2048, L: float = 40.0, seed: int = 1) -> dict:
+    """Real-time throughput workload: trap + 2D lattice V0 = 5, k = 2 pi, g = 500, dt = 5e-4."""
+    p = potential_defaults()
+    k = 2.0 * np.pi / 1.0
+    p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=500.0, wx=1.0, wy=1.0,
+             lat_V0x=5.0, lat_V0y=5.0, lat_kx=k, lat_ky=k)
+    return dict(params=p, dt=5e-4, imag=False, steps=10000,
+                psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed))
+
+
+def cavity_ramp(n: int = 512, L: float = 40.0, seed: int = 2, steps: int = 20000,
+                dt: float = 2e-4) -> dict:
+    """Self-consistent cavity (Sec. 5.3): eta ramped 0 -> 3 over the run, Delta_c = -2, U0 = -0.5, kappa = 1."""
+    p = potential_defaults()
+    k = 2.0 * np.pi / 1.0
+    T = steps * dt
+    p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=100.0, wx=1.0, wy=1.0,
+             cavity=1, eta=0.0, U0=-0.5, dc=-2.0, kappa=1.0, kc=k, Nat=1.0,
+             pump_lattice=1, ctrl_target=2,
+             ctrl_t=np.array([0.0, T]), ctrl_v=np.array([0.0, 3.0]))
+    return dict(params=p, dt=dt, imag=False, steps=steps,
+                psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed))
