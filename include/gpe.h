@@ -1,0 +1,165 @@
+/*
+ * gpe.h -- C ABI of the B300 (sm_103a) split-step Fourier propagator for the
+ * 2D Gross-Pitaevskii equation (TorchGPE, arXiv 2404.14401).
+ *
+ * The problem (Eq. 1, Sec. 2), in oscillator units (Sec. 3.2, hbar = 1):
+ *     i dpsi/dt = [ -lap/(2m) + V(x, y, t, psi) + g |psi|^2 ] psi
+ * on a periodic Nx x Ny grid (Sec. 3.1: the FFT imposes periodicity),
+ * x_j = -Lx/2 + j Lx/Nx, y_i = -Ly/2 + i Ly/Ny.
+ *
+ * One step of length dt is the symmetric (Strang) splitting of Sec. 3.1,
+ * Eqs. (2)-(4), taken in the order  V/2 - T - V/2:
+ *     psi <- exp(-i (V(t) + g|psi|^2) dt/2) psi
+ *     psi <- F^-1 exp(-i k^2 dt / 2m) F psi
+ *     psi <- exp(-i (V(t+dt) + g|psi|^2) dt/2) psi
+ * where each half-step uses the density at its start and, with a cavity,
+ * the field alpha recomputed from that density (Sec. 3.1 last paragraph,
+ * Sec. 5.3).  GPE_IMAG replaces dt by -i dtau and renormalises psi to
+ * unit norm after every step (Sec. 3.3).
+ *
+ * Data layout: psi is complex64 (interleaved float re, im), row-major
+ * [Ny][Nx], x contiguous, in device memory owned by the caller.  All
+ * device memory (psi, workspace, optional potential array) is borrowed:
+ * the library never allocates or frees device memory.  Calls on one
+ * context are not thread-safe; distinct contexts are independent.  Work
+ * is enqueued on the caller's CUDA stream; only gpe_observables,
+ * gpe_get_psi (to host) and gpe_sync wait for it.
+ *
+ * Every call returns a gpe_status; on error, gpe_last_error() gives a
+ * message.  Device-side conditions (non-finite values, an ill-conditioned
+ * cavity denominator, a bounded wait that ran out) are latched in a
+ * device status word and reported by gpe_sync / gpe_observables.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpe_ctx gpe_ctx;
+
+typedef enum {
+    GPE_OK = 0,
+    GPE_EINVAL = 1,      /* bad argument (sizes, pointers, alignment, dt)        */
+    GPE_ENOMEM = 2,      /* workspace smaller than gpe_workspace_size()          */
+    GPE_ECUDA = 3,       /* a CUDA runtime/driver call failed; see gpe_last_error */
+    GPE_ETIMEOUT = 4,    /* a bounded device wait (TMA barrier) ran out          */
+    GPE_ENONFINITE = 5,  /* NaN/Inf found in a norm or cavity reduction          */
+    GPE_EILLCOND = 6     /* |Delta_c - U0 B + i kappa| below 1e-12 (Eq. 14)      */
+} gpe_status;
+
+typedef enum { GPE_REAL = 0, GPE_IMAG = 1 } gpe_mode;
+
+/* Targets of the optional piecewise-linear control v(t). */
+typedef enum {
+    GPE_CTRL_NONE = 0,
+    GPE_CTRL_LATTICE = 1,   /* lattice depths become lat_V0x v(t), lat_V0y v(t) (Eq. 9) */
+    GPE_CTRL_ETA = 2        /* cavity pump eta(t) = v(t) (Sec. 5.3 ramp)               */
+} gpe_ctrl_target;
+
+/*
+ * Potential descriptor (plain data).  V(x, y, t; alpha) is the sum of
+ *   trap     (m/2)(wx^2 x^2 + wy^2 y^2)                        Sec. 5.1
+ *   lattice  s(t) [lat_V0x cos^2(lat_kx x) + lat_V0y cos^2(lat_ky y)]  Eq. (9)
+ *   array    V_scale * V[y][x]   (device float32 [Ny][Nx], borrowed; NULL = none)
+ *   cavity   (Eqs. 10-13, cavity axis x, pump axis y, wavenumber kc)
+ *            V_p = (eta^2/U0) cos^2(kc y)        (if pump_lattice and U0 != 0)
+ *            V_c = U0 |alpha|^2 cos^2(kc x)
+ *            V_i = 2 eta Re(alpha) cos(kc x) cos(kc y)
+ *            alpha = N eta O / (Delta_c - U0 B + i kappa)      Eqs. (14)-(15)
+ *            O = <cos(kc x) cos(kc y)>, B = <cos^2(kc x)> over |psi|^2/norm
+ * where eta = sqrt(V0 U0).  ctrl_t/ctrl_v (host, nctrl points, increasing
+ * times; copied) define v(t), clamped outside [ctrl_t[0], ctrl_t[n-1]].
+ */
+typedef struct {
+    double wx, wy;
+    double lat_V0x, lat_V0y, lat_kx, lat_ky;
+    const float *V;
+    double V_scale;
+    int cavity;
+    double eta, U0, dc, kappa, kc, N;
+    int pump_lattice;
+    int ctrl_target;
+    int nctrl;
+    const double *ctrl_t, *ctrl_v;
+} gpe_potential;
+
+/* Observables of the current state at the context's time t (host struct).
+ *   norm   = int |psi|^2                 ekin = <-lap/2m> (spectral, per axis Parseval)
+ *   epot   = int V |psi|^2 (alpha from this density)
+ *   eint   = (g/2) int |psi|^4           energy = ekin + epot + eint
+ *   mu     = ekin + epot + 2 eint        O, B, alpha as in gpe_potential
+ *   status = latched device status (gpe_status), cleared by this call.     */
+typedef struct {
+    double norm, ekin, epot, eint, energy, mu, O, B, alpha_re, alpha_im, t;
+    int status;
+} gpe_obs;
+
+/* Bytes of device workspace a context of this size needs (0 for bad sizes).
+ * Nx, Ny must be powers of two in [8, 8192] (Sec. 4.1 uses N = 2^n). */
+size_t gpe_workspace_size(int nx, int ny);
+
+/* Create a context.  psi_dev: complex64 [ny][nx], 16-byte aligned, borrowed
+ * for the context's life.  workspace_dev: >= gpe_workspace_size bytes,
+ * 256-byte aligned, borrowed.  stream: a cudaStream_t (NULL = legacy default).
+ * m > 0, Lx, Ly > 0.  The context starts at t = 0 with no potential.
+ * Errors: GPE_EINVAL (sizes/pointers/alignment), GPE_ENOMEM (workspace too
+ * small), GPE_ECUDA. *out is NULL on failure. */
+gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g,
+                      void *psi_dev, void *workspace_dev, size_t ws_bytes,
+                      void *stream, gpe_ctx **out);
+
+/* Set the potential (copied, except the borrowed V array).  Enqueues the
+ * FP64-computed coordinate tables on the stream.  Errors: GPE_EINVAL. */
+gpe_status gpe_set_potential(gpe_ctx *ctx, const gpe_potential *p);
+
+/* Enqueue n >= 0 split steps of length dt > 0 (Sec. 3.1; GPE_IMAG: Sec. 3.3),
+ * advancing the context's time by n dt.  psi is in real space before and
+ * after.  Asynchronous.  Errors: GPE_EINVAL, GPE_ECUDA. */
+gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
+
+/* Compute the observables of psi at the current time; waits for the stream.
+ * Returns the latched device status if it is not GPE_OK (out is filled). */
+gpe_status gpe_observables(gpe_ctx *ctx, gpe_obs *out);
+
+/* Copy psi from src (complex64 [ny][nx]) -- host memory if is_dev == 0,
+ * device memory otherwise.  Stream-ordered (host source must stay valid
+ * until the stream reaches the copy; pinned memory makes it asynchronous). */
+gpe_status gpe_set_psi(gpe_ctx *ctx, const void *src, int is_dev);
+
+/* Copy psi to dst; a host destination waits for the stream. */
+gpe_status gpe_get_psi(gpe_ctx *ctx, void *dst, int is_dev);
+
+/* Set / read the context's time t (used by V(t) and the controls). */
+gpe_status gpe_set_time(gpe_ctx *ctx, double t);
+double gpe_get_time(const gpe_ctx *ctx);
+
+/* In-place 2D DFT of psi with the propagator's own FFT passes (diagnostic):
+ * sign = -1 forward (unnormalised), +1 inverse (divides by nx ny).  The
+ * same row/column kernels as gpe_step with the phases switched off. */
+gpe_status gpe_fft2(gpe_ctx *ctx, int sign);
+
+/* Wait for the stream; return and clear the latched device status. */
+gpe_status gpe_sync(gpe_ctx *ctx);
+
+/* Run one kernel whose bounded barrier wait is given nothing to wait for,
+ * so it must run out after about `spins` polls and latch GPE_ETIMEOUT
+ * (failure-path check of the timeout mechanism; touches no psi data).  */
+gpe_status gpe_debug_timeout_probe(gpe_ctx *ctx, int spins);
+
+/* Release the context (host memory only; borrowed memory is untouched). */
+void gpe_destroy(gpe_ctx *ctx);
+
+/* Message for the last error on ctx (never NULL). */
+const char *gpe_last_error(const gpe_ctx *ctx);
+
+/* Name of a status code. */
+const char *gpe_status_string(gpe_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPE_H */

@@ -1,0 +1,111 @@
+"""B300-native (sm_103a) split-step Fourier propagator for the 2D Gross-Pitaevskii
+equation (TorchGPE, arXiv 2404.14401): symmetric splitting in real and
+imaginary time, with the self-consistent cavity potential of Sec. 5.3.
+
+The compute path is the C ABI of include/gpe.h implemented by hand-written
+CUDA kernels in csrc/ (libgpe.so).  PyTorch provides only device memory and
+streams.  `Simulation` owns the torch allocations a context borrows.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import gpe as abi
+from .gpe import GPE_CTRL_ETA, GPE_CTRL_LATTICE, GPE_CTRL_NONE, GPE_IMAG, GPE_REAL, GPEError  # noqa: F401
+
+
+class Simulation:
+    """One grid: psi (complex64 [ny][nx]) and workspace allocated with torch on
+    `device`, a gpe context bound to `stream` (torch.cuda.Stream or None for
+    the current stream).  Methods are one C call each."""
+
+    def __init__(self, nx, ny, Lx, Ly, m=1.0, g=0.0, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.nx, self.ny, self.Lx, self.Ly, self.m, self.g = nx, ny, Lx, Ly, m, g
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ws = abi.gpe_workspace_size(nx, ny)
+        if ws == 0:
+            raise GPEError(abi.GPE_EINVAL, f"unsupported grid {nx}x{ny}")
+        self.psi = torch.zeros((ny, nx), dtype=torch.complex64, device=self.device)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self._keep = []
+        self.ctx = abi.gpe_create(nx, ny, Lx, Ly, m, g, self.psi.data_ptr(), self.ws.data_ptr(), ws,
+                                  self.stream.cuda_stream)
+
+    # ------------------------------------------------------------ set-up
+    def set_potential(self, p: dict):
+        """p uses the keys of gpe_inputs.potential_defaults(); a `Varr` array is
+        copied to a float32 device tensor that the context borrows."""
+        torch = self.torch
+        pot = abi.gpe_potential()
+        for k in ("wx", "wy", "lat_V0x", "lat_V0y", "lat_kx", "lat_ky", "V_scale", "cavity", "eta", "U0",
+                  "dc", "kappa", "kc", "pump_lattice", "ctrl_target"):
+            setattr(pot, k, p.get(k, 0) if k != "V_scale" else p.get(k, 1.0))
+        pot.N = p.get("Nat", p.get("N", 1.0))
+        keep = []
+        if p.get("Varr") is not None:
+            V = torch.as_tensor(np.asarray(p["Varr"], dtype=np.float32)).to(self.device)
+            keep.append(V)
+            pot.V = V.data_ptr()
+        if p.get("ctrl_t") is not None:
+            t = np.ascontiguousarray(p["ctrl_t"], dtype=np.float64)
+            v = np.ascontiguousarray(p["ctrl_v"], dtype=np.float64)
+            keep += [t, v]
+            pot.nctrl = t.size
+            pot.ctrl_t = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            pot.ctrl_v = v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        abi.gpe_set_potential(self.ctx, pot)
+        self._keep = keep                                    # the device V array stays borrowed
+
+    def set_psi(self, psi):
+        """psi: numpy array (copied from host) or a complex64 cuda tensor."""
+        torch = self.torch
+        if isinstance(psi, np.ndarray):
+            h = torch.from_numpy(np.ascontiguousarray(psi, dtype=np.complex64))
+            abi.gpe_set_psi(self.ctx, h.data_ptr(), False)
+            self.sync()
+        else:
+            t = psi.to(device=self.device, dtype=torch.complex64).contiguous()
+            abi.gpe_set_psi(self.ctx, t.data_ptr(), True)
+            self._tmp = t
+
+    def get_psi(self) -> np.ndarray:
+        out = np.empty((self.ny, self.nx), dtype=np.complex64)
+        abi.gpe_get_psi(self.ctx, out.ctypes.data, False)
+        return out
+
+    # ------------------------------------------------------------ evolution
+    def step(self, n: int, dt: float, imag: bool = False):
+        abi.gpe_step(self.ctx, n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
+
+    def observables(self, check: bool = True) -> dict:
+        return abi.gpe_observables(self.ctx, check)
+
+    def fft2(self, sign: int):
+        abi.gpe_fft2(self.ctx, sign)
+
+    @property
+    def t(self) -> float:
+        return abi.gpe_get_time(self.ctx)
+
+    @t.setter
+    def t(self, value: float):
+        abi.gpe_set_time(self.ctx, value)
+
+    def sync(self) -> int:
+        return abi.gpe_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            abi.gpe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,470 @@
+// gpe_api.cu -- the C ABI of include/gpe.h: context, potential descriptor,
+// and the host scheduler that turns gpe_step(n, dt, mode) into the sequence
+// of row / column passes of the symmetric split-step (Sec. 3.1, Eqs. 2-4;
+// imaginary time Sec. 3.3; cavity Sec. 5.3, Eqs. 10-15).
+//
+// Pass schedules (R = row pass, C = column pass; psi is real-space at entry
+// and exit of every call):
+//   real time, no cavity   R_fwd(V/2) C { R_merged(V) C }^(n-1) R_inv(V/2)
+//       the two half phases V(t_n)/2 of adjacent steps use the same density
+//       (a real phase keeps |psi|) and merge into one full phase;
+//   real time, cavity      as above with a reduce-only row pass before every
+//       phase: alpha needs the grid-wide overlaps of the current density;
+//   imaginary time         { R_fwd([c] V/2) C [R_reduce] R_inv(V/2 + norm) }^n R_scale
+//       the norm of the step's result (Sec. 3.3) and, with a cavity, alpha
+//       are grid-wide, so they are reduced in R_inv and applied in the next
+//       R_fwd as a scale.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/gpe.h"
+#include "gpe_internal.h"
+
+using namespace gpe;
+
+struct gpe_ctx {
+    int nx, ny;
+    double Lx, Ly, m, g;
+    float2 *psi;
+    unsigned char *ws;
+    size_t ws_bytes;
+    cudaStream_t stream;
+    Tables T;
+    CUtensorMap map;
+    int W;
+    gpe_potential pot;
+    std::vector<double> ctrl_t, ctrl_v;
+    double t;
+    double kin_dt;
+    int kin_mode;
+    bool kin_valid;
+    int spins;
+    char err[256];
+};
+
+namespace {
+
+bool pow2_in_range(int n) { return n >= 8 && n <= 8192 && (n & (n - 1)) == 0; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t sc, part_row, part_col, twx, twy, xtab, ytab, kinx, kiny, total;
+};
+
+Layout layout(int nx, int ny)
+{
+    Layout L;
+    size_t o = 0;
+    L.sc = o;        o = align256(o + sizeof(DevScalars));
+    L.part_row = o;  o = align256(o + sizeof(double) * NQ * MAX_BLOCKS);
+    L.part_col = o;  o = align256(o + sizeof(double) * NQ * MAX_BLOCKS);
+    L.twx = o;       o = align256(o + sizeof(float2) * nx);
+    L.twy = o;       o = align256(o + sizeof(float2) * ny);
+    L.xtab = o;      o = align256(o + sizeof(float4) * nx);
+    L.ytab = o;      o = align256(o + sizeof(float4) * ny);
+    L.kinx = o;      o = align256(o + sizeof(float2) * nx);
+    L.kiny = o;      o = align256(o + sizeof(float2) * ny);
+    L.total = o;
+    return L;
+}
+
+gpe_status fail(gpe_ctx *c, gpe_status s, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+gpe_status cuda_check(gpe_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return GPE_OK;
+    return fail(c, GPE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+gpe_status make_tensor_map(gpe_ctx *c)
+{
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(c, GPE_ECUDA, "cuTensorMapEncodeTiled not available");
+        encode = (EncodeTiledFn)fn;
+    }
+    // psi viewed as float32 [ny][2 nx]; box = W complex columns x BR rows
+    const int BR = c->ny < 256 ? c->ny : 256;
+    cuuint64_t dims[2] = {(cuuint64_t)2 * c->nx, (cuuint64_t)c->ny};
+    cuuint64_t strides[1] = {(cuuint64_t)2 * c->nx * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * c->W), (cuuint32_t)BR};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&c->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->psi, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, GPE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GPE_OK;
+}
+
+// piecewise-linear control v(t), clamped at both ends
+double control_value(const gpe_ctx *c, double t)
+{
+    const size_t n = c->ctrl_t.size();
+    if (n == 0) return 1.0;
+    if (t <= c->ctrl_t[0]) return c->ctrl_v[0];
+    if (t >= c->ctrl_t[n - 1]) return c->ctrl_v[n - 1];
+    size_t lo = 0, hi = n - 1;                     // ctrl_t[lo] < t < ctrl_t[hi]
+    while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (c->ctrl_t[mid] < t) lo = mid; else hi = mid;
+    }
+    const double f = (t - c->ctrl_t[lo]) / (c->ctrl_t[hi] - c->ctrl_t[lo]);
+    return c->ctrl_v[lo] + f * (c->ctrl_v[hi] - c->ctrl_v[lo]);
+}
+
+double eta_at(const gpe_ctx *c, double t)
+{
+    return c->pot.ctrl_target == GPE_CTRL_ETA ? control_value(c, t) : c->pot.eta;
+}
+
+PhaseArgs phase_at(const gpe_ctx *c, double t, double h)
+{
+    const gpe_potential &p = c->pot;
+    const double ls = p.ctrl_target == GPE_CTRL_LATTICE ? control_value(c, t) : 1.0;
+    const double eta = eta_at(c, t);
+    PhaseArgs a;
+    a.h = (float)h;
+    a.a_latx = (float)(p.lat_V0x * ls);
+    a.a_laty = (float)(p.lat_V0y * ls);
+    a.a_pump = (p.cavity && p.pump_lattice && p.U0 != 0.0) ? (float)(eta * eta / p.U0) : 0.f;
+    a.U0 = p.cavity ? (float)p.U0 : 0.f;
+    a.two_eta = p.cavity ? (float)(2.0 * eta) : 0.f;
+    a.use_alpha = p.cavity ? 1 : 0;
+    return a;
+}
+
+RedArgs red_at(const gpe_ctx *c, double t)
+{
+    RedArgs r;
+    r.eta = eta_at(c, t);
+    r.U0 = c->pot.U0;
+    r.dc = c->pot.dc;
+    r.kappa = c->pot.kappa;
+    r.N = c->pot.N;
+    r.dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
+    r.cavity = c->pot.cavity;
+    return r;
+}
+
+RowArgs row_args(const gpe_ctx *c)
+{
+    RowArgs a;
+    memset(&a, 0, sizeof(a));
+    a.psi = c->psi;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.V = c->pot.V;
+    a.V_scale = (float)c->pot.V_scale;
+    a.g = (float)c->g;
+    a.T = c->T;
+    a.red = red_at(c, c->t);
+    return a;
+}
+
+ColArgs col_args(const gpe_ctx *c, int imag)
+{
+    ColArgs a;
+    a.psi = c->psi;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.W = c->W;
+    a.G = col_group(c->ny, c->W);
+    a.imag = imag;
+    a.scale = (float)(1.0 / ((double)c->nx * (double)c->ny));   // exact: a power of two
+    a.spins = c->spins;
+    a.T = c->T;
+    return a;
+}
+
+gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag, int use_c)
+{
+    RowArgs a = row_args(c);
+    a.ph = ph;
+    a.red = rd;
+    a.imag = imag;
+    a.use_c = use_c;
+    return cuda_check(c, launch_row(mode, a, c->stream), "row pass");
+}
+
+gpe_status run_col(gpe_ctx *c, int mode, int imag)
+{
+    return cuda_check(c, launch_col(mode, col_args(c, imag), c->map, c->stream), "column pass");
+}
+
+#define TRY(x)                                   \
+    do {                                         \
+        gpe_status _s = (x);                     \
+        if (_s != GPE_OK) return _s;             \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char *gpe_status_string(gpe_status s)
+{
+    switch (s) {
+    case GPE_OK: return "GPE_OK";
+    case GPE_EINVAL: return "GPE_EINVAL";
+    case GPE_ENOMEM: return "GPE_ENOMEM";
+    case GPE_ECUDA: return "GPE_ECUDA";
+    case GPE_ETIMEOUT: return "GPE_ETIMEOUT";
+    case GPE_ENONFINITE: return "GPE_ENONFINITE";
+    case GPE_EILLCOND: return "GPE_EILLCOND";
+    default: return "GPE_UNKNOWN";
+    }
+}
+
+size_t gpe_workspace_size(int nx, int ny)
+{
+    if (!pow2_in_range(nx) || !pow2_in_range(ny)) return 0;
+    return layout(nx, ny).total;
+}
+
+gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, void *psi_dev,
+                      void *workspace_dev, size_t ws_bytes, void *stream, gpe_ctx **out)
+{
+    if (!out) return GPE_EINVAL;
+    *out = nullptr;
+    if (!pow2_in_range(nx) || !pow2_in_range(ny)) return GPE_EINVAL;
+    if (!(Lx > 0.0) || !(Ly > 0.0) || !(m > 0.0) || !isfinite(g)) return GPE_EINVAL;
+    if (!psi_dev || ((uintptr_t)psi_dev & 15u)) return GPE_EINVAL;
+    if (!workspace_dev || ((uintptr_t)workspace_dev & 255u)) return GPE_EINVAL;
+    const Layout L = layout(nx, ny);
+    if (ws_bytes < L.total) return GPE_ENOMEM;
+
+    gpe_ctx *c = new gpe_ctx();
+    c->nx = nx; c->ny = ny; c->Lx = Lx; c->Ly = Ly; c->m = m; c->g = g;
+    c->psi = (float2 *)psi_dev;
+    c->ws = (unsigned char *)workspace_dev;
+    c->ws_bytes = ws_bytes;
+    c->stream = (cudaStream_t)stream;
+    c->W = col_tile_width(nx, ny);
+    c->t = 0.0;
+    c->kin_valid = false;
+    c->spins = 1 << 24;
+    memset(&c->pot, 0, sizeof(c->pot));
+    c->pot.V_scale = 1.0;
+    c->pot.N = 1.0;
+    c->err[0] = 0;
+    Tables &T = c->T;
+    T.sc = (DevScalars *)(c->ws + L.sc);
+    T.part_row = (double *)(c->ws + L.part_row);
+    T.part_col = (double *)(c->ws + L.part_col);
+    T.twx = (float2 *)(c->ws + L.twx);
+    T.twy = (float2 *)(c->ws + L.twy);
+    T.xtab = (float4 *)(c->ws + L.xtab);
+    T.ytab = (float4 *)(c->ws + L.ytab);
+    T.kinx = (float2 *)(c->ws + L.kinx);
+    T.kiny = (float2 *)(c->ws + L.kiny);
+
+    gpe_status s = make_tensor_map(c);
+    if (s == GPE_OK) s = cuda_check(c, cudaMemsetAsync(T.sc, 0, sizeof(DevScalars), c->stream), "memset");
+    if (s == GPE_OK)
+        s = cuda_check(c, launch_tables(T, nx, ny, Lx, Ly, m, 0, 0, 0, 0, 0, c->stream), "tables");
+    if (s != GPE_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return GPE_OK;
+}
+
+gpe_status gpe_set_potential(gpe_ctx *c, const gpe_potential *p)
+{
+    if (!c || !p) return GPE_EINVAL;
+    if (p->nctrl < 0 || (p->nctrl > 0 && (!p->ctrl_t || !p->ctrl_v)))
+        return fail(c, GPE_EINVAL, "control table: nctrl %d with null arrays", p->nctrl);
+    if (p->ctrl_target < GPE_CTRL_NONE || p->ctrl_target > GPE_CTRL_ETA)
+        return fail(c, GPE_EINVAL, "unknown control target %d", p->ctrl_target);
+    if (p->ctrl_target != GPE_CTRL_NONE && p->nctrl < 1)
+        return fail(c, GPE_EINVAL, "control target set without control points");
+    for (int i = 1; i < p->nctrl; ++i)
+        if (!(p->ctrl_t[i] > p->ctrl_t[i - 1]))
+            return fail(c, GPE_EINVAL, "control times must increase");
+    if (p->cavity && !(p->kappa >= 0.0)) return fail(c, GPE_EINVAL, "kappa must be >= 0");
+    if (p->V && ((uintptr_t)p->V & 3u)) return fail(c, GPE_EINVAL, "potential array misaligned");
+    c->pot = *p;
+    c->ctrl_t.assign(p->ctrl_t, p->ctrl_t + p->nctrl);
+    c->ctrl_v.assign(p->ctrl_v, p->ctrl_v + p->nctrl);
+    c->pot.ctrl_t = nullptr;
+    c->pot.ctrl_v = nullptr;
+    return cuda_check(c, launch_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, p->wx, p->wy, p->lat_kx,
+                                       p->lat_ky, p->cavity ? p->kc : 0.0, c->stream),
+                      "tables");
+}
+
+gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
+{
+    if (!c) return GPE_EINVAL;
+    if (n < 0 || !(dt > 0.0) || !isfinite(dt) || (mode != GPE_REAL && mode != GPE_IMAG))
+        return fail(c, GPE_EINVAL, "gpe_step: n %d dt %g mode %d", n, dt, (int)mode);
+    if (n == 0) return GPE_OK;
+    const int imag = mode == GPE_IMAG;
+    if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
+        TRY(cuda_check(c, launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream),
+                       "kinetic tables"));
+        c->kin_valid = true;
+        c->kin_dt = dt;
+        c->kin_mode = (int)mode;
+    }
+    const bool cav = c->pot.cavity != 0;
+    const double t0 = c->t;
+    PhaseArgs none;
+    memset(&none, 0, sizeof(none));
+    if (!imag) {
+        if (cav) TRY(run_row(c, ROW_REDUCE_R, none, red_at(c, t0), 0, 0));
+        TRY(run_row(c, ROW_FWD, phase_at(c, t0, 0.5 * dt), red_at(c, t0), 0, 0));
+        TRY(run_col(c, COL_KIN, 0));
+        for (int s = 1; s < n; ++s) {
+            const double ts = t0 + s * dt;
+            if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, ts), 0, 0));
+            TRY(run_row(c, ROW_MERGED, phase_at(c, ts, dt), red_at(c, ts), 0, 0));
+            TRY(run_col(c, COL_KIN, 0));
+        }
+        const double tn = t0 + n * dt;
+        if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, tn), 0, 0));
+        TRY(run_row(c, ROW_INV, phase_at(c, tn, 0.5 * dt), red_at(c, tn), 0, 0));
+    } else {
+        if (cav) TRY(run_row(c, ROW_REDUCE_R, none, red_at(c, t0), 1, 0));
+        for (int s = 0; s < n; ++s) {
+            const double ts = t0 + s * dt, te = t0 + (s + 1) * dt;
+            TRY(run_row(c, ROW_FWD, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 1, s > 0));
+            TRY(run_col(c, COL_KIN, 1));
+            if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, te), 1, 0));
+            TRY(run_row(c, ROW_INV, phase_at(c, te, 0.5 * dt), red_at(c, te), 1, 0));
+        }
+        TRY(run_row(c, ROW_SCALE, none, red_at(c, t0 + n * dt), 1, 0));
+    }
+    c->t = t0 + n * dt;
+    return GPE_OK;
+}
+
+gpe_status gpe_observables(gpe_ctx *c, gpe_obs *out)
+{
+    if (!c || !out) return GPE_EINVAL;
+    TRY(run_row(c, ROW_OBS, phase_at(c, c->t, 0.0), red_at(c, c->t), 0, 0));
+    TRY(run_col(c, COL_OBS, 0));
+    DevScalars h;
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, c->T.sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy"));
+    TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->status, 0, sizeof(int), c->stream), "memset"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    const double dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
+    const double *S = h.sums[0];
+    const double kx = 2.0 * M_PI / c->Lx, ky = 2.0 * M_PI / c->Ly;
+    memset(out, 0, sizeof(*out));
+    out->t = c->t;
+    out->norm = S[0] * dxdy;
+    out->ekin = (kx * kx * S[6] / c->nx + ky * ky * h.sums[1][0] / c->ny) * dxdy / (2.0 * c->m);
+    double epot = S[1] * dxdy;
+    if (c->pot.cavity) {
+        const double O = S[3] / S[0], B = S[4] / S[0];
+        const double eta = eta_at(c, c->t);
+        const double dr = c->pot.dc - c->pot.U0 * B, di = c->pot.kappa, den = dr * dr + di * di;
+        const double num = c->pot.N * eta * O;
+        const double ar = den > 0 ? num * dr / den : 0.0, ai = den > 0 ? -num * di / den : 0.0;
+        out->O = O;
+        out->B = B;
+        out->alpha_re = ar;
+        out->alpha_im = ai;
+        epot += c->pot.U0 * (ar * ar + ai * ai) * S[4] * dxdy + 2.0 * eta * ar * S[3] * dxdy;
+    }
+    out->epot = epot;
+    out->eint = 0.5 * c->g * S[2] * dxdy;
+    out->energy = out->ekin + out->epot + out->eint;
+    out->mu = out->ekin + out->epot + 2.0 * out->eint;
+    out->status = h.status;
+    if (!isfinite(out->norm) || !isfinite(out->energy)) out->status = out->status ? out->status : GPE_ENONFINITE;
+    return out->status ? fail(c, (gpe_status)out->status, "device status %s", gpe_status_string((gpe_status)out->status))
+                       : GPE_OK;
+}
+
+gpe_status gpe_set_psi(gpe_ctx *c, const void *src, int is_dev)
+{
+    if (!c || !src) return GPE_EINVAL;
+    return cuda_check(c, cudaMemcpyAsync(c->psi, src, sizeof(float2) * c->nx * c->ny,
+                                         is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+                      "set_psi");
+}
+
+gpe_status gpe_get_psi(gpe_ctx *c, void *dst, int is_dev)
+{
+    if (!c || !dst) return GPE_EINVAL;
+    TRY(cuda_check(c, cudaMemcpyAsync(dst, c->psi, sizeof(float2) * c->nx * c->ny,
+                                      is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+                   "get_psi"));
+    if (!is_dev) TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    return GPE_OK;
+}
+
+gpe_status gpe_set_time(gpe_ctx *c, double t)
+{
+    if (!c || !isfinite(t)) return GPE_EINVAL;
+    c->t = t;
+    return GPE_OK;
+}
+
+double gpe_get_time(const gpe_ctx *c) { return c ? c->t : 0.0; }
+
+gpe_status gpe_fft2(gpe_ctx *c, int sign)
+{
+    if (!c || (sign != 1 && sign != -1)) return GPE_EINVAL;
+    PhaseArgs none;
+    memset(&none, 0, sizeof(none));
+    if (sign == -1) {
+        TRY(run_row(c, ROW_FFT_F, none, red_at(c, c->t), 0, 0));
+        TRY(run_col(c, COL_FFT_F, 0));
+    } else {
+        TRY(run_col(c, COL_FFT_I, 0));
+        TRY(run_row(c, ROW_FFT_I, none, red_at(c, c->t), 0, 0));
+    }
+    return GPE_OK;
+}
+
+gpe_status gpe_sync(gpe_ctx *c)
+{
+    if (!c) return GPE_EINVAL;
+    int st = 0;
+    TRY(cuda_check(c, cudaMemcpyAsync(&st, &c->T.sc->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                   "copy"));
+    TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->status, 0, sizeof(int), c->stream), "memset"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    return st ? fail(c, (gpe_status)st, "device status %s", gpe_status_string((gpe_status)st)) : GPE_OK;
+}
+
+gpe_status gpe_debug_timeout_probe(gpe_ctx *c, int spins)
+{
+    if (!c || spins < 1) return GPE_EINVAL;
+    return cuda_check(c, launch_timeout_probe(c->T.sc, spins, c->stream), "timeout probe");
+}
+
+void gpe_destroy(gpe_ctx *c) { delete c; }
+
+const char *gpe_last_error(const gpe_ctx *c) { return c ? c->err : "null context"; }
+
+}  // extern "C"

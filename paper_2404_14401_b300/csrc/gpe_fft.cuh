@@ -1,0 +1,191 @@
+// gpe_fft.cuh -- register/shared-memory Stockham FFT for one pencil (a row or
+// a column of the grid) per group of threads, for sm_103a.
+//
+// The split-step of Sec. 3.1 (Eqs. 3-4) needs F and F^-1 along x and y.  A
+// pencil of N = 2^n complex64 points is spread over TP = N/E threads, thread
+// j holding elements j + r*TP (r < E) in registers -- the natural order that
+// both the first and the last Stockham stage read and write, so a pencil can
+// be loaded from global memory, transformed, multiplied by a phase and
+// transformed back without leaving registers at the ends.  Stages are
+// radix-R Stockham steps (R = 2^(n mod 4, or 4) for the first, 16 after),
+// each thread doing E/R butterflies per stage; between stages the pencil is
+// exchanged through shared memory in a layout padded by one slot per 16
+// elements, which keeps 64-bit accesses of every stage free of bank
+// conflicts.  Twiddles exp(-2 pi i m/N) come from a table computed in double
+// precision and rounded once.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gpe {
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by -i (forward transform) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 mul_mi(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos and sin of 2 pi j / 16
+__host__ __device__ constexpr float cos16(int j)
+{
+    constexpr float C1 = 0.923879532511286756f, C2 = 0.707106781186547524f, C3 = 0.382683432365089772f;
+    switch (j & 15) {
+    case 0: return 1.f;  case 1: return C1;  case 2: return C2;  case 3: return C3;
+    case 4: return 0.f;  case 5: return -C3; case 6: return -C2; case 7: return -C1;
+    case 8: return -1.f; case 9: return -C1; case 10: return -C2; case 11: return -C3;
+    case 12: return 0.f; case 13: return C3; case 14: return C2; default: return C1;
+    }
+}
+__host__ __device__ constexpr float sin16(int j) { return cos16(j - 4); }
+
+// a * W16^J with W16 = exp(-2 pi i/16) (forward) or its conjugate (inverse)
+template <int J, bool INV> __device__ __forceinline__ float2 tw16(float2 a)
+{
+    constexpr int j = J & 15;
+    if constexpr (j == 0) return a;
+    else if constexpr (j == 4) return mul_mi<INV>(a);
+    else if constexpr (j == 8) return make_float2(-a.x, -a.y);
+    else if constexpr (j == 12) return mul_mi<!INV>(a);
+    else {
+        constexpr float c = cos16(j);
+        constexpr float s = INV ? sin16(j) : -sin16(j);
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+template <bool INV> __device__ __forceinline__ void dft2(float2 &a0, float2 &a1)
+{
+    const float2 t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+template <bool INV> __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+{
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+    const float2 t3 = mul_mi<INV>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+// 8-point DFT as 4 x 2: n = 2 n1 + n2, k = k1 + 4 k2
+template <bool INV> __device__ __forceinline__ void dft8(float2 (&a)[8])
+{
+    dft4<INV>(a[0], a[2], a[4], a[6]);
+    dft4<INV>(a[1], a[3], a[5], a[7]);
+    a[3] = tw16<2, INV>(a[3]);
+    a[5] = tw16<4, INV>(a[5]);
+    a[7] = tw16<6, INV>(a[7]);
+    const float2 y0[4] = {a[0], a[2], a[4], a[6]};
+    const float2 y1[4] = {a[1], a[3], a[5], a[7]};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = cadd(y0[k], y1[k]);
+        a[k + 4] = csub(y0[k], y1[k]);
+    }
+}
+
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2
+template <bool INV> __device__ __forceinline__ void dft16(float2 (&a)[16])
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
+    a[5] = tw16<1, INV>(a[5]);
+    a[6] = tw16<2, INV>(a[6]);
+    a[7] = tw16<3, INV>(a[7]);
+    a[9] = tw16<2, INV>(a[9]);
+    a[10] = tw16<4, INV>(a[10]);
+    a[11] = tw16<6, INV>(a[11]);
+    a[13] = tw16<3, INV>(a[13]);
+    a[14] = tw16<6, INV>(a[14]);
+    a[15] = tw16<9, INV>(a[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = a[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = t[i];
+}
+
+template <int R, bool INV> __device__ __forceinline__ void dft(float2 (&a)[R])
+{
+    if constexpr (R == 2) dft2<INV>(a[0], a[1]);
+    else if constexpr (R == 4) dft4<INV>(a[0], a[1], a[2], a[3]);
+    else if constexpr (R == 8) dft8<INV>(a);
+    else dft16<INV>(a);
+}
+
+// padded shared-memory slot of pencil element e: one spare slot per 16
+__device__ __forceinline__ int padx(int e) { return e + (e >> 4); }
+
+// One Stockham stage of radix R after NS points have been combined.
+// Butterfly jp takes x[jp + r N/R], multiplies input r by W_{NS R}^{r (jp mod NS)}
+// and writes output p to y[(jp / NS) NS R + jp mod NS + p NS].
+// sb: this pencil's shared buffer, es: element stride in float2 units.
+template <int N, int E, int R, int NS, bool INV, bool LAST>
+__device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
+                                          const float2 *__restrict__ tw)
+{
+    constexpr int TP = N / E, B = E / R;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int jp = j + q * TP;
+        const int k = jp & (NS - 1);
+        float2 a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[q + B * r];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(&tw[r * k * (N / (NS * R))]);
+                if constexpr (INV) w.y = -w.y;
+                a[r] = cmul(a[r], w);
+            }
+        }
+        dft<R, INV>(a);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int p = 0; p < R; ++p) v[q + B * p] = a[p];
+        } else {
+            const int base = (jp - k) * R + k;
+#pragma unroll
+            for (int p = 0; p < R; ++p) sb[padx(base + p * NS) * es] = a[p];
+        }
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = sb[padx(j + r * TP) * es];
+        __syncthreads();
+    }
+}
+
+// Full transform of one pencil: natural order in v (element j + r TP) in and
+// out.  Forward: X_k = sum_n x_n e^{-2 pi i nk/N}; INV: the conjugate sum,
+// without the 1/N factor.  Every thread of the CTA must call it together.
+template <int N, int E, bool INV, int S = 0, int NS = 1>
+__device__ __forceinline__ void fft_pencil(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
+                                           const float2 *__restrict__ tw)
+{
+    constexpr int LOG = ilog2(N), NST = (LOG + 3) / 4;
+    constexpr int R = (S == 0) ? (1 << (LOG - 4 * (NST - 1))) : 16;
+    constexpr bool LAST = (S == NST - 1);
+    static_assert(E % R == 0, "radix must divide the elements per thread");
+    fft_stage<N, E, R, NS, INV, LAST>(v, sb, j, es, tw);
+    if constexpr (!LAST) fft_pencil<N, E, INV, S + 1, NS * R>(v, sb, j, es, tw);
+}
+
+}  // namespace gpe

@@ -1,0 +1,104 @@
+// gpe_internal.h -- types shared by the host scheduler (gpe_api.cu) and the
+// kernels (gpe_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpe {
+
+constexpr int NQ = 8;              // quantities per reduction partial
+constexpr int MAX_BLOCKS = 8192;   // upper bound on CTAs of one reducing pass
+
+// Scalars living in the workspace.  Written by the last CTA of a reducing
+// pass, read by the passes that follow on the same stream.
+struct DevScalars {
+    double alpha_re, alpha_im;     // cavity field for the next potential phase (Eq. 14)
+    double c;                      // pending normalisation 1/sqrt(norm) (Sec. 3.3)
+    double norm;                   // last reduced norm  int |psi|^2
+    double O, B;                   // last normalised overlaps (Eqs. 14-15)
+    double sums[2][NQ];            // finalised sums: [0] row passes, [1] column passes
+    unsigned int ticket[2];        // last-CTA counters (row / column kernels)
+    int status;                    // first device error (gpe_status), 0 = none
+    int pad;
+};
+
+// Device pointers into the caller's workspace.
+struct Tables {
+    DevScalars *sc;
+    double *part_row;              // [MAX_BLOCKS][NQ] per-CTA partial sums
+    double *part_col;              // [MAX_BLOCKS][NQ]
+    float2 *twx, *twy;             // exp(-2 pi i m / N), m < N (FP64-computed)
+    float4 *xtab, *ytab;           // {(m/2) w^2 x^2, cos^2(k_lat x), cos(kc x), x}
+    float2 *kinx, *kiny;           // kinetic factors (see kinetic_tables_kernel)
+};
+
+// One potential phase, evaluated on the host at the phase's time.
+struct PhaseArgs {
+    float h;                       // theta = (V + g |psi|^2) h
+    float a_latx, a_laty;          // lattice depths at this time (Eq. 9)
+    float a_pump;                  // eta^2 / U0 (pump lattice, Eq. 11) or 0
+    float U0;                      // cavity U0 (Eq. 12)
+    float two_eta;                 // 2 eta (Eq. 13)
+    int use_alpha;                 // read alpha from DevScalars for V_c, V_i
+};
+
+// Cavity reduction / finalisation parameters (Eqs. 14-15).
+struct RedArgs {
+    double eta, U0, dc, kappa, N, dxdy;
+    int cavity;
+};
+
+enum RowMode {
+    ROW_FWD = 0,        // real psi: [scale c] phase, FFT_x, store
+    ROW_MERGED = 1,     // k_x psi: iFFT_x, phase, FFT_x, store
+    ROW_INV = 2,        // k_x psi: iFFT_x, phase, reduce (norm, O, B -> c, alpha), store real
+    ROW_REDUCE_K = 3,   // k_x psi: iFFT_x, reduce (-> alpha), no store
+    ROW_REDUCE_R = 4,   // real psi: reduce (-> alpha), no store
+    ROW_SCALE = 5,      // real psi: multiply by c, store
+    ROW_FFT_F = 6,      // FFT_x only
+    ROW_FFT_I = 7,      // iFFT_x only (no normalisation)
+    ROW_OBS = 8         // real psi: observable sums + FFT_x kinetic sum, no store
+};
+
+enum ColMode {
+    COL_KIN = 0,        // FFT_y, kinetic factor, iFFT_y, store
+    COL_FFT_F = 1,      // FFT_y, store
+    COL_FFT_I = 2,      // iFFT_y, scale, store
+    COL_OBS = 3         // FFT_y, sum ky^2 |.|^2, no store
+};
+
+struct RowArgs {
+    float2 *psi;
+    int nx, ny;
+    const float *V;
+    float V_scale, g;
+    int imag, use_c;
+    PhaseArgs ph;
+    RedArgs red;
+    Tables T;
+};
+
+struct ColArgs {
+    float2 *psi;
+    int nx, ny, W, G;              // tile width, columns transformed at once
+    int imag;
+    float scale;                   // exact power of two (1/(nx ny)) or 1
+    int spins;                     // bound on the TMA barrier wait
+    Tables T;
+};
+
+// Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
+cudaError_t launch_row(int mode, const RowArgs &a, cudaStream_t s);
+cudaError_t launch_col(int mode, const ColArgs &a, const CUtensorMap &map, cudaStream_t s);
+cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m,
+                          double wx, double wy, double lkx, double lky, double kc, cudaStream_t s);
+cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly,
+                                  double m, double dt, int imag, cudaStream_t s);
+cudaError_t launch_timeout_probe(DevScalars *sc, int spins, cudaStream_t s);
+int col_tile_width(int nx, int ny);
+int col_group(int ny, int W);
+int row_rows_per_cta(int nx, int ny);
+
+}  // namespace gpe

@@ -1,0 +1,632 @@
+// gpe_kernels.cu -- sm_103a kernels of the split-step GPE propagator.
+//
+// A step of Sec. 3.1 (Eqs. 3-4) is executed as passes over the grid psi[ny][nx]
+// held in HBM, each pass one kernel that reads and writes psi in place:
+//   row pass    (x axis, rows contiguous): [iFFT_x] potential phase [FFT_x]
+//               with |psi|^2 nonlinearity, V(x,y,t) and the cavity terms of
+//               Eqs. (10)-(13) computed in registers, and FP64 reductions of
+//               norm / cavity overlaps (Eqs. 14-15) fused in;
+//   column pass (y axis): TMA-loaded tile of W columns x ny rows in shared
+//               memory, FFT_y, kinetic factor exp(-i k^2 dt / 2m), iFFT_y.
+// Between passes psi lives in the mixed (k_x, y) representation; it is in
+// real space at the boundary of every public call.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/gpe.h"
+#include "gpe_fft.cuh"
+#include "gpe_internal.h"
+
+namespace gpe {
+
+// ------------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Poll the barrier at most `spins` times; false if it never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int spins)
+{
+    for (int i = 0; i < spins; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void latch_status(DevScalars *sc, int code) { atomicCAS(&sc->status, 0, code); }
+
+// ------------------------------------------------------------------ reductions
+// Sum K per-thread FP32 partials over the CTA in FP64 with a fixed shuffle
+// tree and a fixed warp order; thread 0 writes them to dst[0..K).
+template <int K>
+__device__ __forceinline__ void block_sum(const float (&q)[K], double *__restrict__ dst, double *red)
+{
+    double d[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) d[i] = (double)q[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int width = blockDim.x < 32 ? blockDim.x : 32;
+    const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
+    for (int off = width >> 1; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < K; ++i) d[i] += __shfl_down_sync(mask, d[i], off);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < K; ++i) red[warp * NQ + i] = d[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * NQ + i];
+            dst[i] = s;
+        }
+    }
+}
+
+// After every CTA has stored its partials: the CTA that arrives last sums
+// them in block order (deterministic whatever CTA is last) into out[0..K).
+// Returns true in the last CTA (all threads), with out valid after a barrier.
+template <int K>
+__device__ __forceinline__ bool last_block_total(const double *part, unsigned int *ticket, double *out,
+                                                 double *red)
+{
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc[i] += __ldcg(&part[(size_t)b * NQ + i]);
+    // fixed-order tree over threads (reuse block_sum on doubles via red)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int width = blockDim.x < 32 ? blockDim.x : 32;
+    const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
+    for (int off = width >> 1; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc[i] += __shfl_down_sync(mask, acc[i], off);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < K; ++i) red[warp * NQ + i] = acc[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * NQ + i];
+            out[i] = s;
+        }
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// Norm, overlaps, renormalisation scale and cavity field from the sums
+// S0 = sum |psi|^2, S1 = sum cos(kc x)cos(kc y)|psi|^2, S2 = sum cos^2(kc x)|psi|^2
+// (Sec. 3.3 normalisation; Eqs. 14-15).  One thread, FP64.
+__device__ void finalize_fields(const double *S, const RedArgs &r, DevScalars *sc)
+{
+    const double norm = S[0] * r.dxdy;
+    const double O = S[1] / S[0], B = S[2] / S[0];
+    sc->norm = norm;
+    sc->O = O;
+    sc->B = B;
+    sc->c = 1.0 / sqrt(norm);
+    if (!isfinite(norm) || !(norm > 0.0) || !isfinite(O) || !isfinite(B)) {
+        latch_status(sc, GPE_ENONFINITE);
+        return;
+    }
+    if (r.cavity) {
+        const double dr = r.dc - r.U0 * B, di = r.kappa;
+        const double den = dr * dr + di * di;
+        if (!(den > 1e-24)) {
+            latch_status(sc, GPE_EILLCOND);
+            sc->alpha_re = 0.0;
+            sc->alpha_im = 0.0;
+            return;
+        }
+        const double num = r.N * r.eta * O;          // alpha = num / (dr + i di)
+        sc->alpha_re = num * dr / den;
+        sc->alpha_im = -num * di / den;
+    } else {
+        sc->alpha_re = 0.0;
+        sc->alpha_im = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ row pass
+template <int N> struct RowCfg {
+    static constexpr int E = N >= 16 ? 16 : N;
+    static constexpr int TP = N / E;
+    static constexpr int PS = N + N / 16;          // padded pencil stride (float2)
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const RowArgs a)
+{
+    using C = RowCfg<N>;
+    constexpr int E = C::E, TP = C::TP;
+    extern __shared__ float2 smem[];
+    __shared__ double red[32 * NQ];
+
+    const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
+    const int rpc = blockDim.x / TP;
+    const int y = blockIdx.x * rpc + lr;
+    float2 *row = a.psi + (size_t)y * N;
+    float2 *sb = smem + lr * C::PS;
+    const Tables &T = a.T;
+
+    float2 v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[r] = row[j + r * TP];
+
+    constexpr bool IN_K = (MODE == ROW_MERGED || MODE == ROW_INV || MODE == ROW_REDUCE_K || MODE == ROW_FFT_I);
+    if constexpr (IN_K) fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
+
+    if constexpr (MODE == ROW_FFT_F) fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+
+    if constexpr (MODE == ROW_SCALE) {
+        const float c = (float)T.sc->c;
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * c, v[r].y * c);
+    }
+
+    constexpr bool PHASE = (MODE == ROW_FWD || MODE == ROW_MERGED || MODE == ROW_INV);
+    const float4 yt = T.ytab[y];                    // {trap_y, cos^2(lat ky y), cos(kc y), y}
+    if constexpr (PHASE) {
+        const PhaseArgs &p = a.ph;
+        float cs = 1.f;
+        if (MODE == ROW_FWD && a.use_c) cs = (float)T.sc->c;
+        float acx2 = 0.f, acxcy = 0.f;
+        if (p.use_alpha) {
+            const double ar = T.sc->alpha_re, ai = T.sc->alpha_im;
+            acx2 = (float)((double)p.U0 * (ar * ar + ai * ai));     // V_c amplitude, Eq. (12)
+            acxcy = (float)((double)p.two_eta * ar);                 // V_i amplitude, Eq. (13)
+        }
+        const float vrow = yt.x + p.a_laty * yt.y + p.a_pump * yt.z * yt.z;
+        const float bcx = acxcy * yt.z;
+        const float *Vr = a.V ? a.V + (size_t)y * N : nullptr;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = j + r * TP;
+            const float4 xt = __ldg(&T.xtab[xi]);
+            float V = vrow + xt.x + p.a_latx * xt.y + (acx2 * xt.z + bcx) * xt.z;
+            if (Vr) V += a.V_scale * __ldg(&Vr[xi]);
+            float2 q = v[r];
+            if (MODE == ROW_FWD) q = make_float2(q.x * cs, q.y * cs);
+            const float n = q.x * q.x + q.y * q.y;
+            const float th = (V + a.g * n) * p.h;
+            if (a.imag) {
+                const float f = expf(-th);
+                q = make_float2(q.x * f, q.y * f);
+            } else {
+                // e^{-i th} - 1 = -2 sin^2(th/2) - 2 i sin(th/2) cos(th/2): small
+                // phases keep their relative precision
+                float s, c;
+                sincosf(0.5f * th, &s, &c);
+                const float dr = -2.f * s * s, di = -2.f * s * c;
+                q = make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
+            }
+            v[r] = q;
+        }
+    }
+
+    constexpr bool REDUCE = (MODE == ROW_INV || MODE == ROW_REDUCE_K || MODE == ROW_REDUCE_R);
+    if constexpr (REDUCE) {
+        float q[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float cx = __ldg(&T.xtab[j + r * TP]).z;
+            const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+            q[0] += n;
+            q[1] += cx * n;
+            q[2] += cx * cx * n;
+        }
+        q[1] *= yt.z;
+        block_sum<3>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
+        double S[3];
+        if (last_block_total<3>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0)
+            finalize_fields(S, a.red, T.sc);
+    }
+
+    if constexpr (MODE == ROW_OBS) {
+        // observable sums of the real-space state: S0 |psi|^2, S1 V_static |psi|^2,
+        // S2 |psi|^4, S3 cos cos |psi|^2, S4 cos^2(kc x)|psi|^2, S5 cos^2(kc y)|psi|^2,
+        // then S6 = sum kx^2 |F_x psi|^2 (kinetic energy along x by Parseval)
+        const PhaseArgs &p = a.ph;
+        const float vrow = yt.x + p.a_laty * yt.y + p.a_pump * yt.z * yt.z;
+        const float *Vr = a.V ? a.V + (size_t)y * N : nullptr;
+        float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = j + r * TP;
+            const float4 xt = __ldg(&T.xtab[xi]);
+            float V = vrow + xt.x + p.a_latx * xt.y;
+            if (Vr) V += a.V_scale * __ldg(&Vr[xi]);
+            const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+            q[0] += n;
+            q[1] += V * n;
+            q[2] += n * n;
+            q[3] += xt.z * n;
+            q[4] += xt.z * xt.z * n;
+        }
+        q[3] *= yt.z;
+        q[5] = yt.z * yt.z * q[0];
+        fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int e = j + r * TP;
+            const float kx = (float)(e < N / 2 ? e : e - N);   // in units of 2 pi / Lx
+            q[6] += kx * kx * (v[r].x * v[r].x + v[r].y * v[r].y);
+        }
+        block_sum<7>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
+        double S[7];
+        if (last_block_total<7>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0)
+#pragma unroll
+            for (int i = 0; i < 7; ++i) T.sc->sums[0][i] = S[i];
+        return;
+    }
+
+    if constexpr (MODE == ROW_FWD || MODE == ROW_MERGED) fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+
+    constexpr bool STORE = !(MODE == ROW_REDUCE_K || MODE == ROW_REDUCE_R || MODE == ROW_OBS);
+    if constexpr (STORE) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) row[j + r * TP] = v[r];
+    }
+}
+
+// ------------------------------------------------------------------ column pass
+template <int N> struct ColCfg {
+    static constexpr int E = N >= 16 ? 16 : N;
+    static constexpr int TP = N / E;
+    static constexpr int BR = N < 256 ? N : 256;    // rows per TMA box
+};
+
+// Columns transformed at once by one CTA (the tile holds W of them; the
+// 8192-row case works through its two columns one after the other so that
+// a thread keeps 16 elements and the CTA stays at 512 threads).
+int col_group(int ny, int W) { return ny >= 8192 ? 1 : W; }
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_constant__ CUtensorMap map)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, TP = C::TP;
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double red[32 * NQ];
+
+    // 128-byte aligned tile: dense [N][W] as written by TMA, later reused with
+    // one padding row per 16 rows for the exchanges
+    const uint32_t s0 = smem_u32(smraw);
+    float2 *tile = reinterpret_cast<float2 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+
+    const int W = a.W, G = a.G;
+    const int c0 = blockIdx.x * W;
+    const Tables &T = a.T;
+
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, (uint32_t)(N * W * 8));
+        for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + (size_t)r0 * W, &map, &bar, 2 * c0, r0);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins));
+    if (!ok) {
+        if (threadIdx.x == 0) latch_status(T.sc, GPE_ETIMEOUT);
+        mbar_wait_bounded(&bar, 0, a.spins);        // give copies in flight a last chance
+        return;
+    }
+
+    // Column c uses only the tile slots congruent to c mod W, in both the
+    // dense TMA layout and the padded exchange layout, so column groups
+    // can be transformed one after the other in place.
+    float q[1] = {0.f};
+    for (int g0 = 0; g0 < W; g0 += G) {
+        const int c = g0 + (threadIdx.x & (G - 1)), j = threadIdx.x / G;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = tile[(size_t)(j + r * TP) * W + c];
+        __syncthreads();                             // dense reads done before padded writes
+        float2 *sb = tile + c;
+
+        if constexpr (MODE == COL_FFT_I) {
+            fft_pencil<N, E, true>(v, sb, j, W, T.twy);
+#pragma unroll
+            for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.scale, v[r].y * a.scale);
+        } else {
+            fft_pencil<N, E, false>(v, sb, j, W, T.twy);
+        }
+
+        if constexpr (MODE == COL_KIN) {
+            const float2 dx = __ldg(&T.kinx[c0 + c]);
+            if (a.imag) {
+                // exp(-k^2 dtau / 2m) = Kx Ky, 1/(nx ny) folded into the exact scale
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const float f = dx.x * __ldg(&T.kiny[j + r * TP]).x * a.scale;
+                    v[r] = make_float2(v[r].x * f, v[r].y * f);
+                }
+            } else {
+                // K - 1 = Dx + Dy + Dx Dy with D = exp(-i k^2 dt / 2m) - 1 per axis;
+                // psi <- s (psi + psi (K - 1)), s = 1/(nx ny) exact
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const float2 dy = __ldg(&T.kiny[j + r * TP]);
+                    const float2 d = cadd(cadd(dx, dy), cmul(dx, dy));
+                    const float2 p = v[r];
+                    const float2 pd = cmul(p, d);
+                    v[r] = make_float2((p.x + pd.x) * a.scale, (p.y + pd.y) * a.scale);
+                }
+            }
+            fft_pencil<N, E, true>(v, sb, j, W, T.twy);
+        }
+
+        if constexpr (MODE == COL_OBS) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int e = j + r * TP;
+                const float ky = (float)(e < N / 2 ? e : e - N);    // in units of 2 pi / Ly
+                q[0] += ky * ky * (v[r].x * v[r].x + v[r].y * v[r].y);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; ++r) a.psi[(size_t)(j + r * TP) * a.nx + c0 + c] = v[r];
+        }
+    }
+
+    if constexpr (MODE == COL_OBS) {
+        block_sum<1>(q, T.part_col + (size_t)blockIdx.x * NQ, red);
+        double S[1];
+        if (last_block_total<1>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
+            T.sc->sums[1][0] = S[0];
+    }
+}
+
+// ------------------------------------------------------------------ tables
+// Coordinates, trap and lattice profiles and twiddles in FP64, rounded once.
+__global__ void tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, double m, double wx,
+                              double wy, double lkx, double lky, double kc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nx) {
+        const double x = -0.5 * Lx + (double)i * (Lx / nx);
+        const double cl = cos(lkx * x), cc = cos(kc * x);
+        T.xtab[i] = make_float4((float)(0.5 * m * wx * wx * x * x), (float)(cl * cl), (float)cc, (float)x);
+        double s, c;
+        sincospi(2.0 * i / nx, &s, &c);
+        T.twx[i] = make_float2((float)c, (float)-s);
+    }
+    if (i < ny) {
+        const double y = -0.5 * Ly + (double)i * (Ly / ny);
+        const double cl = cos(lky * y), cc = cos(kc * y);
+        T.ytab[i] = make_float4((float)(0.5 * m * wy * wy * y * y), (float)(cl * cl), (float)cc, (float)y);
+        double s, c;
+        sincospi(2.0 * i / ny, &s, &c);
+        T.twy[i] = make_float2((float)c, (float)-s);
+    }
+}
+
+// Kinetic factors per axis (FP64, rounded once).  Real time: D = e^{-i k^2 dt/2m} - 1
+// written as (-2 sin^2(a/2), -sin a); imaginary time: (e^{-k^2 dt/2m}, 0).
+__global__ void kinetic_tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, double m, double dt,
+                                      int imag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int axis = 0; axis < 2; ++axis) {
+        const int n = axis ? ny : nx;
+        if (i >= n) continue;
+        const double L = axis ? Ly : Lx;
+        const double k = 2.0 * M_PI / L * (double)(i < n / 2 ? i : i - n);
+        const double ang = k * k / (2.0 * m) * dt;
+        float2 out;
+        if (imag) {
+            out = make_float2((float)exp(-ang), 0.f);
+        } else {
+            double s, c;
+            sincos(0.5 * ang, &s, &c);
+            out = make_float2((float)(-2.0 * s * s), (float)(-2.0 * s * c));
+        }
+        (axis ? T.kiny : T.kinx)[i] = out;
+    }
+}
+
+__global__ void timeout_probe_kernel(DevScalars *sc, int spins)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    // nothing ever arrives on this barrier: the bounded wait must give up
+    const bool ok = mbar_wait_bounded(&bar, 0, spins);
+    if (!ok && threadIdx.x == 0) latch_status(sc, GPE_ETIMEOUT);
+}
+
+// ------------------------------------------------------------------ launchers
+int row_rows_per_cta(int nx, int ny)
+{
+    const int E = nx >= 16 ? 16 : nx;
+    const int tp = nx / E;
+    int rpc = 256 / tp;
+    if (rpc < 1) rpc = 1;
+    if (rpc > ny) rpc = ny;
+    return rpc;
+}
+
+int col_tile_width(int nx, int ny)
+{
+    int w = 8192 / ny;
+    if (w < 2) w = 2;
+    if (w > 64) w = 64;
+    if (w > nx) w = nx;
+    return w;
+}
+
+template <int N, int MODE> static cudaError_t row_launch(const RowArgs &a, cudaStream_t s)
+{
+    using C = RowCfg<N>;
+    const int rpc = row_rows_per_cta(N, a.ny);
+    const int threads = rpc * C::TP;
+    const size_t smem = (size_t)rpc * C::PS * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        const int rpc_max = 256 / C::TP > 1 ? 256 / C::TP : 1;
+        const int smem_max = rpc_max * C::PS * (int)sizeof(float2);
+        if (smem_max > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(row_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 smem_max);
+            if (e != cudaSuccess) return e;
+        }
+        attr = true;
+    }
+    row_kernel<N, MODE><<<a.ny / rpc, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N> static cudaError_t row_dispatch_mode(int mode, const RowArgs &a, cudaStream_t s)
+{
+    switch (mode) {
+    case ROW_FWD: return row_launch<N, ROW_FWD>(a, s);
+    case ROW_MERGED: return row_launch<N, ROW_MERGED>(a, s);
+    case ROW_INV: return row_launch<N, ROW_INV>(a, s);
+    case ROW_REDUCE_K: return row_launch<N, ROW_REDUCE_K>(a, s);
+    case ROW_REDUCE_R: return row_launch<N, ROW_REDUCE_R>(a, s);
+    case ROW_SCALE: return row_launch<N, ROW_SCALE>(a, s);
+    case ROW_FFT_F: return row_launch<N, ROW_FFT_F>(a, s);
+    case ROW_FFT_I: return row_launch<N, ROW_FFT_I>(a, s);
+    case ROW_OBS: return row_launch<N, ROW_OBS>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_row(int mode, const RowArgs &a, cudaStream_t s)
+{
+    switch (a.nx) {
+    case 8: return row_dispatch_mode<8>(mode, a, s);
+    case 16: return row_dispatch_mode<16>(mode, a, s);
+    case 32: return row_dispatch_mode<32>(mode, a, s);
+    case 64: return row_dispatch_mode<64>(mode, a, s);
+    case 128: return row_dispatch_mode<128>(mode, a, s);
+    case 256: return row_dispatch_mode<256>(mode, a, s);
+    case 512: return row_dispatch_mode<512>(mode, a, s);
+    case 1024: return row_dispatch_mode<1024>(mode, a, s);
+    case 2048: return row_dispatch_mode<2048>(mode, a, s);
+    case 4096: return row_dispatch_mode<4096>(mode, a, s);
+    case 8192: return row_dispatch_mode<8192>(mode, a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N, int MODE>
+static cudaError_t col_launch(const ColArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    using C = ColCfg<N>;
+    const int threads = a.G * C::TP;
+    const size_t smem = (size_t)(N + N / 16) * a.W * sizeof(float2) + 128;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(col_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    col_kernel<N, MODE><<<a.nx / a.W, threads, smem, s>>>(a, map);
+    return cudaGetLastError();
+}
+
+template <int N> static cudaError_t col_dispatch_mode(int mode, const ColArgs &a, const CUtensorMap &map,
+                                                      cudaStream_t s)
+{
+    switch (mode) {
+    case COL_KIN: return col_launch<N, COL_KIN>(a, map, s);
+    case COL_FFT_F: return col_launch<N, COL_FFT_F>(a, map, s);
+    case COL_FFT_I: return col_launch<N, COL_FFT_I>(a, map, s);
+    case COL_OBS: return col_launch<N, COL_OBS>(a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_col(int mode, const ColArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    switch (a.ny) {
+    case 8: return col_dispatch_mode<8>(mode, a, map, s);
+    case 16: return col_dispatch_mode<16>(mode, a, map, s);
+    case 32: return col_dispatch_mode<32>(mode, a, map, s);
+    case 64: return col_dispatch_mode<64>(mode, a, map, s);
+    case 128: return col_dispatch_mode<128>(mode, a, map, s);
+    case 256: return col_dispatch_mode<256>(mode, a, map, s);
+    case 512: return col_dispatch_mode<512>(mode, a, map, s);
+    case 1024: return col_dispatch_mode<1024>(mode, a, map, s);
+    case 2048: return col_dispatch_mode<2048>(mode, a, map, s);
+    case 4096: return col_dispatch_mode<4096>(mode, a, map, s);
+    case 8192: return col_dispatch_mode<8192>(mode, a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m, double wx,
+                          double wy, double lkx, double lky, double kc, cudaStream_t s)
+{
+    const int n = nx > ny ? nx : ny;
+    tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(T, nx, ny, Lx, Ly, m, wx, wy, lkx, lky, kc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m, double dt,
+                                  int imag, cudaStream_t s)
+{
+    const int n = nx > ny ? nx : ny;
+    kinetic_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(T, nx, ny, Lx, Ly, m, dt, imag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_timeout_probe(DevScalars *sc, int spins, cudaStream_t s)
+{
+    timeout_probe_kernel<<<1, 32, 0, s>>>(sc, spins);
+    return cudaGetLastError();
+}
+
+}  // namespace gpe

@@ -1,0 +1,169 @@
+"""Thin ctypes binding of the C ABI in include/gpe.h.
+
+Functions keep the C names and only marshal arguments (torch tensors are
+passed as device pointers, streams as handles).  Every step of the split-step
+propagator runs in the sm_103a kernels of libgpe.so; there is no Python or
+CPU fallback: if the library is missing or fails to load, this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_double, c_size_t, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, ctypes.c_size_t,
+                                                  ctypes.c_void_p, ctypes.c_char_p)
+
+GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EILLCOND = range(7)
+GPE_REAL, GPE_IMAG = 0, 1
+GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
+
+EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_observables",
+           "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2", "gpe_sync",
+           "gpe_debug_timeout_probe", "gpe_destroy", "gpe_last_error", "gpe_status_string")
+
+
+class gpe_potential(ctypes.Structure):
+    _fields_ = [("wx", c_double), ("wy", c_double),
+                ("lat_V0x", c_double), ("lat_V0y", c_double), ("lat_kx", c_double), ("lat_ky", c_double),
+                ("V", c_void_p), ("V_scale", c_double),
+                ("cavity", c_int),
+                ("eta", c_double), ("U0", c_double), ("dc", c_double), ("kappa", c_double),
+                ("kc", c_double), ("N", c_double),
+                ("pump_lattice", c_int), ("ctrl_target", c_int), ("nctrl", c_int),
+                ("ctrl_t", ctypes.POINTER(c_double)), ("ctrl_v", ctypes.POINTER(c_double))]
+
+
+class gpe_obs(ctypes.Structure):
+    _fields_ = [(k, c_double) for k in ("norm", "ekin", "epot", "eint", "energy", "mu", "O", "B",
+                                        "alpha_re", "alpha_im", "t")] + [("status", c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GPEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libgpe.so (built in-tree by build.py).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    sig = {
+        "gpe_workspace_size": (c_size_t, [c_int, c_int]),
+        "gpe_create": (c_int, [c_int, c_int, c_double, c_double, c_double, c_double, c_void_p, c_void_p,
+                               c_size_t, c_void_p, P(c_void_p)]),
+        "gpe_set_potential": (c_int, [c_void_p, P(gpe_potential)]),
+        "gpe_step": (c_int, [c_void_p, c_int, c_double, c_int]),
+        "gpe_observables": (c_int, [c_void_p, P(gpe_obs)]),
+        "gpe_set_psi": (c_int, [c_void_p, c_void_p, c_int]),
+        "gpe_get_psi": (c_int, [c_void_p, c_void_p, c_int]),
+        "gpe_set_time": (c_int, [c_void_p, c_double]),
+        "gpe_get_time": (c_double, [c_void_p]),
+        "gpe_fft2": (c_int, [c_void_p, c_int]),
+        "gpe_sync": (c_int, [c_void_p]),
+        "gpe_debug_timeout_probe": (c_int, [c_void_p, c_int]),
+        "gpe_destroy": (None, [c_void_p]),
+        "gpe_last_error": (c_char_p, [c_void_p]),
+        "gpe_status_string": (c_char_p, [c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return load().gpe_status_string(int(s)).decode()
+
+
+def _check(ctx, s: int):
+    if s != GPE_OK:
+        msg = load().gpe_last_error(ctx).decode() if ctx else ""
+        raise GPEError(s, msg)
+
+
+# ---------------------------------------------------------------- C names
+def gpe_workspace_size(nx: int, ny: int) -> int:
+    return load().gpe_workspace_size(nx, ny)
+
+
+def gpe_create(nx, ny, Lx, Ly, m, g, psi_ptr, ws_ptr, ws_bytes, stream_handle) -> c_void_p:
+    ctx = c_void_p()
+    _check(None, load().gpe_create(nx, ny, Lx, Ly, m, g, c_void_p(psi_ptr), c_void_p(ws_ptr), ws_bytes,
+                                   c_void_p(stream_handle), ctypes.byref(ctx)))
+    return ctx
+
+
+def gpe_set_potential(ctx, pot: gpe_potential):
+    _check(ctx, load().gpe_set_potential(ctx, ctypes.byref(pot)))
+
+
+def gpe_step(ctx, n: int, dt: float, mode: int):
+    _check(ctx, load().gpe_step(ctx, int(n), float(dt), int(mode)))
+
+
+def gpe_observables(ctx, check: bool = True) -> dict:
+    o = gpe_obs()
+    s = load().gpe_observables(ctx, ctypes.byref(o))
+    if check:
+        _check(ctx, s)
+    return o.as_dict()
+
+
+def gpe_set_psi(ctx, src_ptr: int, is_dev: bool):
+    _check(ctx, load().gpe_set_psi(ctx, c_void_p(src_ptr), int(is_dev)))
+
+
+def gpe_get_psi(ctx, dst_ptr: int, is_dev: bool):
+    _check(ctx, load().gpe_get_psi(ctx, c_void_p(dst_ptr), int(is_dev)))
+
+
+def gpe_set_time(ctx, t: float):
+    _check(ctx, load().gpe_set_time(ctx, float(t)))
+
+
+def gpe_get_time(ctx) -> float:
+    return load().gpe_get_time(ctx)
+
+
+def gpe_fft2(ctx, sign: int):
+    _check(ctx, load().gpe_fft2(ctx, int(sign)))
+
+
+def gpe_sync(ctx) -> int:
+    """Wait for the stream; returns (does not raise) the latched device status."""
+    return load().gpe_sync(ctx)
+
+
+def gpe_debug_timeout_probe(ctx, spins: int):
+    _check(ctx, load().gpe_debug_timeout_probe(ctx, int(spins)))
+
+
+def gpe_destroy(ctx):
+    load().gpe_destroy(ctx)
+
+
+def gpe_last_error(ctx) -> str:
+    return load().gpe_last_error(ctx).decode()
+
+
+def gpe_status_string(s: int) -> str:
+    return status_string(s)

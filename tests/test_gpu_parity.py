@@ -1,0 +1,230 @@
+"""GPU parity: the sm_103a kernels (through the C ABI) against the FP64 oracle.
+
+Both sides get the same seeded inputs from gpe_inputs; the GPU receives them
+rounded to complex64.  Tolerances come from the FP32 arithmetic of the GPU
+path: one forward + inverse FP32 FFT pair has a relative L2 error of a few
+1e-7 (~eps32 sqrt(log2 N)); a split step adds the phase and kinetic factors,
+each rounded once, so after n steps the state error grows at most linearly,
+bounded by 1e-4 after 1000 steps (the propagator's stated tolerance) and
+scaled as 1e-4 n / 1000 (floor 1e-5) below that.  Observables are FP64
+reductions of FP32 products: relative 1e-5.
+"""
+import numpy as np
+import pytest
+
+import gpe_inputs as gi
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sim_for(p):
+    from paper_2404_14401_b300 import Simulation
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    return s
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def state_tol(n):
+    return max(1e-5, 1e-4 * n / 1000)
+
+
+def c64(a):
+    return np.asarray(a, dtype=np.complex64)
+
+
+def rand_state(nx, ny, seed):
+    z = gi.normal(seed, 2 * nx * ny).reshape(2, ny, nx)
+    return z[0] + 1j * z[1]
+
+
+# ------------------------------------------------------------------ FFT passes
+FFT_SHAPES = [(8, 8), (16, 8), (8, 16), (32, 64), (64, 32), (128, 128), (256, 512), (512, 256),
+              (1024, 64), (2048, 32), (4096, 16), (8192, 8), (8, 8192), (16, 4096), (32, 2048),
+              (1024, 1024), (2048, 2048)]
+
+
+@pytest.mark.parametrize("nx,ny", FFT_SHAPES)
+def test_fft2_passes_match_oracle(nx, ny):
+    p = gi.potential_defaults()
+    p.update(nx=nx, ny=ny, Lx=1.0, Ly=1.0, m=1.0, g=0.0)
+    s = sim_for(p)
+    a = c64(rand_state(nx, ny, nx * 131 + ny))
+    s.set_psi(a)
+    s.fft2(-1)
+    got = s.get_psi()
+    ref = oracle.fft2(a.astype(np.complex128), -1)
+    assert rel_l2(got, ref) < 1e-6
+    assert np.max(np.abs(got - ref)) < 1e-5 * np.max(np.abs(ref))
+    s.fft2(+1)
+    back = s.get_psi()
+    assert rel_l2(back, a) < 1e-6
+    assert s.sync() == 0
+
+
+# ------------------------------------------------------------------ split steps
+def run_both(p, psi0, n, dt, imag, t0=0.0):
+    s = sim_for(p)
+    s.set_psi(c64(psi0))
+    s.t = t0
+    s.step(n, dt, imag)
+    got = s.get_psi()
+    obs = s.observables()
+    ref, alpha = oracle.evolve(p, c64(psi0).astype(np.complex128), n, dt, imag, t0=t0)
+    return s, got, obs, ref, alpha
+
+
+@pytest.mark.parametrize("nx,ny,n", [(64, 64, 1), (64, 64, 2), (64, 64, 100), (128, 64, 100),
+                                     (32, 256, 100), (256, 256, 1000)])
+def test_real_time_lattice_matches_oracle(nx, ny, n):
+    w = gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=16.0 * nx / 64, Ly=16.0 * ny / 64)
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=1)
+    s, got, obs, ref, _ = run_both(p, psi0, n, 5e-4, False)
+    assert rel_l2(got, ref) < state_tol(n)
+    ro = oracle.observables(p, ref, t=s.t)
+    assert abs(obs["norm"] - 1.0) < 1e-6                      # norm drift
+    assert abs(obs["norm"] - ro["norm"]) < 1e-6
+    assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
+    assert abs(obs["mu"] - ro["mu"]) < 1e-5 * abs(ro["mu"])
+
+
+@pytest.mark.parametrize("g", [0.0, 100.0])
+def test_imaginary_time_harmonic_trap_matches_oracle(g):
+    """128^2, box 20, V = r^2/2, imaginary dt = 1e-3 for 2000 steps (Sec. 4.1 / 5.1)."""
+    w = gi.harmonic_trap(g=g)
+    p = w["params"]
+    s, got, obs, ref, _ = run_both(p, w["psi0"](), 2000, w["dt"], True)
+    assert rel_l2(got, ref) < 1e-4
+    ro = oracle.observables(p, ref, t=s.t)
+    for k in ("energy", "mu", "ekin", "epot"):
+        assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+    assert abs(obs["norm"] - 1.0) < 1e-6
+    if g == 0.0:
+        assert abs(obs["energy"] - 1.0) < 2e-4                # closed form E = 1
+
+
+def test_imaginary_then_real_time_switches_kinetic_factors():
+    w = gi.harmonic_trap(n=64, L=16.0, g=50.0)
+    p = w["params"]
+    psi0 = w["psi0"]()
+    s = sim_for(p)
+    s.set_psi(c64(psi0))
+    s.step(300, 2e-3, True)
+    s.step(200, 1e-3, False)
+    ref, _ = oracle.evolve(p, c64(psi0).astype(np.complex128), 300, 2e-3, True)
+    ref, _ = oracle.evolve(p, ref, 200, 1e-3, False, t0=0.6)
+    assert rel_l2(s.get_psi(), ref) < state_tol(500)
+
+
+def test_cavity_ramp_matches_oracle():
+    """Self-consistent cavity (Sec. 5.3) with eta ramped in time; alpha on both sides."""
+    w = gi.cavity_ramp(n=64, L=16.0, steps=400, dt=2e-4)
+    p = w["params"]
+    p["ctrl_v"] = np.array([0.0, 6.0])             # strong pump: alpha is far from zero
+    psi0 = gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=2)
+    s, got, obs, ref, alpha = run_both(p, psi0, 400, 2e-4, False)
+    assert rel_l2(got, ref) < state_tol(400)
+    ro = oracle.observables(p, ref, t=s.t)
+    a_gpu = complex(obs["alpha_re"], obs["alpha_im"])
+    a_ref = complex(ro["alpha_re"], ro["alpha_im"])
+    assert abs(a_ref) > 1e-3
+    assert abs(a_gpu - a_ref) < 1e-4 * abs(a_ref) + 1e-7
+    assert abs(obs["norm"] - 1.0) < 1e-6
+
+
+def test_cavity_imaginary_time_matches_oracle():
+    w = gi.cavity_ramp(n=64, L=16.0, steps=300, dt=1e-3)
+    p = dict(w["params"], ctrl_target=0, eta=2.5, ctrl_t=None, ctrl_v=None)
+    psi0 = gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=3)
+    s, got, obs, ref, _ = run_both(p, psi0, 300, 1e-3, True)
+    assert rel_l2(got, ref) < 1e-4
+    ro = oracle.observables(p, ref, t=s.t)
+    assert abs(obs["O"] - ro["O"]) < 1e-5 * max(abs(ro["O"]), 1e-3)
+    assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
+
+
+def test_time_dependent_lattice_control_and_potential_array():
+    """V0(t) from 200 seeded piecewise-linear control points (the adjoint-control
+    workload's potential) plus a static array term, real time."""
+    n = 64
+    p = gi.potential_defaults()
+    t, v = gi.control_points(seed=4, n=200, T=0.2, lo=0.0, hi=8.0)
+    Varr = (0.5 * gi.normal(7, n * n).reshape(n, n)).astype(np.float32).astype(np.float64)
+    p.update(nx=n, ny=n, Lx=16.0, Ly=16.0, m=1.0, g=500.0, wx=1.0, wy=1.0, lat_V0x=1.0, lat_V0y=1.0,
+             lat_kx=2 * np.pi, lat_ky=2 * np.pi, ctrl_target=1, ctrl_t=t, ctrl_v=v, Varr=Varr, V_scale=0.7)
+    psi0 = gi.gaussian_state(n, n, 16.0, 16.0, 1.5, 1e-3, seed=4)
+    s, got, obs, ref, _ = run_both(p, psi0, 400, 5e-4, False)
+    assert rel_l2(got, ref) < state_tol(400)
+
+
+def test_observables_of_a_given_state():
+    w = gi.lattice_real_time(n=128, L=20.0)
+    p = w["params"]
+    psi = gi.gaussian_state(128, 128, 20.0, 20.0, 1.2, 5e-2, seed=9, kx0=1.0)
+    s = sim_for(p)
+    s.set_psi(c64(psi))
+    obs = s.observables()
+    ro = oracle.observables(p, c64(psi).astype(np.complex128))
+    for k in ("norm", "ekin", "epot", "eint", "energy", "mu"):
+        assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+
+
+def test_runs_are_bitwise_deterministic():
+    w = gi.cavity_ramp(n=128, L=16.0, steps=50, dt=2e-4)
+    p = w["params"]
+    psi0 = c64(gi.gaussian_state(128, 128, 16.0, 16.0, 1.5, 1e-2, seed=5))
+    outs = []
+    for _ in range(2):
+        s = sim_for(p)
+        s.set_psi(psi0)
+        s.step(50, 2e-4, False)
+        outs.append(s.get_psi())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_zero_steps_and_bad_arguments():
+    from paper_2404_14401_b300 import GPEError
+    w = gi.harmonic_trap(n=32, L=10.0)
+    s = sim_for(w["params"])
+    psi0 = c64(w["psi0"]())
+    s.set_psi(psi0)
+    s.step(0, 1e-3, False)
+    assert np.array_equal(s.get_psi(), psi0)
+    for bad in [(1, 0.0), (1, -1e-3), (-1, 1e-3), (1, float("nan"))]:
+        with pytest.raises(GPEError):
+            s.step(bad[0], bad[1], False)
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.harmonic_trap(n=32, L=10.0)
+    s = sim_for(w["params"])
+    s.set_psi(c64(w["psi0"]()))
+    abi.gpe_debug_timeout_probe(s.ctx, 64)
+    assert s.sync() == abi.GPE_ETIMEOUT
+    assert s.sync() == abi.GPE_OK                             # latched status was cleared
+    s.step(10, 1e-3, True)
+    assert abs(s.observables()["norm"] - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_full_size_real_time_lattice_first_100_steps(n):
+    """The real-time throughput workload at full size (trap + lattice, g = 500,
+    box 40, dt = 5e-4): the first 100 steps element by element against the
+    oracle, plus norm and energy drift."""
+    w = gi.lattice_real_time(n=n, L=40.0)
+    p = w["params"]
+    psi0 = w["psi0"]()
+    s, got, obs, ref, _ = run_both(p, psi0, 100, w["dt"], False)
+    assert rel_l2(got, ref) < state_tol(100)
+    ro = oracle.observables(p, ref, t=s.t)
+    r0 = oracle.observables(p, c64(psi0).astype(np.complex128))
+    assert abs(obs["norm"] - ro["norm"]) < 1e-6
+    assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
+    assert abs(obs["energy"] - r0["energy"]) < 1e-3 * abs(r0["energy"])     # conserved to O(dt^2)
