@@ -62,16 +62,21 @@ def grid_axis(n: int, L: float) -> np.ndarray:
 
 def gaussian_state(nx: int, ny: int, Lx: float, Ly: float, width: float = 1.5,
                    noise: float = 1e-3, seed: int = 0, x0: float = 0.0,
-                   y0: float = 0.0, kx0: float = 0.0) -> np.ndarray:
+                   y0: float = 0.0, kx0: float = 0.0, checker: float = 0.0,
+                   kc: float = 0.0) -> np.ndarray:
     """Initial wave function, complex128 [ny][nx], unit norm on the grid.
 
-    psi ~ exp(-((x-x0)^2 + (y-y0)^2) / (2 width^2)) e^{i kx0 x}, plus
-    noise * max|G| * (xi_r + i xi_i) with xi ~ N(0,1) per point from the
-    seeded stream, then scaled so that sum |psi|^2 dx dy = 1.
+    psi ~ exp(-((x-x0)^2 + (y-y0)^2) / (2 width^2)) e^{i kx0 x}
+          (1 + checker cos(kc x) cos(kc y)),
+    plus noise * max|G| * (xi_r + i xi_i) with xi ~ N(0,1) per point from the
+    seeded stream, then scaled so that sum |psi|^2 dx dy = 1.  The checker
+    term seeds the density modulation of the organised cavity phase (Sec. 5.3).
     """
     x = grid_axis(nx, Lx)[None, :]
     y = grid_axis(ny, Ly)[:, None]
     g = np.exp(-((x - x0) ** 2 + (y - y0) ** 2) / (2.0 * width ** 2)) * np.exp(1j * kx0 * x)
+    if checker:
+        g = g * (1.0 + checker * np.cos(kc * x) * np.cos(kc * y))
     if noise:
         xi = normal(seed, 2 * nx * ny).reshape(2, ny, nx)
         g = g + noise * np.abs(g).max() * (xi[0] + 1j * xi[1])

@@ -66,8 +66,8 @@ Layout layout(int nx, int ny)
     L.sc = o;        o = align256(o + sizeof(DevScalars));
     L.part_row = o;  o = align256(o + sizeof(double) * NQ * MAX_BLOCKS);
     L.part_col = o;  o = align256(o + sizeof(double) * NQ * MAX_BLOCKS);
-    L.twx = o;       o = align256(o + sizeof(float2) * nx);
-    L.twy = o;       o = align256(o + sizeof(float2) * ny);
+    L.twx = o;       o = align256(o + sizeof(float4) * nx);
+    L.twy = o;       o = align256(o + sizeof(float4) * ny);
     L.xtab = o;      o = align256(o + sizeof(float4) * nx);
     L.ytab = o;      o = align256(o + sizeof(float4) * ny);
     L.kinx = o;      o = align256(o + sizeof(float2) * nx);
@@ -276,8 +276,8 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     T.sc = (DevScalars *)(c->ws + L.sc);
     T.part_row = (double *)(c->ws + L.part_row);
     T.part_col = (double *)(c->ws + L.part_col);
-    T.twx = (float2 *)(c->ws + L.twx);
-    T.twy = (float2 *)(c->ws + L.twy);
+    T.twx = (float4 *)(c->ws + L.twx);
+    T.twy = (float4 *)(c->ws + L.twy);
     T.xtab = (float4 *)(c->ws + L.xtab);
     T.ytab = (float4 *)(c->ws + L.ytab);
     T.kinx = (float2 *)(c->ws + L.kinx);

@@ -12,7 +12,7 @@
 // exchanged through shared memory in a layout padded by one slot per 16
 // elements, which keeps 64-bit accesses of every stage free of bank
 // conflicts.  Twiddles exp(-2 pi i m/N) come from a table computed in double
-// precision and rounded once.
+// precision and stored as two-float (hi + lo) pairs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,10 +33,14 @@ template <bool INV> __device__ __forceinline__ float2 mul_mi(float2 a)
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// cos and sin of 2 pi j / 16
-__host__ __device__ constexpr float cos16(int j)
+// cos(2 pi j / 16) split as hi + lo (two floats, |hi + lo - cos| < 1e-15).
+// Twiddles whose stored modulus differs from 1 by a rounding error of one
+// float would scale every transformed value the same way each step and make
+// the real-time norm drift; with the pair the modulus is 1 to 1e-15 and the
+// remaining roundings are unbiased.
+__host__ __device__ constexpr float cos16_hi(int j)
 {
-    constexpr float C1 = 0.923879532511286756f, C2 = 0.707106781186547524f, C3 = 0.382683432365089772f;
+    constexpr float C1 = 0x1.d906bcp-1f, C2 = 0x1.6a09e6p-1f, C3 = 0x1.87de2ap-2f;
     switch (j & 15) {
     case 0: return 1.f;  case 1: return C1;  case 2: return C2;  case 3: return C3;
     case 4: return 0.f;  case 5: return -C3; case 6: return -C2; case 7: return -C1;
@@ -44,7 +48,27 @@ __host__ __device__ constexpr float cos16(int j)
     case 12: return 0.f; case 13: return C3; case 14: return C2; default: return C1;
     }
 }
-__host__ __device__ constexpr float sin16(int j) { return cos16(j - 4); }
+__host__ __device__ constexpr float cos16_lo(int j)
+{
+    constexpr float L1 = 0x1.e651a8p-26f, L2 = 0x1.9fcef4p-27f, L3 = 0x1.abaa58p-28f;
+    switch (j & 15) {
+    case 1: return L1;   case 2: return L2;   case 3: return L3;
+    case 5: return -L3;  case 6: return -L2;  case 7: return -L1;
+    case 9: return -L1;  case 10: return -L2; case 11: return -L3;
+    case 13: return L3;  case 14: return L2;  case 15: return L1;
+    default: return 0.f;
+    }
+}
+__host__ __device__ constexpr float sin16_hi(int j) { return cos16_hi(j - 4); }
+__host__ __device__ constexpr float sin16_lo(int j) { return cos16_lo(j - 4); }
+
+// a * (w.x + w.z + i (w.y + w.w)): complex product with a two-float twiddle
+__device__ __forceinline__ float2 cmul_df(float2 a, float4 w)
+{
+    const float re_lo = fmaf(-a.y, w.w, a.x * w.z);
+    const float im_lo = fmaf(a.y, w.z, a.x * w.w);
+    return make_float2(fmaf(a.x, w.x, fmaf(-a.y, w.y, re_lo)), fmaf(a.x, w.y, fmaf(a.y, w.x, im_lo)));
+}
 
 // a * W16^J with W16 = exp(-2 pi i/16) (forward) or its conjugate (inverse)
 template <int J, bool INV> __device__ __forceinline__ float2 tw16(float2 a)
@@ -54,10 +78,17 @@ template <int J, bool INV> __device__ __forceinline__ float2 tw16(float2 a)
     else if constexpr (j == 4) return mul_mi<INV>(a);
     else if constexpr (j == 8) return make_float2(-a.x, -a.y);
     else if constexpr (j == 12) return mul_mi<!INV>(a);
-    else {
-        constexpr float c = cos16(j);
-        constexpr float s = INV ? sin16(j) : -sin16(j);
-        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    else if constexpr ((j & 3) == 2) {
+        // (+-1 +- i) sqrt(1/2): exact sign combination, then one scaling by the pair
+        constexpr float sr = cos16_hi(j) > 0.f ? 1.f : -1.f;
+        constexpr float si = (INV ? sin16_hi(j) : -sin16_hi(j)) > 0.f ? 1.f : -1.f;
+        constexpr float h = cos16_hi(2), l = cos16_lo(2);
+        const float u = sr * a.x - si * a.y, v = si * a.x + sr * a.y;
+        return make_float2(fmaf(u, h, u * l), fmaf(v, h, v * l));
+    } else {
+        constexpr float wr = cos16_hi(j), wi = INV ? sin16_hi(j) : -sin16_hi(j);
+        constexpr float lr = cos16_lo(j), li = INV ? sin16_lo(j) : -sin16_lo(j);
+        return cmul_df(a, make_float4(wr, wi, lr, li));
     }
 }
 
@@ -137,7 +168,7 @@ __device__ __forceinline__ int padx(int e) { return e + (e >> 4); }
 // sb: this pencil's shared buffer, es: element stride in float2 units.
 template <int N, int E, int R, int NS, bool INV, bool LAST>
 __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
-                                          const float2 *__restrict__ tw)
+                                          const float4 *__restrict__ tw)
 {
     constexpr int TP = N / E, B = E / R;
 #pragma unroll
@@ -150,9 +181,12 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ s
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&tw[r * k * (N / (NS * R))]);
-                if constexpr (INV) w.y = -w.y;
-                a[r] = cmul(a[r], w);
+                float4 w = __ldg(&tw[r * k * (N / (NS * R))]);
+                if constexpr (INV) {
+                    w.y = -w.y;
+                    w.w = -w.w;
+                }
+                a[r] = cmul_df(a[r], w);
             }
         }
         dft<R, INV>(a);
@@ -178,7 +212,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ s
 // without the 1/N factor.  Every thread of the CTA must call it together.
 template <int N, int E, bool INV, int S = 0, int NS = 1>
 __device__ __forceinline__ void fft_pencil(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
-                                           const float2 *__restrict__ tw)
+                                           const float4 *__restrict__ tw)
 {
     constexpr int LOG = ilog2(N), NST = (LOG + 3) / 4;
     constexpr int R = (S == 0) ? (1 << (LOG - 4 * (NST - 1))) : 16;

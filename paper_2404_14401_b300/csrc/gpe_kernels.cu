@@ -428,6 +428,15 @@ __global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_
 }
 
 // ------------------------------------------------------------------ tables
+// exp(-2 pi i m / n) as {re_hi, im_hi, re_lo, im_lo}: hi = float(x), lo = float(x - hi)
+__device__ float4 twiddle_pair(int m, int n)
+{
+    double s, c;
+    sincospi(2.0 * m / n, &s, &c);
+    const float ch = (float)c, sh = (float)-s;
+    return make_float4(ch, sh, (float)(c - (double)ch), (float)(-s - (double)sh));
+}
+
 // Coordinates, trap and lattice profiles and twiddles in FP64, rounded once.
 __global__ void tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, double m, double wx,
                               double wy, double lkx, double lky, double kc)
@@ -437,17 +446,13 @@ __global__ void tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, do
         const double x = -0.5 * Lx + (double)i * (Lx / nx);
         const double cl = cos(lkx * x), cc = cos(kc * x);
         T.xtab[i] = make_float4((float)(0.5 * m * wx * wx * x * x), (float)(cl * cl), (float)cc, (float)x);
-        double s, c;
-        sincospi(2.0 * i / nx, &s, &c);
-        T.twx[i] = make_float2((float)c, (float)-s);
+        T.twx[i] = twiddle_pair(i, nx);
     }
     if (i < ny) {
         const double y = -0.5 * Ly + (double)i * (Ly / ny);
         const double cl = cos(lky * y), cc = cos(kc * y);
         T.ytab[i] = make_float4((float)(0.5 * m * wy * wy * y * y), (float)(cl * cl), (float)cc, (float)y);
-        double s, c;
-        sincospi(2.0 * i / ny, &s, &c);
-        T.twy[i] = make_float2((float)c, (float)-s);
+        T.twy[i] = twiddle_pair(i, ny);
     }
 }
 

@@ -102,8 +102,12 @@ def test_imaginary_time_harmonic_trap_matches_oracle(g):
     s, got, obs, ref, _ = run_both(p, w["psi0"](), 2000, w["dt"], True)
     assert rel_l2(got, ref) < 1e-4
     ro = oracle.observables(p, ref, t=s.t)
-    for k in ("energy", "mu", "ekin", "epot"):
+    for k in ("energy", "mu"):
         assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+    # E_kin and E_pot alone are first order in the state error, which imaginary
+    # time lets reach ~eps32 / (gap dtau) ~ 2e-5 along the slowest mode
+    for k in ("ekin", "epot"):
+        assert abs(obs[k] - ro[k]) < 1e-4 * abs(ro[k]), k
     assert abs(obs["norm"] - 1.0) < 1e-6
     if g == 0.0:
         assert abs(obs["energy"] - 1.0) < 2e-4                # closed form E = 1
@@ -122,30 +126,38 @@ def test_imaginary_then_real_time_switches_kinetic_factors():
     assert rel_l2(s.get_psi(), ref) < state_tol(500)
 
 
+def cavity_close(obs, ro):
+    """alpha and O from FP64 sums of FP32 products: 1e-6 absolute plus 1e-5 relative."""
+    a_gpu = complex(obs["alpha_re"], obs["alpha_im"])
+    a_ref = complex(ro["alpha_re"], ro["alpha_im"])
+    assert abs(obs["O"] - ro["O"]) < 1e-6 + 1e-5 * abs(ro["O"])
+    assert abs(obs["B"] - ro["B"]) < 1e-6 + 1e-5 * abs(ro["B"])
+    assert abs(a_gpu - a_ref) < 1e-5 + 1e-5 * abs(a_ref)
+
+
 def test_cavity_ramp_matches_oracle():
-    """Self-consistent cavity (Sec. 5.3) with eta ramped in time; alpha on both sides."""
+    """Self-consistent cavity (Sec. 5.3) with eta ramped in time, from a density
+    with a seeded checkerboard modulation so that alpha is of order one."""
     w = gi.cavity_ramp(n=64, L=16.0, steps=400, dt=2e-4)
     p = w["params"]
-    p["ctrl_v"] = np.array([0.0, 6.0])             # strong pump: alpha is far from zero
-    psi0 = gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=2)
+    p["ctrl_v"] = np.array([1.0, 4.0])
+    psi0 = gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=2, checker=0.3, kc=p["kc"])
     s, got, obs, ref, alpha = run_both(p, psi0, 400, 2e-4, False)
     assert rel_l2(got, ref) < state_tol(400)
     ro = oracle.observables(p, ref, t=s.t)
-    a_gpu = complex(obs["alpha_re"], obs["alpha_im"])
-    a_ref = complex(ro["alpha_re"], ro["alpha_im"])
-    assert abs(a_ref) > 1e-3
-    assert abs(a_gpu - a_ref) < 1e-4 * abs(a_ref) + 1e-7
+    assert abs(complex(ro["alpha_re"], ro["alpha_im"])) > 0.05
+    cavity_close(obs, ro)
     assert abs(obs["norm"] - 1.0) < 1e-6
 
 
 def test_cavity_imaginary_time_matches_oracle():
     w = gi.cavity_ramp(n=64, L=16.0, steps=300, dt=1e-3)
-    p = dict(w["params"], ctrl_target=0, eta=2.5, ctrl_t=None, ctrl_v=None)
-    psi0 = gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=3)
+    p = dict(w["params"], ctrl_target=0, eta=10.0, ctrl_t=None, ctrl_v=None)   # organised phase
+    psi0 = gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=3, checker=0.3, kc=p["kc"])
     s, got, obs, ref, _ = run_both(p, psi0, 300, 1e-3, True)
     assert rel_l2(got, ref) < 1e-4
     ro = oracle.observables(p, ref, t=s.t)
-    assert abs(obs["O"] - ro["O"]) < 1e-5 * max(abs(ro["O"]), 1e-3)
+    cavity_close(obs, ro)
     assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
 
 
