@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the split-step GPE propagator on B300.
+
+Workload (real-time throughput configuration): 2D GPE on a 2048 x 2048
+complex64 grid, box [-20, 20]^2, harmonic trap + optical lattice
+V0 (cos^2 kx + cos^2 ky), V0 = 5, k = 2 pi, g = 500, dt = 5e-4, psi0 relaxed
+by imaginary-time evolution (2000 steps of 1e-3).  A batch of B independent
+trajectories (default 8, 256 MB of psi, more than the 126 MB L2) is stepped
+in lockstep through gpe_step_many, so every pass streams psi from HBM.
+
+One timed "step" = one split step of every trajectory.  metric: grid-points
+x steps per second (whole job: all trajectories, all ranks).  Multi-GPU runs
+are replicas (one batch per rank, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method) on the host cores, one trajectory per step as a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-points*steps/s (GPE split step, real time)"
+UNIT = "pt*steps/s"
+BYTES_PER_PT = {"row": 16, "col": 16}          # complex64 read + write per pass
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    return ap.parse_args()
+
+
+def workload(n):
+    import gpe_inputs as gi
+    return gi.lattice_real_time(n=n, L=40.0)
+
+
+def config(args, world):
+    return {"workload": f"real-time lattice GPE {args.size}x{args.size}, {args.batch} trajectories/GPU",
+            "grid": [args.size, args.size], "box": 40.0, "g": 500.0, "V0": 5.0, "dt": 5e-4,
+            "trajectories_per_gpu": args.batch,
+            "resident_bytes_per_gpu": 8 * args.size * args.size * args.batch,
+            "l2": "inputs larger than L2 (psi of all trajectories > 126 MB), no flush",
+            "parallelism": f"replicas x{world}"}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx = max(mx, float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gpe_kernels.cu", "gpe_fft.cuh", "gpe_internal.h"):
+        with open(os.path.join(ROOT, "paper_2404_14401_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, n):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("grid") == f"{n}x{n}" and kv.get("src") == src:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(n, budget_s=12.0, min_steps=1):
+    """Time the FP64 oracle as it stands on one trajectory of the workload:
+    steps until about budget_s of work.  Returns (pt*steps/s, steps, secs, threads)."""
+    import numpy as np
+
+    import oracle
+    w = workload(n)
+    p = w["params"]
+    psi = w["psi0"]().astype(np.complex128)
+    t0 = time.perf_counter()
+    psi, _ = oracle.evolve(p, psi, 1, w["dt"], False)
+    one = time.perf_counter() - t0
+    k = max(min_steps, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    oracle.evolve(p, psi, k, w["dt"], False, t0=w["dt"])
+    secs = time.perf_counter() - t0
+    return n * n * k / secs, k, secs, oracle.threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = args.size
+    w = workload(n)
+    import numpy as np
+    p = w["params"]
+    psi = w["psi0"]().astype(np.complex128)
+    for _ in range(args.warmup):
+        psi, _ = oracle.evolve(p, psi, 1, w["dt"], False)
+    t0 = time.perf_counter()
+    psi, _ = oracle.evolve(p, psi, args.steps, w["dt"], False)
+    secs = time.perf_counter() - t0
+    value = n * n * args.steps / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(config(args, 1), trajectories_per_gpu=1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"one {n}x{n} trajectory, {args.steps} steps per run"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import gpe_inputs as gi
+    from paper_2404_14401_b300 import Simulation
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n, B = args.size, args.batch
+    w = workload(n)
+    p = w["params"]
+    dt = w["dt"]
+
+    # inputs: one imaginary-time relaxed state (on the GPU), then per-trajectory
+    # seeded complex noise of 1e-3 so the trajectories differ
+    sims = [Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev) for _ in range(B)]
+    for s in sims:
+        s.set_potential(p)
+    sims[0].set_psi(w["psi0"]().astype(np.complex64))
+    sims[0].step(2000, 1e-3, imag=True)
+    sims[0].t = 0.0
+    base = sims[0].psi.clone()
+    for b, s in enumerate(sims):
+        z = gi.normal(100 + b + 1000 * rank, 2 * n * n).reshape(2, n, n)
+        noise = torch.from_numpy((z[0] + 1j * z[1]).astype(np.complex64)).to(dev)
+        x = base * (1 + 1e-3 * noise)
+        x = x / torch.sqrt(torch.sum(torch.abs(x) ** 2) * (p["Lx"] / n) * (p["Ly"] / n))
+        s.set_psi(x)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up, then exactly `steps` lockstep steps of all trajectories
+    Simulation.step_many(sims, args.warmup, dt)
+    torch.cuda.synchronize()
+    barrier()
+    launches0 = sum(s.launches for s in sims)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local_rank) if rank == 0 else None
+    time.sleep(0.4 if clocks else 0.0)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    Simulation.step_many(sims, args.steps, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    launches = sum(s.launches for s in sims) - launches0
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    status = [s.sync() for s in sims]
+    obs = sims[0].observables()
+
+    # per-kernel durations on the same workload, with events around each pass
+    prof_steps = min(args.steps, 100)
+    for s in sims:
+        s.profile(True)
+    Simulation.step_many(sims, prof_steps, dt)
+    pr = [s.profile_read() for s in sims]
+    for s in sims:
+        s.profile(False)
+    row_ms = sum(x["row_ms"] for x in pr) / sum(x["row_launches"] for x in pr)
+    col_ms = sum(x["col_ms"] for x in pr) / sum(x["col_launches"] for x in pr)
+    dom = "col" if col_ms >= row_ms else "row"
+    dom_ms = max(row_ms, col_ms)
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = BYTES_PER_PT[dom] * n * n
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    kname = {"row": f"row_kernel<{n},ROW_MERGED>", "col": f"col_kernel<{n},COL_KIN>"}[dom]
+    traffic = recorded_traffic(kname, n)
+
+    # end to end through the public API from pinned host buffers: upload every
+    # trajectory, step, read every trajectory and the observables back
+    host_in = [torch.from_numpy(s.get_psi()).pin_memory() for s in sims]
+    host_out = [torch.empty((n, n), dtype=torch.complex64).pin_memory() for _ in sims]
+    from paper_2404_14401_b300 import gpe as abi
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for s, h in zip(sims, host_in):
+        abi.gpe_set_psi(s.ctx, h.data_ptr(), False)
+    Simulation.step_many(sims, e2e_steps, dt)
+    for s, h in zip(sims, host_out):
+        abi.gpe_get_psi(s.ctx, h.data_ptr(), False)
+    obs_e2e = sims[0].observables()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 8 * n * n * B
+    d2h = 8 * n * n * B + 100
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, k, secs, thr = oracle_sample(n)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"one {n}x{n} trajectory of the workload, {k} FP64 split steps ({secs:.1f} s)"}
+
+    if rank != 0:
+        return
+    total_pts = n * n * B * world
+    value = total_pts * args.steps / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32), f64 reductions",
+        "data": "synthetic (seeded Gaussian relaxed in imaginary time, + seeded noise)",
+        "config": config(args, world),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes,
+                     "avg_launch_ms": dom_ms, "row_pass_ms": row_ms, "col_pass_ms": col_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": total_pts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps,
+                "note": f"one job of {e2e_steps} steps: pinned h2d of every psi, gpe_step_many, d2h of every psi + observables"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "check": {"norm": obs["norm"], "energy": obs["energy"], "status": status,
+                  "norm_after_e2e": obs_e2e["norm"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -121,6 +121,13 @@ gpe_status gpe_set_potential(gpe_ctx *ctx, const gpe_potential *p);
  * after.  Asynchronous.  Errors: GPE_EINVAL, GPE_ECUDA. */
 gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
 
+/* Enqueue n steps on each of `count` contexts in lockstep: step s of every
+ * context is enqueued (on that context's stream) before step s+1 of any,
+ * so the grids share one pass schedule -- e.g. a batch of trajectories of a
+ * parameter sweep (Sec. 5.3 phase diagram), possibly of different sizes.
+ * Same argument rules and errors as gpe_step; contexts must be distinct. */
+gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode);
+
 /* Compute the observables of psi at the current time; waits for the stream.
  * Returns the latched device status if it is not GPE_OK (out is filled). */
 gpe_status gpe_observables(gpe_ctx *ctx, gpe_obs *out);
@@ -149,6 +156,18 @@ gpe_status gpe_sync(gpe_ctx *ctx);
  * so it must run out after about `spins` polls and latch GPE_ETIMEOUT
  * (failure-path check of the timeout mechanism; touches no psi data).  */
 gpe_status gpe_debug_timeout_probe(gpe_ctx *ctx, int spins);
+
+/* Diagnostics: with enable = 1 every pass this context launches is bracketed
+ * by CUDA events on its stream; gpe_profile_read waits for the stream and
+ * returns the summed device milliseconds and launch counts of row passes and
+ * column passes since profiling was enabled (then resets them).  Events cost
+ * a few microseconds per pass; leave profiling off for throughput runs. */
+gpe_status gpe_profile(gpe_ctx *ctx, int enable);
+gpe_status gpe_profile_read(gpe_ctx *ctx, double *row_ms, int *row_launches, double *col_ms,
+                            int *col_launches);
+
+/* Number of kernels this context has launched since it was created. */
+long long gpe_launch_count(const gpe_ctx *ctx);
 
 /* Release the context (host memory only; borrowed memory is untouched). */
 void gpe_destroy(gpe_ctx *ctx);

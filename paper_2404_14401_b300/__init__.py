@@ -82,6 +82,21 @@ class Simulation:
     def step(self, n: int, dt: float, imag: bool = False):
         abi.gpe_step(self.ctx, n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
 
+    @staticmethod
+    def step_many(sims, n: int, dt: float, imag: bool = False):
+        """n lockstep steps on several simulations (one pass schedule)."""
+        abi.gpe_step_many([s.ctx for s in sims], n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
+
+    def profile(self, enable: bool):
+        abi.gpe_profile(self.ctx, enable)
+
+    def profile_read(self) -> dict:
+        return abi.gpe_profile_read(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return abi.gpe_launch_count(self.ctx)
+
     def observables(self, check: bool = True) -> dict:
         return abi.gpe_observables(self.ctx, check)
 

@@ -22,6 +22,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <utility>
 #include <vector>
 
 #include "../../include/gpe.h"
@@ -46,6 +47,13 @@ struct gpe_ctx {
     int kin_mode;
     bool kin_valid;
     int spins;
+    long long launches;
+    // per-pass event timing (gpe_profile)
+    bool prof;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    double prof_ms[2];
+    int prof_n[2];
     char err[256];
 };
 
@@ -201,6 +209,37 @@ ColArgs col_args(const gpe_ctx *c, int imag)
     return a;
 }
 
+cudaEvent_t take_event(gpe_ctx *c)
+{
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch one pass, bracketed by events when profiling (kind 0 row, 1 column).
+template <class F> gpe_status timed_launch(gpe_ctx *c, int kind, F &&launch, const char *what)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        cudaEventRecord(e0, c->stream);
+    }
+    const cudaError_t err = launch();
+    if (err != cudaSuccess) return cuda_check(c, err, what);
+    c->launches++;
+    if (c->prof) {
+        cudaEventRecord(e1, c->stream);
+        c->ev_pending.push_back({kind, {e0, e1}});
+    }
+    return GPE_OK;
+}
+
 gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag, int use_c)
 {
     RowArgs a = row_args(c);
@@ -208,12 +247,13 @@ gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd,
     a.red = rd;
     a.imag = imag;
     a.use_c = use_c;
-    return cuda_check(c, launch_row(mode, a, c->stream), "row pass");
+    return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream); }, "row pass");
 }
 
 gpe_status run_col(gpe_ctx *c, int mode, int imag)
 {
-    return cuda_check(c, launch_col(mode, col_args(c, imag), c->map, c->stream), "column pass");
+    const ColArgs a = col_args(c, imag);
+    return timed_launch(c, 1, [&] { return launch_col(mode, a, c->map, c->stream); }, "column pass");
 }
 
 #define TRY(x)                                   \
@@ -268,6 +308,10 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->t = 0.0;
     c->kin_valid = false;
     c->spins = 1 << 24;
+    c->launches = 0;
+    c->prof = false;
+    c->prof_ms[0] = c->prof_ms[1] = 0.0;
+    c->prof_n[0] = c->prof_n[1] = 0;
     memset(&c->pot, 0, sizeof(c->pot));
     c->pot.V_scale = 1.0;
     c->pot.N = 1.0;
@@ -287,6 +331,7 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     if (s == GPE_OK) s = cuda_check(c, cudaMemsetAsync(T.sc, 0, sizeof(DevScalars), c->stream), "memset");
     if (s == GPE_OK)
         s = cuda_check(c, launch_tables(T, nx, ny, Lx, Ly, m, 0, 0, 0, 0, 0, c->stream), "tables");
+    if (s == GPE_OK) c->launches++;
     if (s != GPE_OK) {
         delete c;
         return s;
@@ -314,54 +359,110 @@ gpe_status gpe_set_potential(gpe_ctx *c, const gpe_potential *p)
     c->ctrl_v.assign(p->ctrl_v, p->ctrl_v + p->nctrl);
     c->pot.ctrl_t = nullptr;
     c->pot.ctrl_v = nullptr;
-    return cuda_check(c, launch_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, p->wx, p->wy, p->lat_kx,
-                                       p->lat_ky, p->cavity ? p->kc : 0.0, c->stream),
-                      "tables");
+    return timed_launch(c, 2, [&] {
+        return launch_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, p->wx, p->wy, p->lat_kx, p->lat_ky,
+                             p->cavity ? p->kc : 0.0, c->stream);
+    }, "tables");
 }
 
-gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
+}  // extern "C"
+
+namespace {
+
+gpe_status step_check(gpe_ctx *c, int n, double dt, gpe_mode mode)
 {
     if (!c) return GPE_EINVAL;
     if (n < 0 || !(dt > 0.0) || !isfinite(dt) || (mode != GPE_REAL && mode != GPE_IMAG))
         return fail(c, GPE_EINVAL, "gpe_step: n %d dt %g mode %d", n, dt, (int)mode);
-    if (n == 0) return GPE_OK;
+    return GPE_OK;
+}
+
+// Passes before step 0: kinetic factors for (dt, mode) and, with a cavity,
+// alpha of the initial density (Eq. 14).
+gpe_status step_prologue(gpe_ctx *c, double dt, gpe_mode mode)
+{
     const int imag = mode == GPE_IMAG;
     if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
-        TRY(cuda_check(c, launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream),
-                       "kinetic tables"));
+        TRY(timed_launch(c, 2, [&] {
+            return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
+        }, "kinetic tables"));
         c->kin_valid = true;
         c->kin_dt = dt;
         c->kin_mode = (int)mode;
     }
-    const bool cav = c->pot.cavity != 0;
-    const double t0 = c->t;
     PhaseArgs none;
     memset(&none, 0, sizeof(none));
-    if (!imag) {
-        if (cav) TRY(run_row(c, ROW_REDUCE_R, none, red_at(c, t0), 0, 0));
-        TRY(run_row(c, ROW_FWD, phase_at(c, t0, 0.5 * dt), red_at(c, t0), 0, 0));
-        TRY(run_col(c, COL_KIN, 0));
-        for (int s = 1; s < n; ++s) {
-            const double ts = t0 + s * dt;
+    if (c->pot.cavity) TRY(run_row(c, ROW_REDUCE_R, none, red_at(c, c->t), imag, 0));
+    return GPE_OK;
+}
+
+// The passes of step s (0 <= s < n) starting from the context's time c->t.
+gpe_status step_part(gpe_ctx *c, int s, double dt, gpe_mode mode)
+{
+    const bool cav = c->pot.cavity != 0;
+    const double ts = c->t + s * dt, te = c->t + (s + 1) * dt;
+    PhaseArgs none;
+    memset(&none, 0, sizeof(none));
+    if (mode == GPE_REAL) {
+        if (s == 0) {
+            TRY(run_row(c, ROW_FWD, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0));
+        } else {
             if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, ts), 0, 0));
             TRY(run_row(c, ROW_MERGED, phase_at(c, ts, dt), red_at(c, ts), 0, 0));
-            TRY(run_col(c, COL_KIN, 0));
         }
-        const double tn = t0 + n * dt;
-        if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, tn), 0, 0));
+        TRY(run_col(c, COL_KIN, 0));
+    } else {
+        TRY(run_row(c, ROW_FWD, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 1, s > 0));
+        TRY(run_col(c, COL_KIN, 1));
+        if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, te), 1, 0));
+        TRY(run_row(c, ROW_INV, phase_at(c, te, 0.5 * dt), red_at(c, te), 1, 0));
+    }
+    return GPE_OK;
+}
+
+// Passes after step n-1: the last half phase (real time) or the pending
+// normalisation (imaginary time); advances the context's time.
+gpe_status step_epilogue(gpe_ctx *c, int n, double dt, gpe_mode mode)
+{
+    const double tn = c->t + n * dt;
+    PhaseArgs none;
+    memset(&none, 0, sizeof(none));
+    if (mode == GPE_REAL) {
+        if (c->pot.cavity) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, tn), 0, 0));
         TRY(run_row(c, ROW_INV, phase_at(c, tn, 0.5 * dt), red_at(c, tn), 0, 0));
     } else {
-        if (cav) TRY(run_row(c, ROW_REDUCE_R, none, red_at(c, t0), 1, 0));
-        for (int s = 0; s < n; ++s) {
-            const double ts = t0 + s * dt, te = t0 + (s + 1) * dt;
-            TRY(run_row(c, ROW_FWD, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 1, s > 0));
-            TRY(run_col(c, COL_KIN, 1));
-            if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, te), 1, 0));
-            TRY(run_row(c, ROW_INV, phase_at(c, te, 0.5 * dt), red_at(c, te), 1, 0));
-        }
-        TRY(run_row(c, ROW_SCALE, none, red_at(c, t0 + n * dt), 1, 0));
+        TRY(run_row(c, ROW_SCALE, none, red_at(c, tn), 1, 0));
     }
-    c->t = t0 + n * dt;
+    c->t = tn;
+    return GPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
+{
+    TRY(step_check(c, n, dt, mode));
+    if (n == 0) return GPE_OK;
+    TRY(step_prologue(c, dt, mode));
+    for (int s = 0; s < n; ++s) TRY(step_part(c, s, dt, mode));
+    return step_epilogue(c, n, dt, mode);
+}
+
+gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode)
+{
+    if (!ctxs || count < 1) return GPE_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        TRY(step_check(ctxs[i], n, dt, mode));
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(ctxs[i], GPE_EINVAL, "gpe_step_many: repeated context");
+    }
+    if (n == 0) return GPE_OK;
+    for (int i = 0; i < count; ++i) TRY(step_prologue(ctxs[i], dt, mode));
+    for (int s = 0; s < n; ++s)
+        for (int i = 0; i < count; ++i) TRY(step_part(ctxs[i], s, dt, mode));
+    for (int i = 0; i < count; ++i) TRY(step_epilogue(ctxs[i], n, dt, mode));
     return GPE_OK;
 }
 
@@ -460,10 +561,52 @@ gpe_status gpe_sync(gpe_ctx *c)
 gpe_status gpe_debug_timeout_probe(gpe_ctx *c, int spins)
 {
     if (!c || spins < 1) return GPE_EINVAL;
-    return cuda_check(c, launch_timeout_probe(c->T.sc, spins, c->stream), "timeout probe");
+    return timed_launch(c, 2, [&] { return launch_timeout_probe(c->T.sc, spins, c->stream); }, "timeout probe");
 }
 
-void gpe_destroy(gpe_ctx *c) { delete c; }
+gpe_status gpe_profile(gpe_ctx *c, int enable)
+{
+    if (!c) return GPE_EINVAL;
+    c->prof = enable != 0;
+    return GPE_OK;
+}
+
+gpe_status gpe_profile_read(gpe_ctx *c, double *row_ms, int *row_launches, double *col_ms, int *col_launches)
+{
+    if (!c) return GPE_EINVAL;
+    TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    for (auto &p : c->ev_pending) {
+        float ms = 0.f;
+        if (p.first < 2 && cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+            c->prof_ms[p.first] += ms;
+            c->prof_n[p.first] += 1;
+        }
+        c->ev_free.push_back(p.second.first);
+        c->ev_free.push_back(p.second.second);
+    }
+    c->ev_pending.clear();
+    if (row_ms) *row_ms = c->prof_ms[0];
+    if (row_launches) *row_launches = c->prof_n[0];
+    if (col_ms) *col_ms = c->prof_ms[1];
+    if (col_launches) *col_launches = c->prof_n[1];
+    c->prof_ms[0] = c->prof_ms[1] = 0.0;
+    c->prof_n[0] = c->prof_n[1] = 0;
+    return GPE_OK;
+}
+
+long long gpe_launch_count(const gpe_ctx *c) { return c ? c->launches : -1; }
+
+void gpe_destroy(gpe_ctx *c)
+{
+    if (!c) return;
+    if (!c->ev_pending.empty()) cudaStreamSynchronize(c->stream);
+    for (auto &p : c->ev_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    delete c;
+}
 
 const char *gpe_last_error(const gpe_ctx *c) { return c ? c->err : "null context"; }
 

@@ -19,9 +19,10 @@ GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EIL
 GPE_REAL, GPE_IMAG = 0, 1
 GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 
-EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_observables",
-           "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2", "gpe_sync",
-           "gpe_debug_timeout_probe", "gpe_destroy", "gpe_last_error", "gpe_status_string")
+EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_step_many",
+           "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
+           "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_launch_count",
+           "gpe_destroy", "gpe_last_error", "gpe_status_string")
 
 
 class gpe_potential(ctypes.Structure):
@@ -71,6 +72,10 @@ def load() -> ctypes.CDLL:
                                c_size_t, c_void_p, P(c_void_p)]),
         "gpe_set_potential": (c_int, [c_void_p, P(gpe_potential)]),
         "gpe_step": (c_int, [c_void_p, c_int, c_double, c_int]),
+        "gpe_step_many": (c_int, [P(c_void_p), c_int, c_int, c_double, c_int]),
+        "gpe_profile": (c_int, [c_void_p, c_int]),
+        "gpe_profile_read": (c_int, [c_void_p, P(c_double), P(c_int), P(c_double), P(c_int)]),
+        "gpe_launch_count": (ctypes.c_longlong, [c_void_p]),
         "gpe_observables": (c_int, [c_void_p, P(gpe_obs)]),
         "gpe_set_psi": (c_int, [c_void_p, c_void_p, c_int]),
         "gpe_get_psi": (c_int, [c_void_p, c_void_p, c_int]),
@@ -118,6 +123,27 @@ def gpe_set_potential(ctx, pot: gpe_potential):
 
 def gpe_step(ctx, n: int, dt: float, mode: int):
     _check(ctx, load().gpe_step(ctx, int(n), float(dt), int(mode)))
+
+
+def gpe_step_many(ctxs, n: int, dt: float, mode: int):
+    arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    _check(ctxs[0] if ctxs else None, load().gpe_step_many(arr, len(ctxs), int(n), float(dt), int(mode)))
+
+
+def gpe_profile(ctx, enable: bool):
+    _check(ctx, load().gpe_profile(ctx, int(enable)))
+
+
+def gpe_profile_read(ctx) -> dict:
+    rm, cm = c_double(), c_double()
+    rn, cn = c_int(), c_int()
+    _check(ctx, load().gpe_profile_read(ctx, ctypes.byref(rm), ctypes.byref(rn), ctypes.byref(cm),
+                                        ctypes.byref(cn)))
+    return dict(row_ms=rm.value, row_launches=rn.value, col_ms=cm.value, col_launches=cn.value)
+
+
+def gpe_launch_count(ctx) -> int:
+    return int(load().gpe_launch_count(ctx))
 
 
 def gpe_observables(ctx, check: bool = True) -> dict:
