@@ -169,6 +169,29 @@ gpe_status gpe_profile_read(gpe_ctx *ctx, double *row_ms, int *row_launches, dou
 /* Number of kernels this context has launched since it was created. */
 long long gpe_launch_count(const gpe_ctx *ctx);
 
+/* Allocation-free variant for callers that may not allocate device memory
+ * (the paper has no counterpart; this is a library convenience).  Some
+ * callers only hold pointers handed to them: a plug-in whose host
+ * application owns every device allocation through its own pool, or a hook
+ * that must not call cudaMalloc/cudaFree because those can synchronise the
+ * whole device.  They cannot supply the workspace gpe_create borrows, so
+ * this call runs the row-pass density reduction with its scratch in a fixed
+ * array inside the library (about 200 KB, held on every GPU that loads the
+ * library until the process exits) and returns
+ *     out[0] = int |psi|^2 dx dy,
+ *     out[1] = O = <cos(kc x) cos(kc y)>,  out[2] = B = <cos^2(kc x)>
+ * (averages over |psi|^2 / norm, the overlaps of Eqs. 14-15) for psi
+ * complex64 [ny][nx] on the device (16-byte aligned), box Lx x Ly.  It waits
+ * for `stream` and writes out on the host.  nx, ny: powers of two from 8 to
+ * GPE_STATIC_MAX_N; larger grids return GPE_ENOMEM, malformed ones
+ * GPE_EINVAL.  The first call on a device looks up the array's device
+ * address (make that first call before any stream capture that includes
+ * it).  Every call uses the same array: calls that overlap on the GPU (other
+ * streams or threads) race and give wrong results.  Nothing is allocated. */
+#define GPE_STATIC_MAX_N 2048
+gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, double Lx, double Ly, double kc,
+                               void *stream, double *out);
+
 /* Release the context (host memory only; borrowed memory is untouched). */
 void gpe_destroy(gpe_ctx *ctx);
 

@@ -22,7 +22,7 @@ GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_step_many",
            "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
            "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_launch_count",
-           "gpe_destroy", "gpe_last_error", "gpe_status_string")
+           "gpe_overlaps_static", "gpe_destroy", "gpe_last_error", "gpe_status_string")
 
 
 class gpe_potential(ctypes.Structure):
@@ -84,6 +84,8 @@ def load() -> ctypes.CDLL:
         "gpe_fft2": (c_int, [c_void_p, c_int]),
         "gpe_sync": (c_int, [c_void_p]),
         "gpe_debug_timeout_probe": (c_int, [c_void_p, c_int]),
+        "gpe_overlaps_static": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p,
+                                        P(c_double)]),
         "gpe_destroy": (None, [c_void_p]),
         "gpe_last_error": (c_char_p, [c_void_p]),
         "gpe_status_string": (c_char_p, [c_int]),
@@ -181,6 +183,16 @@ def gpe_sync(ctx) -> int:
 
 def gpe_debug_timeout_probe(ctx, spins: int):
     _check(ctx, load().gpe_debug_timeout_probe(ctx, int(spins)))
+
+
+def gpe_overlaps_static(psi_ptr: int, nx: int, ny: int, Lx: float, Ly: float, kc: float,
+                        stream_handle: int):
+    """Norm and cavity overlaps (norm, O, B) of a device psi with the library's
+    fixed scratch instead of a workspace; raises GPEError on a bad status."""
+    out = (c_double * 3)()
+    s = load().gpe_overlaps_static(c_void_p(psi_ptr), nx, ny, Lx, Ly, kc, c_void_p(stream_handle), out)
+    _check(None, s)
+    return out[0], out[1], out[2]
 
 
 def gpe_destroy(ctx):
