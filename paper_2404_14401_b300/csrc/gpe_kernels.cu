@@ -324,28 +324,56 @@ template <int N> struct ColCfg {
     static constexpr int E = N >= 16 ? 16 : N;
     static constexpr int TP = N / E;
     static constexpr int BR = N < 256 ? N : 256;    // rows per TMA box
+    static constexpr int PS = N + N / 16;          // padded pencil stride (float2)
 };
 
-// Columns transformed at once by one CTA (the tile holds W of them; the
-// 8192-row case works through its two columns one after the other so that
-// a thread keeps 16 elements and the CTA stays at 512 threads).
-int col_group(int ny, int W) { return ny >= 8192 ? 1 : W; }
+// Tile width for columns of length N: W columns x N rows = 4096 elements
+// (32 KB) when possible, at least 2 columns (a 16-byte TMA box row).
+__host__ __device__ constexpr int col_w_default(int n)
+{
+    return 4096 / n < 2 ? 2 : (4096 / n > 64 ? 64 : 4096 / n);
+}
+// Columns transformed at once: 256 threads (512 for N >= 4096); the 8192-row
+// tile does its second column in a second round.
+__host__ __device__ constexpr int col_g(int n, int w)
+{
+    const int tp = n >= 16 ? n / 16 : 1;
+    const int t = n >= 4096 ? 512 : 256;
+    const int g = t / tp < 1 ? 1 : t / tp;
+    return g > w ? w : g;
+}
+__host__ __device__ constexpr bool col_w_valid(int n, int w)
+{
+    return w == col_w_default(n) || (w >= 8 && w < col_w_default(n));
+}
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_constant__ CUtensorMap map)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+
+// Column pass over a tile of W columns: TMA load of the dense [N][W] tile,
+// per-column FFT through padded per-column exchange buffers, the kinetic
+// factor, inverse FFT, results written back into the dense tile and stored
+// with TMA.
+template <int N, int W, int MODE>
+__global__ void __launch_bounds__(col_g(N, W) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
+    col_kernel(const ColArgs a, const __grid_constant__ CUtensorMap map)
 {
     using C = ColCfg<N>;
-    constexpr int E = C::E, TP = C::TP;
+    constexpr int E = C::E, TP = C::TP, G = col_g(N, W);
+    constexpr bool INPLACE = (G == W);   // exchange buffers may overlay the dense tile
     extern __shared__ unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ double red[32 * NQ];
 
-    // 128-byte aligned tile: dense [N][W] as written by TMA, later reused with
-    // one padding row per 16 rows for the exchanges
     const uint32_t s0 = smem_u32(smraw);
     float2 *tile = reinterpret_cast<float2 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    float2 *pen = INPLACE ? tile : tile + N * W;
 
-    const int W = a.W, G = a.G;
     const int c0 = blockIdx.x * W;
     const Tables &T = a.T;
 
@@ -362,24 +390,23 @@ __global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_
         return;
     }
 
-    // Column c uses only the tile slots congruent to c mod W, in both the
-    // dense TMA layout and the padded exchange layout, so column groups
-    // can be transformed one after the other in place.
+    const int j = threadIdx.x % TP, cg = threadIdx.x / TP;
+    float2 *sb = pen + cg * C::PS;
     float q[1] = {0.f};
+#pragma unroll 1
     for (int g0 = 0; g0 < W; g0 += G) {
-        const int c = g0 + (threadIdx.x & (G - 1)), j = threadIdx.x / G;
+        const int c = g0 + cg;
         float2 v[E];
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = tile[(size_t)(j + r * TP) * W + c];
-        __syncthreads();                             // dense reads done before padded writes
-        float2 *sb = tile + c;
+        for (int r = 0; r < E; ++r) v[r] = tile[(j + r * TP) * W + c];
+        if constexpr (INPLACE) __syncthreads();      // dense reads done before exchange writes
 
         if constexpr (MODE == COL_FFT_I) {
-            fft_pencil<N, E, true>(v, sb, j, W, T.twy);
+            fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.scale, v[r].y * a.scale);
         } else {
-            fft_pencil<N, E, false>(v, sb, j, W, T.twy);
+            fft_pencil<N, E, false>(v, sb, j, 1, T.twy);
         }
 
         if constexpr (MODE == COL_KIN) {
@@ -403,7 +430,7 @@ __global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_
                     v[r] = make_float2((p.x + pd.x) * a.scale, (p.y + pd.y) * a.scale);
                 }
             }
-            fft_pencil<N, E, true>(v, sb, j, W, T.twy);
+            fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
         }
 
         if constexpr (MODE == COL_OBS) {
@@ -414,9 +441,11 @@ __global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_
                 q[0] += ky * ky * (v[r].x * v[r].x + v[r].y * v[r].y);
             }
         } else {
+            // every exchange read of this round finished at the last stage's barrier
 #pragma unroll
-            for (int r = 0; r < E; ++r) a.psi[(size_t)(j + r * TP) * a.nx + c0 + c] = v[r];
+            for (int r = 0; r < E; ++r) tile[(j + r * TP) * W + c] = v[r];
         }
+        if constexpr (!INPLACE) __syncthreads();
     }
 
     if constexpr (MODE == COL_OBS) {
@@ -424,6 +453,15 @@ __global__ void __launch_bounds__(512) col_kernel(const ColArgs a, const __grid_
         double S[1];
         if (last_block_total<1>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
             T.sc->sums[1][0] = S[0];
+    } else {
+        // make the generic-proxy tile writes visible to the TMA engine, then store
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, tile + (size_t)r0 * W, 2 * c0, r0);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // tile read before exit
+        }
     }
 }
 
@@ -503,12 +541,11 @@ int row_rows_per_cta(int nx, int ny)
 
 int col_tile_width(int nx, int ny)
 {
-    int w = 8192 / ny;
-    if (w < 2) w = 2;
-    if (w > 64) w = 64;
-    if (w > nx) w = nx;
-    return w;
+    const int w = col_w_default(ny);
+    return w > nx ? nx : w;
 }
+
+int col_group(int ny, int W) { return col_g(ny, W); }
 
 template <int N, int MODE> static cudaError_t row_launch(const RowArgs &a, cudaStream_t s)
 {
@@ -565,31 +602,51 @@ cudaError_t launch_row(int mode, const RowArgs &a, cudaStream_t s)
     }
 }
 
-template <int N, int MODE>
+template <int N, int W, int MODE>
 static cudaError_t col_launch(const ColArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     using C = ColCfg<N>;
-    const int threads = a.G * C::TP;
-    const size_t smem = (size_t)(N + N / 16) * a.W * sizeof(float2) + 128;
+    constexpr int G = col_g(N, W);
+    constexpr size_t smem = (G == W ? (size_t)W * C::PS : (size_t)N * W + (size_t)G * C::PS) * sizeof(float2) + 128;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(col_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(col_kernel<N, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
         attr = true;
     }
-    col_kernel<N, MODE><<<a.nx / a.W, threads, smem, s>>>(a, map);
+    col_kernel<N, W, MODE><<<a.nx / W, G * C::TP, smem, s>>>(a, map);
     return cudaGetLastError();
 }
 
-template <int N> static cudaError_t col_dispatch_mode(int mode, const ColArgs &a, const CUtensorMap &map,
-                                                      cudaStream_t s)
+template <int N, int W> static cudaError_t col_dispatch_mode(int mode, const ColArgs &a, const CUtensorMap &map,
+                                                             cudaStream_t s)
 {
-    switch (mode) {
-    case COL_KIN: return col_launch<N, COL_KIN>(a, map, s);
-    case COL_FFT_F: return col_launch<N, COL_FFT_F>(a, map, s);
-    case COL_FFT_I: return col_launch<N, COL_FFT_I>(a, map, s);
-    case COL_OBS: return col_launch<N, COL_OBS>(a, map, s);
+    if constexpr (!col_w_valid(N, W)) {
+        return cudaErrorInvalidValue;
+    } else {
+        switch (mode) {
+        case COL_KIN: return col_launch<N, W, COL_KIN>(a, map, s);
+        case COL_FFT_F: return col_launch<N, W, COL_FFT_F>(a, map, s);
+        case COL_FFT_I: return col_launch<N, W, COL_FFT_I>(a, map, s);
+        case COL_OBS: return col_launch<N, W, COL_OBS>(a, map, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+template <int N> static cudaError_t col_dispatch_w(int mode, const ColArgs &a, const CUtensorMap &map,
+                                                   cudaStream_t s)
+{
+    switch (a.W) {
+    case 2: return col_dispatch_mode<N, 2>(mode, a, map, s);
+    case 4: return col_dispatch_mode<N, 4>(mode, a, map, s);
+    case 8: return col_dispatch_mode<N, 8>(mode, a, map, s);
+    case 16: return col_dispatch_mode<N, 16>(mode, a, map, s);
+    case 32: return col_dispatch_mode<N, 32>(mode, a, map, s);
+    case 64: return col_dispatch_mode<N, 64>(mode, a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -597,17 +654,17 @@ template <int N> static cudaError_t col_dispatch_mode(int mode, const ColArgs &a
 cudaError_t launch_col(int mode, const ColArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     switch (a.ny) {
-    case 8: return col_dispatch_mode<8>(mode, a, map, s);
-    case 16: return col_dispatch_mode<16>(mode, a, map, s);
-    case 32: return col_dispatch_mode<32>(mode, a, map, s);
-    case 64: return col_dispatch_mode<64>(mode, a, map, s);
-    case 128: return col_dispatch_mode<128>(mode, a, map, s);
-    case 256: return col_dispatch_mode<256>(mode, a, map, s);
-    case 512: return col_dispatch_mode<512>(mode, a, map, s);
-    case 1024: return col_dispatch_mode<1024>(mode, a, map, s);
-    case 2048: return col_dispatch_mode<2048>(mode, a, map, s);
-    case 4096: return col_dispatch_mode<4096>(mode, a, map, s);
-    case 8192: return col_dispatch_mode<8192>(mode, a, map, s);
+    case 8: return col_dispatch_w<8>(mode, a, map, s);
+    case 16: return col_dispatch_w<16>(mode, a, map, s);
+    case 32: return col_dispatch_w<32>(mode, a, map, s);
+    case 64: return col_dispatch_w<64>(mode, a, map, s);
+    case 128: return col_dispatch_w<128>(mode, a, map, s);
+    case 256: return col_dispatch_w<256>(mode, a, map, s);
+    case 512: return col_dispatch_w<512>(mode, a, map, s);
+    case 1024: return col_dispatch_w<1024>(mode, a, map, s);
+    case 2048: return col_dispatch_w<2048>(mode, a, map, s);
+    case 4096: return col_dispatch_w<4096>(mode, a, map, s);
+    case 8192: return col_dispatch_w<8192>(mode, a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }
