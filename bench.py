@@ -259,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_hbm_peak()
     alg_bytes = BYTES_PER_PT[dom] * n * n
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    kname = {"row": f"row_kernel<{n},ROW_MERGED>", "col": f"col_kernel<{n},COL_KIN>"}[dom]
+    kname = {"row": f"row_kernel<{n},ROW_PT>", "col": f"col_kernel<{n},COL_T>"}[dom]
     traffic = recorded_traffic(kname, n)
 
     # end to end through the public API from pinned host buffers: upload every

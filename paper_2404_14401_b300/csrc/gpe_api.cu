@@ -3,17 +3,22 @@
 // of row / column passes of the symmetric split-step (Sec. 3.1, Eqs. 2-4;
 // imaginary time Sec. 3.3; cavity Sec. 5.3, Eqs. 10-15).
 //
-// Pass schedules (R = row pass, C = column pass; psi is real-space at entry
-// and exit of every call):
-//   real time, no cavity   R_fwd(V/2) C { R_merged(V) C }^(n-1) R_inv(V/2)
-//       the two half phases V(t_n)/2 of adjacent steps use the same density
-//       (a real phase keeps |psi|) and merge into one full phase;
-//   real time, cavity      as above with a reduce-only row pass before every
-//       phase: alpha needs the grid-wide overlaps of the current density;
-//   imaginary time         { R_fwd([c] V/2) C [R_reduce] R_inv(V/2 + norm) }^n R_scale
-//       the norm of the step's result (Sec. 3.3) and, with a cavity, alpha
-//       are grid-wide, so they are reduced in R_inv and applied in the next
-//       R_fwd as a scale.
+// Pass schedules (R = row pass: potential phase then T_x; C = column pass:
+// T_y, optionally followed by a phase and reductions).  The kinetic
+// propagator F^-1 K F equals T_x T_y exactly (K is separable), so psi is in
+// real space between passes:
+//   real time, no cavity  R(V/2) C { R(V) C }^(n-2) R(V) C+V/2
+//       adjacent half phases V(t_k)/2 see the same density (a real phase
+//       keeps |psi|) and merge into one full phase; the last one is applied
+//       by the last column pass;
+//   real time, cavity     [reduce] { R(V) C+reduce }^n R(V/2): alpha needs the
+//       grid-wide overlaps of the current density, which the column pass
+//       reduces from its results;
+//   imaginary time        { R([c] V/2) C+V/2+norm }^n scale: the column pass
+//       applies the second half phase and reduces the norm (Sec. 3.3), the
+//       next row pass applies the scale; with a cavity the second half phase
+//       needs alpha of the post-kinetic density, so it runs in an extra row
+//       pass after a reducing column pass.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -179,9 +184,9 @@ RedArgs red_at(const gpe_ctx *c, double t)
     return r;
 }
 
-RowArgs row_args(const gpe_ctx *c)
+PassArgs pass_args(const gpe_ctx *c, const PhaseArgs &ph, const RedArgs &rd, int imag, int use_c)
 {
-    RowArgs a;
+    PassArgs a;
     memset(&a, 0, sizeof(a));
     a.psi = c->psi;
     a.nx = c->nx;
@@ -189,22 +194,13 @@ RowArgs row_args(const gpe_ctx *c)
     a.V = c->pot.V;
     a.V_scale = (float)c->pot.V_scale;
     a.g = (float)c->g;
-    a.T = c->T;
-    a.red = red_at(c, c->t);
-    return a;
-}
-
-ColArgs col_args(const gpe_ctx *c, int imag)
-{
-    ColArgs a;
-    a.psi = c->psi;
-    a.nx = c->nx;
-    a.ny = c->ny;
-    a.W = c->W;
-    a.G = col_group(c->ny, c->W);
     a.imag = imag;
-    a.scale = (float)(1.0 / ((double)c->nx * (double)c->ny));   // exact: a power of two
+    a.use_c = use_c;
+    a.sx = (float)(1.0 / c->nx);          // exact: powers of two
+    a.sy = (float)(1.0 / c->ny);
     a.spins = c->spins;
+    a.ph = ph;
+    a.red = rd;
     a.T = c->T;
     return a;
 }
@@ -242,17 +238,13 @@ template <class F> gpe_status timed_launch(gpe_ctx *c, int kind, F &&launch, con
 
 gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag, int use_c)
 {
-    RowArgs a = row_args(c);
-    a.ph = ph;
-    a.red = rd;
-    a.imag = imag;
-    a.use_c = use_c;
+    const PassArgs a = pass_args(c, ph, rd, imag, use_c);
     return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream); }, "row pass");
 }
 
-gpe_status run_col(gpe_ctx *c, int mode, int imag)
+gpe_status run_col(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag)
 {
-    const ColArgs a = col_args(c, imag);
+    const PassArgs a = pass_args(c, ph, rd, imag, 0);
     return timed_launch(c, 1, [&] { return launch_col(mode, a, c->map, c->stream); }, "column pass");
 }
 
@@ -397,39 +389,47 @@ gpe_status step_prologue(gpe_ctx *c, double dt, gpe_mode mode)
 }
 
 // The passes of step s (0 <= s < n) starting from the context's time c->t.
-gpe_status step_part(gpe_ctx *c, int s, double dt, gpe_mode mode)
+// Row pass: phase then T_x; column pass: T_y, in imaginary time also the
+// closing half phase with the norm of the result (the next row pass scales
+// by 1/sqrt(norm)), with a cavity the overlaps that set alpha for the next
+// phase, and in real time without cavity the closing half phase of the last
+// step.
+gpe_status step_part(gpe_ctx *c, int s, int n, double dt, gpe_mode mode)
 {
     const bool cav = c->pot.cavity != 0;
     const double ts = c->t + s * dt, te = c->t + (s + 1) * dt;
     PhaseArgs none;
     memset(&none, 0, sizeof(none));
     if (mode == GPE_REAL) {
-        if (s == 0) {
-            TRY(run_row(c, ROW_FWD, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0));
-        } else {
-            if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, ts), 0, 0));
-            TRY(run_row(c, ROW_MERGED, phase_at(c, ts, dt), red_at(c, ts), 0, 0));
-        }
-        TRY(run_col(c, COL_KIN, 0));
+        TRY(run_row(c, ROW_PT, phase_at(c, ts, s == 0 ? 0.5 * dt : dt), red_at(c, ts), 0, 0));
+        if (cav)
+            TRY(run_col(c, COL_T_R, none, red_at(c, te), 0));
+        else if (s == n - 1)
+            TRY(run_col(c, COL_T_PR, phase_at(c, te, 0.5 * dt), red_at(c, te), 0));
+        else
+            TRY(run_col(c, COL_T, none, red_at(c, te), 0));
     } else {
-        TRY(run_row(c, ROW_FWD, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 1, s > 0));
-        TRY(run_col(c, COL_KIN, 1));
-        if (cav) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, te), 1, 0));
-        TRY(run_row(c, ROW_INV, phase_at(c, te, 0.5 * dt), red_at(c, te), 1, 0));
+        TRY(run_row(c, ROW_PT, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 1, s > 0));
+        if (cav) {
+            TRY(run_col(c, COL_T_R, none, red_at(c, te), 1));
+            TRY(run_row(c, ROW_PHASE_R, phase_at(c, te, 0.5 * dt), red_at(c, te), 1, 0));
+        } else {
+            TRY(run_col(c, COL_T_PR, phase_at(c, te, 0.5 * dt), red_at(c, te), 1));
+        }
     }
     return GPE_OK;
 }
 
-// Passes after step n-1: the last half phase (real time) or the pending
-// normalisation (imaginary time); advances the context's time.
+// Passes after step n-1: with a cavity in real time the closing half phase
+// (it needs alpha of the final density); in imaginary time the pending
+// normalisation.  Advances the context's time.
 gpe_status step_epilogue(gpe_ctx *c, int n, double dt, gpe_mode mode)
 {
     const double tn = c->t + n * dt;
     PhaseArgs none;
     memset(&none, 0, sizeof(none));
     if (mode == GPE_REAL) {
-        if (c->pot.cavity) TRY(run_row(c, ROW_REDUCE_K, none, red_at(c, tn), 0, 0));
-        TRY(run_row(c, ROW_INV, phase_at(c, tn, 0.5 * dt), red_at(c, tn), 0, 0));
+        if (c->pot.cavity) TRY(run_row(c, ROW_PHASE, phase_at(c, tn, 0.5 * dt), red_at(c, tn), 0, 0));
     } else {
         TRY(run_row(c, ROW_SCALE, none, red_at(c, tn), 1, 0));
     }
@@ -446,7 +446,7 @@ gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
     TRY(step_check(c, n, dt, mode));
     if (n == 0) return GPE_OK;
     TRY(step_prologue(c, dt, mode));
-    for (int s = 0; s < n; ++s) TRY(step_part(c, s, dt, mode));
+    for (int s = 0; s < n; ++s) TRY(step_part(c, s, n, dt, mode));
     return step_epilogue(c, n, dt, mode);
 }
 
@@ -461,7 +461,7 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
     if (n == 0) return GPE_OK;
     for (int i = 0; i < count; ++i) TRY(step_prologue(ctxs[i], dt, mode));
     for (int s = 0; s < n; ++s)
-        for (int i = 0; i < count; ++i) TRY(step_part(ctxs[i], s, dt, mode));
+        for (int i = 0; i < count; ++i) TRY(step_part(ctxs[i], s, n, dt, mode));
     for (int i = 0; i < count; ++i) TRY(step_epilogue(ctxs[i], n, dt, mode));
     return GPE_OK;
 }
@@ -470,7 +470,7 @@ gpe_status gpe_observables(gpe_ctx *c, gpe_obs *out)
 {
     if (!c || !out) return GPE_EINVAL;
     TRY(run_row(c, ROW_OBS, phase_at(c, c->t, 0.0), red_at(c, c->t), 0, 0));
-    TRY(run_col(c, COL_OBS, 0));
+    TRY(run_col(c, COL_OBS, phase_at(c, c->t, 0.0), red_at(c, c->t), 0));
     DevScalars h;
     TRY(cuda_check(c, cudaMemcpyAsync(&h, c->T.sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy"));
     TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->status, 0, sizeof(int), c->stream), "memset"));
@@ -539,9 +539,9 @@ gpe_status gpe_fft2(gpe_ctx *c, int sign)
     memset(&none, 0, sizeof(none));
     if (sign == -1) {
         TRY(run_row(c, ROW_FFT_F, none, red_at(c, c->t), 0, 0));
-        TRY(run_col(c, COL_FFT_F, 0));
+        TRY(run_col(c, COL_FFT_F, none, red_at(c, c->t), 0));
     } else {
-        TRY(run_col(c, COL_FFT_I, 0));
+        TRY(run_col(c, COL_FFT_I, none, red_at(c, c->t), 0));
         TRY(run_row(c, ROW_FFT_I, none, red_at(c, c->t), 0, 0));
     }
     return GPE_OK;

@@ -50,55 +50,51 @@ struct RedArgs {
     int cavity;
 };
 
+// Row passes (x axis).  T_x = F_x^-1 K_x F_x is the x part of the kinetic
+// propagator; F^-1 K F = T_x T_y exactly because K = K_x K_y is separable.
 enum RowMode {
-    ROW_FWD = 0,        // real psi: [scale c] phase, FFT_x, store
-    ROW_MERGED = 1,     // k_x psi: iFFT_x, phase, FFT_x, store
-    ROW_INV = 2,        // k_x psi: iFFT_x, phase, reduce (norm, O, B -> c, alpha), store real
-    ROW_REDUCE_K = 3,   // k_x psi: iFFT_x, reduce (-> alpha), no store
-    ROW_REDUCE_R = 4,   // real psi: reduce (-> alpha), no store
-    ROW_SCALE = 5,      // real psi: multiply by c, store
-    ROW_FFT_F = 6,      // FFT_x only
-    ROW_FFT_I = 7,      // iFFT_x only (no normalisation)
-    ROW_OBS = 8         // real psi: observable sums + FFT_x kinetic sum, no store
+    ROW_PT = 0,         // [scale c] potential phase, T_x, store
+    ROW_PHASE = 1,      // potential phase, store
+    ROW_PHASE_R = 2,    // potential phase, reduce (norm, O, B -> c, alpha), store
+    ROW_REDUCE_R = 3,   // reduce (-> c, alpha), no store
+    ROW_SCALE = 4,      // multiply by c, store
+    ROW_FFT_F = 5,      // F_x only
+    ROW_FFT_I = 6,      // F_x^-1 (with 1/nx)
+    ROW_OBS = 7         // observable sums + F_x kinetic sum, no store
 };
 
+// Column passes (y axis), on TMA-loaded tiles of W columns.
 enum ColMode {
-    COL_KIN = 0,        // FFT_y, kinetic factor, iFFT_y, store
-    COL_FFT_F = 1,      // FFT_y, store
-    COL_FFT_I = 2,      // iFFT_y, scale, store
-    COL_OBS = 3         // FFT_y, sum ky^2 |.|^2, no store
+    COL_T = 0,          // T_y, store
+    COL_T_R = 1,        // T_y, reduce (-> c, alpha), store
+    COL_T_PR = 2,       // T_y, potential phase, reduce, store
+    COL_FFT_F = 3,      // F_y only
+    COL_FFT_I = 4,      // F_y^-1 (with 1/ny)
+    COL_OBS = 5         // F_y, sum ky^2 |.|^2, no store
 };
 
-struct RowArgs {
+struct PassArgs {
     float2 *psi;
     int nx, ny;
     const float *V;
     float V_scale, g;
     int imag, use_c;
+    float sx, sy;                  // exact 1/nx, 1/ny
+    int spins;                     // bound on the TMA barrier wait
     PhaseArgs ph;
     RedArgs red;
     Tables T;
 };
 
-struct ColArgs {
-    float2 *psi;
-    int nx, ny, W, G;              // tile width, columns transformed at once
-    int imag;
-    float scale;                   // exact power of two (1/(nx ny)) or 1
-    int spins;                     // bound on the TMA barrier wait
-    Tables T;
-};
-
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
-cudaError_t launch_row(int mode, const RowArgs &a, cudaStream_t s);
-cudaError_t launch_col(int mode, const ColArgs &a, const CUtensorMap &map, cudaStream_t s);
+cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
 cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m,
                           double wx, double wy, double lkx, double lky, double kc, cudaStream_t s);
 cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly,
                                   double m, double dt, int imag, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevScalars *sc, int spins, cudaStream_t s);
 int col_tile_width(int nx, int ny);
-int col_group(int ny, int W);
 int row_rows_per_cta(int nx, int ny);
 
 }  // namespace gpe

@@ -1,15 +1,15 @@
 // gpe_kernels.cu -- sm_103a kernels of the split-step GPE propagator.
 //
-// A step of Sec. 3.1 (Eqs. 3-4) is executed as passes over the grid psi[ny][nx]
-// held in HBM, each pass one kernel that reads and writes psi in place:
-//   row pass    (x axis, rows contiguous): [iFFT_x] potential phase [FFT_x]
-//               with |psi|^2 nonlinearity, V(x,y,t) and the cavity terms of
-//               Eqs. (10)-(13) computed in registers, and FP64 reductions of
-//               norm / cavity overlaps (Eqs. 14-15) fused in;
-//   column pass (y axis): TMA-loaded tile of W columns x ny rows in shared
-//               memory, FFT_y, kinetic factor exp(-i k^2 dt / 2m), iFFT_y.
-// Between passes psi lives in the mixed (k_x, y) representation; it is in
-// real space at the boundary of every public call.
+// A step of Sec. 3.1 (Eqs. 3-4), V/2 - T - V/2, is executed as passes over
+// psi[ny][nx] in HBM, each pass one kernel reading and writing psi in place.
+// The kinetic propagator F^-1 exp(-i (kx^2 + ky^2) dt / 2m) F factorises
+// exactly into T_x T_y with T_a = F_a^-1 exp(-i ka^2 dt / 2m) F_a along one
+// axis, so psi is in real space between passes:
+//   row pass    (x, rows contiguous): potential phase (V(x,y,t) + g|psi|^2 and
+//               the cavity terms of Eqs. 10-13, in registers), then T_x;
+//   column pass (y, TMA-loaded tiles of W columns): T_y, then optionally the
+//               closing half phase, with the norm and cavity overlaps
+//               (Eqs. 14-15) reduced in FP64 from the result.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -177,6 +177,91 @@ __device__ void finalize_fields(const double *S, const RedArgs &r, DevScalars *s
     }
 }
 
+// ------------------------------------------------------------------ pointwise pieces
+// Per-CTA potential coefficients.  V at a point is
+//   F + t.x + A t.y + (B t.z + C) t.z
+// where t is the coordinate-table entry {trap, cos^2(k_lat .), cos(kc .), .}
+// of the axis that varies along the pencil and F, A, B, C fold in the fixed
+// axis: row pencils vary x (A = lattice x depth, B = U0|alpha|^2, C = 2 eta
+// Re(alpha) cos(kc y)); column pencils vary y (A = lattice y depth, B = pump
+// depth eta^2/U0, C = 2 eta Re(alpha) cos(kc x)).  Eqs. (9)-(13).
+struct PotCoefs {
+    float F, A, B, C;
+};
+
+__device__ __forceinline__ void alpha_terms(const PassArgs &a, float &acx2, float &acxcy)
+{
+    acx2 = 0.f;
+    acxcy = 0.f;
+    if (a.ph.use_alpha) {
+        const double ar = a.T.sc->alpha_re, ai = a.T.sc->alpha_im;
+        acx2 = (float)((double)a.ph.U0 * (ar * ar + ai * ai));     // V_c amplitude, Eq. (12)
+        acxcy = (float)((double)a.ph.two_eta * ar);                 // V_i amplitude, Eq. (13)
+    }
+}
+
+// row pencil at fixed y (yt = ytab[y])
+__device__ __forceinline__ PotCoefs row_coefs(const PassArgs &a, float4 yt)
+{
+    float acx2, acxcy;
+    alpha_terms(a, acx2, acxcy);
+    return PotCoefs{yt.x + a.ph.a_laty * yt.y + a.ph.a_pump * yt.z * yt.z, a.ph.a_latx, acx2, acxcy * yt.z};
+}
+
+// column pencil at fixed x (xt = xtab[x])
+__device__ __forceinline__ PotCoefs col_coefs(const PassArgs &a, float4 xt)
+{
+    float acx2, acxcy;
+    alpha_terms(a, acx2, acxcy);
+    return PotCoefs{xt.x + a.ph.a_latx * xt.y + acx2 * xt.z * xt.z, a.ph.a_laty, a.ph.a_pump, acxcy * xt.z};
+}
+
+__device__ __forceinline__ float pot_at(const PotCoefs &p, float4 t)
+{
+    return p.F + t.x + p.A * t.y + (p.B * t.z + p.C) * t.z;
+}
+
+// psi <- exp(-i theta) psi (real time) or exp(-theta) psi (imaginary time),
+// theta = (V + g |psi|^2) h (Sec. 3.1, Sec. 3.3)
+__device__ __forceinline__ float2 phase_mul(float2 q, float V, float g, float h, int imag)
+{
+    const float n = q.x * q.x + q.y * q.y;
+    const float th = (V + g * n) * h;
+    if (imag) {
+        const float f = expf(-th);
+        return make_float2(q.x * f, q.y * f);
+    }
+    // e^{-i th} - 1 = -2 sin^2(th/2) - 2 i sin(th/2) cos(th/2): small phases keep
+    // their relative precision and |1 + d| = 1 up to unbiased rounding
+    float s, c;
+    sincosf(0.5f * th, &s, &c);
+    const float dr = -2.f * s * s, di = -2.f * s * c;
+    return make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
+}
+
+// one axis of the kinetic propagator in k-space: real time psi <- s (psi + psi D)
+// with D = exp(-i k^2 dt / 2m) - 1, imaginary time psi <- s K psi with
+// K = exp(-k^2 dtau / 2m); s = 1/n exact (the inverse FFT's normalisation)
+template <int E, int TP>
+__device__ __forceinline__ void kinetic_axis(float2 (&v)[E], const float2 *__restrict__ D, int j, float s, int imag)
+{
+    if (imag) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float f = __ldg(&D[j + r * TP]).x * s;
+            v[r] = make_float2(v[r].x * f, v[r].y * f);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 d = __ldg(&D[j + r * TP]);
+            const float2 p = v[r];
+            const float2 pd = cmul(p, d);
+            v[r] = make_float2((p.x + pd.x) * s, (p.y + pd.y) * s);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ row pass
 template <int N> struct RowCfg {
     static constexpr int E = N >= 16 ? 16 : N;
@@ -185,7 +270,7 @@ template <int N> struct RowCfg {
 };
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const RowArgs a)
+__global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassArgs a)
 {
     using C = RowCfg<N>;
     constexpr int E = C::E, TP = C::TP;
@@ -203,58 +288,35 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const RowArg
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = row[j + r * TP];
 
-    constexpr bool IN_K = (MODE == ROW_MERGED || MODE == ROW_INV || MODE == ROW_REDUCE_K || MODE == ROW_FFT_I);
-    if constexpr (IN_K) fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
-
-    if constexpr (MODE == ROW_FFT_F) fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
-
     if constexpr (MODE == ROW_SCALE) {
         const float c = (float)T.sc->c;
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * c, v[r].y * c);
     }
+    if constexpr (MODE == ROW_FFT_F) fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+    if constexpr (MODE == ROW_FFT_I) {
+        fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.sx, v[r].y * a.sx);
+    }
 
-    constexpr bool PHASE = (MODE == ROW_FWD || MODE == ROW_MERGED || MODE == ROW_INV);
-    const float4 yt = T.ytab[y];                    // {trap_y, cos^2(lat ky y), cos(kc y), y}
+    const float4 yt = T.ytab[y];
+    constexpr bool PHASE = (MODE == ROW_PT || MODE == ROW_PHASE || MODE == ROW_PHASE_R);
     if constexpr (PHASE) {
-        const PhaseArgs &p = a.ph;
+        const PotCoefs pc = row_coefs(a, yt);
         float cs = 1.f;
-        if (MODE == ROW_FWD && a.use_c) cs = (float)T.sc->c;
-        float acx2 = 0.f, acxcy = 0.f;
-        if (p.use_alpha) {
-            const double ar = T.sc->alpha_re, ai = T.sc->alpha_im;
-            acx2 = (float)((double)p.U0 * (ar * ar + ai * ai));     // V_c amplitude, Eq. (12)
-            acxcy = (float)((double)p.two_eta * ar);                 // V_i amplitude, Eq. (13)
-        }
-        const float vrow = yt.x + p.a_laty * yt.y + p.a_pump * yt.z * yt.z;
-        const float bcx = acxcy * yt.z;
+        if (MODE == ROW_PT && a.use_c) cs = (float)T.sc->c;
         const float *Vr = a.V ? a.V + (size_t)y * N : nullptr;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int xi = j + r * TP;
-            const float4 xt = __ldg(&T.xtab[xi]);
-            float V = vrow + xt.x + p.a_latx * xt.y + (acx2 * xt.z + bcx) * xt.z;
+            float V = pot_at(pc, __ldg(&T.xtab[xi]));
             if (Vr) V += a.V_scale * __ldg(&Vr[xi]);
-            float2 q = v[r];
-            if (MODE == ROW_FWD) q = make_float2(q.x * cs, q.y * cs);
-            const float n = q.x * q.x + q.y * q.y;
-            const float th = (V + a.g * n) * p.h;
-            if (a.imag) {
-                const float f = expf(-th);
-                q = make_float2(q.x * f, q.y * f);
-            } else {
-                // e^{-i th} - 1 = -2 sin^2(th/2) - 2 i sin(th/2) cos(th/2): small
-                // phases keep their relative precision
-                float s, c;
-                sincosf(0.5f * th, &s, &c);
-                const float dr = -2.f * s * s, di = -2.f * s * c;
-                q = make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
-            }
-            v[r] = q;
+            v[r] = phase_mul(make_float2(v[r].x * cs, v[r].y * cs), V, a.g, a.ph.h, a.imag);
         }
     }
 
-    constexpr bool REDUCE = (MODE == ROW_INV || MODE == ROW_REDUCE_K || MODE == ROW_REDUCE_R);
+    constexpr bool REDUCE = (MODE == ROW_PHASE_R || MODE == ROW_REDUCE_R);
     if constexpr (REDUCE) {
         float q[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -310,9 +372,13 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const RowArg
         return;
     }
 
-    if constexpr (MODE == ROW_FWD || MODE == ROW_MERGED) fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+    if constexpr (MODE == ROW_PT) {
+        fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+        kinetic_axis<E, TP>(v, T.kinx, j, a.sx, a.imag);
+        fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
+    }
 
-    constexpr bool STORE = !(MODE == ROW_REDUCE_K || MODE == ROW_REDUCE_R || MODE == ROW_OBS);
+    constexpr bool STORE = !(MODE == ROW_REDUCE_R || MODE == ROW_OBS);
     if constexpr (STORE) {
 #pragma unroll
         for (int r = 0; r < E; ++r) row[j + r * TP] = v[r];
@@ -327,24 +393,18 @@ template <int N> struct ColCfg {
     static constexpr int PS = N + N / 16;          // padded pencil stride (float2)
 };
 
-// Tile width for columns of length N: W columns x N rows = 4096 elements
-// (32 KB) when possible, at least 2 columns (a 16-byte TMA box row).
-__host__ __device__ constexpr int col_w_default(int n)
-{
-    return 4096 / n < 2 ? 2 : (4096 / n > 64 ? 64 : 4096 / n);
-}
-// Columns transformed at once: 256 threads (512 for N >= 4096); the 8192-row
-// tile does its second column in a second round.
-__host__ __device__ constexpr int col_g(int n, int w)
+// Tile width for columns of length N: 4096 elements when N >= 512, 8 columns
+// below (a grid is at least 8 wide, so the width is a function of N only);
+// at least 2 columns (a 16-byte TMA box row).
+__host__ __device__ constexpr int col_w(int n) { return 4096 / n < 2 ? 2 : (4096 / n > 8 ? 8 : 4096 / n); }
+// Columns transformed at once: up to 256 threads (512 for N >= 4096); the
+// 8192-row tile does its second column in a second round.
+__host__ __device__ constexpr int col_g(int n)
 {
     const int tp = n >= 16 ? n / 16 : 1;
     const int t = n >= 4096 ? 512 : 256;
     const int g = t / tp < 1 ? 1 : t / tp;
-    return g > w ? w : g;
-}
-__host__ __device__ constexpr bool col_w_valid(int n, int w)
-{
-    return w == col_w_default(n) || (w >= 8 && w < col_w_default(n));
+    return g > col_w(n) ? col_w(n) : g;
 }
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
@@ -357,14 +417,14 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void 
 
 // Column pass over a tile of W columns: TMA load of the dense [N][W] tile,
 // per-column FFT through padded per-column exchange buffers, the kinetic
-// factor, inverse FFT, results written back into the dense tile and stored
-// with TMA.
-template <int N, int W, int MODE>
-__global__ void __launch_bounds__(col_g(N, W) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
-    col_kernel(const ColArgs a, const __grid_constant__ CUtensorMap map)
+// factor, inverse FFT, optional closing phase and reductions, results written
+// back into the dense tile and stored with TMA.
+template <int N, int MODE>
+__global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
+    col_kernel(const PassArgs a, const __grid_constant__ CUtensorMap map)
 {
     using C = ColCfg<N>;
-    constexpr int E = C::E, TP = C::TP, G = col_g(N, W);
+    constexpr int E = C::E, TP = C::TP, W = col_w(N), G = col_g(N);
     constexpr bool INPLACE = (G == W);   // exchange buffers may overlay the dense tile
     extern __shared__ unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -390,9 +450,10 @@ __global__ void __launch_bounds__(col_g(N, W) * ColCfg<N>::TP, N >= 4096 ? 1 : 3
         return;
     }
 
+    constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
     const int j = threadIdx.x % TP, cg = threadIdx.x / TP;
     float2 *sb = pen + cg * C::PS;
-    float q[1] = {0.f};
+    float q[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
     for (int g0 = 0; g0 < W; g0 += G) {
         const int c = g0 + cg;
@@ -404,33 +465,40 @@ __global__ void __launch_bounds__(col_g(N, W) * ColCfg<N>::TP, N >= 4096 ? 1 : 3
         if constexpr (MODE == COL_FFT_I) {
             fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
 #pragma unroll
-            for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.scale, v[r].y * a.scale);
+            for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.sy, v[r].y * a.sy);
         } else {
             fft_pencil<N, E, false>(v, sb, j, 1, T.twy);
         }
 
-        if constexpr (MODE == COL_KIN) {
-            const float2 dx = __ldg(&T.kinx[c0 + c]);
-            if (a.imag) {
-                // exp(-k^2 dtau / 2m) = Kx Ky, 1/(nx ny) folded into the exact scale
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
-                    const float f = dx.x * __ldg(&T.kiny[j + r * TP]).x * a.scale;
-                    v[r] = make_float2(v[r].x * f, v[r].y * f);
-                }
-            } else {
-                // K - 1 = Dx + Dy + Dx Dy with D = exp(-i k^2 dt / 2m) - 1 per axis;
-                // psi <- s (psi + psi (K - 1)), s = 1/(nx ny) exact
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
-                    const float2 dy = __ldg(&T.kiny[j + r * TP]);
-                    const float2 d = cadd(cadd(dx, dy), cmul(dx, dy));
-                    const float2 p = v[r];
-                    const float2 pd = cmul(p, d);
-                    v[r] = make_float2((p.x + pd.x) * a.scale, (p.y + pd.y) * a.scale);
-                }
-            }
+        if constexpr (MODE == COL_T || MODE == COL_T_R || MODE == COL_T_PR) {
+            kinetic_axis<E, TP>(v, T.kiny, j, a.sy, a.imag);
             fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
+        }
+
+        if constexpr (MODE == COL_T_PR) {
+            const float4 xt = __ldg(&T.xtab[c0 + c]);
+            const PotCoefs pc = col_coefs(a, xt);
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int yi = j + r * TP;
+                float V = pot_at(pc, __ldg(&T.ytab[yi]));
+                if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
+                v[r] = phase_mul(v[r], V, a.g, a.ph.h, a.imag);
+            }
+        }
+
+        if constexpr (REDUCE) {
+            const float cx = __ldg(&T.xtab[c0 + c]).z;
+            float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+                n0 += n;
+                n1 += __ldg(&T.ytab[j + r * TP]).z * n;
+            }
+            q[0] += n0;
+            q[1] += cx * n1;
+            q[2] += cx * cx * n0;
         }
 
         if constexpr (MODE == COL_OBS) {
@@ -449,20 +517,28 @@ __global__ void __launch_bounds__(col_g(N, W) * ColCfg<N>::TP, N >= 4096 ? 1 : 3
     }
 
     if constexpr (MODE == COL_OBS) {
-        block_sum<1>(q, T.part_col + (size_t)blockIdx.x * NQ, red);
+        float q1[1] = {q[0]};
+        block_sum<1>(q1, T.part_col + (size_t)blockIdx.x * NQ, red);
         double S[1];
         if (last_block_total<1>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
             T.sc->sums[1][0] = S[0];
-    } else {
-        // make the generic-proxy tile writes visible to the TMA engine, then store
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, tile + (size_t)r0 * W, 2 * c0, r0);
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // tile read before exit
-        }
+        return;
     }
+
+    // make the generic-proxy tile writes visible to the TMA engine, then store
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, tile + (size_t)r0 * W, 2 * c0, r0);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    if constexpr (REDUCE) {
+        block_sum<3>(q, T.part_col + (size_t)blockIdx.x * NQ, red);
+        double S[3];
+        if (last_block_total<3>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
+            finalize_fields(S, a.red, T.sc);
+    }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // tile read before exit
 }
 
 // ------------------------------------------------------------------ tables
@@ -541,13 +617,11 @@ int row_rows_per_cta(int nx, int ny)
 
 int col_tile_width(int nx, int ny)
 {
-    const int w = col_w_default(ny);
-    return w > nx ? nx : w;
+    (void)nx;
+    return col_w(ny);
 }
 
-int col_group(int ny, int W) { return col_g(ny, W); }
-
-template <int N, int MODE> static cudaError_t row_launch(const RowArgs &a, cudaStream_t s)
+template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
 {
     using C = RowCfg<N>;
     const int rpc = row_rows_per_cta(N, a.ny);
@@ -568,13 +642,12 @@ template <int N, int MODE> static cudaError_t row_launch(const RowArgs &a, cudaS
     return cudaGetLastError();
 }
 
-template <int N> static cudaError_t row_dispatch_mode(int mode, const RowArgs &a, cudaStream_t s)
+template <int N> static cudaError_t row_dispatch_mode(int mode, const PassArgs &a, cudaStream_t s)
 {
     switch (mode) {
-    case ROW_FWD: return row_launch<N, ROW_FWD>(a, s);
-    case ROW_MERGED: return row_launch<N, ROW_MERGED>(a, s);
-    case ROW_INV: return row_launch<N, ROW_INV>(a, s);
-    case ROW_REDUCE_K: return row_launch<N, ROW_REDUCE_K>(a, s);
+    case ROW_PT: return row_launch<N, ROW_PT>(a, s);
+    case ROW_PHASE: return row_launch<N, ROW_PHASE>(a, s);
+    case ROW_PHASE_R: return row_launch<N, ROW_PHASE_R>(a, s);
     case ROW_REDUCE_R: return row_launch<N, ROW_REDUCE_R>(a, s);
     case ROW_SCALE: return row_launch<N, ROW_SCALE>(a, s);
     case ROW_FFT_F: return row_launch<N, ROW_FFT_F>(a, s);
@@ -584,7 +657,7 @@ template <int N> static cudaError_t row_dispatch_mode(int mode, const RowArgs &a
     }
 }
 
-cudaError_t launch_row(int mode, const RowArgs &a, cudaStream_t s)
+cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s)
 {
     switch (a.nx) {
     case 8: return row_dispatch_mode<8>(mode, a, s);
@@ -602,69 +675,53 @@ cudaError_t launch_row(int mode, const RowArgs &a, cudaStream_t s)
     }
 }
 
-template <int N, int W, int MODE>
-static cudaError_t col_launch(const ColArgs &a, const CUtensorMap &map, cudaStream_t s)
+template <int N, int MODE>
+static cudaError_t col_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     using C = ColCfg<N>;
-    constexpr int G = col_g(N, W);
+    constexpr int W = col_w(N), G = col_g(N);
     constexpr size_t smem = (G == W ? (size_t)W * C::PS : (size_t)N * W + (size_t)G * C::PS) * sizeof(float2) + 128;
     static bool attr = false;
     if (!attr) {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(col_kernel<N, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(col_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
         attr = true;
     }
-    col_kernel<N, W, MODE><<<a.nx / W, G * C::TP, smem, s>>>(a, map);
+    col_kernel<N, MODE><<<a.nx / W, G * C::TP, smem, s>>>(a, map);
     return cudaGetLastError();
 }
 
-template <int N, int W> static cudaError_t col_dispatch_mode(int mode, const ColArgs &a, const CUtensorMap &map,
-                                                             cudaStream_t s)
+template <int N> static cudaError_t col_dispatch_mode(int mode, const PassArgs &a, const CUtensorMap &map,
+                                                      cudaStream_t s)
 {
-    if constexpr (!col_w_valid(N, W)) {
-        return cudaErrorInvalidValue;
-    } else {
-        switch (mode) {
-        case COL_KIN: return col_launch<N, W, COL_KIN>(a, map, s);
-        case COL_FFT_F: return col_launch<N, W, COL_FFT_F>(a, map, s);
-        case COL_FFT_I: return col_launch<N, W, COL_FFT_I>(a, map, s);
-        case COL_OBS: return col_launch<N, W, COL_OBS>(a, map, s);
-        default: return cudaErrorInvalidValue;
-        }
-    }
-}
-
-template <int N> static cudaError_t col_dispatch_w(int mode, const ColArgs &a, const CUtensorMap &map,
-                                                   cudaStream_t s)
-{
-    switch (a.W) {
-    case 2: return col_dispatch_mode<N, 2>(mode, a, map, s);
-    case 4: return col_dispatch_mode<N, 4>(mode, a, map, s);
-    case 8: return col_dispatch_mode<N, 8>(mode, a, map, s);
-    case 16: return col_dispatch_mode<N, 16>(mode, a, map, s);
-    case 32: return col_dispatch_mode<N, 32>(mode, a, map, s);
-    case 64: return col_dispatch_mode<N, 64>(mode, a, map, s);
+    switch (mode) {
+    case COL_T: return col_launch<N, COL_T>(a, map, s);
+    case COL_T_R: return col_launch<N, COL_T_R>(a, map, s);
+    case COL_T_PR: return col_launch<N, COL_T_PR>(a, map, s);
+    case COL_FFT_F: return col_launch<N, COL_FFT_F>(a, map, s);
+    case COL_FFT_I: return col_launch<N, COL_FFT_I>(a, map, s);
+    case COL_OBS: return col_launch<N, COL_OBS>(a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_col(int mode, const ColArgs &a, const CUtensorMap &map, cudaStream_t s)
+cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     switch (a.ny) {
-    case 8: return col_dispatch_w<8>(mode, a, map, s);
-    case 16: return col_dispatch_w<16>(mode, a, map, s);
-    case 32: return col_dispatch_w<32>(mode, a, map, s);
-    case 64: return col_dispatch_w<64>(mode, a, map, s);
-    case 128: return col_dispatch_w<128>(mode, a, map, s);
-    case 256: return col_dispatch_w<256>(mode, a, map, s);
-    case 512: return col_dispatch_w<512>(mode, a, map, s);
-    case 1024: return col_dispatch_w<1024>(mode, a, map, s);
-    case 2048: return col_dispatch_w<2048>(mode, a, map, s);
-    case 4096: return col_dispatch_w<4096>(mode, a, map, s);
-    case 8192: return col_dispatch_w<8192>(mode, a, map, s);
+    case 8: return col_dispatch_mode<8>(mode, a, map, s);
+    case 16: return col_dispatch_mode<16>(mode, a, map, s);
+    case 32: return col_dispatch_mode<32>(mode, a, map, s);
+    case 64: return col_dispatch_mode<64>(mode, a, map, s);
+    case 128: return col_dispatch_mode<128>(mode, a, map, s);
+    case 256: return col_dispatch_mode<256>(mode, a, map, s);
+    case 512: return col_dispatch_mode<512>(mode, a, map, s);
+    case 1024: return col_dispatch_mode<1024>(mode, a, map, s);
+    case 2048: return col_dispatch_mode<2048>(mode, a, map, s);
+    case 4096: return col_dispatch_mode<4096>(mode, a, map, s);
+    case 8192: return col_dispatch_mode<8192>(mode, a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -89,7 +89,7 @@ extern "C" gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, d
     if (cudaMemsetAsync(T.sc, 0, sizeof(DevScalars), s) != cudaSuccess) return GPE_ECUDA;
     if (launch_tables(T, nx, ny, Lx, Ly, 1.0, 0.0, 0.0, 0.0, 0.0, kc, s) != cudaSuccess) return GPE_ECUDA;
 
-    RowArgs a;
+    PassArgs a;
     memset(&a, 0, sizeof(a));
     a.psi = const_cast<float2 *>(static_cast<const float2 *>(psi_dev));   // read only in this mode
     a.nx = nx;
