@@ -92,19 +92,41 @@ template <int J, bool INV> __device__ __forceinline__ float2 tw16(float2 a)
     }
 }
 
+// packed two-lane float add / subtract (one f32x2 instruction for a complex add)
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 template <bool INV> __device__ __forceinline__ void dft2(float2 &a0, float2 &a1)
 {
     const float2 t = a0;
-    a0 = cadd(t, a1);
-    a1 = csub(t, a1);
+    a0 = add2(t, a1);
+    a1 = sub2(t, a1);
 }
 
 template <bool INV> __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
 {
-    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
-    const float2 t3 = mul_mi<INV>(csub(a1, a3));
-    a0 = cadd(t0, t2);
-    a2 = csub(t0, t2);
+    const float2 t0 = add2(a0, a2), t1 = sub2(a0, a2), t2 = add2(a1, a3);
+    const float2 t3 = mul_mi<INV>(sub2(a1, a3));
+    a0 = add2(t0, t2);
+    a2 = sub2(t0, t2);
     a1 = cadd(t1, t3);
     a3 = csub(t1, t3);
 }
@@ -121,8 +143,8 @@ template <bool INV> __device__ __forceinline__ void dft8(float2 (&a)[8])
     const float2 y1[4] = {a[1], a[3], a[5], a[7]};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        a[k] = cadd(y0[k], y1[k]);
-        a[k + 4] = csub(y0[k], y1[k]);
+        a[k] = add2(y0[k], y1[k]);
+        a[k + 4] = sub2(y0[k], y1[k]);
     }
 }
 

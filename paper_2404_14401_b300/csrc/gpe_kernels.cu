@@ -222,7 +222,12 @@ __device__ __forceinline__ float pot_at(const PotCoefs &p, float4 t)
 }
 
 // psi <- exp(-i theta) psi (real time) or exp(-theta) psi (imaginary time),
-// theta = (V + g |psi|^2) h (Sec. 3.1, Sec. 3.3)
+// theta = (V + g |psi|^2) h (Sec. 3.1, Sec. 3.3).  Real time multiplies by
+// 1 + d with d = exp(-i theta) - 1 = -2 sin^2(theta/2) - 2 i sin(theta/2)
+// cos(theta/2): small phases keep their relative precision and |1 + d| = 1
+// up to unbiased rounding.  For |theta| <= 1, sin and cos of w = theta/2 come
+// from their Taylor series in w^2 (remainders w^11/11! and w^10/10! below
+// 3e-10); larger phases use sincosf.
 __device__ __forceinline__ float2 phase_mul(float2 q, float V, float g, float h, int imag)
 {
     const float n = q.x * q.x + q.y * q.y;
@@ -231,10 +236,21 @@ __device__ __forceinline__ float2 phase_mul(float2 q, float V, float g, float h,
         const float f = expf(-th);
         return make_float2(q.x * f, q.y * f);
     }
-    // e^{-i th} - 1 = -2 sin^2(th/2) - 2 i sin(th/2) cos(th/2): small phases keep
-    // their relative precision and |1 + d| = 1 up to unbiased rounding
+    const float w = 0.5f * th;
     float s, c;
-    sincosf(0.5f * th, &s, &c);
+    if (fabsf(th) <= 1.f) {
+        const float v = w * w;
+        float ps = fmaf(v, 1.f / 362880.f, -1.f / 5040.f);     // sin w = w (1 - v/3! + v^2/5! - ...)
+        ps = fmaf(v, ps, 1.f / 120.f);
+        ps = fmaf(v, ps, -1.f / 6.f);
+        s = fmaf(w * v, ps, w);
+        float pc = fmaf(v, 1.f / 40320.f, -1.f / 720.f);       // cos w = 1 - v/2! + v^2/4! - ...
+        pc = fmaf(v, pc, 1.f / 24.f);
+        pc = fmaf(v, pc, -0.5f);
+        c = fmaf(v, pc, 1.f);
+    } else {
+        sincosf(w, &s, &c);
+    }
     const float dr = -2.f * s * s, di = -2.f * s * c;
     return make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
 }
