@@ -11,8 +11,9 @@
 // each thread doing E/R butterflies per stage; between stages the pencil is
 // exchanged through shared memory in a layout padded by one slot per 16
 // elements, which keeps 64-bit accesses of every stage free of bank
-// conflicts.  Twiddles exp(-2 pi i m/N) come from a table computed in double
-// precision and stored as two-float (hi + lo) pairs.
+// conflicts.  Twiddles come from a per-stage table (consecutive lanes read
+// consecutive entries) computed in double precision and stored as two-float
+// (hi + lo) pairs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -184,13 +185,30 @@ template <int R, bool INV> __device__ __forceinline__ void dft(float2 (&a)[R])
 // padded shared-memory slot of pencil element e: one spare slot per 16
 __device__ __forceinline__ int padx(int e) { return e + (e >> 4); }
 
+// Radix schedule of an N-point transform: stage 0 has radix 2^(n mod 4) (16
+// when n is a multiple of 4), the others 16; NS = points combined before a stage.
+__host__ __device__ constexpr int fft_stages(int n) { return (ilog2(n) + 3) / 4; }
+__host__ __device__ constexpr int fft_radix(int n, int s)
+{
+    return s == 0 ? (1 << (ilog2(n) - 4 * (fft_stages(n) - 1))) : 16;
+}
+__host__ __device__ constexpr int fft_ns(int n, int s) { return s == 0 ? 1 : fft_ns(n, s - 1) * fft_radix(n, s - 1); }
+// Twiddle table layout: stage s >= 1 owns (R - 1) NS consecutive entries,
+// entry (r - 1) NS + k = W_{NS R}^{r k}, so the lanes of a warp (consecutive k)
+// read consecutive entries.  Offset of stage s; the total is below n.
+__host__ __device__ constexpr int fft_tw_offset(int n, int s)
+{
+    return s <= 1 ? 0 : fft_tw_offset(n, s - 1) + (fft_radix(n, s - 1) - 1) * fft_ns(n, s - 1);
+}
+
 // One Stockham stage of radix R after NS points have been combined.
 // Butterfly jp takes x[jp + r N/R], multiplies input r by W_{NS R}^{r (jp mod NS)}
 // and writes output p to y[(jp / NS) NS R + jp mod NS + p NS].
-// sb: this pencil's shared buffer, es: element stride in float2 units.
+// sb: this pencil's shared buffer, es: element stride in float2 units,
+// tws: this stage's twiddle block.
 template <int N, int E, int R, int NS, bool INV, bool LAST>
 __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
-                                          const float4 *__restrict__ tw)
+                                          const float4 *__restrict__ tws)
 {
     constexpr int TP = N / E, B = E / R;
 #pragma unroll
@@ -203,7 +221,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ s
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float4 w = __ldg(&tw[r * k * (N / (NS * R))]);
+                float4 w = __ldg(&tws[(r - 1) * NS + k]);
                 if constexpr (INV) {
                     w.y = -w.y;
                     w.w = -w.w;
@@ -232,16 +250,16 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ s
 // Full transform of one pencil: natural order in v (element j + r TP) in and
 // out.  Forward: X_k = sum_n x_n e^{-2 pi i nk/N}; INV: the conjugate sum,
 // without the 1/N factor.  Every thread of the CTA must call it together.
-template <int N, int E, bool INV, int S = 0, int NS = 1>
+// tw: the per-stage twiddle table of this axis (fft_tw_offset layout).
+template <int N, int E, bool INV, int S = 0>
 __device__ __forceinline__ void fft_pencil(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
                                            const float4 *__restrict__ tw)
 {
-    constexpr int LOG = ilog2(N), NST = (LOG + 3) / 4;
-    constexpr int R = (S == 0) ? (1 << (LOG - 4 * (NST - 1))) : 16;
-    constexpr bool LAST = (S == NST - 1);
+    constexpr int R = fft_radix(N, S), NS = fft_ns(N, S);
+    constexpr bool LAST = (S == fft_stages(N) - 1);
     static_assert(E % R == 0, "radix must divide the elements per thread");
-    fft_stage<N, E, R, NS, INV, LAST>(v, sb, j, es, tw);
-    if constexpr (!LAST) fft_pencil<N, E, INV, S + 1, NS * R>(v, sb, j, es, tw);
+    fft_stage<N, E, R, NS, INV, LAST>(v, sb, j, es, tw + fft_tw_offset(N, S));
+    if constexpr (!LAST) fft_pencil<N, E, INV, S + 1>(v, sb, j, es, tw);
 }
 
 }  // namespace gpe

@@ -558,11 +558,22 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
 }
 
 // ------------------------------------------------------------------ tables
-// exp(-2 pi i m / n) as {re_hi, im_hi, re_lo, im_lo}: hi = float(x), lo = float(x - hi)
-__device__ float4 twiddle_pair(int m, int n)
+// Entry i of the per-stage twiddle table of an n-point axis (fft_tw_offset
+// layout): W_{NS R}^{r k} = exp(-2 pi i r k / (NS R)) as {re_hi, im_hi, re_lo,
+// im_lo}, hi = float(x), lo = float(x - hi).  Entries past the table are 1.
+__device__ float4 twiddle_entry(int i, int n)
 {
+    long long num = 0, den = 1;
+    for (int s = 1; s < fft_stages(n); ++s) {
+        const int ns = fft_ns(n, s), R = fft_radix(n, s), off = fft_tw_offset(n, s);
+        if (i >= off && i < off + (R - 1) * ns) {
+            const int r = (i - off) / ns + 1, k = (i - off) % ns;
+            num = (long long)r * k;
+            den = (long long)ns * R;
+        }
+    }
     double s, c;
-    sincospi(2.0 * m / n, &s, &c);
+    sincospi(2.0 * (double)(num % den) / (double)den, &s, &c);
     const float ch = (float)c, sh = (float)-s;
     return make_float4(ch, sh, (float)(c - (double)ch), (float)(-s - (double)sh));
 }
@@ -576,13 +587,13 @@ __global__ void tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, do
         const double x = -0.5 * Lx + (double)i * (Lx / nx);
         const double cl = cos(lkx * x), cc = cos(kc * x);
         T.xtab[i] = make_float4((float)(0.5 * m * wx * wx * x * x), (float)(cl * cl), (float)cc, (float)x);
-        T.twx[i] = twiddle_pair(i, nx);
+        T.twx[i] = twiddle_entry(i, nx);
     }
     if (i < ny) {
         const double y = -0.5 * Ly + (double)i * (Ly / ny);
         const double cl = cos(lky * y), cc = cos(kc * y);
         T.ytab[i] = make_float4((float)(0.5 * m * wy * wy * y * y), (float)(cl * cl), (float)cc, (float)y);
-        T.twy[i] = twiddle_pair(i, ny);
+        T.twy[i] = twiddle_entry(i, ny);
     }
 }
 
