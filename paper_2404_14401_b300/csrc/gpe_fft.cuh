@@ -200,12 +200,14 @@ __host__ __device__ constexpr int fft_tw_offset(int n, int s)
 {
     return s <= 1 ? 0 : fft_tw_offset(n, s - 1) + (fft_radix(n, s - 1) - 1) * fft_ns(n, s - 1);
 }
+// entries of the whole table
+__host__ __device__ constexpr int fft_tw_count(int n) { return fft_tw_offset(n, fft_stages(n)); }
 
 // One Stockham stage of radix R after NS points have been combined.
 // Butterfly jp takes x[jp + r N/R], multiplies input r by W_{NS R}^{r (jp mod NS)}
 // and writes output p to y[(jp / NS) NS R + jp mod NS + p NS].
 // sb: this pencil's shared buffer, es: element stride in float2 units,
-// tws: this stage's twiddle block.
+// tws: this stage's twiddle block (shared or read-only global memory).
 template <int N, int E, int R, int NS, bool INV, bool LAST>
 __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
                                           const float4 *__restrict__ tws)
@@ -221,7 +223,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ s
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float4 w = __ldg(&tws[(r - 1) * NS + k]);
+                float4 w = tws[(r - 1) * NS + k];
                 if constexpr (INV) {
                     w.y = -w.y;
                     w.w = -w.w;

@@ -278,11 +278,21 @@ __device__ __forceinline__ void kinetic_axis(float2 (&v)[E], const float2 *__res
     }
 }
 
+// Copy an axis' twiddle table into shared memory (every thread of the CTA;
+// visible to the first twiddled stage through the barrier of the stage-0
+// exchange that precedes it).
+template <int N>
+__device__ __forceinline__ void stage_twiddles(float4 *__restrict__ dst, const float4 *__restrict__ src)
+{
+    for (int i = threadIdx.x; i < fft_tw_count(N); i += blockDim.x) dst[i] = __ldg(&src[i]);
+}
+
 // ------------------------------------------------------------------ row pass
 template <int N> struct RowCfg {
     static constexpr int E = N >= 16 ? 16 : N;
     static constexpr int TP = N / E;
     static constexpr int PS = N + N / 16;          // padded pencil stride (float2)
+    static constexpr int TWN = fft_tw_count(N);    // twiddle entries staged in shared memory
 };
 
 template <int N, int MODE>
@@ -290,8 +300,10 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 {
     using C = RowCfg<N>;
     constexpr int E = C::E, TP = C::TP;
-    extern __shared__ float2 smem[];
+    extern __shared__ float4 smem4[];
     __shared__ double red[32 * NQ];
+    float4 *stw = smem4;                                     // twiddles (C::TWN entries)
+    float2 *smem = reinterpret_cast<float2 *>(smem4 + C::TWN);
 
     const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
     const int rpc = blockDim.x / TP;
@@ -299,6 +311,8 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     float2 *row = a.psi + (size_t)y * N;
     float2 *sb = smem + lr * C::PS;
     const Tables &T = a.T;
+    constexpr bool FFT = (MODE == ROW_PT || MODE == ROW_FFT_F || MODE == ROW_FFT_I || MODE == ROW_OBS);
+    if constexpr (FFT) stage_twiddles<N>(stw, T.twx);
 
     float2 v[E];
 #pragma unroll
@@ -309,9 +323,9 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * c, v[r].y * c);
     }
-    if constexpr (MODE == ROW_FFT_F) fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+    if constexpr (MODE == ROW_FFT_F) fft_pencil<N, E, false>(v, sb, j, 1, stw);
     if constexpr (MODE == ROW_FFT_I) {
-        fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
+        fft_pencil<N, E, true>(v, sb, j, 1, stw);
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.sx, v[r].y * a.sx);
     }
@@ -373,7 +387,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
         }
         q[3] *= yt.z;
         q[5] = yt.z * yt.z * q[0];
-        fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+        fft_pencil<N, E, false>(v, sb, j, 1, stw);
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int e = j + r * TP;
@@ -389,9 +403,9 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     }
 
     if constexpr (MODE == ROW_PT) {
-        fft_pencil<N, E, false>(v, sb, j, 1, T.twx);
+        fft_pencil<N, E, false>(v, sb, j, 1, stw);
         kinetic_axis<E, TP>(v, T.kinx, j, a.sx, a.imag);
-        fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
+        fft_pencil<N, E, true>(v, sb, j, 1, stw);
     }
 
     constexpr bool STORE = !(MODE == ROW_REDUCE_R || MODE == ROW_OBS);
@@ -407,6 +421,8 @@ template <int N> struct ColCfg {
     static constexpr int TP = N / E;
     static constexpr int BR = N < 256 ? N : 256;    // rows per TMA box
     static constexpr int PS = N + N / 16;          // padded pencil stride (float2)
+    // twiddles staged in shared memory except for 8192 rows (no room left)
+    static constexpr int TWN = N >= 8192 ? 0 : fft_tw_count(N);
 };
 
 // Tile width for columns of length N: 4096 elements when N >= 512, 8 columns
@@ -449,9 +465,12 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     const uint32_t s0 = smem_u32(smraw);
     float2 *tile = reinterpret_cast<float2 *>(smraw + ((128u - (s0 & 127u)) & 127u));
     float2 *pen = INPLACE ? tile : tile + N * W;
+    float4 *stw = reinterpret_cast<float4 *>(tile + (INPLACE ? W * C::PS : N * W + G * C::PS));
 
     const int c0 = blockIdx.x * W;
     const Tables &T = a.T;
+    const float4 *tw = C::TWN ? stw : T.twy;
+    if constexpr (C::TWN > 0) stage_twiddles<N>(stw, T.twy);
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
@@ -479,16 +498,16 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
         if constexpr (INPLACE) __syncthreads();      // dense reads done before exchange writes
 
         if constexpr (MODE == COL_FFT_I) {
-            fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
+            fft_pencil<N, E, true>(v, sb, j, 1, tw);
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = make_float2(v[r].x * a.sy, v[r].y * a.sy);
         } else {
-            fft_pencil<N, E, false>(v, sb, j, 1, T.twy);
+            fft_pencil<N, E, false>(v, sb, j, 1, tw);
         }
 
         if constexpr (MODE == COL_T || MODE == COL_T_R || MODE == COL_T_PR) {
             kinetic_axis<E, TP>(v, T.kiny, j, a.sy, a.imag);
-            fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
+            fft_pencil<N, E, true>(v, sb, j, 1, tw);
         }
 
         if constexpr (MODE == COL_T_PR) {
@@ -653,11 +672,11 @@ template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cuda
     using C = RowCfg<N>;
     const int rpc = row_rows_per_cta(N, a.ny);
     const int threads = rpc * C::TP;
-    const size_t smem = (size_t)rpc * C::PS * sizeof(float2);
+    const size_t smem = (size_t)rpc * C::PS * sizeof(float2) + (size_t)C::TWN * sizeof(float4);
     static bool attr = false;
     if (!attr) {
         const int rpc_max = 256 / C::TP > 1 ? 256 / C::TP : 1;
-        const int smem_max = rpc_max * C::PS * (int)sizeof(float2);
+        const int smem_max = rpc_max * C::PS * (int)sizeof(float2) + C::TWN * (int)sizeof(float4);
         if (smem_max > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(row_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  smem_max);
@@ -707,7 +726,8 @@ static cudaError_t col_launch(const PassArgs &a, const CUtensorMap &map, cudaStr
 {
     using C = ColCfg<N>;
     constexpr int W = col_w(N), G = col_g(N);
-    constexpr size_t smem = (G == W ? (size_t)W * C::PS : (size_t)N * W + (size_t)G * C::PS) * sizeof(float2) + 128;
+    constexpr size_t smem = (G == W ? (size_t)W * C::PS : (size_t)N * W + (size_t)G * C::PS) * sizeof(float2) +
+                            (size_t)C::TWN * sizeof(float4) + 128;
     static bool attr = false;
     if (!attr) {
         if (smem > 48 * 1024) {
