@@ -52,6 +52,7 @@ struct gpe_ctx {
     int kin_mode;
     bool kin_valid;
     int spins;
+    int stream_passes;       // use the persistent streaming passes where they apply
     long long launches;
     // per-pass event timing (gpe_profile)
     bool prof;
@@ -239,12 +240,16 @@ template <class F> gpe_status timed_launch(gpe_ctx *c, int kind, F &&launch, con
 gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag, int use_c)
 {
     const PassArgs a = pass_args(c, ph, rd, imag, use_c);
+    if (mode == ROW_PT && c->stream_passes && row_stream_ok(c->nx, c->ny))
+        return timed_launch(c, 0, [&] { return launch_row_stream(a, c->stream); }, "row pass");
     return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream); }, "row pass");
 }
 
 gpe_status run_col(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag)
 {
     const PassArgs a = pass_args(c, ph, rd, imag, 0);
+    if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR) && c->stream_passes && col_stream_ok(c->nx, c->ny))
+        return timed_launch(c, 1, [&] { return launch_col_stream(mode, a, c->map, c->stream); }, "column pass");
     return timed_launch(c, 1, [&] { return launch_col(mode, a, c->map, c->stream); }, "column pass");
 }
 
@@ -300,6 +305,7 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->t = 0.0;
     c->kin_valid = false;
     c->spins = 1 << 24;
+    c->stream_passes = getenv("GPE_NO_STREAM_PASSES") ? 0 : 1;
     c->launches = 0;
     c->prof = false;
     c->prof_ms[0] = c->prof_ms[1] = 0.0;

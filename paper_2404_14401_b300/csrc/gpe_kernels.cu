@@ -65,6 +65,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+__device__ __forceinline__ void bulk_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store_1d(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void latch_status(DevScalars *sc, int code) { atomicCAS(&sc->status, 0, code); }
 
 // ------------------------------------------------------------------ reductions
@@ -287,6 +304,18 @@ __device__ __forceinline__ void stage_twiddles(float4 *__restrict__ dst, const f
     for (int i = threadIdx.x; i < fft_tw_count(N); i += blockDim.x) dst[i] = __ldg(&src[i]);
 }
 
+// Asynchronous variant: one bulk copy of the table into shared memory whose
+// bytes complete on `bar`.  The caller (thread 0) has already armed `bar` with
+// a single arrive.expect_tx covering these bytes (a barrier of count 1 takes
+// exactly one arrival per phase).
+template <int N> __host__ __device__ constexpr uint32_t twiddle_bytes() { return (uint32_t)(fft_tw_count(N) * 16); }
+template <int N>
+__device__ __forceinline__ void stage_twiddles_async(float4 *__restrict__ dst, const float4 *__restrict__ src,
+                                                     uint64_t *bar)
+{
+    bulk_load_1d(dst, src, twiddle_bytes<N>(), bar);
+}
+
 // ------------------------------------------------------------------ row pass
 template <int N> struct RowCfg {
     static constexpr int E = N >= 16 ? 16 : N;
@@ -312,11 +341,25 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     float2 *sb = smem + lr * C::PS;
     const Tables &T = a.T;
     constexpr bool FFT = (MODE == ROW_PT || MODE == ROW_FFT_F || MODE == ROW_FFT_I || MODE == ROW_OBS);
-    if constexpr (FFT) stage_twiddles<N>(stw, T.twx);
+    __shared__ __align__(8) uint64_t twbar;
+    if constexpr (FFT && C::TWN > 0) {
+        if (threadIdx.x == 0) mbar_init(&twbar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&twbar, twiddle_bytes<N>());
+            stage_twiddles_async<N>(stw, T.twx, &twbar);
+        }
+    }
 
     float2 v[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = row[j + r * TP];
+    if constexpr (FFT && C::TWN > 0) {
+        if (!__syncthreads_and(mbar_wait_bounded(&twbar, 0, a.spins))) {
+            if (threadIdx.x == 0) latch_status(T.sc, GPE_ETIMEOUT);
+            return;
+        }
+    }
 
     if constexpr (MODE == ROW_SCALE) {
         const float c = (float)T.sc->c;
@@ -470,12 +513,13 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     const int c0 = blockIdx.x * W;
     const Tables &T = a.T;
     const float4 *tw = C::TWN ? stw : T.twy;
-    if constexpr (C::TWN > 0) stage_twiddles<N>(stw, T.twy);
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar, (uint32_t)(N * W * 8));
+        // one arrival per phase: the tile and the twiddle table share it
+        mbar_expect_tx(&bar, (uint32_t)(N * W * 8) + (C::TWN > 0 ? twiddle_bytes<N>() : 0u));
+        if constexpr (C::TWN > 0) stage_twiddles_async<N>(stw, T.twy, &bar);
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + (size_t)r0 * W, &map, &bar, 2 * c0, r0);
     }
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins));
@@ -574,6 +618,215 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
             finalize_fields(S, a.red, T.sc);
     }
     if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // tile read before exit
+}
+
+// ------------------------------------------------------------------ streaming passes
+// Persistent versions of the two hot passes (row: phase + T_x; column: T_y
+// [+ phase] [+ reductions]), used for 4096-point axes where they measured
+// faster than the one-shot passes (at 2048 and below the one-shot passes, with
+// three CTAs per SM, are faster).  Each CTA walks work items (a group of whole
+// rows, or a tile of W columns) with stride gridDim.x, double-buffered in
+// shared memory: while item i is transformed in one buffer, the TMA engine
+// loads item i + gridDim.x into the other; results are written back into the
+// buffer and stored with TMA.  The twiddle table is staged once per CTA.
+template <int N> struct RowStreamCfg {
+    static constexpr int E = 16, TP = N / 16, THREADS = 256, RPC = THREADS / TP;
+    static constexpr int PS = N + N / 16;
+    static constexpr int BUF = RPC * PS;                       // float2 per buffer (padded layout)
+    static constexpr bool STW = fft_tw_count(N) * 16 <= 40960; // twiddles in shared memory
+    static constexpr int TWN = STW ? fft_tw_count(N) : 0;
+    static constexpr int CTAS_PER_SM = 2;
+    static constexpr size_t SMEM = (size_t)2 * BUF * 8 + (size_t)TWN * 16 + 128;
+};
+
+template <int N>
+__global__ void __launch_bounds__(256, 2) row_stream_kernel(const PassArgs a, int nitems)
+{
+    using C = RowStreamCfg<N>;
+    constexpr int E = C::E, TP = C::TP, RPC = C::RPC;
+    constexpr uint32_t BYTES = RPC * N * 8;
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const uint32_t s0 = smem_u32(smraw);
+    float2 *buf0 = reinterpret_cast<float2 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    float4 *stw = reinterpret_cast<float4 *>(buf0 + 2 * C::BUF);
+    const Tables &T = a.T;
+    const float4 *tw = C::STW ? stw : T.twx;
+    if constexpr (C::STW) stage_twiddles<N>(stw, T.twx);
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < nitems) {
+        mbar_expect_tx(&bar[0], BYTES);
+        bulk_load_1d(buf0, a.psi + (size_t)blockIdx.x * RPC * N, BYTES, &bar[0]);
+    }
+    const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
+    uint32_t parity = 0;      // bit b: phase of bar[b]
+    int it = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+        const int b = it & 1;
+        float2 *buf = buf0 + b * C::BUF;
+        const int next = item + gridDim.x;
+        if (threadIdx.x == 0 && next < nitems) {
+            bulk_wait_read_all();                     // the other buffer's last store has read it
+            mbar_expect_tx(&bar[b ^ 1], BYTES);
+            bulk_load_1d(buf0 + (b ^ 1) * C::BUF, a.psi + (size_t)next * RPC * N, BYTES, &bar[b ^ 1]);
+        }
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], (parity >> b) & 1u, a.spins));
+        parity ^= 1u << b;
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                latch_status(T.sc, GPE_ETIMEOUT);
+                if (next < nitems) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, a.spins);
+            }
+            break;
+        }
+        const int y = item * RPC + lr;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = buf[lr * N + j + r * TP];
+        __syncthreads();                              // dense reads done before exchange writes
+        float2 *sb = buf + lr * C::PS;
+
+        const float4 yt = T.ytab[y];
+        const PotCoefs pc = row_coefs(a, yt);
+        float cs = 1.f;
+        if (a.use_c) cs = (float)T.sc->c;
+        const float *Vr = a.V ? a.V + (size_t)y * N : nullptr;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = j + r * TP;
+            float V = pot_at(pc, __ldg(&T.xtab[xi]));
+            if (Vr) V += a.V_scale * __ldg(&Vr[xi]);
+            v[r] = phase_mul(make_float2(v[r].x * cs, v[r].y * cs), V, a.g, a.ph.h, a.imag);
+        }
+        fft_pencil<N, E, false>(v, sb, j, 1, tw);
+        kinetic_axis<E, TP>(v, T.kinx, j, a.sx, a.imag);
+        fft_pencil<N, E, true>(v, sb, j, 1, tw);
+#pragma unroll
+        for (int r = 0; r < E; ++r) buf[lr * N + j + r * TP] = v[r];
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_store_1d(a.psi + (size_t)item * RPC * N, buf, BYTES);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait_read_all();
+}
+
+template <int N> struct ColStreamCfg {
+    static constexpr int E = 16, TP = N / 16, W = col_w(N), G = col_g(N), THREADS = G * TP;
+    static constexpr int BR = N < 256 ? N : 256;
+    static constexpr int PS = N + N / 16;
+    static constexpr int BUF = W * PS;                           // float2 per buffer (padded layout)
+    static constexpr bool STW = fft_tw_count(N) * 16 <= 40960;
+    static constexpr int TWN = STW ? fft_tw_count(N) : 0;
+    static constexpr int CTAS_PER_SM = N >= 4096 ? 1 : 2;
+    static constexpr size_t SMEM = (size_t)2 * BUF * 8 + (size_t)TWN * 16 + 128;
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTAS_PER_SM)
+    col_stream_kernel(const PassArgs a, const __grid_constant__ CUtensorMap map, int nitems)
+{
+    using C = ColStreamCfg<N>;
+    constexpr int E = C::E, TP = C::TP, W = C::W;
+    static_assert(C::G == W, "one round per tile");
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double red[32 * NQ];
+    const uint32_t s0 = smem_u32(smraw);
+    float2 *buf0 = reinterpret_cast<float2 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    float4 *stw = reinterpret_cast<float4 *>(buf0 + 2 * C::BUF);
+    const Tables &T = a.T;
+    const float4 *tw = C::STW ? stw : T.twy;
+    if constexpr (C::STW) stage_twiddles<N>(stw, T.twy);
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < nitems) {
+        mbar_expect_tx(&bar[0], (uint32_t)(N * W * 8));
+        for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(buf0 + r0 * W, &map, &bar[0], 2 * blockIdx.x * W, r0);
+    }
+    constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
+    const int j = threadIdx.x % TP, c = threadIdx.x / TP;
+    float q[3] = {0.f, 0.f, 0.f};
+    uint32_t parity = 0;
+    int it = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+        const int b = it & 1;
+        float2 *buf = buf0 + b * C::BUF;
+        const int next = item + gridDim.x;
+        if (threadIdx.x == 0 && next < nitems) {
+            bulk_wait_read_all();
+            float2 *nb = buf0 + (b ^ 1) * C::BUF;
+            mbar_expect_tx(&bar[b ^ 1], (uint32_t)(N * W * 8));
+            for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(nb + r0 * W, &map, &bar[b ^ 1], 2 * next * W, r0);
+        }
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], (parity >> b) & 1u, a.spins));
+        parity ^= 1u << b;
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                latch_status(T.sc, GPE_ETIMEOUT);
+                if (next < nitems) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, a.spins);
+            }
+            break;
+        }
+        const int c0 = item * W;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = buf[(j + r * TP) * W + c];
+        __syncthreads();
+        float2 *sb = buf + c * C::PS;
+        fft_pencil<N, E, false>(v, sb, j, 1, tw);
+        kinetic_axis<E, TP>(v, T.kiny, j, a.sy, a.imag);
+        fft_pencil<N, E, true>(v, sb, j, 1, tw);
+        if constexpr (MODE == COL_T_PR) {
+            const PotCoefs pc = col_coefs(a, __ldg(&T.xtab[c0 + c]));
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int yi = j + r * TP;
+                float V = pot_at(pc, __ldg(&T.ytab[yi]));
+                if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
+                v[r] = phase_mul(v[r], V, a.g, a.ph.h, a.imag);
+            }
+        }
+        if constexpr (REDUCE) {
+            const float cx = __ldg(&T.xtab[c0 + c]).z;
+            float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+                n0 += n;
+                n1 += __ldg(&T.ytab[j + r * TP]).z * n;
+            }
+            q[0] += n0;
+            q[1] += cx * n1;
+            q[2] += cx * cx * n0;
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) buf[(j + r * TP) * W + c] = v[r];
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, buf + r0 * W, 2 * c0, r0);
+            bulk_commit();
+        }
+    }
+    if constexpr (REDUCE) {
+        block_sum<3>(q, T.part_col + (size_t)blockIdx.x * NQ, red);
+        double S[3];
+        if (last_block_total<3>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
+            finalize_fields(S, a.red, T.sc);
+    }
+    if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
 // ------------------------------------------------------------------ tables
@@ -769,6 +1022,82 @@ cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cuda
     case 2048: return col_dispatch_mode<2048>(mode, a, map, s);
     case 4096: return col_dispatch_mode<4096>(mode, a, map, s);
     case 8192: return col_dispatch_mode<8192>(mode, a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+template <int N> static cudaError_t row_stream_launch(const PassArgs &a, cudaStream_t s)
+{
+    using C = RowStreamCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(row_stream_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int items = a.ny / C::RPC;
+    int grid = C::CTAS_PER_SM * sm_count();
+    if (grid > items) grid = items;
+    row_stream_kernel<N><<<grid, C::THREADS, C::SMEM, s>>>(a, items);
+    return cudaGetLastError();
+}
+
+// Streaming row pass for ROW_PT when the grid has enough rows; false = not applicable.
+bool row_stream_ok(int nx, int ny) { return nx == 4096 && ny >= 8; }
+
+cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s)
+{
+    switch (a.nx) {
+    case 4096: return row_stream_launch<4096>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N, int MODE> static cudaError_t col_stream_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    using C = ColStreamCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(col_stream_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int items = a.nx / C::W;
+    int grid = C::CTAS_PER_SM * sm_count();
+    if (grid > items) grid = items;
+    col_stream_kernel<N, MODE><<<grid, C::THREADS, C::SMEM, s>>>(a, map, items);
+    return cudaGetLastError();
+}
+
+bool col_stream_ok(int nx, int ny) { return ny == 4096 && nx >= 8 * col_w(ny); }
+
+template <int N> static cudaError_t col_stream_mode(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    switch (mode) {
+    case COL_T: return col_stream_launch<N, COL_T>(a, map, s);
+    case COL_T_R: return col_stream_launch<N, COL_T_R>(a, map, s);
+    case COL_T_PR: return col_stream_launch<N, COL_T_PR>(a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_col_stream(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    switch (a.ny) {
+    case 4096: return col_stream_mode<4096>(mode, a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }

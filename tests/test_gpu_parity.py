@@ -240,3 +240,61 @@ def test_full_size_real_time_lattice_first_100_steps(n):
     assert abs(obs["norm"] - ro["norm"]) < 1e-6
     assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
     assert abs(obs["energy"] - r0["energy"]) < 1e-3 * abs(r0["energy"])     # conserved to O(dt^2)
+
+
+# ------------------------------------------------------------------ streaming passes
+# Axes of 4096 points run the persistent, double-buffered row (nx = 4096) and
+# column (ny = 4096) passes; these cases cover their imaginary-time, cavity and
+# real-time paths against the oracle and against the one-shot passes.
+STREAM_SHAPES = [(4096, 64), (64, 4096)]
+
+
+def box(n):
+    return 0.02 * n if n >= 1024 else 10.0
+
+
+@pytest.mark.parametrize("nx,ny", STREAM_SHAPES)
+def test_streaming_imaginary_time_matches_oracle(nx, ny):
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=11)
+    s, got, obs, ref, _ = run_both(p, psi0, 40, 2e-3, True)
+    assert rel_l2(got, ref) < 1e-5
+    ro = oracle.observables(p, ref, t=s.t)
+    assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
+    assert abs(obs["norm"] - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("nx,ny", STREAM_SHAPES)
+def test_streaming_cavity_real_time_matches_oracle(nx, ny):
+    w = gi.cavity_ramp(n=64, L=16.0, steps=40, dt=2e-4)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny), ctrl_v=np.array([1.0, 4.0]))
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-2, seed=12, checker=0.3, kc=p["kc"])
+    s, got, obs, ref, _ = run_both(p, psi0, 40, 2e-4, False)
+    assert rel_l2(got, ref) < 1e-5
+    cavity_close(obs, oracle.observables(p, ref, t=s.t))
+
+
+@pytest.mark.parametrize("nx,ny", STREAM_SHAPES)
+def test_streaming_real_time_matches_oracle(nx, ny):
+    w = gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=13)
+    s, got, obs, ref, _ = run_both(p, psi0, 30, 5e-4, False)
+    assert rel_l2(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("nx,ny", STREAM_SHAPES)
+def test_streaming_and_one_shot_passes_agree_bitwise(nx, ny, monkeypatch):
+    w = gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=14))
+    outs = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("GPE_NO_STREAM_PASSES", env)
+        s = sim_for(p)
+        s.set_psi(psi0)
+        s.step(10, w["dt"], False)
+        outs.append(s.get_psi())
+    assert np.array_equal(outs[0], outs[1])
