@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 
     float2 v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = row[j + r * TP];
+    for (int r = 0; r < E; ++r) v[r] = __ldcs(&row[j + r * TP]);    // streamed: keep the tables in L1
     if constexpr (FFT && C::TWN > 0) {
         if (!__syncthreads_and(mbar_wait_bounded(&twbar, 0, a.spins))) {
             if (threadIdx.x == 0) latch_status(T.sc, GPE_ETIMEOUT);
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     constexpr bool STORE = !(MODE == ROW_REDUCE_R || MODE == ROW_OBS);
     if constexpr (STORE) {
 #pragma unroll
-        for (int r = 0; r < E; ++r) row[j + r * TP] = v[r];
+        for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
     }
 }
 
