@@ -53,6 +53,7 @@ struct gpe_ctx {
     bool kin_valid;
     int spins;
     int stream_passes;       // use the persistent streaming passes where they apply
+    int group_rows;          // use the grouped persistent row pass where it applies
     long long launches;
     // per-pass event timing (gpe_profile)
     bool prof;
@@ -242,6 +243,8 @@ gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd,
     const PassArgs a = pass_args(c, ph, rd, imag, use_c);
     if (mode == ROW_PT && c->stream_passes && row_stream_ok(c->nx, c->ny))
         return timed_launch(c, 0, [&] { return launch_row_stream(a, c->stream); }, "row pass");
+    if (mode == ROW_PT && c->group_rows && row_group_ok(c->nx, c->ny))
+        return timed_launch(c, 0, [&] { return launch_row_group(a, c->stream); }, "row pass");
     return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream); }, "row pass");
 }
 
@@ -306,6 +309,7 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->kin_valid = false;
     c->spins = 1 << 24;
     c->stream_passes = getenv("GPE_NO_STREAM_PASSES") ? 0 : 1;
+    c->group_rows = getenv("GPE_NO_GROUP_ROWS") ? 0 : 1;
     c->launches = 0;
     c->prof = false;
     c->prof_ms[0] = c->prof_ms[1] = 0.0;

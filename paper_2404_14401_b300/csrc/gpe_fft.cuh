@@ -208,9 +208,9 @@ __host__ __device__ constexpr int fft_tw_count(int n) { return fft_tw_offset(n, 
 // and writes output p to y[(jp / NS) NS R + jp mod NS + p NS].
 // sb: this pencil's shared buffer, es: element stride in float2 units,
 // tws: this stage's twiddle block (shared or read-only global memory).
-template <int N, int E, int R, int NS, bool INV, bool LAST>
+template <int N, int E, int R, int NS, bool INV, bool LAST, class Sync>
 __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
-                                          const float4 *__restrict__ tws)
+                                          const float4 *__restrict__ tws, const Sync &sync)
 {
     constexpr int TP = N / E, B = E / R;
 #pragma unroll
@@ -242,26 +242,40 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[E], float2 *__restrict__ s
         }
     }
     if constexpr (!LAST) {
-        __syncthreads();
+        sync();
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = sb[padx(j + r * TP) * es];
-        __syncthreads();
+        sync();
     }
 }
 
+// Barrier between the scatter and the gather of an exchange: the whole CTA
+// (the default) or one named barrier of a group of warps that owns its
+// pencil buffers (id >= 1; n threads, a multiple of 32).
+struct CtaSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+    int id, n;
+    __device__ __forceinline__ void operator()() const
+    {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
+
 // Full transform of one pencil: natural order in v (element j + r TP) in and
 // out.  Forward: X_k = sum_n x_n e^{-2 pi i nk/N}; INV: the conjugate sum,
-// without the 1/N factor.  Every thread of the CTA must call it together.
-// tw: the per-stage twiddle table of this axis (fft_tw_offset layout).
-template <int N, int E, bool INV, int S = 0>
+// without the 1/N factor.  Every thread that `sync` covers must call it
+// together.  tw: the per-stage twiddle table of this axis (fft_tw_offset layout).
+template <int N, int E, bool INV, int S = 0, class Sync = CtaSync>
 __device__ __forceinline__ void fft_pencil(float2 (&v)[E], float2 *__restrict__ sb, int j, int es,
-                                           const float4 *__restrict__ tw)
+                                           const float4 *__restrict__ tw, const Sync &sync = Sync())
 {
     constexpr int R = fft_radix(N, S), NS = fft_ns(N, S);
     constexpr bool LAST = (S == fft_stages(N) - 1);
     static_assert(E % R == 0, "radix must divide the elements per thread");
-    fft_stage<N, E, R, NS, INV, LAST>(v, sb, j, es, tw + fft_tw_offset(N, S));
-    if constexpr (!LAST) fft_pencil<N, E, INV, S + 1>(v, sb, j, es, tw);
+    fft_stage<N, E, R, NS, INV, LAST>(v, sb, j, es, tw + fft_tw_offset(N, S), sync);
+    if constexpr (!LAST) fft_pencil<N, E, INV, S + 1>(v, sb, j, es, tw, sync);
 }
 
 }  // namespace gpe

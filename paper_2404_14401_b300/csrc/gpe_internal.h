@@ -92,6 +92,8 @@ cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cuda
 cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s);
 cudaError_t launch_col_stream(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
 bool row_stream_ok(int nx, int ny);
+bool row_group_ok(int nx, int ny);
+cudaError_t launch_row_group(const PassArgs &a, cudaStream_t s);
 bool col_stream_ok(int nx, int ny);
 cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m,
                           double wx, double wy, double lkx, double lky, double kc, cudaStream_t s);

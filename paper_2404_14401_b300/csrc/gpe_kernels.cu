@@ -458,6 +458,161 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     }
 }
 
+// ------------------------------------------------------------------ grouped row pass
+// ROW_PT for 512..2048-point rows with one CTA per SM: NG = 4 groups of 128
+// threads (RG = 128 / TP rows, 16 KB, per work item).  The CTA copies the
+// twiddle, coordinate and kinetic tables into shared memory once, so the
+// pointwise steps read them there instead of through L1/L2.  Each group
+// streams its items through two buffers: while it transforms one, TMA is
+// already copying the next one in, and the finished item goes back to HBM by
+// a TMA store from the buffer it was transformed in.  A group synchronises
+// only its own warps (a named barrier), so the groups drift apart as
+// separate CTAs would while sharing one copy of the tables.
+template <int N> struct RowGroupCfg {
+    static constexpr int E = 16, TP = N / 16, GT = 128, NG = 4, THREADS = GT * NG;
+    static constexpr int RG = GT / TP;                       // rows per item
+    static constexpr int PS = N + N / 16;                    // padded pencil stride (float2)
+    static constexpr int BUF = RG * PS;                      // float2 per buffer
+    static constexpr uint32_t ITEM_BYTES = RG * N * 8;
+    static constexpr int TWN = fft_tw_count(N);
+    static constexpr uint32_t TAB_BYTES = TWN * 16 + N * 16 + N * 8;
+    // dynamic shared memory: twiddles | x coordinate table | x kinetic factors | NG x 2 buffers
+    static constexpr size_t OFF_X = (size_t)TWN * 16;
+    static constexpr size_t OFF_K = OFF_X + (size_t)N * 16;
+    static constexpr size_t OFF_B = OFF_K + (size_t)N * 8;
+    static constexpr size_t SMEM = OFF_B + (size_t)NG * 2 * BUF * 8;
+    static_assert(TP <= GT && GT % TP == 0, "a group holds whole rows");
+    static_assert(OFF_B % 16 == 0 && (BUF * 8) % 16 == 0 && ITEM_BYTES % 16 == 0, "bulk copies need 16 B");
+    static_assert(SMEM <= 232448, "shared memory of one CTA");
+};
+
+// AND of p over the threads of a named barrier (all of them must arrive)
+__device__ __forceinline__ bool group_all(bool p, int id, int n)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.and.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+template <int N>
+__global__ void __launch_bounds__(RowGroupCfg<N>::THREADS, 1) row_group_kernel(const PassArgs a, int nitems)
+{
+    using C = RowGroupCfg<N>;
+    constexpr int E = C::E, TP = C::TP, RG = C::RG;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t tbar;
+    __shared__ __align__(8) uint64_t full[C::NG][2];
+    float4 *stw = reinterpret_cast<float4 *>(smraw);
+    const float4 *sx = reinterpret_cast<const float4 *>(smraw + C::OFF_X);
+    const float2 *sk = reinterpret_cast<const float2 *>(smraw + C::OFF_K);
+    const Tables &T = a.T;
+    const int g = threadIdx.x / C::GT, t = threadIdx.x % C::GT;
+    const int lr = t / TP, j = t % TP;
+    float2 *buf0 = reinterpret_cast<float2 *>(smraw + C::OFF_B) + (size_t)g * 2 * C::BUF;
+    const GroupSync gs{1 + g, C::GT};
+    const bool leader = (t == 0);
+    const int gstride = gridDim.x * C::NG;
+    const int first = blockIdx.x * C::NG + g;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&tbar, 1);
+        for (int i = 0; i < C::NG; ++i) {
+            mbar_init(&full[i][0], 1);
+            mbar_init(&full[i][1], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&tbar, C::TAB_BYTES);
+        bulk_load_1d(stw, T.twx, C::TWN * 16, &tbar);
+        bulk_load_1d(smraw + C::OFF_X, T.xtab, N * 16, &tbar);
+        bulk_load_1d(smraw + C::OFF_K, T.kinx, N * 8, &tbar);
+    }
+    if (leader && first < nitems) {
+        mbar_expect_tx(&full[g][0], C::ITEM_BYTES);
+        bulk_load_1d(buf0, a.psi + (size_t)first * RG * N, C::ITEM_BYTES, &full[g][0]);
+    }
+    const float cs = a.use_c ? (float)T.sc->c : 1.f;
+    if (!__syncthreads_and(mbar_wait_bounded(&tbar, 0, a.spins))) {
+        if (threadIdx.x == 0) {
+            latch_status(T.sc, GPE_ETIMEOUT);
+            mbar_wait_bounded(&tbar, 0, a.spins);
+        }
+        if (leader && first < nitems) mbar_wait_bounded(&full[g][0], 0, a.spins);
+        return;
+    }
+
+    uint32_t parity = 0;      // bit b: phase of full[g][b]
+    int it = 0;
+    for (int item = first; item < nitems; item += gstride, ++it) {
+        const int b = it & 1;
+        float2 *buf = buf0 + b * C::BUF;
+        const int next = item + gstride;
+        if (!group_all(mbar_wait_bounded(&full[g][b], (parity >> b) & 1u, a.spins), 1 + g, C::GT)) {
+            if (leader) {
+                latch_status(T.sc, GPE_ETIMEOUT);
+                mbar_wait_bounded(&full[g][b], (parity >> b) & 1u, a.spins);
+            }
+            break;
+        }
+        parity ^= 1u << b;
+        const int y = item * RG + lr;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = buf[lr * N + j + r * TP];
+        if (leader && next < nitems) {
+            bulk_wait_read_all();                    // the store of the other buffer has read it
+            mbar_expect_tx(&full[g][b ^ 1], C::ITEM_BYTES);
+            bulk_load_1d(buf0 + (b ^ 1) * C::BUF, a.psi + (size_t)next * RG * N, C::ITEM_BYTES, &full[g][b ^ 1]);
+        }
+        gs();                                        // dense reads done before the exchange writes
+        float2 *sb = buf + lr * C::PS;
+
+        const PotCoefs pc = row_coefs(a, __ldg(&T.ytab[y]));
+        const float *Vr = a.V ? a.V + (size_t)y * N : nullptr;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = j + r * TP;
+            float V = pot_at(pc, sx[xi]);
+            if (Vr) V += a.V_scale * __ldg(&Vr[xi]);
+            v[r] = phase_mul(make_float2(v[r].x * cs, v[r].y * cs), V, a.g, a.ph.h, a.imag);
+        }
+        fft_pencil<N, E, false>(v, sb, j, 1, stw, gs);
+        if (a.imag) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float f = sk[j + r * TP].x * a.sx;
+                v[r] = make_float2(v[r].x * f, v[r].y * f);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float2 d = sk[j + r * TP];
+                const float2 p = v[r];
+                const float2 pd = cmul(p, d);
+                v[r] = make_float2((p.x + pd.x) * a.sx, (p.y + pd.y) * a.sx);
+            }
+        }
+        fft_pencil<N, E, true>(v, sb, j, 1, stw, gs);
+#pragma unroll
+        for (int r = 0; r < E; ++r) buf[lr * N + j + r * TP] = v[r];
+        fence_proxy_async();                         // generic-proxy writes visible to the TMA store
+        gs();
+        if (leader) {
+            bulk_store_1d(a.psi + (size_t)item * RG * N, buf, C::ITEM_BYTES);
+            bulk_commit();
+        }
+    }
+    if (leader) bulk_wait_read_all();
+}
+
 // ------------------------------------------------------------------ column pass
 template <int N> struct ColCfg {
     static constexpr int E = N >= 16 ? 16 : N;
@@ -1035,6 +1190,35 @@ static int sm_count()
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
     }
     return n;
+}
+
+template <int N> static cudaError_t row_group_launch(const PassArgs &a, cudaStream_t s)
+{
+    using C = RowGroupCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(row_group_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int items = a.ny / C::RG;
+    int grid = sm_count();
+    if (grid * C::NG > items) grid = (items + C::NG - 1) / C::NG;
+    row_group_kernel<N><<<grid, C::THREADS, C::SMEM, s>>>(a, items);
+    return cudaGetLastError();
+}
+
+bool row_group_ok(int nx, int ny) { return (nx == 512 || nx == 1024 || nx == 2048) && ny % (2048 / nx) == 0; }
+
+cudaError_t launch_row_group(const PassArgs &a, cudaStream_t s)
+{
+    switch (a.nx) {
+    case 512: return row_group_launch<512>(a, s);
+    case 1024: return row_group_launch<1024>(a, s);
+    case 2048: return row_group_launch<2048>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int N> static cudaError_t row_stream_launch(const PassArgs &a, cudaStream_t s)

@@ -298,3 +298,27 @@ def test_streaming_and_one_shot_passes_agree_bitwise(nx, ny, monkeypatch):
         s.step(10, w["dt"], False)
         outs.append(s.get_psi())
     assert np.array_equal(outs[0], outs[1])
+
+
+
+# ------------------------------------------------------------------ grouped row pass
+# Rows of 512..2048 points run the grouped persistent row pass (tables in
+# shared memory, TMA double buffering per group of warps); it must give
+# exactly the one-shot row pass's result.  (512, 4096) gives groups several
+# items, so both buffers and the store/reload hand-over are exercised.
+@pytest.mark.parametrize("nx,ny,imag", [(512, 16, False), (1024, 8, True), (2048, 8, False),
+                                        (2048, 64, True), (512, 4096, False)])
+def test_grouped_and_one_shot_row_passes_agree_bitwise(nx, ny, imag, monkeypatch):
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=15))
+    outs = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("GPE_NO_GROUP_ROWS", env)
+        s = sim_for(p)
+        s.set_psi(psi0)
+        s.step(10, 2e-3 if imag else w["dt"], imag)
+        outs.append(s.get_psi())
+    assert np.array_equal(outs[0], outs[1])
+
