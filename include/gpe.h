@@ -122,10 +122,15 @@ gpe_status gpe_set_potential(gpe_ctx *ctx, const gpe_potential *p);
 gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
 
 /* Enqueue n steps on each of `count` contexts in lockstep: step s of every
- * context is enqueued (on that context's stream) before step s+1 of any,
- * so the grids share one pass schedule -- e.g. a batch of trajectories of a
- * parameter sweep (Sec. 5.3 phase diagram), possibly of different sizes.
- * Same argument rules and errors as gpe_step; contexts must be distinct. */
+ * context is enqueued before step s+1 of any, so the grids share one pass
+ * schedule -- e.g. a batch of trajectories of a parameter sweep (Sec. 5.3
+ * phase diagram), possibly of different sizes.  With count > 1 the passes
+ * run on two streams owned by the library (created on first use per device),
+ * so that passes of different contexts overlap on the GPU; each context's
+ * steps are ordered after the work already on its own stream, and its stream
+ * waits for them, so callers see the same ordering as with gpe_step.
+ * Contexts must be on the current device.  Same argument rules and errors as
+ * gpe_step; contexts must be distinct. */
 gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode);
 
 /* Compute the observables of psi at the current time; waits for the stream.

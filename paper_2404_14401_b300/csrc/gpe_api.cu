@@ -27,6 +27,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -55,6 +56,7 @@ struct gpe_ctx {
     int stream_passes;       // use the persistent streaming passes where they apply
     int group_rows;          // use the grouped persistent row pass where it applies
     long long launches;
+    cudaEvent_t ev_fork, ev_join;   // ordering of gpe_step_many's lanes with this context's stream
     // per-pass event timing (gpe_profile)
     bool prof;
     std::vector<cudaEvent_t> ev_free;
@@ -67,6 +69,35 @@ struct gpe_ctx {
 namespace {
 
 bool pow2_in_range(int n) { return n >= 8 && n <= 8192 && (n & (n - 1)) == 0; }
+
+// Streams of the library on which gpe_step_many runs contexts side by side
+// (created on first use per device, kept until the process exits).  Two
+// lanes let the passes of one trajectory fill the SMs that the other's pass
+// leaves idle at its end, and hide the gaps between launches.
+constexpr int kLanes = 2;
+struct Lanes {
+    cudaStream_t s[kLanes];
+};
+Lanes *lanes_for_current_device()
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static Lanes *lanes[kMaxDev] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!lanes[dev]) {
+        Lanes *L = new Lanes;
+        for (int i = 0; i < kLanes; ++i)
+            if (cudaStreamCreateWithFlags(&L->s[i], cudaStreamNonBlocking) != cudaSuccess) {
+                for (int k = 0; k < i; ++k) cudaStreamDestroy(L->s[k]);
+                delete L;
+                return nullptr;
+            }
+        lanes[dev] = L;
+    }
+    return lanes[dev];
+}
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -329,12 +360,17 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     T.kinx = (float2 *)(c->ws + L.kinx);
     T.kiny = (float2 *)(c->ws + L.kiny);
 
+    c->ev_fork = c->ev_join = nullptr;
     gpe_status s = make_tensor_map(c);
+    if (s == GPE_OK) s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+    if (s == GPE_OK) s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
     if (s == GPE_OK) s = cuda_check(c, cudaMemsetAsync(T.sc, 0, sizeof(DevScalars), c->stream), "memset");
     if (s == GPE_OK)
         s = cuda_check(c, launch_tables(T, nx, ny, Lx, Ly, m, 0, 0, 0, 0, 0, c->stream), "tables");
     if (s == GPE_OK) c->launches++;
     if (s != GPE_OK) {
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
         delete c;
         return s;
     }
@@ -469,11 +505,40 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
             if (ctxs[j] == ctxs[i]) return fail(ctxs[i], GPE_EINVAL, "gpe_step_many: repeated context");
     }
     if (n == 0) return GPE_OK;
-    for (int i = 0; i < count; ++i) TRY(step_prologue(ctxs[i], dt, mode));
-    for (int s = 0; s < n; ++s)
-        for (int i = 0; i < count; ++i) TRY(step_part(ctxs[i], s, n, dt, mode));
-    for (int i = 0; i < count; ++i) TRY(step_epilogue(ctxs[i], n, dt, mode));
-    return GPE_OK;
+    // Contexts are spread over the library's lanes: each context's work is
+    // ordered after what its own stream held (fork) and its stream waits for
+    // that work (join), so the caller sees the usual per-stream ordering
+    // while passes of different contexts overlap on the GPU.
+    Lanes *L = (count > 1 && !getenv("GPE_SERIAL_MANY")) ? lanes_for_current_device() : nullptr;
+    const int nl = L ? (count < kLanes ? count : kLanes) : 0;
+    std::vector<cudaStream_t> own(count);
+    for (int i = 0; i < count; ++i) own[i] = ctxs[i]->stream;
+    gpe_status st = GPE_OK;
+    if (L) {
+        for (int i = 0; i < count && st == GPE_OK; ++i) {
+            gpe_ctx *c = ctxs[i];
+            st = cuda_check(c, cudaEventRecord(c->ev_fork, own[i]), "fork record");
+            if (st == GPE_OK) st = cuda_check(c, cudaStreamWaitEvent(L->s[i % nl], c->ev_fork, 0), "fork wait");
+        }
+        if (st != GPE_OK) return st;
+        for (int i = 0; i < count; ++i) ctxs[i]->stream = L->s[i % nl];
+    }
+    for (int i = 0; i < count && st == GPE_OK; ++i) st = step_prologue(ctxs[i], dt, mode);
+    for (int s = 0; s < n && st == GPE_OK; ++s)
+        for (int i = 0; i < count && st == GPE_OK; ++i) st = step_part(ctxs[i], s, n, dt, mode);
+    for (int i = 0; i < count && st == GPE_OK; ++i) st = step_epilogue(ctxs[i], n, dt, mode);
+    if (L) {
+        // join even after an error: every context's stream waits for its lane
+        for (int i = 0; i < count; ++i) {
+            gpe_ctx *c = ctxs[i];
+            c->stream = own[i];
+            const gpe_status j1 = cuda_check(c, cudaEventRecord(c->ev_join, L->s[i % nl]), "join record");
+            const gpe_status j2 = j1 == GPE_OK ? cuda_check(c, cudaStreamWaitEvent(own[i], c->ev_join, 0), "join wait")
+                                               : j1;
+            if (st == GPE_OK) st = j2;
+        }
+    }
+    return st;
 }
 
 gpe_status gpe_observables(gpe_ctx *c, gpe_obs *out)
@@ -615,6 +680,8 @@ void gpe_destroy(gpe_ctx *c)
         cudaEventDestroy(p.second.second);
     }
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
     delete c;
 }
 

@@ -322,3 +322,38 @@ def test_grouped_and_one_shot_row_passes_agree_bitwise(nx, ny, imag, monkeypatch
         outs.append(s.get_psi())
     assert np.array_equal(outs[0], outs[1])
 
+
+
+# ------------------------------------------------------------------ lockstep lanes
+# gpe_step_many runs the contexts on two library streams.  Each trajectory
+# must come out exactly as when stepped alone, including a context whose
+# state was set by an asynchronous device copy on its own stream just before
+# the call (the lanes must wait for it) and contexts of different sizes,
+# modes of imaginary and real time, with and without a cavity.
+@pytest.mark.parametrize("imag", [False, True])
+def test_lockstep_lanes_match_single_context_stepping(imag):
+    import torch
+    from paper_2404_14401_b300 import Simulation
+    cases = [(256, 256, False), (512, 128, True), (2048, 64, False)]
+    dt = 2e-3 if imag else 5e-4
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
+    sims, alone, states = [], [], []
+    for k, (nx, ny, cav) in enumerate(cases):
+        p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+        if cav:
+            p.update(cavity=1, eta=2.0, U0=-0.5, dc=-2.0, kappa=1.0, kc=2 * np.pi, Nat=1.0, pump_lattice=1)
+        psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-2, seed=40 + k, checker=0.2,
+                                     kc=p.get("kc", 0.0)))
+        a = sim_for(p)
+        a.set_psi(psi0)
+        a.step(20, dt, imag)
+        alone.append(a.get_psi())
+        s = sim_for(p)
+        dev = torch.from_numpy(psi0).cuda()
+        torch.cuda.synchronize()
+        s.set_psi(dev)                       # asynchronous copy on the context's stream
+        sims.append(s)
+        states.append(dev)
+    Simulation.step_many(sims, 20, dt, imag)
+    for s, ref in zip(sims, alone):
+        assert np.array_equal(s.get_psi(), ref)
