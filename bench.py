@@ -158,12 +158,14 @@ def oracle_sample(n, budget_s=12.0, min_steps=1):
     w = workload(n)
     p = w["params"]
     psi = w["psi0"]().astype(np.complex128)
+    dt = w["dt"]
+    psi, _ = oracle.evolve(p, psi, 1, dt, False)               # first step: thread pool, page faults
     t0 = time.perf_counter()
-    psi, _ = oracle.evolve(p, psi, 1, w["dt"], False)
-    one = time.perf_counter() - t0
-    k = max(min_steps, int(budget_s / max(one, 1e-6)) - 1)
+    psi, _ = oracle.evolve(p, psi, 2, dt, False, t0=dt)        # per-step cost
+    per = (time.perf_counter() - t0) / 2
+    k = max(min_steps, int(budget_s / max(per, 1e-6)))
     t0 = time.perf_counter()
-    oracle.evolve(p, psi, k, w["dt"], False, t0=w["dt"])
+    oracle.evolve(p, psi, k, dt, False, t0=3 * dt)
     secs = time.perf_counter() - t0
     return n * n * k / secs, k, secs, oracle.threads()
 
