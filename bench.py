@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch elementwise baseline leg")
     return ap.parse_args()
 
 
@@ -134,6 +135,11 @@ def row_kernel_name(n):
     return f"row_kernel<{n},ROW_PT>"
 
 
+def col_kernel_name(n):
+    """Kernel of the interior real-time column pass for an n x n grid."""
+    return f"col_stream_kernel<{n},COL_T>" if n == 4096 else f"col_kernel<{n},COL_T>"
+
+
 def recorded_traffic(kernel, n):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
@@ -146,6 +152,68 @@ def recorded_traffic(kernel, n):
         if kv.get("kernel") == kernel and kv.get("grid") == f"{n}x{n}" and kv.get("src") == src:
             return float(kv["dram_bytes_per_launch"])
     return None
+
+
+# ------------------------------------------------------------------ cuFFT baseline leg
+def cufft_baseline(psis, p, dt, steps, dev):
+    """The same real-time steps written the plain way: torch.fft.fft2 / ifft2
+    (cuFFT) and torch elementwise kernels in complex64, one trajectory after
+    the other (the per-instance loop).  Adjacent half phases are merged as in
+    the library, so both do the same arithmetic per step.  Returns
+    (pt*steps/s, ms per lockstep step, kernels per step and trajectory)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import gpe_inputs as gi
+    n = p["nx"]
+    x = torch.from_numpy(gi.grid_axis(n, p["Lx"])).to(dev)
+    y = torch.from_numpy(gi.grid_axis(n, p["Ly"])).to(dev)
+    vx = 0.5 * p["m"] * p["wx"] ** 2 * x ** 2 + p["lat_V0x"] * torch.cos(p["lat_kx"] * x) ** 2
+    vy = 0.5 * p["m"] * p["wy"] ** 2 * y ** 2 + p["lat_V0y"] * torch.cos(p["lat_ky"] * y) ** 2
+    V = (vy[:, None] + vx[None, :]).float()
+    k = torch.from_numpy(2 * math.pi / p["Lx"] * np.fft.fftfreq(n, 1.0 / n)).to(dev)
+    K = torch.polar(torch.ones(n, n, dtype=torch.float64, device=dev),
+                    -(k[:, None] ** 2 + k[None, :] ** 2) * dt / (2 * p["m"])).to(torch.complex64)
+    g = p["g"]
+    work = [q.clone() for q in psis]
+
+    def phase(q, h):
+        th = torch.addcmul(V, q.real, q.real, value=g)
+        th.addcmul_(q.imag, q.imag, value=g).mul_(-h)
+        q.mul_(torch.polar(torch.ones_like(th), th))
+
+    def step(q, h):
+        phase(q, h)
+        f = torch.fft.fft2(q)
+        f.mul_(K)
+        q.copy_(torch.fft.ifft2(f))
+
+    def run(nsteps, lockstep):
+        if lockstep:                      # step s of every trajectory before step s+1
+            for s_ in range(nsteps):
+                for q in work:
+                    step(q, 0.5 * dt if s_ == 0 else dt)
+        else:                             # all steps of one trajectory, then the next
+            for q in work:
+                for s_ in range(nsteps):
+                    step(q, 0.5 * dt if s_ == 0 else dt)
+        for q in work:
+            phase(q, 0.5 * dt)
+
+    out = {}
+    for lockstep in (False, True):
+        run(2, lockstep)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(steps, lockstep)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["lockstep" if lockstep else "per_instance"] = (len(work) * n * n * steps / (ms * 1e-3), ms / steps)
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -277,7 +345,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_hbm_peak()
     alg_bytes = BYTES_PER_PT[dom] * n * n
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    kname = {"row": row_kernel_name(n), "col": f"col_kernel<{n},COL_T>"}[dom]
+    kname = {"row": row_kernel_name(n), "col": col_kernel_name(n)}[dom]
     traffic = recorded_traffic(kname, n)
 
     # end to end through the public API from pinned host buffers: upload every
@@ -303,6 +371,18 @@ def run_ours(args, rank, world, local_rank):
     h2d = 8 * n * n * B
     d2h = 8 * n * n * B + 100
 
+    # the plain cuFFT + torch elementwise loop on the same trajectories
+    cufft = None
+    if not args.no_cufft:
+        cb = cufft_baseline([s.psi for s in sims], p, dt, min(args.steps, 100), dev)
+        ours = n * n * B * args.steps / (ms * 1e-3)
+        (cv, cms), (lv, lms) = cb["per_instance"], cb["lockstep"]
+        cufft = {"value": cv * world, "unit": UNIT, "ms_per_step": cms,
+                 "kind": "torch.fft.fft2/ifft2 (cuFFT) + torch elementwise phases, complex64, per-trajectory "
+                         f"loop ({8 * n * n >> 20} MB per trajectory)",
+                 "lockstep_value": lv * world, "lockstep_ms_per_step": lms,
+                 "ours_over_cufft": ours / cv, "ours_over_cufft_lockstep": ours / lv}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, k, secs, thr = oracle_sample(n)
@@ -324,6 +404,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes,
                      "avg_launch_ms": dom_ms, "row_pass_ms": row_ms, "col_pass_ms": col_ms},
         "cpu_baseline": cpu,
+        "cufft_baseline": cufft,
         "e2e": {"value": total_pts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": f"one job of {e2e_steps} steps: pinned h2d of every psi, gpe_step_many, d2h of every psi + observables"},
