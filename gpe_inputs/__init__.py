@@ -124,6 +124,28 @@ def lattice_real_time(n: int = 2048, L: float = 40.0, seed: int = 1) -> dict:
                 psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed))
 
 
+def target_gaussian(nx: int, ny: int, Lx: float, Ly: float) -> np.ndarray:
+    """Ground state of the isotropic trap in oscillator units, exp(-r^2/2)/sqrt(pi)."""
+    x, y = grid_axis(nx, Lx), grid_axis(ny, Ly)
+    return np.exp(-0.5 * (x[None, :] ** 2 + y[:, None] ** 2)) / np.sqrt(np.pi)
+
+
+def adjoint_control(n: int = 512, L: float = 20.0, steps: int = 4000, dt: float = 5e-4, npts: int = 200,
+                    g: float = 100.0, seed: int = 4) -> dict:
+    """Lattice-depth control for the adjoint: trap + lattice of wavenumber 2 pi
+    whose depth is v(t) (lat_V0x = lat_V0y = 1, control target lattice), with
+    npts piecewise-linear points seeded uniformly in [0, 8] over the run; the
+    objective's target state is the trap ground state."""
+    t, v = control_points(seed, npts, steps * dt, 0.0, 8.0)
+    p = potential_defaults()
+    k = 2.0 * np.pi
+    p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=g, wx=1.0, wy=1.0, lat_V0x=1.0, lat_V0y=1.0,
+             lat_kx=k, lat_ky=k, ctrl_target=1, ctrl_t=t, ctrl_v=v)
+    return dict(params=p, dt=dt, imag=False, steps=steps,
+                psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed),
+                phi=lambda: target_gaussian(n, n, L, L))
+
+
 def cavity_ramp(n: int = 512, L: float = 40.0, seed: int = 2, steps: int = 20000,
                 dt: float = 2e-4) -> dict:
     """Self-consistent cavity (Sec. 5.3): eta ramped 0 -> 3 over the run, Delta_c = -2, U0 = -0.5, kappa = 1."""

@@ -21,6 +21,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                   (no closed form): "parity unpinned" for that trajectory.
   observables     pinned: E = mu = 1 for the oscillator ground state,
                   kinetic energy of a Gaussian in closed form
+  adjoint         pinned: gradient of J = E(psi_T) + |<phi|psi_T>|^2 with
+                  respect to the lattice control values against central
+                  finite differences of the forward oracle; zero gradient
+                  for control points the evolution never reaches
 """
 from __future__ import annotations
 
@@ -78,8 +82,9 @@ def _load():
         lib.orc_observables.argtypes = [pp, dp, ctypes.c_double, dp]
         lib.orc_potential.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_threads.argtypes = []
+        lib.orc_adjoint.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         for f in (lib.orc_fft1, lib.orc_fft2, lib.orc_evolve, lib.orc_observables,
-                  lib.orc_potential, lib.orc_threads):
+                  lib.orc_potential, lib.orc_threads, lib.orc_adjoint):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -172,3 +177,20 @@ def potential(p: dict, t: float = 0.0, alpha: complex = 0.0) -> np.ndarray:
     V = np.zeros(P.shape)
     _load().orc_potential(P.ref(), float(t), float(np.real(alpha)), float(np.imag(alpha)), _dptr(V))
     return V
+
+
+def adjoint(p: dict, psi0: np.ndarray, phi: np.ndarray, steps: int, dt: float, t0: float = 0.0):
+    """J = E(psi_T) + |<phi|psi_T>|^2 after `steps` real-time steps from psi0,
+    and dJ/dv_i for the lattice control values p["ctrl_v"] (discrete adjoint,
+    reverse sweep over stored states).  Returns (J, grad)."""
+    P = Params(p)
+    x = np.ascontiguousarray(psi0, dtype=np.complex128)
+    f = np.ascontiguousarray(phi, dtype=np.complex128)
+    assert x.shape == P.shape and f.shape == P.shape
+    J = np.zeros(1)
+    grad = np.zeros(max(int(P.s.nctrl), 1))
+    rc = _load().orc_adjoint(P.ref(), _dptr(x.view(np.float64)), _dptr(f.view(np.float64)), int(steps),
+                             float(dt), float(t0), _dptr(J), _dptr(grad))
+    if rc:
+        raise ValueError("orc_adjoint needs a lattice control table and no cavity")
+    return float(J[0]), grad[:int(P.s.nctrl)]

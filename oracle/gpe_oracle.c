@@ -391,3 +391,128 @@ int orc_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint of the real-time V/2 - T - V/2 evolution (control   */
+/* of the lattice depth, Sec. 5.2 Eq. (9) with a piecewise-linear V0(t)) */
+/*                                                                       */
+/* Objective: J = E(psi_T) + |<phi|psi_T>|^2 with E the GP energy at the */
+/* final time (the observables above) and <phi|psi> = int conj(phi) psi. */
+/* lambda = dJ/d conj(psi) (Wirtinger), so dJ = 2 Re sum conj(lambda)   */
+/* dpsi.  For a phase sub-step psi' = exp(-i theta) psi with theta =     */
+/* h (V + g |psi|^2), mu = exp(+i theta) lambda' gives                   */
+/*   lambda = mu + 2 h g Im(conj(mu) psi) psi,                            */
+/*   dJ/dV(r) += 2 h Im(conj(mu) psi)(r);                                 */
+/* for the kinetic sub-step (unitary) lambda = F^-1 conj(K) F lambda'.   */
+/* The terminal adjoint is lambda_T = dxdy (H psi_T + <phi|psi_T> phi)   */
+/* with H psi = F^-1[(k^2/2m) F psi] + (V(T) + g |psi|^2) psi.           */
+/* dV/dv = L(r) = V0x cos^2(kx x) + V0y cos^2(ky y) for the lattice      */
+/* control v(t), and dv(t)/dv_i is the piecewise-linear hat weight of    */
+/* control point i at time t (clamped at both ends, as ctrl_eval).       */
+/* ------------------------------------------------------------------ */
+static void ctrl_weights(const orc_params *p, double t, double *grad, double gv)
+{
+    int n = p->nctrl;
+    if (n <= 0) return;
+    if (t <= p->ctrl_t[0]) { grad[0] += gv; return; }
+    if (t >= p->ctrl_t[n - 1]) { grad[n - 1] += gv; return; }
+    int i = 0;
+    while (i + 1 < n && p->ctrl_t[i + 1] < t) i++;
+    double f = (t - p->ctrl_t[i]) / (p->ctrl_t[i + 1] - p->ctrl_t[i]);
+    grad[i] += (1.0 - f) * gv;
+    grad[i + 1] += f * gv;
+}
+
+static double lattice_mode(const orc_params *p, int xi, int yi)
+{
+    double x = xcoord(xi, p->nx, p->Lx), y = xcoord(yi, p->ny, p->Ly);
+    double cx = cos(p->lat_kx * x), cy = cos(p->lat_ky * y);
+    return p->lat_V0x * cx * cx + p->lat_V0y * cy * cy;
+}
+
+/* Adjoint of a real-time phase sub-step whose input was psi_in, applied
+ * to lam in place; returns sum_r 2 h Im(conj(mu) psi_in) L(r) (dJ/dv at t). */
+static double phase_adjoint(const orc_params *p, cplx *lam, const cplx *psi_in, double t, double h)
+{
+    double gv = 0.0;
+    for (int y = 0; y < p->ny; y++)
+        for (int x = 0; x < p->nx; x++) {
+            size_t i = (size_t)y * p->nx + x;
+            double n = creal(psi_in[i]) * creal(psi_in[i]) + cimag(psi_in[i]) * cimag(psi_in[i]);
+            double theta = (potential_at(p, x, y, t, 0.0) + p->g * n) * h;
+            cplx mu = cexp(I * theta) * lam[i];
+            double q = cimag(conj(mu) * psi_in[i]);
+            lam[i] = mu + 2.0 * h * p->g * q * psi_in[i];
+            gv += 2.0 * h * q * lattice_mode(p, x, y);
+        }
+    return gv;
+}
+
+/* J and dJ/dctrl_v[i] (grad_out[nctrl]) for nsteps real-time steps of dt
+ * from psi0 (interleaved complex128) at time t0.  phi: target state.
+ * Requires ctrl_target = lattice and no cavity; returns -1 otherwise.    */
+int orc_adjoint(const orc_params *p, const double *psi0, const double *phi_d, int nsteps, double dt,
+                double t0, double *J_out, double *grad_out)
+{
+    if (!is_pow2(p->nx) || !is_pow2(p->ny) || nsteps < 0) return -1;
+    if (p->cavity || p->ctrl_target != CTRL_LATTICE || p->paper_order) return -1;
+    size_t n = (size_t)p->nx * p->ny;
+    double dx = p->Lx / p->nx, dy = p->Ly / p->ny;
+    const cplx *phi = (const cplx *)phi_d;
+    /* forward: boundary states psi_s and the closing-phase inputs psi_b */
+    cplx *st = malloc(sizeof(cplx) * n * (size_t)(nsteps + 1));
+    cplx *sb = malloc(sizeof(cplx) * n * (size_t)(nsteps > 0 ? nsteps : 1));
+    memcpy(st, psi0, sizeof(cplx) * n);
+    for (int s = 0; s < nsteps; s++) {
+        double t = t0 + s * dt;
+        cplx *cur = st + n * (size_t)(s + 1);
+        memcpy(cur, st + n * (size_t)s, sizeof(cplx) * n);
+        potential_phase(p, cur, t, 0.5 * dt, 0);
+        kinetic(p, cur, dt, 0);
+        memcpy(sb + n * (size_t)s, cur, sizeof(cplx) * n);
+        potential_phase(p, cur, t + dt, 0.5 * dt, 0);
+    }
+    const cplx *psiT = st + n * (size_t)nsteps;
+    double tT = t0 + nsteps * dt;
+
+    /* objective */
+    double obs[10];
+    orc_observables(p, (const double *)psiT, tT, obs);
+    cplx c = 0.0;
+    for (size_t i = 0; i < n; i++) c += conj(phi[i]) * psiT[i] * dx * dy;
+    *J_out = obs[4] + creal(c * conj(c));
+
+    for (int i = 0; i < p->nctrl; i++) grad_out[i] = 0.0;
+    /* terminal adjoint and the explicit dependence of E on v(T) */
+    cplx *lam = malloc(sizeof(cplx) * n);
+    memcpy(lam, psiT, sizeof(cplx) * n);
+    orc_fft2((double *)lam, p->nx, p->ny, -1);
+    for (int y = 0; y < p->ny; y++) {
+        double ky = kcoord(y, p->ny, p->Ly);
+        for (int x = 0; x < p->nx; x++) {
+            double kx = kcoord(x, p->nx, p->Lx);
+            lam[(size_t)y * p->nx + x] *= (kx * kx + ky * ky) / (2.0 * p->m);
+        }
+    }
+    orc_fft2((double *)lam, p->nx, p->ny, +1);
+    double gT = 0.0;
+    for (int y = 0; y < p->ny; y++)
+        for (int x = 0; x < p->nx; x++) {
+            size_t i = (size_t)y * p->nx + x;
+            cplx v = psiT[i];
+            double d = creal(v) * creal(v) + cimag(v) * cimag(v);
+            lam[i] = (lam[i] + (potential_at(p, x, y, tT, 0.0) + p->g * d) * v + c * phi[i]) * dx * dy;
+            gT += d * lattice_mode(p, x, y) * dx * dy;
+        }
+    ctrl_weights(p, tT, grad_out, gT);
+
+    /* reverse sweep */
+    for (int s = nsteps - 1; s >= 0; s--) {
+        double t = t0 + s * dt;
+        ctrl_weights(p, t + dt, grad_out, phase_adjoint(p, lam, sb + n * (size_t)s, t + dt, 0.5 * dt));
+        kinetic(p, lam, -dt, 0);                      /* conjugate kinetic phase */
+        ctrl_weights(p, t, grad_out, phase_adjoint(p, lam, st + n * (size_t)s, t, 0.5 * dt));
+    }
+    free(lam); free(st); free(sb);
+    return 0;
+}
