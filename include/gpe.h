@@ -197,6 +197,33 @@ long long gpe_launch_count(const gpe_ctx *ctx);
 gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, double Lx, double Ly, double kc,
                                void *stream, double *out);
 
+/* ---- Adjoint of the real-time split step (lattice-depth control) ------
+ * For the control of the lattice depth v(t) (ctrl_target GPE_CTRL_LATTICE:
+ * V = trap + v(t) (lat_V0x cos^2(kx x) + lat_V0y cos^2(ky y)), Sec. 5.2 Eq. 9)
+ * and the objective J = E(psi_T) + |<phi|psi_T>|^2 (E: the GP energy of the
+ * state after nsteps real-time steps of dt, <phi|psi> = sum conj(phi) psi
+ * dx dy), gpe_adjoint_lattice returns J and dJ/dv_i for every control value
+ * v_i of the context's control table.  It is the discrete adjoint of the
+ * V/2 - T - V/2 steps gpe_step takes: the steps are run forward keeping a
+ * checkpoint every S = ceil(sqrt(nsteps)) steps, then swept in reverse one
+ * segment at a time (each segment's states recomputed from its checkpoint),
+ * with per point lambda <- mu + 2 h g Im(conj(mu) psi) psi, mu = exp(i theta)
+ * lambda for each half phase and the conjugate kinetic propagator in between,
+ * starting from lambda_T = dx dy (H psi_T + <phi|psi_T> phi).
+ *
+ * phi_dev: target state, complex64 [ny][nx] on the device (borrowed, 16-byte
+ * aligned).  adj_ws: device scratch of at least
+ * gpe_adjoint_workspace_size(nx, ny, nsteps) bytes (256-byte aligned,
+ * borrowed): (ceil(nsteps/S) + S + 3) copies of psi plus 2 nsteps + 1
+ * doubles.  grad_out: host array of nctrl doubles.  The call synchronises the
+ * context's stream.  On return psi is the final state and the context's time
+ * has advanced by nsteps dt, as after gpe_step.  Errors: GPE_EINVAL (no
+ * lattice control table, a cavity, bad sizes or pointers), GPE_ENOMEM
+ * (workspace too small), GPE_ECUDA, device statuses as gpe_step. */
+size_t gpe_adjoint_workspace_size(int nx, int ny, int nsteps);
+gpe_status gpe_adjoint_lattice(gpe_ctx *ctx, int nsteps, double dt, const void *phi_dev, void *adj_ws,
+                               size_t adj_ws_bytes, double *J_out, double *grad_out);
+
 /* Release the context (host memory only; borrowed memory is untouched). */
 void gpe_destroy(gpe_ctx *ctx);
 

@@ -33,6 +33,7 @@ class Simulation:
         self.psi = torch.zeros((ny, nx), dtype=torch.complex64, device=self.device)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
         self._keep = []
+        self._ctrl = None
         self.ctx = abi.gpe_create(nx, ny, Lx, Ly, m, g, self.psi.data_ptr(), self.ws.data_ptr(), ws,
                                   self.stream.cuda_stream)
 
@@ -47,6 +48,7 @@ class Simulation:
             setattr(pot, k, p.get(k, 0) if k != "V_scale" else p.get(k, 1.0))
         pot.N = p.get("Nat", p.get("N", 1.0))
         keep = []
+        self._ctrl = None
         if p.get("Varr") is not None:
             V = torch.as_tensor(np.asarray(p["Varr"], dtype=np.float32)).to(self.device)
             keep.append(V)
@@ -56,6 +58,7 @@ class Simulation:
             v = np.ascontiguousarray(p["ctrl_v"], dtype=np.float64)
             keep += [t, v]
             pot.nctrl = t.size
+            self._ctrl = v
             pot.ctrl_t = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             pot.ctrl_v = v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         abi.gpe_set_potential(self.ctx, pot)
@@ -86,6 +89,22 @@ class Simulation:
     def step_many(sims, n: int, dt: float, imag: bool = False):
         """n lockstep steps on several simulations (one pass schedule)."""
         abi.gpe_step_many([s.ctx for s in sims], n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
+
+    def adjoint_lattice(self, phi, nsteps: int, dt: float):
+        """J = E(psi_T) + |<phi|psi_T>|^2 after nsteps real-time steps from the
+        current state, and dJ/dv_i for the lattice control values set with
+        set_potential (ctrl_target = GPE_CTRL_LATTICE).  One C call (checkpointed
+        forward, then the reverse sweep); psi is the final state afterwards.
+        phi: complex64 cuda tensor or numpy array [ny][nx]."""
+        torch = self.torch
+        phi_t = torch.as_tensor(np.asarray(phi, dtype=np.complex64) if isinstance(phi, np.ndarray) else phi)
+        phi_t = phi_t.to(device=self.device, dtype=torch.complex64).contiguous()
+        nbytes = abi.gpe_adjoint_workspace_size(self.nx, self.ny, nsteps)
+        if getattr(self, "_adj_ws", None) is None or self._adj_ws.numel() < nbytes:
+            self._adj_ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        nctrl = 0 if self._ctrl is None else len(self._ctrl)
+        return abi.gpe_adjoint_lattice(self.ctx, nsteps, dt, phi_t.data_ptr(), self._adj_ws.data_ptr(),
+                                       self._adj_ws.numel(), nctrl)
 
     def profile(self, enable: bool):
         abi.gpe_profile(self.ctx, enable)

@@ -143,7 +143,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-gpe_status make_tensor_map(gpe_ctx *c)
+// TMA view of a [ny][nx] complex64 array as float32 [ny][2 nx] with box
+// W complex columns x BR rows (the column pass's tile)
+gpe_status encode_map(gpe_ctx *c, void *base, CUtensorMap *out)
 {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
@@ -160,12 +162,14 @@ gpe_status make_tensor_map(gpe_ctx *c)
     cuuint64_t strides[1] = {(cuuint64_t)2 * c->nx * sizeof(float)};
     cuuint32_t box[2] = {(cuuint32_t)(2 * c->W), (cuuint32_t)BR};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&c->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->psi, dims, strides, box, estr,
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(c, GPE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return GPE_OK;
 }
+
+gpe_status make_tensor_map(gpe_ctx *c) { return encode_map(c, c->psi, &c->map); }
 
 // piecewise-linear control v(t), clamped at both ends
 double control_value(const gpe_ctx *c, double t)
@@ -496,6 +500,151 @@ gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
     return step_epilogue(c, n, dt, mode);
 }
 
+// ---------------------------------------------------------------- adjoint
+// Layout of the adjoint workspace for n steps: S = ceil(sqrt(n)) steps per
+// segment, K = ceil(n / S) segments.  Checkpoints psi_{kS} (k < K) and psi_n,
+// the S + 1 states of one segment, lambda, and the 2n + 1 per-phase dJ/dv.
+struct AdjLayout {
+    int S, K;
+    size_t P, ck, st, lam, g, total;
+};
+static AdjLayout adj_layout(int nx, int ny, int n)
+{
+    AdjLayout L;
+    L.S = 1;
+    while ((long long)L.S * L.S < n) ++L.S;
+    L.K = (n + L.S - 1) / L.S;
+    L.P = align256(sizeof(float2) * (size_t)nx * ny);
+    L.ck = 0;
+    L.st = L.ck + (size_t)(L.K + 1) * L.P;
+    L.lam = L.st + (size_t)(L.S + 1) * L.P;
+    L.g = L.lam + L.P;
+    L.total = L.g + align256(sizeof(double) * (size_t)(2 * n + 1));
+    return L;
+}
+
+// hat weight of control point i at time t, as control_value evaluates v(t)
+static void control_weights(const gpe_ctx *c, double t, double gv, double *grad)
+{
+    const size_t n = c->ctrl_t.size();
+    if (t <= c->ctrl_t[0]) { grad[0] += gv; return; }
+    if (t >= c->ctrl_t[n - 1]) { grad[n - 1] += gv; return; }
+    size_t lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (c->ctrl_t[mid] < t) lo = mid; else hi = mid;
+    }
+    const double f = (t - c->ctrl_t[lo]) / (c->ctrl_t[hi] - c->ctrl_t[lo]);
+    grad[lo] += (1.0 - f) * gv;
+    grad[hi] += f * gv;
+}
+
+static gpe_status copy_d2d(gpe_ctx *c, void *dst, const void *src)
+{
+    return cuda_check(c, cudaMemcpyAsync(dst, src, sizeof(float2) * (size_t)c->nx * c->ny,
+                                         cudaMemcpyDeviceToDevice, c->stream), "adjoint copy");
+}
+
+static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, unsigned char *ws,
+                              const AdjLayout &L, double *J_out, double *grad)
+{
+    float2 *ck = (float2 *)(ws + L.ck), *st = (float2 *)(ws + L.st), *lam = (float2 *)(ws + L.lam);
+    double *gdev = (double *)(ws + L.g);
+    const size_t P = L.P / sizeof(float2);
+    const double t0 = c->t, tT = t0 + n * dt;
+    const double dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
+    CUtensorMap lam_map;
+    TRY(encode_map(c, lam, &lam_map));
+
+    // forward, one V/2 - T - V/2 step per call, keeping a checkpoint every S steps
+    TRY(copy_d2d(c, ck, c->psi));
+    for (int s = 0; s < n; ++s) {
+        TRY(gpe_step(c, 1, dt, GPE_REAL));
+        if ((s + 1) % L.S == 0 && s + 1 < n) TRY(copy_d2d(c, ck + (size_t)((s + 1) / L.S) * P, c->psi));
+    }
+    float2 *psiT = ck + (size_t)L.K * P;
+    TRY(copy_d2d(c, psiT, c->psi));
+
+    // J = E(psi_T) + |<phi|psi_T>|^2
+    gpe_obs o;
+    TRY(gpe_observables(c, &o));
+    PhaseArgs none;
+    memset(&none, 0, sizeof(none));
+    TRY(timed_launch(c, 2, [&] {
+        return launch_adj_overlap(psiT, phi, c->T, c->nx, c->ny, (float)c->pot.lat_V0x, (float)c->pot.lat_V0y,
+                                  c->stream);
+    }, "adjoint overlap"));
+    DevScalars h;
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, c->T.sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    const double cre = h.sums[0][0] * dxdy, cim = h.sums[0][1] * dxdy;
+    *J_out = o.energy + cre * cre + cim * cim;
+    control_weights(c, tT, h.sums[0][2] * dxdy, grad);            // E depends on v(T) through V
+
+    // terminal adjoint lambda_T = dxdy (H psi_T + c phi)
+    TRY(copy_d2d(c, lam, psiT));
+    const RedArgs rd = red_at(c, tT);
+    PassArgs a = pass_args(c, none, rd, 0, 0);
+    a.psi = lam;
+    TRY(timed_launch(c, 0, [&] { return launch_row(ROW_FFT_F, a, c->stream); }, "adjoint fft"));
+    TRY(timed_launch(c, 1, [&] { return launch_col(COL_FFT_F, a, lam_map, c->stream); }, "adjoint fft"));
+    TRY(timed_launch(c, 2, [&] {
+        return launch_kin_energy_mul(lam, c->nx, c->ny, c->Lx, c->Ly, c->m, c->stream);
+    }, "adjoint kinetic"));
+    TRY(timed_launch(c, 1, [&] { return launch_col(COL_FFT_I, a, lam_map, c->stream); }, "adjoint fft"));
+    TRY(timed_launch(c, 0, [&] { return launch_row(ROW_FFT_I, a, c->stream); }, "adjoint fft"));
+    PassArgs aT = pass_args(c, phase_at(c, tT, 0.5 * dt), rd, 0, 0);
+    TRY(timed_launch(c, 2, [&] {
+        return launch_adj_terminal(lam, psiT, phi, aT, (float)cre, (float)cim, (float)dxdy, c->stream);
+    }, "adjoint terminal"));
+
+    // reverse sweep, segment by segment: recompute the segment's states from
+    // its checkpoint, then the two adjoint passes of each step
+    for (int k = L.K - 1; k >= 0; --k) {
+        const int s0 = k * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
+        TRY(copy_d2d(c, c->psi, ck + (size_t)k * P));
+        c->t = t0 + s0 * dt;
+        TRY(copy_d2d(c, st, c->psi));
+        for (int i = 1; i <= s1 - s0; ++i) {
+            TRY(gpe_step(c, 1, dt, GPE_REAL));
+            TRY(copy_d2d(c, st + (size_t)i * P, c->psi));
+        }
+        for (int s = s1 - 1; s >= s0; --s) {
+            const double ts = t0 + s * dt, te = ts + dt;
+            PassArgs ar = pass_args(c, phase_at(c, te, 0.5 * dt), red_at(c, te), 0, 0);
+            ar.psi = lam;
+            ar.psi2 = st + (size_t)(s + 1 - s0) * P;
+            ar.gout = gdev + 2 * s + 1;
+            ar.L0x = (float)c->pot.lat_V0x;
+            ar.L0y = (float)c->pot.lat_V0y;
+            TRY(timed_launch(c, 0, [&] { return launch_row(ROW_ADJ, ar, c->stream); }, "adjoint row pass"));
+            PassArgs ac = pass_args(c, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0);
+            ac.psi = lam;
+            ac.psi2 = st + (size_t)(s - s0) * P;
+            ac.gout = gdev + 2 * s;
+            ac.L0x = ar.L0x;
+            ac.L0y = ar.L0y;
+            TRY(timed_launch(c, 1, [&] { return launch_col(COL_ADJ, ac, lam_map, c->stream); },
+                             "adjoint column pass"));
+        }
+    }
+    // leave the context at the final state and time, as gpe_step would
+    TRY(copy_d2d(c, c->psi, psiT));
+    c->t = tT;
+
+    std::vector<double> g(2 * (size_t)n);
+    TRY(cuda_check(c, cudaMemcpyAsync(g.data(), gdev, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->stream),
+                   "copy"));
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, c->T.sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    if (h.status) return fail(c, (gpe_status)h.status, "device status %s", gpe_status_string((gpe_status)h.status));
+    for (int s = 0; s < n; ++s) {
+        control_weights(c, t0 + s * dt, g[2 * s], grad);
+        control_weights(c, t0 + (s + 1) * dt, g[2 * s + 1], grad);
+    }
+    return GPE_OK;
+}
+
 gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode)
 {
     if (!ctxs || count < 1) return GPE_EINVAL;
@@ -670,6 +819,29 @@ gpe_status gpe_profile_read(gpe_ctx *c, double *row_ms, int *row_launches, doubl
 }
 
 long long gpe_launch_count(const gpe_ctx *c) { return c ? c->launches : -1; }
+
+size_t gpe_adjoint_workspace_size(int nx, int ny, int nsteps)
+{
+    if (!pow2_in_range(nx) || !pow2_in_range(ny) || nsteps < 1) return 0;
+    return adj_layout(nx, ny, nsteps).total;
+}
+
+gpe_status gpe_adjoint_lattice(gpe_ctx *c, int nsteps, double dt, const void *phi_dev, void *adj_ws,
+                               size_t adj_ws_bytes, double *J_out, double *grad_out)
+{
+    if (!c || !J_out || !grad_out) return GPE_EINVAL;
+    TRY(step_check(c, nsteps, dt, GPE_REAL));
+    if (nsteps < 1) return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: nsteps %d", nsteps);
+    if (!phi_dev || ((uintptr_t)phi_dev & 15u) || !adj_ws || ((uintptr_t)adj_ws & 255u))
+        return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: null or misaligned buffer");
+    if (c->pot.cavity || c->pot.ctrl_target != GPE_CTRL_LATTICE || c->ctrl_t.empty())
+        return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: needs a lattice control table and no cavity");
+    const AdjLayout L = adj_layout(c->nx, c->ny, nsteps);
+    if (adj_ws_bytes < L.total) return fail(c, GPE_ENOMEM, "gpe_adjoint_lattice: workspace %zu < %zu", adj_ws_bytes,
+                                            L.total);
+    for (size_t i = 0; i < c->ctrl_t.size(); ++i) grad_out[i] = 0.0;
+    return adjoint_run(c, nsteps, dt, (const float2 *)phi_dev, (unsigned char *)adj_ws, L, J_out, grad_out);
+}
 
 void gpe_destroy(gpe_ctx *c)
 {

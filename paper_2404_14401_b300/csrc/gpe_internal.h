@@ -60,7 +60,8 @@ enum RowMode {
     ROW_SCALE = 4,      // multiply by c, store
     ROW_FFT_F = 5,      // F_x only
     ROW_FFT_I = 6,      // F_x^-1 (with 1/nx)
-    ROW_OBS = 7         // observable sums + F_x kinetic sum, no store
+    ROW_OBS = 7,        // observable sums + F_x kinetic sum, no store
+    ROW_ADJ = 8         // adjoint of a closing half phase (psi2 = its output), then T_x^H; reduce dJ/dv
 };
 
 // Column passes (y axis), on TMA-loaded tiles of W columns.
@@ -70,7 +71,8 @@ enum ColMode {
     COL_T_PR = 2,       // T_y, potential phase, reduce, store
     COL_FFT_F = 3,      // F_y only
     COL_FFT_I = 4,      // F_y^-1 (with 1/ny)
-    COL_OBS = 5         // F_y, sum ky^2 |.|^2, no store
+    COL_OBS = 5,        // F_y, sum ky^2 |.|^2, no store
+    COL_ADJ = 6         // T_y^H, then the adjoint of an opening half phase (psi2 = its input); reduce dJ/dv
 };
 
 struct PassArgs {
@@ -84,6 +86,12 @@ struct PassArgs {
     PhaseArgs ph;
     RedArgs red;
     Tables T;
+    // adjoint passes: the forward state the phase adjoint needs ([ny][nx]),
+    // where the last CTA writes the reduced dJ/dv, and the base lattice
+    // depths L = L0x cos^2(k x) + L0y cos^2(k y) = dV/dv (Eq. 9)
+    const float2 *psi2;
+    double *gout;
+    float L0x, L0y;
 };
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
@@ -100,6 +108,11 @@ cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly,
 cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly,
                                   double m, double dt, int imag, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevScalars *sc, int spins, cudaStream_t s);
+cudaError_t launch_kin_energy_mul(float2 *f, int nx, int ny, double Lx, double Ly, double m, cudaStream_t s);
+cudaError_t launch_adj_overlap(const float2 *psi, const float2 *phi, const Tables &T, int nx, int ny, float L0x,
+                               float L0y, cudaStream_t s);
+cudaError_t launch_adj_terminal(float2 *lam, const float2 *psi, const float2 *phi, const PassArgs &a, float c_re,
+                                float c_im, float dxdy, cudaStream_t s);
 int col_tile_width(int nx, int ny);
 int row_rows_per_cta(int nx, int ny);
 

@@ -272,10 +272,49 @@ __device__ __forceinline__ float2 phase_mul(float2 q, float V, float g, float h,
     return make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
 }
 
+// psi <- exp(-i theta) psi for a given theta (real time), in the same 1 + d
+// form as phase_mul; used by the adjoint passes, whose theta comes from the
+// forward state rather than from the value being rotated.
+__device__ __forceinline__ float2 phase_rot(float2 q, float th)
+{
+    const float w = 0.5f * th;
+    float s, c;
+    if (fabsf(th) <= 1.f) {
+        const float v = w * w;
+        float ps = fmaf(v, 1.f / 362880.f, -1.f / 5040.f);
+        ps = fmaf(v, ps, 1.f / 120.f);
+        ps = fmaf(v, ps, -1.f / 6.f);
+        s = fmaf(w * v, ps, w);
+        float pc = fmaf(v, 1.f / 40320.f, -1.f / 720.f);
+        pc = fmaf(v, pc, 1.f / 24.f);
+        pc = fmaf(v, pc, -0.5f);
+        c = fmaf(v, pc, 1.f);
+    } else {
+        sincosf(w, &s, &c);
+    }
+    const float dr = -2.f * s * s, di = -2.f * s * c;
+    return make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
+}
+
+// Adjoint of one real-time half phase at one point (discrete adjoint of
+// psi' = exp(-i theta) psi, theta = h (V + g |psi|^2)): lam = mu + 2 h g
+// Im(conj(mu) psi) psi with mu = exp(+i theta) lam'; returns Im(conj(mu) psi),
+// whose 2 h L(r) multiple is dJ/dv at this point.  `psi` is the phase's input.
+__device__ __forceinline__ float phase_adjoint(float2 &lam, float2 psi, float V, float g, float h)
+{
+    const float th = (V + g * (psi.x * psi.x + psi.y * psi.y)) * h;
+    const float2 mu = phase_rot(lam, -th);
+    const float q = mu.x * psi.y - mu.y * psi.x;
+    const float f = 2.f * h * g * q;
+    lam = make_float2(fmaf(f, psi.x, mu.x), fmaf(f, psi.y, mu.y));
+    return q;
+}
+
 // one axis of the kinetic propagator in k-space: real time psi <- s (psi + psi D)
 // with D = exp(-i k^2 dt / 2m) - 1, imaginary time psi <- s K psi with
-// K = exp(-k^2 dtau / 2m); s = 1/n exact (the inverse FFT's normalisation)
-template <int E, int TP>
+// K = exp(-k^2 dtau / 2m); s = 1/n exact (the inverse FFT's normalisation).
+// CONJ: the adjoint (conjugate) propagator, D -> conj(D).
+template <int E, int TP, bool CONJ = false>
 __device__ __forceinline__ void kinetic_axis(float2 (&v)[E], const float2 *__restrict__ D, int j, float s, int imag)
 {
     if (imag) {
@@ -287,7 +326,8 @@ __device__ __forceinline__ void kinetic_axis(float2 (&v)[E], const float2 *__res
     } else {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            const float2 d = __ldg(&D[j + r * TP]);
+            float2 d = __ldg(&D[j + r * TP]);
+            if constexpr (CONJ) d.y = -d.y;
             const float2 p = v[r];
             const float2 pd = cmul(p, d);
             v[r] = make_float2((p.x + pd.x) * s, (p.y + pd.y) * s);
@@ -340,7 +380,8 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     float2 *row = a.psi + (size_t)y * N;
     float2 *sb = smem + lr * C::PS;
     const Tables &T = a.T;
-    constexpr bool FFT = (MODE == ROW_PT || MODE == ROW_FFT_F || MODE == ROW_FFT_I || MODE == ROW_OBS);
+    constexpr bool FFT = (MODE == ROW_PT || MODE == ROW_FFT_F || MODE == ROW_FFT_I || MODE == ROW_OBS ||
+                          MODE == ROW_ADJ);
     __shared__ __align__(8) uint64_t twbar;
     if constexpr (FFT && C::TWN > 0) {
         if (threadIdx.x == 0) mbar_init(&twbar, 1);
@@ -449,6 +490,38 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
         fft_pencil<N, E, false>(v, sb, j, 1, stw);
         kinetic_axis<E, TP>(v, T.kinx, j, a.sx, a.imag);
         fft_pencil<N, E, true>(v, sb, j, 1, stw);
+    }
+
+    if constexpr (MODE == ROW_ADJ) {
+        // v = lambda after the step; psi2 = the step's output, whose density
+        // is the closing phase's (a phase keeps |psi|), so the phase input is
+        // exp(+i theta) psi2 and Im(conj(mu) input) = Im(conj(lambda) psi2)
+        const PotCoefs pc = row_coefs(a, yt);
+        const float2 *p2 = a.psi2 + (size_t)y * N;
+        float gq = 0.f;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = j + r * TP;
+            const float4 xt = __ldg(&T.xtab[xi]);
+            float V = pot_at(pc, xt);
+            if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)y * N + xi]);
+            const float2 o = __ldg(&p2[xi]);
+            const float th = (V + a.g * (o.x * o.x + o.y * o.y)) * a.ph.h;
+            const float2 in = phase_rot(o, -th);               // the phase's input
+            float2 lam = v[r];
+            gq += phase_adjoint(lam, in, V, a.g, a.ph.h) * (a.L0x * xt.y + a.L0y * yt.y);
+            v[r] = lam;
+        }
+        fft_pencil<N, E, false>(v, sb, j, 1, stw);
+        kinetic_axis<E, TP, true>(v, T.kinx, j, a.sx, 0);
+        fft_pencil<N, E, true>(v, sb, j, 1, stw);
+#pragma unroll
+        for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
+        float q1[1] = {2.f * a.ph.h * gq};
+        block_sum<1>(q1, T.part_row + (size_t)blockIdx.x * NQ, red);
+        double S[1];
+        if (last_block_total<1>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0) *a.gout = S[0];
+        return;
     }
 
     constexpr bool STORE = !(MODE == ROW_REDUCE_R || MODE == ROW_OBS);
@@ -709,6 +782,26 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
             fft_pencil<N, E, true>(v, sb, j, 1, tw);
         }
 
+        if constexpr (MODE == COL_ADJ) {
+            // v = lambda; T_y^H, then the adjoint of the opening half phase
+            // whose input psi2 is the step's initial state
+            kinetic_axis<E, TP, true>(v, T.kiny, j, a.sy, 0);
+            fft_pencil<N, E, true>(v, sb, j, 1, tw);
+            const float4 xt = __ldg(&T.xtab[c0 + c]);
+            const PotCoefs pc = col_coefs(a, xt);
+            float gq = 0.f;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int yi = j + r * TP;
+                const float4 yt = __ldg(&T.ytab[yi]);
+                float V = pot_at(pc, yt);
+                if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
+                const float2 in = __ldg(&a.psi2[(size_t)yi * a.nx + c0 + c]);
+                gq += phase_adjoint(v[r], in, V, a.g, a.ph.h) * (a.L0x * xt.y + a.L0y * yt.y);
+            }
+            q[0] += 2.f * a.ph.h * gq;
+        }
+
         if constexpr (MODE == COL_T_PR) {
             const float4 xt = __ldg(&T.xtab[c0 + c]);
             const PotCoefs pc = col_coefs(a, xt);
@@ -771,6 +864,12 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
         double S[3];
         if (last_block_total<3>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
             finalize_fields(S, a.red, T.sc);
+    }
+    if constexpr (MODE == COL_ADJ) {
+        float q1[1] = {q[0]};
+        block_sum<1>(q1, T.part_col + (size_t)blockIdx.x * NQ, red);
+        double S[1];
+        if (last_block_total<1>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0) *a.gout = S[0];
     }
     if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // tile read before exit
 }
@@ -1048,6 +1147,64 @@ __global__ void kinetic_tables_kernel(Tables T, int nx, int ny, double Lx, doubl
     }
 }
 
+// ------------------------------------------------------------------ adjoint: terminal pieces
+// Spectrum times the kinetic energy density: f_k <- f_k (kx^2 + ky^2) / 2m
+// (k in FFT order), for H psi = F^-1[(k^2/2m) F psi] + ... in the terminal
+// adjoint dJ/dconj(psi_T) of the final energy.
+__global__ void kin_energy_mul_kernel(float2 *f, int nx, int ny, double Lx, double Ly, double m)
+{
+    const size_t n = (size_t)nx * ny;
+    const double ax = 2.0 * M_PI / Lx, ay = 2.0 * M_PI / Ly;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)(i / nx);
+        const double kx = ax * (x < nx / 2 ? x : x - nx), ky = ay * (y < ny / 2 ? y : y - ny);
+        const float e = (float)((kx * kx + ky * ky) / (2.0 * m));
+        f[i] = make_float2(f[i].x * e, f[i].y * e);
+    }
+}
+
+// S0 + i S1 = sum conj(phi) psi, S2 = sum |psi|^2 L (L = dV/dv of the
+// lattice control), without the cell area; the last CTA stores them in sums[0].
+__global__ void __launch_bounds__(256) adj_overlap_kernel(const float2 *__restrict__ psi,
+                                                          const float2 *__restrict__ phi, Tables T, int nx,
+                                                          int ny, float L0x, float L0y)
+{
+    __shared__ double red[32 * NQ];
+    const size_t n = (size_t)nx * ny;
+    float q[3] = {0.f, 0.f, 0.f};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)(i / nx);
+        const float2 v = psi[i], f = phi[i];
+        q[0] += f.x * v.x + f.y * v.y;
+        q[1] += f.x * v.y - f.y * v.x;
+        q[2] += (v.x * v.x + v.y * v.y) * (L0x * __ldg(&T.xtab[x]).y + L0y * __ldg(&T.ytab[y]).y);
+    }
+    block_sum<3>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
+    double S[3];
+    if (last_block_total<3>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) T.sc->sums[0][k] = S[k];
+}
+
+// lam <- dxdy (lam + (V(T) + g |psi|^2) psi + c phi), lam holding the
+// kinetic part F^-1[(k^2/2m) F psi] on entry: the terminal adjoint of
+// J = E(psi_T) + |<phi|psi_T>|^2 with c = <phi|psi_T>.
+__global__ void adj_terminal_kernel(float2 *__restrict__ lam, const float2 *__restrict__ psi,
+                                    const float2 *__restrict__ phi, const PassArgs a, float c_re, float c_im,
+                                    float dxdy)
+{
+    const size_t n = (size_t)a.nx * a.ny;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % a.nx), y = (int)(i / a.nx);
+        const PotCoefs pc = row_coefs(a, __ldg(&a.T.ytab[y]));
+        float V = pot_at(pc, __ldg(&a.T.xtab[x]));
+        if (a.V) V += a.V_scale * __ldg(&a.V[i]);
+        const float2 v = psi[i], f = phi[i], k = lam[i];
+        const float w = V + a.g * (v.x * v.x + v.y * v.y);
+        lam[i] = make_float2(dxdy * (k.x + w * v.x + c_re * f.x - c_im * f.y),
+                             dxdy * (k.y + w * v.y + c_re * f.y + c_im * f.x));
+    }
+}
+
 __global__ void timeout_probe_kernel(DevScalars *sc, int spins)
 {
     __shared__ __align__(8) uint64_t bar;
@@ -1107,6 +1264,7 @@ template <int N> static cudaError_t row_dispatch_mode(int mode, const PassArgs &
     case ROW_FFT_F: return row_launch<N, ROW_FFT_F>(a, s);
     case ROW_FFT_I: return row_launch<N, ROW_FFT_I>(a, s);
     case ROW_OBS: return row_launch<N, ROW_OBS>(a, s);
+    case ROW_ADJ: return row_launch<N, ROW_ADJ>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1159,6 +1317,7 @@ template <int N> static cudaError_t col_dispatch_mode(int mode, const PassArgs &
     case COL_FFT_F: return col_launch<N, COL_FFT_F>(a, map, s);
     case COL_FFT_I: return col_launch<N, COL_FFT_I>(a, map, s);
     case COL_OBS: return col_launch<N, COL_OBS>(a, map, s);
+    case COL_ADJ: return col_launch<N, COL_ADJ>(a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1299,6 +1458,32 @@ cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, do
 {
     const int n = nx > ny ? nx : ny;
     kinetic_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(T, nx, ny, Lx, Ly, m, dt, imag);
+    return cudaGetLastError();
+}
+
+static int grid_for(size_t n, int cap)
+{
+    const size_t b = (n + 255) / 256;
+    return (int)(b < (size_t)cap ? b : (size_t)cap);
+}
+
+cudaError_t launch_kin_energy_mul(float2 *f, int nx, int ny, double Lx, double Ly, double m, cudaStream_t s)
+{
+    kin_energy_mul_kernel<<<grid_for((size_t)nx * ny, 4 * 148), 256, 0, s>>>(f, nx, ny, Lx, Ly, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_overlap(const float2 *psi, const float2 *phi, const Tables &T, int nx, int ny, float L0x,
+                               float L0y, cudaStream_t s)
+{
+    adj_overlap_kernel<<<grid_for((size_t)nx * ny, 1024), 256, 0, s>>>(psi, phi, T, nx, ny, L0x, L0y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_terminal(float2 *lam, const float2 *psi, const float2 *phi, const PassArgs &a, float c_re,
+                                float c_im, float dxdy, cudaStream_t s)
+{
+    adj_terminal_kernel<<<grid_for((size_t)a.nx * a.ny, 4 * 148), 256, 0, s>>>(lam, psi, phi, a, c_re, c_im, dxdy);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,8 @@ GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_step_many",
            "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
            "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_launch_count",
-           "gpe_overlaps_static", "gpe_destroy", "gpe_last_error", "gpe_status_string")
+           "gpe_overlaps_static", "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_destroy",
+           "gpe_last_error", "gpe_status_string")
 
 
 class gpe_potential(ctypes.Structure):
@@ -85,6 +86,9 @@ def load() -> ctypes.CDLL:
         "gpe_sync": (c_int, [c_void_p]),
         "gpe_debug_timeout_probe": (c_int, [c_void_p, c_int]),
         "gpe_overlaps_static": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p,
+                                        P(c_double)]),
+        "gpe_adjoint_workspace_size": (c_size_t, [c_int, c_int, c_int]),
+        "gpe_adjoint_lattice": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_size_t, P(c_double),
                                         P(c_double)]),
         "gpe_destroy": (None, [c_void_p]),
         "gpe_last_error": (c_char_p, [c_void_p]),
@@ -193,6 +197,19 @@ def gpe_overlaps_static(psi_ptr: int, nx: int, ny: int, Lx: float, Ly: float, kc
     s = load().gpe_overlaps_static(c_void_p(psi_ptr), nx, ny, Lx, Ly, kc, c_void_p(stream_handle), out)
     _check(None, s)
     return out[0], out[1], out[2]
+
+
+def gpe_adjoint_workspace_size(nx: int, ny: int, nsteps: int) -> int:
+    return load().gpe_adjoint_workspace_size(nx, ny, nsteps)
+
+
+def gpe_adjoint_lattice(ctx, nsteps: int, dt: float, phi_ptr: int, ws_ptr: int, ws_bytes: int, nctrl: int):
+    """(J, [dJ/dv_i]) of the lattice-depth control; raises GPEError on a bad status."""
+    J = c_double()
+    grad = (c_double * max(nctrl, 1))()
+    _check(ctx, load().gpe_adjoint_lattice(ctx, int(nsteps), float(dt), c_void_p(phi_ptr), c_void_p(ws_ptr),
+                                           ws_bytes, ctypes.byref(J), grad))
+    return J.value, [grad[i] for i in range(nctrl)]
 
 
 def gpe_destroy(ctx):
