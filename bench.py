@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch elementwise baseline leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-control leg")
     return ap.parse_args()
 
 
@@ -216,6 +217,65 @@ def cufft_baseline(psis, p, dt, steps, dev):
     return out
 
 
+# ------------------------------------------------------------------ adjoint leg
+def adjoint_leg(dev, with_oracle):
+    """The adjoint-control workload (512^2, 4000 real-time steps, 200 lattice
+    control points): one gpe_adjoint_lattice call (checkpointed forward and
+    reverse sweep) timed end to end, the adjoint passes timed with events,
+    and, beside it, the FP64 oracle adjoint on a bounded sample of steps."""
+    import numpy as np
+    import torch
+
+    import gpe_inputs as gi
+    from paper_2404_14401_b300 import Simulation
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.adjoint_control()
+    p, n, dt, steps = w["params"], w["params"]["nx"], w["dt"], w["steps"]
+    psi0 = w["psi0"]().astype(np.complex64)
+    phi = torch.from_numpy(w["phi"]().astype(np.complex64)).to(dev)
+    sim = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
+    sim.set_potential(p)
+    sim.set_psi(psi0)
+    sim.adjoint_lattice(phi, 64, dt)                      # warm-up (tables, modules)
+    sim.set_psi(psi0)
+    sim.t = 0.0
+    sim.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, grad = sim.adjoint_lattice(phi, steps, dt)
+    wall = time.perf_counter() - t0
+    rms, rn = abi.gpe_profile_read_kind(sim.ctx, abi.GPE_PASS_ADJ_ROW)
+    cms, cn = abi.gpe_profile_read_kind(sim.ctx, abi.GPE_PASS_ADJ_COL)
+    sim.profile(False)
+    peak, peak_kind = measured_hbm_peak()
+    dom_ms, dom = max((rms / max(rn, 1), "ROW_ADJ"), (cms / max(cn, 1), "COL_ADJ"))
+    alg = 24 * n * n                                      # lambda read + write, forward state read
+    out = {"workload": f"adjoint control {n}x{n}, {steps} real-time steps, {len(p['ctrl_v'])} lattice control "
+                       "points, J = E(psi_T) + |<phi|psi_T>|^2",
+           "value": n * n * steps / wall, "unit": "pt*steps/s (checkpointed forward + reverse sweep)",
+           "wall_s": wall, "J": J, "grad_norm": float(np.linalg.norm(grad)),
+           "adjoint_row_pass_ms": rms / max(rn, 1), "adjoint_col_pass_ms": cms / max(cn, 1),
+           "roofline": {"bound": "hbm", "kernel": f"{'row' if dom == 'ROW_ADJ' else 'col'}_kernel<{n},{dom}>",
+                        "achieved": alg / (dom_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / (dom_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                        "alg_bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs",
+                        "note": "the 2 MB state stays in L2 across passes"}}
+    if with_oracle:
+        import oracle
+        x0 = psi0.astype(np.complex128)
+        f = w["phi"]()
+        t1 = time.perf_counter()
+        oracle.adjoint(p, x0, f, 2, dt)
+        per = (time.perf_counter() - t1) / 2
+        k = max(2, int(8.0 / per))
+        t1 = time.perf_counter()
+        oracle.adjoint(p, x0, f, k, dt)
+        osec = time.perf_counter() - t1
+        out["cpu_baseline"] = {"value": n * n * k / osec, "unit": out["unit"], "cores": oracle.threads(),
+                               "kind": "oracle", "sample": f"FP64 adjoint of the first {k} steps ({osec:.1f} s)"}
+    return out
+
+
 # ------------------------------------------------------------------ CPU oracle leg
 def oracle_sample(n, budget_s=12.0, min_steps=1):
     """Time the FP64 oracle as it stands on one trajectory of the workload:
@@ -383,6 +443,10 @@ def run_ours(args, rank, world, local_rank):
                  "lockstep_value": lv * world, "lockstep_ms_per_step": lms,
                  "ours_over_cufft": ours / cv, "ours_over_cufft_lockstep": ours / lv}
 
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        adj = adjoint_leg(dev, not args.no_cpu)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, k, secs, thr = oracle_sample(n)
@@ -405,6 +469,7 @@ def run_ours(args, rank, world, local_rank):
                      "avg_launch_ms": dom_ms, "row_pass_ms": row_ms, "col_pass_ms": col_ms},
         "cpu_baseline": cpu,
         "cufft_baseline": cufft,
+        "adjoint": adj,
         "e2e": {"value": total_pts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": f"one job of {e2e_steps} steps: pinned h2d of every psi, gpe_step_many, d2h of every psi + observables"},

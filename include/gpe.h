@@ -171,6 +171,15 @@ gpe_status gpe_profile(gpe_ctx *ctx, int enable);
 gpe_status gpe_profile_read(gpe_ctx *ctx, double *row_ms, int *row_launches, double *col_ms,
                             int *col_launches);
 
+/* Per-kind variant of gpe_profile_read: milliseconds and launch count of the
+ * timed launches of one kind since the last read of that kind (then reset).
+ * Kinds: GPE_PASS_ROW, GPE_PASS_COL (forward passes), GPE_PASS_OTHER (tables,
+ * pointwise kernels), GPE_PASS_ADJ_ROW, GPE_PASS_ADJ_COL (adjoint passes).
+ * Errors: GPE_EINVAL for an unknown kind, GPE_ECUDA. */
+enum { GPE_PASS_ROW = 0, GPE_PASS_COL = 1, GPE_PASS_OTHER = 2, GPE_PASS_ADJ_ROW = 3, GPE_PASS_ADJ_COL = 4,
+       GPE_PASS_KINDS = 5 };
+gpe_status gpe_profile_read_kind(gpe_ctx *ctx, int kind, double *ms, int *launches);
+
 /* Number of kernels this context has launched since it was created. */
 long long gpe_launch_count(const gpe_ctx *ctx);
 

@@ -61,8 +61,8 @@ struct gpe_ctx {
     bool prof;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
-    double prof_ms[2];
-    int prof_n[2];
+    double prof_ms[GPE_PASS_KINDS];   // per pass kind: see gpe_profile_read_kind
+    int prof_n[GPE_PASS_KINDS];
     char err[256];
 };
 
@@ -347,8 +347,10 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->group_rows = getenv("GPE_NO_GROUP_ROWS") ? 0 : 1;
     c->launches = 0;
     c->prof = false;
-    c->prof_ms[0] = c->prof_ms[1] = 0.0;
-    c->prof_n[0] = c->prof_n[1] = 0;
+    for (int k = 0; k < GPE_PASS_KINDS; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
     memset(&c->pot, 0, sizeof(c->pot));
     c->pot.V_scale = 1.0;
     c->pot.N = 1.0;
@@ -617,14 +619,15 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
             ar.gout = gdev + 2 * s + 1;
             ar.L0x = (float)c->pot.lat_V0x;
             ar.L0y = (float)c->pot.lat_V0y;
-            TRY(timed_launch(c, 0, [&] { return launch_row(ROW_ADJ, ar, c->stream); }, "adjoint row pass"));
+            TRY(timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream); },
+                             "adjoint row pass"));
             PassArgs ac = pass_args(c, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0);
             ac.psi = lam;
             ac.psi2 = st + (size_t)(s - s0) * P;
             ac.gout = gdev + 2 * s;
             ac.L0x = ar.L0x;
             ac.L0y = ar.L0y;
-            TRY(timed_launch(c, 1, [&] { return launch_col(COL_ADJ, ac, lam_map, c->stream); },
+            TRY(timed_launch(c, GPE_PASS_ADJ_COL, [&] { return launch_col(COL_ADJ, ac, lam_map, c->stream); },
                              "adjoint column pass"));
         }
     }
@@ -795,13 +798,12 @@ gpe_status gpe_profile(gpe_ctx *c, int enable)
     return GPE_OK;
 }
 
-gpe_status gpe_profile_read(gpe_ctx *c, double *row_ms, int *row_launches, double *col_ms, int *col_launches)
+static gpe_status drain_profile(gpe_ctx *c)
 {
-    if (!c) return GPE_EINVAL;
     TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
     for (auto &p : c->ev_pending) {
         float ms = 0.f;
-        if (p.first < 2 && cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+        if (p.first < GPE_PASS_KINDS && cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
             c->prof_ms[p.first] += ms;
             c->prof_n[p.first] += 1;
         }
@@ -809,12 +811,30 @@ gpe_status gpe_profile_read(gpe_ctx *c, double *row_ms, int *row_launches, doubl
         c->ev_free.push_back(p.second.second);
     }
     c->ev_pending.clear();
+    return GPE_OK;
+}
+
+gpe_status gpe_profile_read(gpe_ctx *c, double *row_ms, int *row_launches, double *col_ms, int *col_launches)
+{
+    if (!c) return GPE_EINVAL;
+    TRY(drain_profile(c));
     if (row_ms) *row_ms = c->prof_ms[0];
     if (row_launches) *row_launches = c->prof_n[0];
     if (col_ms) *col_ms = c->prof_ms[1];
     if (col_launches) *col_launches = c->prof_n[1];
     c->prof_ms[0] = c->prof_ms[1] = 0.0;
     c->prof_n[0] = c->prof_n[1] = 0;
+    return GPE_OK;
+}
+
+gpe_status gpe_profile_read_kind(gpe_ctx *c, int kind, double *ms, int *launches)
+{
+    if (!c || kind < 0 || kind >= GPE_PASS_KINDS) return GPE_EINVAL;
+    TRY(drain_profile(c));
+    if (ms) *ms = c->prof_ms[kind];
+    if (launches) *launches = c->prof_n[kind];
+    c->prof_ms[kind] = 0.0;
+    c->prof_n[kind] = 0;
     return GPE_OK;
 }
 

@@ -21,7 +21,7 @@ GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 
 EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_step_many",
            "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
-           "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_launch_count",
+           "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_profile_read_kind", "gpe_launch_count",
            "gpe_overlaps_static", "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_destroy",
            "gpe_last_error", "gpe_status_string")
 
@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
         "gpe_step_many": (c_int, [P(c_void_p), c_int, c_int, c_double, c_int]),
         "gpe_profile": (c_int, [c_void_p, c_int]),
         "gpe_profile_read": (c_int, [c_void_p, P(c_double), P(c_int), P(c_double), P(c_int)]),
+        "gpe_profile_read_kind": (c_int, [c_void_p, c_int, P(c_double), P(c_int)]),
         "gpe_launch_count": (ctypes.c_longlong, [c_void_p]),
         "gpe_observables": (c_int, [c_void_p, P(gpe_obs)]),
         "gpe_set_psi": (c_int, [c_void_p, c_void_p, c_int]),
@@ -146,6 +147,16 @@ def gpe_profile_read(ctx) -> dict:
     _check(ctx, load().gpe_profile_read(ctx, ctypes.byref(rm), ctypes.byref(rn), ctypes.byref(cm),
                                         ctypes.byref(cn)))
     return dict(row_ms=rm.value, row_launches=rn.value, col_ms=cm.value, col_launches=cn.value)
+
+
+GPE_PASS_ROW, GPE_PASS_COL, GPE_PASS_OTHER, GPE_PASS_ADJ_ROW, GPE_PASS_ADJ_COL = range(5)
+
+
+def gpe_profile_read_kind(ctx, kind: int) -> tuple:
+    """(milliseconds, launches) of one pass kind since its last read."""
+    ms, n = c_double(), c_int()
+    _check(ctx, load().gpe_profile_read_kind(ctx, int(kind), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def gpe_launch_count(ctx) -> int:

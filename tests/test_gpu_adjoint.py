@@ -105,3 +105,20 @@ def test_adjoint_argument_errors():
     with pytest.raises(abi.GPEError) as e:
         abi.gpe_adjoint_lattice(s.ctx, steps, dt, f.data_ptr(), small.data_ptr(), 1024, len(p["ctrl_v"]))
     assert e.value.status == abi.GPE_ENOMEM
+
+
+def test_adjoint_passes_are_profiled_per_kind():
+    from paper_2404_14401_b300 import gpe as abi
+    from paper_2404_14401_b300 import Simulation
+    p, psi0, phi, steps, dt = case(steps=9)
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    s.set_psi(np.asarray(psi0, dtype=np.complex64))
+    s.profile(True)
+    s.adjoint_lattice(phi, steps, dt)
+    for kind in (abi.GPE_PASS_ADJ_ROW, abi.GPE_PASS_ADJ_COL):
+        ms, n = abi.gpe_profile_read_kind(s.ctx, kind)
+        assert n == steps and ms > 0.0
+    assert abi.gpe_profile_read_kind(s.ctx, abi.GPE_PASS_ADJ_ROW) == (0.0, 0)     # reset by the read
+    with pytest.raises(abi.GPEError):
+        abi.gpe_profile_read_kind(s.ctx, 5)
