@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch elementwise baseline leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-control leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched phase-diagram sweep leg")
     return ap.parse_args()
 
 
@@ -217,6 +218,62 @@ def cufft_baseline(psis, p, dt, steps, dev):
     return out
 
 
+# ------------------------------------------------------------------ sweep leg
+def sweep_leg(dev, steps=40):
+    """The batched phase-diagram sweep (384 cavity instances: 128 at 256^2,
+    192 at 512^2, 64 at 1024^2, imaginary time): lockstep gpe_step_many over
+    all instances (two library streams, interior steps replayed from a CUDA
+    graph) against the plain per-instance loop of gpe_step on one stream."""
+    import numpy as np
+    import torch
+
+    import gpe_inputs as gi
+    from paper_2404_14401_b300 import Simulation
+    ws = gi.phase_diagram_sweep()
+    sims, tuned = [], {}
+    for w in ws:
+        p = w["params"]
+        s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
+        s.set_potential(p)
+        s.set_psi(torch.from_numpy(w["psi0"]().astype(np.complex64)).to(dev))
+        if p["nx"] not in tuned:                          # one autotuner run per grid size
+            tuned[p["nx"]] = s.tune(w["dt"], imag=True)
+        s.variants = tuned[p["nx"]]["variants"]
+        sims.append(s)
+    pts = sum(s.nx * s.ny for s in sims)
+    dt = ws[0]["dt"]
+    Simulation.step_many(sims, 5, dt, imag=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sum(s.launches for s in sims)
+    e0.record()
+    Simulation.step_many(sims, steps, dt, imag=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sum(s.launches for s in sims) - l0
+    # the per-instance loop: every instance steps alone, one after the other
+    base_steps = 10
+    torch.cuda.synchronize()
+    e0.record()
+    for s in sims:
+        s.step(base_steps, dt, imag=True)
+    e1.record()
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1)
+    status = [s.sync() for s in sims]
+    return {"workload": "phase-diagram sweep: 384 cavity instances (128 x 256^2, 192 x 512^2, 64 x 1024^2), "
+                        "imaginary time, (eta, Delta_c) uniform in [0,4] x [-5,0]",
+            "points": pts, "steps": steps, "value": pts * steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / steps, "gpu_launches_per_step": launches / steps,
+            "bytes_per_point_step": 48,
+            "hbm_frac_of_measured": pts * 48 / (ms / steps * 1e-3) / 1e9 / measured_hbm_peak()[0],
+            "per_instance_loop": {"value": pts * base_steps / (bms * 1e-3), "ms_per_step": bms / base_steps},
+            "lockstep_over_loop": (pts * steps / ms) / (pts * base_steps / bms),
+            "status_nonzero": sum(1 for x in status if x),
+            "autotuner": {str(k): v for k, v in tuned.items()}}
+
+
 # ------------------------------------------------------------------ adjoint leg
 def adjoint_leg(dev, with_oracle):
     """The adjoint-control workload (512^2, 4000 real-time steps, 200 lattice
@@ -361,6 +418,11 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
 
+    # the autotuner's choice of pass variants for this grid, applied to every trajectory
+    tune = sims[0].tune(dt)
+    for s in sims:
+        s.variants = tune["variants"]
+
     # warm-up, then exactly `steps` lockstep steps of all trajectories
     Simulation.step_many(sims, args.warmup, dt)
     torch.cuda.synchronize()
@@ -443,6 +505,10 @@ def run_ours(args, rank, world, local_rank):
                  "lockstep_value": lv * world, "lockstep_ms_per_step": lms,
                  "ours_over_cufft": ours / cv, "ours_over_cufft_lockstep": ours / lv}
 
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = sweep_leg(dev)
+
     adj = None
     if rank == 0 and not args.no_adjoint:
         adj = adjoint_leg(dev, not args.no_cpu)
@@ -462,7 +528,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32), f64 reductions",
         "data": "synthetic (seeded Gaussian relaxed in imaginary time, + seeded noise)",
-        "config": config(args, world),
+        "config": dict(config(args, world), pass_variants=tune),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes,
@@ -470,6 +536,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "cufft_baseline": cufft,
         "adjoint": adj,
+        "sweep": sweep,
         "e2e": {"value": total_pts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": f"one job of {e2e_steps} steps: pinned h2d of every psi, gpe_step_many, d2h of every psi + observables"},

@@ -124,6 +124,28 @@ def lattice_real_time(n: int = 2048, L: float = 40.0, seed: int = 1) -> dict:
                 psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed))
 
 
+def phase_diagram_sweep(seed: int = 3, L: float = 20.0, dt: float = 1e-3, g: float = 100.0,
+                        counts=((256, 128), (512, 192), (1024, 64))) -> list:
+    """Batched sweep of cavity instances (Sec. 5.3 phase diagram): for each
+    (grid n, count) pair, `count` instances on an n x n grid, with (eta, Delta_c)
+    drawn uniformly from [0, 4] x [-5, 0]; trap, U0 = -0.5, kappa = 1, pump
+    lattice on, imaginary time.  Returns a list of workload dicts."""
+    total = sum(c for _, c in counts)
+    u = uniform(seed, 2 * total)
+    out, k = [], 0
+    for n, cnt in counts:
+        for _ in range(cnt):
+            p = potential_defaults()
+            p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=g, wx=1.0, wy=1.0, cavity=1,
+                     eta=4.0 * u[2 * k], dc=-5.0 * u[2 * k + 1], U0=-0.5, kappa=1.0,
+                     kc=2.0 * np.pi, Nat=1.0, pump_lattice=1)
+            out.append(dict(params=p, dt=dt, imag=True,
+                            psi0=lambda n=n, k=k: gaussian_state(n, n, L, L, 1.5, 1e-3, seed + 1000 + k,
+                                                                 checker=0.1, kc=2.0 * np.pi)))
+            k += 1
+    return out
+
+
 def target_gaussian(nx: int, ny: int, Lx: float, Ly: float) -> np.ndarray:
     """Ground state of the isotropic trap in oscillator units, exp(-r^2/2)/sqrt(pi)."""
     x, y = grid_axis(nx, Lx), grid_axis(ny, Ly)

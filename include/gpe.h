@@ -206,6 +206,29 @@ long long gpe_launch_count(const gpe_ctx *ctx);
 gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, double Lx, double Ly, double kc,
                                void *stream, double *out);
 
+/* ---- Pass variants and the autotuner ----------------------------------
+ * Each pass has more than one kernel design for some grids: the row pass
+ * of 512..2048-point rows has a grouped persistent variant (one CTA per SM,
+ * tables in shared memory, TMA double buffering), rows and columns of 4096
+ * points a streaming persistent variant; every grid has the one-shot
+ * variant (a CTA per group of rows or per TMA tile of columns).  A context
+ * starts with every applicable variant on.  The bits select them: */
+enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
+int gpe_get_pass_variants(const gpe_ctx *ctx);                /* -1 for a null context */
+gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants); /* GPE_EINVAL outside 0..7 */
+/* Autotuner: times every applicable variant of the interior row pass
+ * (potential phase + T_x) and column pass (T_y) of a step of dt in `mode`
+ * on a copy of psi in scratch_dev (>= nx*ny*8 bytes, 256-byte aligned,
+ * borrowed; psi itself is not changed), `reps` launches each after one
+ * warm-up, with CUDA events on the context's stream, and selects the fastest
+ * row and column variants for this context.  variants_out receives the bits;
+ * times_out (5 doubles or NULL) the mean milliseconds of the row pass
+ * one-shot / grouped / streaming and the column pass one-shot / streaming,
+ * NaN where a variant does not apply.  Synchronises the stream.  Errors:
+ * GPE_EINVAL, GPE_ECUDA. */
+gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, size_t scratch_bytes, int reps,
+                    int *variants_out, double *times_out);
+
 /* ---- Adjoint of the real-time split step (lattice-depth control) ------
  * For the control of the lattice depth v(t) (ctrl_target GPE_CTRL_LATTICE:
  * V = trap + v(t) (lat_V0x cos^2(kx x) + lat_V0y cos^2(ky y)), Sec. 5.2 Eq. 9)

@@ -90,6 +90,25 @@ class Simulation:
         """n lockstep steps on several simulations (one pass schedule)."""
         abi.gpe_step_many([s.ctx for s in sims], n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
 
+    def tune(self, dt: float, imag: bool = False, reps: int = 5) -> dict:
+        """Time the applicable kernel variants of the interior passes on a copy
+        of psi and keep the fastest (gpe_tune).  Returns the chosen variant bits
+        and the per-variant milliseconds."""
+        torch = self.torch
+        scratch = torch.empty(8 * self.nx * self.ny, dtype=torch.uint8, device=self.device)
+        v, t = abi.gpe_tune(self.ctx, dt, abi.GPE_IMAG if imag else abi.GPE_REAL, scratch.data_ptr(),
+                            scratch.numel(), reps)
+        keys = ("row_one_shot", "row_grouped", "row_streaming", "col_one_shot", "col_streaming")
+        return {"variants": v, "ms": {k: (None if x != x else x) for k, x in zip(keys, t)}}
+
+    @property
+    def variants(self) -> int:
+        return abi.gpe_get_pass_variants(self.ctx)
+
+    @variants.setter
+    def variants(self, v: int):
+        abi.gpe_set_pass_variants(self.ctx, v)
+
     def adjoint_lattice(self, phi, nsteps: int, dt: float):
         """J = E(psi_T) + |<phi|psi_T>|^2 after nsteps real-time steps from the
         current state, and dJ/dv_i for the lattice control values set with

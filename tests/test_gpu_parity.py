@@ -357,3 +357,63 @@ def test_lockstep_lanes_match_single_context_stepping(imag):
     Simulation.step_many(sims, 20, dt, imag)
     for s, ref in zip(sims, alone):
         assert np.array_equal(s.get_psi(), ref)
+
+
+# ------------------------------------------------------------------ graph replay
+# With two or more contexts and no time-dependent control, gpe_step_many
+# captures one interior lockstep step into a CUDA graph and replays it.  The
+# result and the launch count must equal those of per-pass launches.
+@pytest.mark.parametrize("imag", [False, True])
+def test_graph_replay_matches_per_pass_launches(imag, monkeypatch):
+    from paper_2404_14401_b300 import Simulation
+    cases = [(256, 256, False), (128, 512, True), (64, 64, False)]
+    dt = 2e-3 if imag else 5e-4
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
+    runs = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("GPE_NO_GRAPH", env)
+        sims = []
+        for k, (nx, ny, cav) in enumerate(cases):
+            p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+            if cav:
+                p.update(cavity=1, eta=2.0, U0=-0.5, dc=-2.0, kappa=1.0, kc=2 * np.pi, Nat=1.0, pump_lattice=1)
+            s = sim_for(p)
+            s.set_psi(c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-2, seed=50 + k, checker=0.2,
+                                            kc=p.get("kc", 0.0))))
+            sims.append(s)
+        l0 = [s.launches for s in sims]
+        Simulation.step_many(sims, 12, dt, imag)
+        runs.append(([s.get_psi() for s in sims], [s.launches - a for s, a in zip(sims, l0)]))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    assert runs[0][1] == runs[1][1]
+
+
+# ------------------------------------------------------------------ autotuner
+@pytest.mark.parametrize("nx,ny", [(2048, 64), (4096, 64), (64, 4096), (128, 128)])
+def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    s = sim_for(p)
+    psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=60))
+    s.set_psi(psi0)
+    r = s.tune(w["dt"], reps=3)
+    v, ms = r["variants"], {k: (np.nan if x is None else x) for k, x in r["ms"].items()}
+    assert np.array_equal(s.get_psi(), psi0)                     # the tuner worked on a copy
+    assert s.variants == v
+    group_ok = nx in (512, 1024, 2048)
+    assert np.isnan(ms["row_grouped"]) != group_ok
+    assert np.isnan(ms["row_streaming"]) != (nx == 4096)
+    assert np.isnan(ms["col_streaming"]) != (ny == 4096)
+    rows = [ms["row_one_shot"], ms["row_grouped"], ms["row_streaming"]]
+    best = int(np.nanargmin(rows))
+    assert (v & abi.GPE_VARIANT_GROUP_ROWS != 0) == (best == 1)
+    assert (v & abi.GPE_VARIANT_STREAM_ROWS != 0) == (best == 2)
+    assert (v & abi.GPE_VARIANT_STREAM_COLS != 0) == (not np.isnan(ms["col_streaming"])
+                                                       and ms["col_streaming"] < ms["col_one_shot"])
+    # stepping with the chosen variants still matches the oracle
+    s.step(20, w["dt"], False)
+    ref, _ = oracle.evolve(p, psi0.astype(np.complex128), 20, w["dt"], False)
+    assert rel_l2(s.get_psi(), ref) < 1e-5
