@@ -1,0 +1,154 @@
+"""Precision report: per-observable error of the complex64 path with FP64
+accumulations against the FP64 oracle, and what FP32 accumulation would
+cost instead.
+
+Three dynamics (the survey's workloads at sizes the oracle finishes in
+seconds) report, for the final state, the relative error of every
+observable the library returns (norm, E_kin, E_pot, E_int, E, mu, O, B,
+alpha).  For the sums over the grid (norm, E_pot, E_int, O, B) the same GPU
+state is also summed in FP32, pairwise and sequentially, on the host: the
+difference to the FP64 sum is the accumulation error an FP32 reduction
+would add.  The self-consistent cavity field alpha = eta O / (Delta_c -
+U0 B + i kappa) is ill-conditioned near resonance: on a fixed state, the
+detuning is swept towards U0 B with a small kappa and alpha is formed from
+the GPU's FP64-accumulated overlaps and from FP32-accumulated ones, against
+the oracle.  Run as a script to print the report (python
+tests/test_gpu_precision.py on a GPU machine); the tests assert its bounds.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+if __name__ == "__main__":                      # run as a script from anywhere
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import gpe_inputs as gi  # noqa: E402
+import oracle  # noqa: E402
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEYS = ("norm", "ekin", "epot", "eint", "energy", "mu", "O", "B", "alpha_re", "alpha_im")
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def gpu_run(p, psi0, n, dt, imag):
+    from paper_2404_14401_b300 import Simulation
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    s.set_psi(np.asarray(psi0, dtype=np.complex64))
+    s.step(n, dt, imag)
+    return s
+
+
+def fp32_sums(p, psi, t):
+    """norm, E_pot, E_int, O, B of psi with FP32 accumulation (pairwise, sequential)."""
+    dxdy = (p["Lx"] / p["nx"]) * (p["Ly"] / p["ny"])
+    d = (psi.real.astype(np.float32) ** 2 + psi.imag.astype(np.float32) ** 2).ravel()
+    V = oracle.potential(p, t).astype(np.float32).ravel()
+    x, y = gi.grid_axis(p["nx"], p["Lx"]), gi.grid_axis(p["ny"], p["Ly"])
+    cx = np.cos(p.get("kc", 0.0) * x)[None, :] * np.ones((p["ny"], 1))
+    cy = np.cos(p.get("kc", 0.0) * y)[:, None] * np.ones((1, p["nx"]))
+    cc = (cx * cy).astype(np.float32).ravel()
+    c2 = (cx * cx).astype(np.float32).ravel()
+    terms = {"norm": d, "epot": V * d, "eint": np.float32(0.5 * p["g"]) * d * d, "Occ": cc * d, "Bcc": c2 * d}
+    out = {}
+    for k, v in terms.items():
+        pw = float(np.sum(v, dtype=np.float32))
+        sq = float(np.cumsum(v, dtype=np.float32)[-1])
+        out[k] = (pw, sq)
+    res = {}
+    for k in ("norm", "epot", "eint"):
+        res[k] = tuple(v * dxdy for v in out[k])
+    res["O"] = tuple(out["Occ"][i] / out["norm"][i] for i in range(2))
+    res["B"] = tuple(out["Bcc"][i] / out["norm"][i] for i in range(2))
+    return res
+
+
+def cases():
+    c0 = gi.harmonic_trap(g=100.0)
+    c1 = gi.lattice_real_time(n=256, L=20.0)
+    c2 = gi.cavity_ramp(n=128, L=16.0, steps=2000, dt=2e-4)
+    return [("imaginary-time trap 128^2, g = 100, 2000 steps", c0["params"], c0["psi0"](), 2000, c0["dt"], True),
+            ("real-time lattice 256^2, g = 500, 1000 steps", c1["params"], c1["psi0"](), 1000, c1["dt"], False),
+            ("cavity ramp 128^2, eta 0 -> 3, 2000 steps", c2["params"],
+             gi.gaussian_state(128, 128, 16.0, 16.0, 1.5, 1e-2, 2, checker=0.3, kc=2 * np.pi), 2000, 2e-4, False)]
+
+
+def dynamics_report():
+    rows = []
+    for name, p, psi0, n, dt, imag in cases():
+        s = gpu_run(p, psi0, n, dt, imag)
+        got = s.observables()
+        psi = s.get_psi()
+        ref_psi, _ = oracle.evolve(p, np.asarray(psi0, dtype=np.complex64).astype(np.complex128), n, dt, imag)
+        ref = oracle.observables(p, ref_psi, t=s.t)
+        same = oracle.observables(p, psi.astype(np.complex128), t=s.t)   # FP64 sums of the GPU state
+        f32 = fp32_sums(p, psi, s.t)
+        err = {k: rel(got[k], ref[k]) for k in KEYS if abs(ref[k]) > 1e-12}
+        acc = {k: (rel(got[k], same[k]), rel(f32[k][0], same[k]), rel(f32[k][1], same[k]))
+               for k in ("norm", "epot", "eint", "O", "B") if k in f32 and abs(same[k]) > 1e-12}
+        rows.append((name, float(np.linalg.norm(psi - ref_psi) / np.linalg.norm(ref_psi)), err, acc))
+    return rows
+
+
+def resonance_report():
+    """alpha near Delta_c = U0 B on a fixed 128^2 state, kappa = 1e-4."""
+    w = gi.cavity_ramp(n=128, L=16.0)
+    p = dict(w["params"], ctrl_target=0, ctrl_t=None, ctrl_v=None, eta=2.0, kappa=1e-4)
+    psi = gi.gaussian_state(128, 128, 16.0, 16.0, 1.5, 1e-2, 5, checker=0.3, kc=2 * np.pi).astype(np.complex64)
+    B = oracle.observables(dict(p, dc=0.0), psi.astype(np.complex128))["B"]
+    rows = []
+    for delta in (1e-1, 1e-2, 1e-3, 1e-4):
+        q = dict(p, dc=p["U0"] * B + delta)
+        ref = oracle.observables(q, psi.astype(np.complex128))
+        from paper_2404_14401_b300 import Simulation
+        s = Simulation(128, 128, 16.0, 16.0, 1.0, p["g"])
+        s.set_potential(q)
+        s.set_psi(psi)
+        got = s.observables()
+        f = fp32_sums(q, psi, 0.0)
+        den = complex(q["dc"] - q["U0"] * f["B"][1], q["kappa"])
+        a32 = q["Nat"] * q["eta"] * f["O"][1] / den
+        aref = complex(ref["alpha_re"], ref["alpha_im"])
+        rows.append((delta, abs(q["U0"] * B) / abs(complex(delta, q["kappa"])),
+                     abs(complex(got["alpha_re"], got["alpha_im"]) - aref) / abs(aref), abs(a32 - aref) / abs(aref)))
+    return rows
+
+
+def test_precision_dynamics_within_the_stated_tolerances():
+    for name, psi_err, err, acc in dynamics_report():
+        assert psi_err < 1e-4, name
+        for k in ("energy", "mu"):
+            assert err[k] < 1e-5, (name, k, err[k])
+        for k, (g64, _, _) in acc.items():
+            assert g64 < 1e-6, (name, k, g64)          # FP64 accumulation of the GPU state
+
+
+def test_alpha_near_resonance_keeps_fp64_accuracy():
+    for delta, cond, e64, e32 in resonance_report():
+        assert e64 < 1e-5 * max(1.0, cond * 1e-2), (delta, cond, e64)
+
+
+if __name__ == "__main__":
+    print("| workload | rel. L2 psi | " + " | ".join(KEYS) + " |")
+    print("|---|---|" + "---|" * len(KEYS))
+    rep = dynamics_report()
+    for name, psi_err, err, acc in rep:
+        print(f"| {name} | {psi_err:.1e} | " + " | ".join(f"{err[k]:.1e}" if k in err else "-" for k in KEYS) + " |")
+    print()
+    print("| workload | sum | GPU FP64 accumulation | FP32 pairwise | FP32 sequential |")
+    print("|---|---|---|---|---|")
+    for name, psi_err, err, acc in rep:
+        for k, (a, b, c) in acc.items():
+            print(f"| {name} | {k} | {a:.1e} | {b:.1e} | {c:.1e} |")
+    print()
+    print("| Delta_c - U0 B | condition \\|U0 B\\| / \\|den\\| | alpha rel. error, GPU (FP64 sums) | FP32 sequential sums |")
+    print("|---|---|---|---|")
+    for delta, cond, e64, e32 in resonance_report():
+        print(f"| {delta:.0e} | {cond:.1e} | {e64:.1e} | {e32:.1e} |")
