@@ -21,6 +21,8 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                   (no closed form): "parity unpinned" for that trajectory.
   observables     pinned: E = mu = 1 for the oscillator ground state,
                   kinetic energy of a Gaussian in closed form
+  momentum pops   pinned: plane-wave superpositions give |c_n|^2 exactly;
+                  the Raman-Nath populations of a lattice flash
   adjoint         pinned: gradient of J = E(psi_T) + |<phi|psi_T>|^2 with
                   respect to the lattice control values against central
                   finite differences of the forward oracle; zero gradient
@@ -83,8 +85,9 @@ def _load():
         lib.orc_potential.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_threads.argtypes = []
         lib.orc_adjoint.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_momentum_populations.argtypes = [pp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
         for f in (lib.orc_fft1, lib.orc_fft2, lib.orc_evolve, lib.orc_observables,
-                  lib.orc_potential, lib.orc_threads, lib.orc_adjoint):
+                  lib.orc_potential, lib.orc_threads, lib.orc_adjoint, lib.orc_momentum_populations):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -194,3 +197,16 @@ def adjoint(p: dict, psi0: np.ndarray, phi: np.ndarray, steps: int, dt: float, t
     if rc:
         raise ValueError("orc_adjoint needs a lattice control table and no cavity")
     return float(J[0]), grad[:int(P.s.nctrl)]
+
+
+def momentum_populations(p: dict, psi: np.ndarray, axis: int, k0: float, nmax: int) -> np.ndarray:
+    """Fractions of |F psi|^2 in the momentum windows |k - 2 n k0| < k0 along
+    `axis` (0: x, 1: y), n = -nmax..nmax (Kapitza-Dirac readout, Sec. 5.2)."""
+    P = Params(p)
+    x = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros(2 * nmax + 1)
+    rc = _load().orc_momentum_populations(P.ref(), _dptr(x.view(np.float64)), int(axis), float(k0), int(nmax),
+                                          _dptr(out))
+    if rc:
+        raise ValueError("orc_momentum_populations: bad arguments")
+    return out

@@ -516,3 +516,38 @@ int orc_adjoint(const orc_params *p, const double *psi0, const double *phi_d, in
     free(lam); free(st); free(sb);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Momentum-state populations (Sec. 5.2, Kapitza-Dirac): the fraction   */
+/* of sum_k |F psi|^2 whose momentum along `axis` (0: x, 1: y) lies     */
+/* within k0 of 2 n k0, summed over the other axis, n = -nmax..nmax.    */
+/* A momentum exactly between two windows (|k - 2 n k0| = k0) goes to   */
+/* the window of smaller |n|.                                            */
+/* ------------------------------------------------------------------ */
+int orc_momentum_populations(const orc_params *p, const double *data, int axis, double k0, int nmax,
+                             double *out)
+{
+    if (!is_pow2(p->nx) || !is_pow2(p->ny) || (axis != 0 && axis != 1) || !(k0 > 0.0) || nmax < 0) return -1;
+    size_t n = (size_t)p->nx * p->ny;
+    cplx *f = malloc(sizeof(cplx) * n);
+    memcpy(f, data, sizeof(cplx) * n);
+    orc_fft2((double *)f, p->nx, p->ny, -1);
+    for (int i = 0; i <= 2 * nmax; i++) out[i] = 0.0;
+    double total = 0.0;
+    for (int y = 0; y < p->ny; y++)
+        for (int x = 0; x < p->nx; x++) {
+            cplx v = f[(size_t)y * p->nx + x];
+            double w = creal(v) * creal(v) + cimag(v) * cimag(v);
+            total += w;
+            double k = axis == 0 ? kcoord(x, p->nx, p->Lx) : kcoord(y, p->ny, p->Ly);
+            double r = k / (2.0 * k0);                 /* window n: |r - n| <= 1/2 */
+            int b = (int)floor(fabs(r) + 0.5);
+            if (fabs(fabs(r) - (b - 0.5)) < 1e-12 && b > 0) b -= 1;   /* ties to smaller |n| */
+            if (b > nmax) continue;
+            int idx = (r < 0 ? -b : b) + nmax;
+            out[idx] += w;
+        }
+    for (int i = 0; i <= 2 * nmax; i++) out[i] /= total;
+    free(f);
+    return 0;
+}

@@ -289,3 +289,31 @@ def test_cavity_potential_terms_at_lattice_points():
     assert abs(V[i0, i0] - (vp + p["U0"] * abs(alpha) ** 2 + 2 * p["eta"] * alpha.real)) < 1e-12
     i1 = 8 + 1                                         # x = 0.5 = pi/(2 kc) for kc = pi
     assert abs(V[i0, i1] - vp) < 1e-12
+
+
+# ------------------------------------------------------------ momentum populations (Sec. 5.2)
+def test_momentum_populations_of_plane_wave_superpositions():
+    """sum_n c_n exp(2 i n k y) times any x envelope has populations |c_n|^2 / sum |c|^2."""
+    L, k = 2 * np.pi, 2.0
+    x, y = gi.grid_axis(32, L), gi.grid_axis(64, L)
+    c = {-2: 0.3, -1: 0.5j, 0: 1.0, 1: -0.4, 3: 0.2}
+    psi = sum(v * np.exp(2j * n * k * y)[:, None] for n, v in c.items()) * np.exp(-x ** 2)[None, :]
+    p = base(32, L)
+    p["ny"] = 64
+    got = oracle.momentum_populations(p, psi, 1, k, 3)
+    w = np.array([abs(c.get(n, 0.0)) ** 2 for n in range(-3, 4)])
+    assert np.max(np.abs(got - w / w.sum())) < 1e-12
+    # along x the same state has everything in n = 0 (the x envelope is narrow in k only
+    # up to its own width, so use a wide window)
+    assert oracle.momentum_populations(p, psi, 0, 50.0, 1)[1] > 1 - 1e-12
+
+
+def test_momentum_populations_raman_nath_flash():
+    L, k, V0, t = 2 * np.pi, 1.0, 100.0, 0.02
+    p = base(8, L, lat_V0y=V0, lat_ky=k)
+    p["ny"] = 64
+    out, _ = oracle.evolve(p, gi.uniform_state(8, 64, L, L), 200, t / 200, imag=False)
+    got = oracle.momentum_populations(p, out, 1, k, 3)
+    assert np.max(np.abs(got - lattice_populations(out, p, 3))) < 1e-12
+    rn = scipy.special.jv(np.arange(-3, 4), V0 * t / 2) ** 2
+    assert np.max(np.abs(got - rn)) < 2e-3
