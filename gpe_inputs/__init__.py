@@ -124,6 +124,19 @@ def lattice_real_time(n: int = 2048, L: float = 40.0, seed: int = 1) -> dict:
                 psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed))
 
 
+def kapitza_dirac(n: int = 256, L: float = 16.0, V0: float = 100.0, tau: float = 0.01, dt: float = 1e-4,
+                  g: float = 0.0, seed: int = 5) -> dict:
+    """Lattice flash along y (Sec. 5.2): trap + V0 cos^2(k y) with k = 2 pi
+    switched on for a duration tau (control v(t) = 1 up to tau, 0 from
+    tau + dt/10 on), read out as momentum populations of |2 n k>."""
+    p = potential_defaults()
+    k = 2.0 * np.pi
+    p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=g, wx=1.0, wy=1.0, lat_V0y=V0, lat_ky=k, ctrl_target=1,
+             ctrl_t=np.array([0.0, tau, tau + 0.1 * dt]), ctrl_v=np.array([1.0, 1.0, 0.0]))
+    return dict(params=p, dt=dt, imag=False, steps=int(round(tau / dt)), k=k,
+                psi0=lambda: gaussian_state(n, n, L, L, 1.5, 0.0, seed))
+
+
 def phase_diagram_sweep(seed: int = 3, L: float = 20.0, dt: float = 1e-3, g: float = 100.0,
                         counts=((256, 128), (512, 192), (1024, 64))) -> list:
     """Batched sweep of cavity instances (Sec. 5.3 phase diagram): for each

@@ -206,6 +206,18 @@ long long gpe_launch_count(const gpe_ctx *ctx);
 gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, double Lx, double Ly, double kc,
                                void *stream, double *out);
 
+/* Momentum-state populations (Kapitza-Dirac readout, Sec. 5.2): the
+ * fractions of sum_k |F psi|^2 whose momentum along `axis` (0: x, 1: y) lies
+ * within k0 of 2 n k0, summed over the other axis, for n = -nmax..nmax
+ * (0 <= nmax <= 3); a momentum exactly between two windows counts for the
+ * smaller |n|.  pop_out: 2 nmax + 1 doubles, n = -nmax first.  The transform
+ * runs on a copy of psi in scratch_dev (>= nx*ny*8 bytes, 256-byte aligned,
+ * borrowed); psi is not changed.  FP64 accumulation.  Synchronises the
+ * stream.  Errors: GPE_EINVAL, GPE_ENONFINITE (empty or non-finite state),
+ * GPE_ECUDA. */
+gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax, void *scratch_dev,
+                                    size_t scratch_bytes, double *pop_out);
+
 /* ---- Pass variants and the autotuner ----------------------------------
  * Each pass has more than one kernel design for some grids: the row pass
  * of 512..2048-point rows has a grouped persistent variant (one CTA per SM,

@@ -90,6 +90,13 @@ class Simulation:
         """n lockstep steps on several simulations (one pass schedule)."""
         abi.gpe_step_many([s.ctx for s in sims], n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
 
+    def momentum_populations(self, axis: int, k0: float, nmax: int = 3) -> np.ndarray:
+        """Kapitza-Dirac readout: fractions of the momentum distribution in the
+        windows |k - 2 n k0| < k0 along `axis`, n = -nmax..nmax."""
+        torch = self.torch
+        scratch = torch.empty(8 * self.nx * self.ny, dtype=torch.uint8, device=self.device)
+        return np.array(abi.gpe_momentum_populations(self.ctx, axis, k0, nmax, scratch.data_ptr(), scratch.numel()))
+
     def tune(self, dt: float, imag: bool = False, reps: int = 5) -> dict:
         """Time the applicable kernel variants of the interior passes on a copy
         of psi and keep the fastest (gpe_tune).  Returns the chosen variant bits

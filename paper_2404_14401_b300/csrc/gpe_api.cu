@@ -923,6 +923,37 @@ gpe_status gpe_profile_read_kind(gpe_ctx *c, int kind, double *ms, int *launches
 
 long long gpe_launch_count(const gpe_ctx *c) { return c ? c->launches : -1; }
 
+gpe_status gpe_momentum_populations(gpe_ctx *c, int axis, double k0, int nmax, void *scratch_dev,
+                                    size_t scratch_bytes, double *pop_out)
+{
+    if (!c || !pop_out || (axis != 0 && axis != 1) || !(k0 > 0.0) || !isfinite(k0) || nmax < 0 || nmax > 3)
+        return c ? fail(c, GPE_EINVAL, "gpe_momentum_populations: axis %d k0 %g nmax %d", axis, k0, nmax)
+                 : GPE_EINVAL;
+    const size_t bytes = sizeof(float2) * (size_t)c->nx * c->ny;
+    if (!scratch_dev || ((uintptr_t)scratch_dev & 255u) || scratch_bytes < bytes)
+        return fail(c, GPE_EINVAL, "gpe_momentum_populations: scratch of %zu bytes (256-aligned) needed", bytes);
+    float2 *f = (float2 *)scratch_dev;
+    TRY(cuda_check(c, cudaMemcpyAsync(f, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy"));
+    CUtensorMap fmap;
+    TRY(encode_map(c, f, &fmap));
+    PhaseArgs none;
+    memset(&none, 0, sizeof(none));
+    PassArgs a = pass_args(c, none, red_at(c, c->t), 0, 0);
+    a.psi = f;
+    TRY(timed_launch(c, 0, [&] { return launch_row(ROW_FFT_F, a, c->stream); }, "populations fft"));
+    TRY(timed_launch(c, 1, [&] { return launch_col(COL_FFT_F, a, fmap, c->stream); }, "populations fft"));
+    TRY(timed_launch(c, 2, [&] {
+        return launch_kbin(f, c->T, c->nx, c->ny, c->Lx, c->Ly, axis, k0, nmax, c->stream);
+    }, "populations"));
+    DevScalars h;
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, c->T.sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
+    const double total = h.sums[0][7];
+    if (!(total > 0.0) || !isfinite(total)) return fail(c, GPE_ENONFINITE, "gpe_momentum_populations: total %g", total);
+    for (int i = 0; i <= 2 * nmax; ++i) pop_out[i] = h.sums[0][i] / total;
+    return GPE_OK;
+}
+
 int gpe_get_pass_variants(const gpe_ctx *c)
 {
     if (!c) return -1;

@@ -108,6 +108,8 @@ cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly,
 cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly,
                                   double m, double dt, int imag, cudaStream_t s);
 cudaError_t launch_timeout_probe(DevScalars *sc, int spins, cudaStream_t s);
+cudaError_t launch_kbin(const float2 *f, const Tables &T, int nx, int ny, double Lx, double Ly, int axis, double k0,
+                        int nmax, cudaStream_t s);
 cudaError_t launch_kin_energy_mul(float2 *f, int nx, int ny, double Lx, double Ly, double m, cudaStream_t s);
 cudaError_t launch_adj_overlap(const float2 *psi, const float2 *phi, const Tables &T, int nx, int ny, float L0x,
                                float L0y, cudaStream_t s);

@@ -1205,6 +1205,40 @@ __global__ void adj_terminal_kernel(float2 *__restrict__ lam, const float2 *__re
     }
 }
 
+// ------------------------------------------------------------------ momentum populations
+// Kapitza-Dirac readout (Sec. 5.2) on a spectrum f = F psi: the weight
+// |f|^2 of every mode whose momentum along `axis` is within k0 of 2 n k0
+// (n = -nmax..nmax, nmax <= 3; a momentum exactly between two windows goes
+// to the smaller |n|), summed over the other axis; q[7] is the total.  The
+// last CTA stores the 8 sums in sums[0].
+__global__ void __launch_bounds__(256) kbin_kernel(const float2 *__restrict__ f, Tables T, int nx, int ny, double Lx,
+                                                   double Ly, int axis, double k0, int nmax)
+{
+    __shared__ double red[32 * NQ];
+    const size_t n = (size_t)nx * ny;
+    float q[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)(i / nx);
+        const float2 v = f[i];
+        const float w = v.x * v.x + v.y * v.y;
+        q[7] += w;
+        const int m = axis == 0 ? (x < nx / 2 ? x : x - nx) : (y < ny / 2 ? y : y - ny);
+        const double r = 2.0 * M_PI / (axis == 0 ? Lx : Ly) * m / (2.0 * k0);
+        int b = (int)floor(fabs(r) + 0.5);
+        if (b > 0 && fabs(fabs(r) - (b - 0.5)) < 1e-12) b -= 1;
+        if (b <= nmax) {
+            const int idx = (r < 0 ? -b : b) + nmax;
+#pragma unroll
+            for (int k = 0; k < 7; ++k)
+                if (k == idx) q[k] += w;                 // register-resident bins
+        }
+    }
+    block_sum<8>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
+    double S[8];
+    if (last_block_total<8>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) T.sc->sums[0][k] = S[k];
+}
+
 __global__ void timeout_probe_kernel(DevScalars *sc, int spins)
 {
     __shared__ __align__(8) uint64_t bar;
@@ -1484,6 +1518,13 @@ cudaError_t launch_adj_terminal(float2 *lam, const float2 *psi, const float2 *ph
                                 float c_im, float dxdy, cudaStream_t s)
 {
     adj_terminal_kernel<<<grid_for((size_t)a.nx * a.ny, 4 * 148), 256, 0, s>>>(lam, psi, phi, a, c_re, c_im, dxdy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kbin(const float2 *f, const Tables &T, int nx, int ny, double Lx, double Ly, int axis, double k0,
+                        int nmax, cudaStream_t s)
+{
+    kbin_kernel<<<grid_for((size_t)nx * ny, 1024), 256, 0, s>>>(f, T, nx, ny, Lx, Ly, axis, k0, nmax);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_step_many",
            "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
            "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_profile_read_kind", "gpe_launch_count",
-           "gpe_overlaps_static", "gpe_get_pass_variants", "gpe_set_pass_variants", "gpe_tune",
+           "gpe_overlaps_static", "gpe_momentum_populations", "gpe_get_pass_variants", "gpe_set_pass_variants", "gpe_tune",
            "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_destroy",
            "gpe_last_error", "gpe_status_string")
 
@@ -89,6 +89,7 @@ def load() -> ctypes.CDLL:
         "gpe_debug_timeout_probe": (c_int, [c_void_p, c_int]),
         "gpe_overlaps_static": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p,
                                         P(c_double)]),
+        "gpe_momentum_populations": (c_int, [c_void_p, c_int, c_double, c_int, c_void_p, c_size_t, P(c_double)]),
         "gpe_get_pass_variants": (c_int, [c_void_p]),
         "gpe_set_pass_variants": (c_int, [c_void_p, c_int]),
         "gpe_tune": (c_int, [c_void_p, c_double, c_int, c_void_p, c_size_t, c_int, P(c_int), P(c_double)]),
@@ -212,6 +213,14 @@ def gpe_overlaps_static(psi_ptr: int, nx: int, ny: int, Lx: float, Ly: float, kc
     s = load().gpe_overlaps_static(c_void_p(psi_ptr), nx, ny, Lx, Ly, kc, c_void_p(stream_handle), out)
     _check(None, s)
     return out[0], out[1], out[2]
+
+
+def gpe_momentum_populations(ctx, axis: int, k0: float, nmax: int, scratch_ptr: int, scratch_bytes: int) -> list:
+    """Populations of the momentum windows around 2 n k0 along `axis`, n = -nmax..nmax."""
+    out = (c_double * (2 * nmax + 1))()
+    _check(ctx, load().gpe_momentum_populations(ctx, int(axis), float(k0), int(nmax), c_void_p(scratch_ptr),
+                                                scratch_bytes, out))
+    return [out[i] for i in range(2 * nmax + 1)]
 
 
 GPE_VARIANT_GROUP_ROWS, GPE_VARIANT_STREAM_ROWS, GPE_VARIANT_STREAM_COLS = 1, 2, 4

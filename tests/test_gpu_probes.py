@@ -1,0 +1,55 @@
+"""Probe workloads on the GPU (Sec. 5.2 Kapitza-Dirac flash).
+
+The momentum-population readout (gpe_momentum_populations) is compared with
+the oracle's on the same state, and a whole flash (trap + lattice pulse
+through the control table, then the readout) with the oracle's flash; with
+g = 0 and a short pulse both follow the Raman-Nath Bessel populations.
+"""
+import numpy as np
+import pytest
+import scipy.special
+
+import gpe_inputs as gi
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sim(p, psi):
+    from paper_2404_14401_b300 import Simulation
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    s.set_psi(np.asarray(psi, dtype=np.complex64))
+    return s
+
+
+def test_population_readout_matches_oracle_on_a_given_state():
+    w = gi.kapitza_dirac(n=128, L=16.0)
+    p = w["params"]
+    x, y = gi.grid_axis(128, 16.0), gi.grid_axis(128, 16.0)
+    k = w["k"]
+    c = {-2: 0.3, -1: 0.5j, 0: 1.0, 1: -0.4}
+    psi = (sum(v * np.exp(2j * n * k * y)[:, None] for n, v in c.items())
+           * np.exp(-(x ** 2)[None, :] / 4 - (y ** 2)[:, None] / 8)).astype(np.complex64)
+    s = sim(p, psi)
+    got = s.momentum_populations(1, k, 3)
+    ref = oracle.momentum_populations(p, psi.astype(np.complex128), 1, k, 3)
+    assert np.max(np.abs(got - ref)) < 1e-6
+    assert np.array_equal(s.get_psi(), psi)                       # psi untouched
+
+
+@pytest.mark.parametrize("g", [0.0, 50.0])
+def test_kapitza_dirac_flash_matches_oracle(g):
+    w = gi.kapitza_dirac(g=g)
+    p, steps, dt, k = w["params"], w["steps"], w["dt"], w["k"]
+    psi0 = w["psi0"]()
+    s = sim(p, psi0)
+    s.step(steps + 20, dt, False)                                 # flash, then 20 steps with the lattice off
+    got = s.momentum_populations(1, k, 3)
+    ref_psi, _ = oracle.evolve(p, psi0.astype(np.complex64).astype(np.complex128), steps + 20, dt, False)
+    ref = oracle.momentum_populations(p, ref_psi, 1, k, 3)
+    assert np.max(np.abs(got - ref)) < 1e-5
+    if g == 0.0:
+        rn = scipy.special.jv(np.arange(-3, 4), p["lat_V0y"] * w["steps"] * dt / 2) ** 2
+        assert np.max(np.abs(got - rn)) < 2e-2                     # Raman-Nath, up to kinetic and trap phases
