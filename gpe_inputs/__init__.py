@@ -103,7 +103,7 @@ def potential_defaults() -> dict:
     return dict(wx=0.0, wy=0.0, lat_V0x=0.0, lat_V0y=0.0, lat_kx=0.0, lat_ky=0.0,
                 Varr=None, V_scale=1.0, cavity=0, eta=0.0, U0=0.0, dc=0.0,
                 kappa=0.0, kc=0.0, Nat=1.0, pump_lattice=1, ctrl_target=0,
-                ctrl_t=None, ctrl_v=None)
+                ctrl_t=None, ctrl_v=None, probe_omega=0.0, probe_delta=0.0, probe_phi=0.0)
 
 
 def harmonic_trap(n: int = 128, L: float = 20.0, g: float = 0.0, seed: int = 0) -> dict:

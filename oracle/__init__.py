@@ -65,6 +65,7 @@ class _Params(ctypes.Structure):
         ("ctrl_target", ctypes.c_int), ("nctrl", ctypes.c_int),
         ("ctrl_t", ctypes.POINTER(ctypes.c_double)), ("ctrl_v", ctypes.POINTER(ctypes.c_double)),
         ("paper_order", ctypes.c_int),
+        ("probe_omega", ctypes.c_double), ("probe_delta", ctypes.c_double), ("probe_phi", ctypes.c_double),
     ]
 
 
@@ -106,7 +107,7 @@ class Params:
         for name, _ in _Params._fields_:
             if name in ("Varr", "ctrl_t", "ctrl_v", "nctrl", "paper_order"):
                 continue
-            setattr(s, name, p[name])
+            setattr(s, name, p.get(name, 0.0) if name.startswith("probe_") else p[name])
         if p.get("Varr") is not None:
             v = np.ascontiguousarray(p["Varr"], dtype=np.float64)
             assert v.shape == (p["ny"], p["nx"])

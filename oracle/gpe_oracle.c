@@ -77,6 +77,9 @@ typedef struct {
     const double *ctrl_t, *ctrl_v;
     /* 0: V/2 - T - V/2 (default), 1: T/2 - V - T/2 as printed in Eq. (4)      */
     int paper_order;
+    /* on-axis cavity probe (Sec. 5.4): alpha' = alpha + delta_alpha(t) with
+     * delta_alpha = Omega_c exp(i (Delta_p t + phi)) / (Delta_c - U0 B + i kappa) */
+    double probe_omega, probe_delta, probe_phi;
 } orc_params;
 
 enum { CTRL_NONE = 0, CTRL_LATTICE = 1, CTRL_ETA = 2 };
@@ -224,7 +227,8 @@ static cplx cavity_alpha(const orc_params *p, const cplx *psi, double t)
     overlaps ov = density_overlaps(p, psi);
     double eta = eta_at(p, t);
     cplx den = (p->dc - p->U0 * ov.B) + I * p->kappa;
-    return p->Nat * eta * ov.O / den;
+    cplx probe = p->probe_omega * cexp(I * (p->probe_delta * t + p->probe_phi));
+    return (p->Nat * eta * ov.O + probe) / den;
 }
 
 /* V(x, y, t) for a given cavity field alpha, Eqs. (9)-(13) plus trap.   */

@@ -317,3 +317,37 @@ def test_momentum_populations_raman_nath_flash():
     assert np.max(np.abs(got - lattice_populations(out, p, 3))) < 1e-12
     rn = scipy.special.jv(np.arange(-3, 4), V0 * t / 2) ** 2
     assert np.max(np.abs(got - rn)) < 2e-3
+
+
+# ------------------------------------------------------------ cavity probe (Sec. 5.4)
+def test_probe_alone_gives_the_driven_cavity_field():
+    """eta = 0: the field is only the probe's, Omega exp(i(Dp t + phi)) / (Delta_c - U0 B + i kappa),
+    with B the density overlap of the state (direct quadrature here)."""
+    p = cavity_params(eta=0.0, probe_omega=0.3, probe_delta=7.0, probe_phi=0.4)
+    psi = gi.gaussian_state(32, 32, p["Lx"], p["Ly"], 1.0, 1e-2, seed=31, checker=0.2, kc=p["kc"])
+    t = 0.123
+    o = oracle.observables(p, psi, t=t)
+    x, y = gi.grid_axis(32, p["Lx"]), gi.grid_axis(32, p["Ly"])
+    d = np.abs(psi) ** 2
+    B = np.sum(np.cos(p["kc"] * x)[None, :] ** 2 * d) / np.sum(d)
+    want = 0.3 * np.exp(1j * (7.0 * t + 0.4)) / (p["dc"] - p["U0"] * B + 1j * p["kappa"])
+    assert abs(complex(o["alpha_re"], o["alpha_im"]) - want) < 1e-14
+
+
+def test_probe_response_is_linear_for_weak_probes():
+    """The change of the field trajectory scales with Omega_c for weak probes."""
+    p = cavity_params(eta=1.5)
+    psi0 = gi.gaussian_state(32, 32, p["Lx"], p["Ly"], 1.0, 1e-2, seed=32, checker=0.2, kc=p["kc"])
+    a0 = oracle.evolve(p, psi0, 60, 1e-3, False)[1]
+    d = [oracle.evolve(dict(p, probe_omega=om, probe_delta=5.0, probe_phi=0.2), psi0, 60, 1e-3, False)[1] - a0
+         for om in (1e-4, 2e-4)]
+    assert abs(d[0]) > 1e-6
+    assert abs(d[1] / d[0] - 2.0) < 1e-3
+
+
+def test_zero_probe_is_the_plain_cavity():
+    p = cavity_params(eta=1.5)
+    psi0 = gi.gaussian_state(32, 32, p["Lx"], p["Ly"], 1.0, 1e-2, seed=33, checker=0.2, kc=p["kc"])
+    a, _ = oracle.evolve(p, psi0, 20, 1e-3, False)
+    b, _ = oracle.evolve(dict(p, probe_omega=0.0, probe_delta=5.0, probe_phi=1.0), psi0, 20, 1e-3, False)
+    assert np.array_equal(a, b)
