@@ -137,6 +137,20 @@ def kapitza_dirac(n: int = 256, L: float = 16.0, V0: float = 100.0, tau: float =
                 psi0=lambda: gaussian_state(n, n, L, L, 1.5, 0.0, seed))
 
 
+def bragg_probe(n: int = 512, L: float = 20.0, eta: float = 2.0, omega: float = 0.05, delta_p: float = 20.0,
+                phi: float = 0.3, steps: int = 4000, dt: float = 2e-4, seed: int = 6) -> dict:
+    """Bragg spectroscopy of the cavity soft mode (Sec. 5.4): the cavity
+    setup of the self-organisation workload at a fixed pump eta, with a weak
+    on-axis probe of strength omega detuned by delta_p; the response is the
+    cavity field alpha(t)."""
+    p = potential_defaults()
+    p.update(nx=n, ny=n, Lx=L, Ly=L, m=1.0, g=100.0, wx=1.0, wy=1.0, cavity=1, eta=eta, U0=-0.5, dc=-2.0,
+             kappa=1.0, kc=2.0 * np.pi, Nat=1.0, pump_lattice=1, probe_omega=omega, probe_delta=delta_p,
+             probe_phi=phi)
+    return dict(params=p, dt=dt, imag=False, steps=steps,
+                psi0=lambda: gaussian_state(n, n, L, L, 1.5, 1e-3, seed, checker=0.2, kc=2.0 * np.pi))
+
+
 def phase_diagram_sweep(seed: int = 3, L: float = 20.0, dt: float = 1e-3, g: float = 100.0,
                         counts=((256, 128), (512, 192), (1024, 64))) -> list:
     """Batched sweep of cavity instances (Sec. 5.3 phase diagram): for each

@@ -85,6 +85,11 @@ typedef struct {
     int ctrl_target;
     int nctrl;
     const double *ctrl_t, *ctrl_v;
+    /* on-axis cavity probe (Sec. 5.4, Bragg spectroscopy of the soft mode):
+     * alpha' = alpha + probe_omega exp(i (probe_delta t + probe_phi))
+     *                  / (Delta_c - U0 B + i kappa), used for V_c, V_i and the
+     * observables; 0 = no probe */
+    double probe_omega, probe_delta, probe_phi;
 } gpe_potential;
 
 /* Observables of the current state at the context's time t (host struct).

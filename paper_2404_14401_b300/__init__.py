@@ -44,7 +44,7 @@ class Simulation:
         torch = self.torch
         pot = abi.gpe_potential()
         for k in ("wx", "wy", "lat_V0x", "lat_V0y", "lat_kx", "lat_ky", "V_scale", "cavity", "eta", "U0",
-                  "dc", "kappa", "kc", "pump_lattice", "ctrl_target"):
+                  "dc", "kappa", "kc", "pump_lattice", "ctrl_target", "probe_omega", "probe_delta", "probe_phi"):
             setattr(pot, k, p.get(k, 0) if k != "V_scale" else p.get(k, 1.0))
         pot.N = p.get("Nat", p.get("N", 1.0))
         keep = []

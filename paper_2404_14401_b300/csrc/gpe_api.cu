@@ -240,6 +240,10 @@ RedArgs red_at(const gpe_ctx *c, double t)
     r.N = c->pot.N;
     r.dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
     r.cavity = c->pot.cavity;
+    r.probe_omega = c->pot.probe_omega;
+    r.probe_delta = c->pot.probe_delta;
+    r.probe_phi = c->pot.probe_phi;
+    r.t = t;
     return r;
 }
 
@@ -420,6 +424,8 @@ gpe_status gpe_set_potential(gpe_ctx *c, const gpe_potential *p)
         if (!(p->ctrl_t[i] > p->ctrl_t[i - 1]))
             return fail(c, GPE_EINVAL, "control times must increase");
     if (p->cavity && !(p->kappa >= 0.0)) return fail(c, GPE_EINVAL, "kappa must be >= 0");
+    if (!isfinite(p->probe_omega) || !isfinite(p->probe_delta) || !isfinite(p->probe_phi))
+        return fail(c, GPE_EINVAL, "probe parameters must be finite");
     if (p->V && ((uintptr_t)p->V & 3u)) return fail(c, GPE_EINVAL, "potential array misaligned");
     c->pot = *p;
     c->ctrl_t.assign(p->ctrl_t, p->ctrl_t + p->nctrl);
@@ -797,8 +803,9 @@ gpe_status gpe_observables(gpe_ctx *c, gpe_obs *out)
         const double O = S[3] / S[0], B = S[4] / S[0];
         const double eta = eta_at(c, c->t);
         const double dr = c->pot.dc - c->pot.U0 * B, di = c->pot.kappa, den = dr * dr + di * di;
-        const double num = c->pot.N * eta * O;
-        const double ar = den > 0 ? num * dr / den : 0.0, ai = den > 0 ? -num * di / den : 0.0;
+        const double ph = c->pot.probe_delta * c->t + c->pot.probe_phi;
+        const double a = c->pot.N * eta * O + c->pot.probe_omega * cos(ph), b = c->pot.probe_omega * sin(ph);
+        const double ar = den > 0 ? (a * dr + b * di) / den : 0.0, ai = den > 0 ? (b * dr - a * di) / den : 0.0;
         out->O = O;
         out->B = B;
         out->alpha_re = ar;

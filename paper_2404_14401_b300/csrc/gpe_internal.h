@@ -48,6 +48,9 @@ struct PhaseArgs {
 struct RedArgs {
     double eta, U0, dc, kappa, N, dxdy;
     int cavity;
+    // on-axis cavity probe at the time t of the reduction (Sec. 5.4):
+    // alpha' = alpha + Omega_c exp(i (Delta_p t + phi)) / (Delta_c - U0 B + i kappa)
+    double probe_omega, probe_delta, probe_phi, t;
 };
 
 // Row passes (x axis).  T_x = F_x^-1 K_x F_x is the x part of the kinetic

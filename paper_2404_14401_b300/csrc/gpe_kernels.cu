@@ -185,9 +185,12 @@ __device__ void finalize_fields(const double *S, const RedArgs &r, DevScalars *s
             sc->alpha_im = 0.0;
             return;
         }
-        const double num = r.N * r.eta * O;          // alpha = num / (dr + i di)
-        sc->alpha_re = num * dr / den;
-        sc->alpha_im = -num * di / den;
+        // alpha = (num + probe) / (dr + i di), probe = Omega_c exp(i (Delta_p t + phi))
+        double ps = 0.0, pc = 0.0;
+        if (r.probe_omega != 0.0) sincos(r.probe_delta * r.t + r.probe_phi, &ps, &pc);
+        const double a = r.N * r.eta * O + r.probe_omega * pc, b = r.probe_omega * ps;
+        sc->alpha_re = (a * dr + b * di) / den;
+        sc->alpha_im = (b * dr - a * di) / den;
     } else {
         sc->alpha_re = 0.0;
         sc->alpha_im = 0.0;

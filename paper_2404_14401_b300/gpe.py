@@ -35,7 +35,8 @@ class gpe_potential(ctypes.Structure):
                 ("eta", c_double), ("U0", c_double), ("dc", c_double), ("kappa", c_double),
                 ("kc", c_double), ("N", c_double),
                 ("pump_lattice", c_int), ("ctrl_target", c_int), ("nctrl", c_int),
-                ("ctrl_t", ctypes.POINTER(c_double)), ("ctrl_v", ctypes.POINTER(c_double))]
+                ("ctrl_t", ctypes.POINTER(c_double)), ("ctrl_v", ctypes.POINTER(c_double)),
+                ("probe_omega", c_double), ("probe_delta", c_double), ("probe_phi", c_double)]
 
 
 class gpe_obs(ctypes.Structure):

@@ -53,3 +53,26 @@ def test_kapitza_dirac_flash_matches_oracle(g):
     if g == 0.0:
         rn = scipy.special.jv(np.arange(-3, 4), p["lat_V0y"] * w["steps"] * dt / 2) ** 2
         assert np.max(np.abs(got - rn)) < 2e-2                     # Raman-Nath, up to kinetic and trap phases
+
+
+def test_bragg_probe_cavity_field_matches_oracle():
+    """On-axis probe (Sec. 5.4): the cavity field alpha(t), sampled every 40
+    steps, follows the oracle's; the probe visibly changes it."""
+    w = gi.bragg_probe(n=128, L=16.0, steps=400)
+    p, dt = w["params"], w["dt"]
+    psi0 = w["psi0"]().astype(np.complex64)
+    s = sim(p, psi0)
+    quiet = sim(dict(p, probe_omega=0.0), psi0)
+    ref = psi0.astype(np.complex128)
+    t = 0.0
+    for _ in range(10):
+        s.step(40, dt, False)
+        quiet.step(40, dt, False)
+        ref, _ = oracle.evolve(p, ref, 40, dt, False, t0=t)
+        t += 40 * dt
+        got, q = s.observables(), quiet.observables()
+        want = oracle.observables(p, ref, t=t)
+        a, b = complex(got["alpha_re"], got["alpha_im"]), complex(want["alpha_re"], want["alpha_im"])
+        assert abs(a - b) < 1e-5 * abs(b) + 1e-7, (t, a, b)
+        assert abs(a - complex(q["alpha_re"], q["alpha_im"])) > 1e-3 * abs(b)
+    assert float(np.linalg.norm(s.get_psi() - ref) / np.linalg.norm(ref)) < 1e-5
