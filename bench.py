@@ -110,6 +110,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ replicas
+# One process per GPU, each stepping its own batch of trajectories (no data
+# exchange): only the timing is combined, as the maximum over ranks.
+def replica_seed(b, rank):
+    """Noise seed of trajectory b on `rank` (distinct across all ranks)."""
+    return 100 + b + 1000 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (x itself on one process)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -407,7 +425,7 @@ def run_ours(args, rank, world, local_rank):
     sims[0].t = 0.0
     base = sims[0].psi.clone()
     for b, s in enumerate(sims):
-        z = gi.normal(100 + b + 1000 * rank, 2 * n * n).reshape(2, n, n)
+        z = gi.normal(replica_seed(b, rank), 2 * n * n).reshape(2, n, n)
         noise = torch.from_numpy((z[0] + 1j * z[1]).astype(np.complex64)).to(dev)
         x = base * (1 + 1e-3 * noise)
         x = x / torch.sqrt(torch.sum(torch.abs(x) ** 2) * (p["Lx"] / n) * (p["Ly"] / n))
@@ -442,10 +460,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     launches = sum(s.launches for s in sims) - launches0
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     status = [s.sync() for s in sims]
     obs = sims[0].observables()
 
@@ -486,10 +501,7 @@ def run_ours(args, rank, world, local_rank):
         abi.gpe_get_psi(s.ctx, h.data_ptr(), False)
     obs_e2e = sims[0].observables()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     h2d = 8 * n * n * B
     d2h = 8 * n * n * B + 100
 
