@@ -32,7 +32,7 @@ def _rank_main(rank, world, port, out):
 def test_replicas_take_the_maximum_time_and_distinct_inputs():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
