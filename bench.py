@@ -352,7 +352,7 @@ def adjoint_leg(dev, with_oracle):
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_sample(n, budget_s=12.0, min_steps=1):
+def oracle_sample(n, budget_s=16.0, min_steps=1):
     """Time the FP64 oracle as it stands on one trajectory of the workload:
     steps until about budget_s of work.  Returns (pt*steps/s, steps, secs, threads)."""
     import numpy as np
@@ -436,10 +436,10 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
 
-    # the autotuner's choice of pass variants for this grid, applied to every trajectory
-    tune = sims[0].tune(dt)
-    for s in sims:
-        s.variants = tune["variants"]
+    # the autotuner's view of this grid (reported).  The timed run keeps the
+    # default variants, which were measured fastest on this lockstep
+    # workload; the tuner times one grid in isolation, with its data in L2.
+    tune = dict(sims[0].tune(dt), used=sims[0].variants)
 
     # warm-up, then exactly `steps` lockstep steps of all trajectories
     Simulation.step_many(sims, args.warmup, dt)
