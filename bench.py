@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch elementwise baseline leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-control leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched phase-diagram sweep leg")
+    ap.add_argument("--no-grids", action="store_true", help="skip the grid-size leg (1024^2 .. 8192^2)")
     return ap.parse_args()
 
 
@@ -292,6 +293,73 @@ def sweep_leg(dev, steps=40):
             "autotuner": {str(k): v for k, v in tuned.items()}}
 
 
+# ------------------------------------------------------------------ grid-size leg
+GRID_CASES = ((1024, 8, 400), (4096, 2, 200), (8192, 1, 100))   # (n, trajectories, timed steps)
+
+
+def grids_leg(dev):
+    """The real-time lattice workload (box 40, trap + lattice V0 = 5, k = 2 pi,
+    g = 500, dt = 5e-4) at other grid sizes, each batch more than the 126 MB
+    L2 except 1024^2 x 8 (64 MB, the smallest case of the throughput
+    configuration): lockstep steps timed with CUDA events, then the mean
+    duration of each pass kind with the lanes off, against the measured HBM
+    rate at 16 B/point per pass.  psi0 is the normalised Gaussian of width 1.5
+    (built on the device; the rate does not depend on the state)."""
+    import torch
+
+    import gpe_inputs as gi
+    from paper_2404_14401_b300 import Simulation
+    peak, peak_kind = measured_hbm_peak()
+    out = []
+    for n, B, steps in GRID_CASES:
+        w = gi.lattice_real_time(n=n, L=40.0)
+        p, dt = w["params"], w["dt"]
+        x = (torch.arange(n, device=dev, dtype=torch.float64) - n // 2) * (p["Lx"] / n)
+        r2 = x[None, :] ** 2 + x[:, None] ** 2
+        psi0 = torch.exp(-r2 / (2 * 1.5 ** 2))
+        psi0 = (psi0 / torch.sqrt(torch.sum(psi0 ** 2) * (p["Lx"] / n) ** 2)).to(torch.complex64)
+        del x, r2
+        sims = []
+        for _ in range(B):
+            s = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
+            s.set_potential(p)
+            s.set_psi(psi0)
+            sims.append(s)
+        del psi0
+        Simulation.step_many(sims, 5, dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Simulation.step_many(sims, steps, dt)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        for s in sims:
+            s.profile(True)
+        os.environ["GPE_SERIAL_MANY"] = "1"
+        Simulation.step_many(sims, 20, dt)
+        del os.environ["GPE_SERIAL_MANY"]
+        pr = [s.profile_read() for s in sims]
+        for s in sims:
+            s.profile(False)
+        row_ms = sum(q["row_ms"] for q in pr) / sum(q["row_launches"] for q in pr)
+        col_ms = sum(q["col_ms"] for q in pr) / sum(q["col_launches"] for q in pr)
+        status = [s.sync() for s in sims]
+        norm = sims[0].observables()["norm"]
+        pts = n * n * B
+        gbs = lambda t: 16 * n * n / (t * 1e-3) / 1e9          # noqa: E731
+        out.append({"grid": [n, n], "trajectories": B, "resident_bytes": 8 * pts, "steps": steps,
+                    "value": pts * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                    "step_frac_of_measured_hbm": 32 * pts / (ms / steps * 1e-3) / 1e9 / peak,
+                    "row_kernel": row_kernel_name(n), "row_pass_ms": row_ms, "row_frac": gbs(row_ms) / peak,
+                    "col_kernel": col_kernel_name(n), "col_pass_ms": col_ms, "col_frac": gbs(col_ms) / peak,
+                    "norm_after": norm, "status_nonzero": sum(1 for q in status if q)})
+        del sims
+        torch.cuda.empty_cache()
+    return {"workload": "real-time lattice GPE (box 40, V0 = 5, k = 2 pi, g = 500, dt = 5e-4) at other grid sizes",
+            "peak": peak, "peak_source": f"{peak_kind} hbm_gbs", "cases": out}
+
+
 # ------------------------------------------------------------------ adjoint leg
 def adjoint_leg(dev, with_oracle):
     """The adjoint-control workload (512^2, 4000 real-time steps, 200 lattice
@@ -523,6 +591,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_sweep:
         sweep = sweep_leg(dev)
 
+    grids = None
+    if rank == 0 and not args.no_grids:
+        grids = grids_leg(dev)
+
     adj = None
     if rank == 0 and not args.no_adjoint:
         adj = adjoint_leg(dev, not args.no_cpu)
@@ -551,6 +623,7 @@ def run_ours(args, rank, world, local_rank):
         "cufft_baseline": cufft,
         "adjoint": adj,
         "sweep": sweep,
+        "grids": grids,
         "e2e": {"value": total_pts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": f"one job of {e2e_steps} steps: pinned h2d of every psi, gpe_step_many, d2h of every psi + observables"},

@@ -43,15 +43,19 @@ def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
 
 
 def normal(seed: int, n: int) -> np.ndarray:
-    """n standard normals by Box-Muller on consecutive uniform pairs."""
+    """n standard normals by Box-Muller on consecutive uniform pairs (made in
+    chunks of 2^21 pairs; the values depend only on the stream position)."""
     m = (n + 1) // 2
-    u = uniform(seed, 2 * m)
-    u1 = 1.0 - u[0::2]                      # (0, 1]: log is finite
-    u2 = u[1::2]
-    r = np.sqrt(-2.0 * np.log(u1))
     z = np.empty(2 * m)
-    z[0::2] = r * np.cos(2.0 * np.pi * u2)
-    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    chunk = 1 << 21
+    for a in range(0, m, chunk):
+        b = min(m, a + chunk)
+        u = uniform(seed, 2 * (b - a), offset=2 * a)
+        u1 = 1.0 - u[0::2]                  # (0, 1]: log is finite
+        u2 = u[1::2]
+        r = np.sqrt(-2.0 * np.log(u1))
+        z[2 * a:2 * b:2] = r * np.cos(2.0 * np.pi * u2)
+        z[2 * a + 1:2 * b:2] = r * np.sin(2.0 * np.pi * u2)
     return z[:n]
 
 

@@ -242,6 +242,29 @@ def test_full_size_real_time_lattice_first_100_steps(n):
     assert abs(obs["energy"] - r0["energy"]) < 1e-3 * abs(r0["energy"])     # conserved to O(dt^2)
 
 
+@pytest.mark.parametrize("n", [4096, 8192])
+def test_grids_larger_than_l2_match_oracle_and_conserve(n):
+    """The same workload on grids whose state exceeds the 126 MB L2 (128 MB
+    and 512 MB): the first 10 steps element by element against the oracle;
+    then on the GPU alone the energy after 100 steps (conserved to O(dt^2),
+    bound as at 2048^2) and the norm after 1000 (exact for the unitary step)."""
+    w = gi.lattice_real_time(n=n, L=40.0)
+    p = w["params"]
+    psi0 = c64(w["psi0"]())
+    s, got, obs, ref, _ = run_both(p, psi0, 10, w["dt"], False)
+    assert rel_l2(got, ref) < state_tol(10)
+    del got, ref
+    ro = oracle.observables(p, psi0.astype(np.complex128))
+    assert abs(obs["norm"] - ro["norm"]) < 1e-6
+    s.step(90, w["dt"])
+    o = s.observables()
+    assert abs(o["energy"] - ro["energy"]) < 1e-3 * abs(ro["energy"])
+    s.step(900, w["dt"])
+    o = s.observables()
+    assert s.sync() == 0
+    assert abs(o["norm"] - ro["norm"]) < 1e-6
+
+
 # ------------------------------------------------------------------ streaming passes
 # Axes of 4096 points run the persistent, double-buffered row (nx = 4096) and
 # column (ny = 4096) passes; these cases cover their imaginary-time, cavity and
