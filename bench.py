@@ -403,6 +403,19 @@ def adjoint_leg(dev, with_oracle):
                         "frac": alg / (dom_ms * 1e-3) / 1e9 / peak, "traffic": None,
                         "alg_bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs",
                         "note": "the 2 MB state stays in L2 across passes"}}
+    # the same call with the reverse sweep stepping backward in time (no checkpoints)
+    sim.set_psi(psi0)
+    sim.t = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Jr, gr = sim.adjoint_lattice(phi, steps, dt, reverse=True)
+    rwall = time.perf_counter() - t0
+    g0, g1 = np.asarray(grad), np.asarray(gr)
+    out["reverse_sweep"] = {
+        "value": n * n * steps / rwall, "wall_s": rwall, "J_equal": Jr == J,
+        "grad_max_abs_diff_over_max": float(np.max(np.abs(g1 - g0)) / np.max(np.abs(g0))),
+        "workspace_bytes": abi.gpe_adjoint_workspace_size_ex(n, n, steps, abi.GPE_ADJ_REVERSE),
+        "checkpoint_workspace_bytes": abi.gpe_adjoint_workspace_size_ex(n, n, steps, abi.GPE_ADJ_CHECKPOINT)}
     if with_oracle:
         import oracle
         x0 = psi0.astype(np.complex128)

@@ -273,6 +273,24 @@ size_t gpe_adjoint_workspace_size(int nx, int ny, int nsteps);
 gpe_status gpe_adjoint_lattice(gpe_ctx *ctx, int nsteps, double dt, const void *phi_dev, void *adj_ws,
                                size_t adj_ws_bytes, double *J_out, double *grad_out);
 
+/* The same adjoint with a choice of how the reverse sweep gets the forward
+ * states (GPE_ADJ_CHECKPOINT: the calls above).  GPE_ADJ_REVERSE keeps no
+ * checkpoints: since each real-time half phase keeps |psi| and the kinetic
+ * step is unitary, psi_s = U(dt)^-1 psi_{s+1} is one step of -dt from
+ * t_{s+1} (conjugate phases on the same densities, T(-dt)), taken before the
+ * adjoint passes of step s.  Exact in exact arithmetic; in FP32 the
+ * recovered states carry the rounding of the steps taken back, so the
+ * gradient differs from the checkpointed one by about that much (the
+ * reverse sweep costs the same passes as the recomputation it replaces).
+ * Workspace (gpe_adjoint_workspace_size_ex): 3 copies of psi, the kinetic
+ * factors of -dt and 2 nsteps + 1 doubles, independent of the number of
+ * steps apart from those doubles.  Returns 0 / GPE_EINVAL for an unknown
+ * variant; otherwise as gpe_adjoint_workspace_size / gpe_adjoint_lattice. */
+typedef enum { GPE_ADJ_CHECKPOINT = 0, GPE_ADJ_REVERSE = 1 } gpe_adjoint_variant;
+size_t gpe_adjoint_workspace_size_ex(int nx, int ny, int nsteps, int variant);
+gpe_status gpe_adjoint_lattice_ex(gpe_ctx *ctx, int nsteps, double dt, int variant, const void *phi_dev,
+                                  void *adj_ws, size_t adj_ws_bytes, double *J_out, double *grad_out);
+
 /* Release the context (host memory only; borrowed memory is untouched). */
 void gpe_destroy(gpe_ctx *ctx);
 

@@ -116,21 +116,24 @@ class Simulation:
     def variants(self, v: int):
         abi.gpe_set_pass_variants(self.ctx, v)
 
-    def adjoint_lattice(self, phi, nsteps: int, dt: float):
+    def adjoint_lattice(self, phi, nsteps: int, dt: float, reverse: bool = False):
         """J = E(psi_T) + |<phi|psi_T>|^2 after nsteps real-time steps from the
         current state, and dJ/dv_i for the lattice control values set with
-        set_potential (ctrl_target = GPE_CTRL_LATTICE).  One C call (checkpointed
-        forward, then the reverse sweep); psi is the final state afterwards.
-        phi: complex64 cuda tensor or numpy array [ny][nx]."""
+        set_potential (ctrl_target = GPE_CTRL_LATTICE).  One C call (forward,
+        then the reverse sweep, whose states come from sqrt(nsteps)
+        checkpoints, or with reverse=True from steps backward in time); psi is
+        the final state afterwards.  phi: complex64 cuda tensor or numpy array
+        [ny][nx]."""
         torch = self.torch
         phi_t = torch.as_tensor(np.asarray(phi, dtype=np.complex64) if isinstance(phi, np.ndarray) else phi)
         phi_t = phi_t.to(device=self.device, dtype=torch.complex64).contiguous()
-        nbytes = abi.gpe_adjoint_workspace_size(self.nx, self.ny, nsteps)
+        variant = abi.GPE_ADJ_REVERSE if reverse else abi.GPE_ADJ_CHECKPOINT
+        nbytes = abi.gpe_adjoint_workspace_size_ex(self.nx, self.ny, nsteps, variant)
         if getattr(self, "_adj_ws", None) is None or self._adj_ws.numel() < nbytes:
             self._adj_ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         nctrl = 0 if self._ctrl is None else len(self._ctrl)
-        return abi.gpe_adjoint_lattice(self.ctx, nsteps, dt, phi_t.data_ptr(), self._adj_ws.data_ptr(),
-                                       self._adj_ws.numel(), nctrl)
+        return abi.gpe_adjoint_lattice_ex(self.ctx, nsteps, dt, variant, phi_t.data_ptr(), self._adj_ws.data_ptr(),
+                                          self._adj_ws.numel(), nctrl)
 
     def profile(self, enable: bool):
         abi.gpe_profile(self.ctx, enable)

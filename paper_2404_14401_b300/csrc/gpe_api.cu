@@ -535,21 +535,35 @@ gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
 // Layout of the adjoint workspace for n steps: S = ceil(sqrt(n)) steps per
 // segment, K = ceil(n / S) segments.  Checkpoints psi_{kS} (k < K) and psi_n,
 // the S + 1 states of one segment, lambda, and the 2n + 1 per-phase dJ/dv.
+// GPE_ADJ_REVERSE keeps no checkpoints: ck holds psi_T only, st one state,
+// and kx / ky the kinetic factors of -dt for the backward steps.
 struct AdjLayout {
-    int S, K;
-    size_t P, ck, st, lam, g, total;
+    int S, K, variant;
+    size_t P, ck, st, lam, g, kx, ky, total;
 };
-static AdjLayout adj_layout(int nx, int ny, int n)
+static AdjLayout adj_layout(int nx, int ny, int n, int variant = GPE_ADJ_CHECKPOINT)
 {
     AdjLayout L;
-    L.S = 1;
-    while ((long long)L.S * L.S < n) ++L.S;
-    L.K = (n + L.S - 1) / L.S;
+    L.variant = variant;
     L.P = align256(sizeof(float2) * (size_t)nx * ny);
     L.ck = 0;
-    L.st = L.ck + (size_t)(L.K + 1) * L.P;
-    L.lam = L.st + (size_t)(L.S + 1) * L.P;
-    L.g = L.lam + L.P;
+    if (variant == GPE_ADJ_REVERSE) {
+        L.S = n;
+        L.K = 0;
+        L.st = L.ck + L.P;
+        L.lam = L.st + L.P;
+        L.kx = L.lam + L.P;
+        L.ky = L.kx + align256(sizeof(float2) * (size_t)nx);
+        L.g = L.ky + align256(sizeof(float2) * (size_t)ny);
+    } else {
+        L.S = 1;
+        while ((long long)L.S * L.S < n) ++L.S;
+        L.K = (n + L.S - 1) / L.S;
+        L.st = L.ck + (size_t)(L.K + 1) * L.P;
+        L.lam = L.st + (size_t)(L.S + 1) * L.P;
+        L.kx = L.ky = 0;
+        L.g = L.lam + L.P;
+    }
     L.total = L.g + align256(sizeof(double) * (size_t)(2 * n + 1));
     return L;
 }
@@ -576,6 +590,24 @@ static gpe_status copy_d2d(gpe_ctx *c, void *dst, const void *src)
                                          cudaMemcpyDeviceToDevice, c->stream), "adjoint copy");
 }
 
+// One real-time step backward in time, psi_s = U(dt)^-1 psi_{s+1}, from the
+// context's time t_{s+1}: the executed step with -dt.  Each half phase keeps
+// |psi|, so its inverse is the conjugate phase evaluated on the same density
+// (the density after it), and T(-dt) = T(dt)^-1; V at t_{s+1} opens and V at
+// t_s closes, as in the forward step.  The kinetic factors of -dt (kx, ky)
+// stand in for the context's tables during the two passes.
+static gpe_status step_backward(gpe_ctx *c, double dt, float2 *kx, float2 *ky)
+{
+    float2 *fx = c->T.kinx, *fy = c->T.kiny;
+    c->T.kinx = kx;
+    c->T.kiny = ky;
+    gpe_status st = step_part(c, 0, 1, -dt, GPE_REAL);
+    if (st == GPE_OK) st = step_epilogue(c, 1, -dt, GPE_REAL);
+    c->T.kinx = fx;
+    c->T.kiny = fy;
+    return st;
+}
+
 static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, unsigned char *ws,
                               const AdjLayout &L, double *J_out, double *grad)
 {
@@ -584,14 +616,17 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     const size_t P = L.P / sizeof(float2);
     const double t0 = c->t, tT = t0 + n * dt;
     const double dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
+    const bool reverse = L.variant == GPE_ADJ_REVERSE;
     CUtensorMap lam_map;
     TRY(encode_map(c, lam, &lam_map));
 
-    // forward, one V/2 - T - V/2 step per call, keeping a checkpoint every S steps
-    TRY(copy_d2d(c, ck, c->psi));
+    // forward, one V/2 - T - V/2 step per call, keeping a checkpoint every S
+    // steps (none when the reverse sweep steps backward instead)
+    if (!reverse) TRY(copy_d2d(c, ck, c->psi));
     for (int s = 0; s < n; ++s) {
         TRY(gpe_step(c, 1, dt, GPE_REAL));
-        if ((s + 1) % L.S == 0 && s + 1 < n) TRY(copy_d2d(c, ck + (size_t)((s + 1) / L.S) * P, c->psi));
+        if (!reverse && (s + 1) % L.S == 0 && s + 1 < n)
+            TRY(copy_d2d(c, ck + (size_t)((s + 1) / L.S) * P, c->psi));
     }
     float2 *psiT = ck + (size_t)L.K * P;
     TRY(copy_d2d(c, psiT, c->psi));
@@ -629,9 +664,50 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         return launch_adj_terminal(lam, psiT, phi, aT, (float)cre, (float)cim, (float)dxdy, c->stream);
     }, "adjoint terminal"));
 
+    // adjoint passes of step s: the row pass with the step's end state psi_{s+1},
+    // the column pass with its initial state psi_s
+    auto adjoint_step = [&](int s, const float2 *psi_s, const float2 *psi_s1) -> gpe_status {
+        const double ts = t0 + s * dt, te = ts + dt;
+        PassArgs ar = pass_args(c, phase_at(c, te, 0.5 * dt), red_at(c, te), 0, 0);
+        ar.psi = lam;
+        ar.psi2 = psi_s1;
+        ar.gout = gdev + 2 * s + 1;
+        ar.L0x = (float)c->pot.lat_V0x;
+        ar.L0y = (float)c->pot.lat_V0y;
+        TRY(timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream); },
+                         "adjoint row pass"));
+        PassArgs ac = pass_args(c, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0);
+        ac.psi = lam;
+        ac.psi2 = psi_s;
+        ac.gout = gdev + 2 * s;
+        ac.L0x = ar.L0x;
+        ac.L0y = ar.L0y;
+        TRY(timed_launch(c, GPE_PASS_ADJ_COL, [&] { return launch_col(COL_ADJ, ac, lam_map, c->stream); },
+                         "adjoint column pass"));
+        return GPE_OK;
+    };
+
+    if (reverse) {
+        // reverse sweep without checkpoints: psi_s from psi_{s+1} by one step
+        // backward in time (exact in exact arithmetic; in FP32 the recovered
+        // states carry the rounding of the steps taken back)
+        float2 *kx = (float2 *)(ws + L.kx), *ky = (float2 *)(ws + L.ky);
+        Tables Tb = c->T;
+        Tb.kinx = kx;
+        Tb.kiny = ky;
+        TRY(timed_launch(c, 2, [&] {
+            return launch_kinetic_tables(Tb, c->nx, c->ny, c->Lx, c->Ly, c->m, -dt, 0, c->stream);
+        }, "kinetic tables"));
+        for (int s = n - 1; s >= 0; --s) {
+            TRY(copy_d2d(c, st, c->psi));                         // psi_{s+1}
+            TRY(step_backward(c, dt, kx, ky));                    // psi <- psi_s, t <- t_s
+            TRY(adjoint_step(s, c->psi, st));
+        }
+    }
+
     // reverse sweep, segment by segment: recompute the segment's states from
     // its checkpoint, then the two adjoint passes of each step
-    for (int k = L.K - 1; k >= 0; --k) {
+    for (int k = L.K - 1; k >= 0 && !reverse; --k) {
         const int s0 = k * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
         TRY(copy_d2d(c, c->psi, ck + (size_t)k * P));
         c->t = t0 + s0 * dt;
@@ -640,25 +716,8 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
             TRY(gpe_step(c, 1, dt, GPE_REAL));
             TRY(copy_d2d(c, st + (size_t)i * P, c->psi));
         }
-        for (int s = s1 - 1; s >= s0; --s) {
-            const double ts = t0 + s * dt, te = ts + dt;
-            PassArgs ar = pass_args(c, phase_at(c, te, 0.5 * dt), red_at(c, te), 0, 0);
-            ar.psi = lam;
-            ar.psi2 = st + (size_t)(s + 1 - s0) * P;
-            ar.gout = gdev + 2 * s + 1;
-            ar.L0x = (float)c->pot.lat_V0x;
-            ar.L0y = (float)c->pot.lat_V0y;
-            TRY(timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream); },
-                             "adjoint row pass"));
-            PassArgs ac = pass_args(c, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0);
-            ac.psi = lam;
-            ac.psi2 = st + (size_t)(s - s0) * P;
-            ac.gout = gdev + 2 * s;
-            ac.L0x = ar.L0x;
-            ac.L0y = ar.L0y;
-            TRY(timed_launch(c, GPE_PASS_ADJ_COL, [&] { return launch_col(COL_ADJ, ac, lam_map, c->stream); },
-                             "adjoint column pass"));
-        }
+        for (int s = s1 - 1; s >= s0; --s)
+            TRY(adjoint_step(s, st + (size_t)(s - s0) * P, st + (size_t)(s + 1 - s0) * P));
     }
     // leave the context at the final state and time, as gpe_step would
     TRY(copy_d2d(c, c->psi, psiT));
@@ -1034,21 +1093,36 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
 
 size_t gpe_adjoint_workspace_size(int nx, int ny, int nsteps)
 {
+    return gpe_adjoint_workspace_size_ex(nx, ny, nsteps, GPE_ADJ_CHECKPOINT);
+}
+
+size_t gpe_adjoint_workspace_size_ex(int nx, int ny, int nsteps, int variant)
+{
     if (!pow2_in_range(nx) || !pow2_in_range(ny) || nsteps < 1) return 0;
-    return adj_layout(nx, ny, nsteps).total;
+    if (variant != GPE_ADJ_CHECKPOINT && variant != GPE_ADJ_REVERSE) return 0;
+    return adj_layout(nx, ny, nsteps, variant).total;
 }
 
 gpe_status gpe_adjoint_lattice(gpe_ctx *c, int nsteps, double dt, const void *phi_dev, void *adj_ws,
                                size_t adj_ws_bytes, double *J_out, double *grad_out)
 {
+    return gpe_adjoint_lattice_ex(c, nsteps, dt, GPE_ADJ_CHECKPOINT, phi_dev, adj_ws, adj_ws_bytes, J_out,
+                                  grad_out);
+}
+
+gpe_status gpe_adjoint_lattice_ex(gpe_ctx *c, int nsteps, double dt, int variant, const void *phi_dev,
+                                  void *adj_ws, size_t adj_ws_bytes, double *J_out, double *grad_out)
+{
     if (!c || !J_out || !grad_out) return GPE_EINVAL;
+    if (variant != GPE_ADJ_CHECKPOINT && variant != GPE_ADJ_REVERSE)
+        return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: variant %d", variant);
     TRY(step_check(c, nsteps, dt, GPE_REAL));
     if (nsteps < 1) return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: nsteps %d", nsteps);
     if (!phi_dev || ((uintptr_t)phi_dev & 15u) || !adj_ws || ((uintptr_t)adj_ws & 255u))
         return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: null or misaligned buffer");
     if (c->pot.cavity || c->pot.ctrl_target != GPE_CTRL_LATTICE || c->ctrl_t.empty())
         return fail(c, GPE_EINVAL, "gpe_adjoint_lattice: needs a lattice control table and no cavity");
-    const AdjLayout L = adj_layout(c->nx, c->ny, nsteps);
+    const AdjLayout L = adj_layout(c->nx, c->ny, nsteps, variant);
     if (adj_ws_bytes < L.total) return fail(c, GPE_ENOMEM, "gpe_adjoint_lattice: workspace %zu < %zu", adj_ws_bytes,
                                             L.total);
     for (size_t i = 0; i < c->ctrl_t.size(); ++i) grad_out[i] = 0.0;

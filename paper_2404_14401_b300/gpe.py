@@ -23,7 +23,8 @@ EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", 
            "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
            "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_profile_read_kind", "gpe_launch_count",
            "gpe_overlaps_static", "gpe_momentum_populations", "gpe_get_pass_variants", "gpe_set_pass_variants", "gpe_tune",
-           "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_destroy",
+           "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_adjoint_workspace_size_ex",
+           "gpe_adjoint_lattice_ex", "gpe_destroy",
            "gpe_last_error", "gpe_status_string")
 
 
@@ -97,6 +98,9 @@ def load() -> ctypes.CDLL:
         "gpe_adjoint_workspace_size": (c_size_t, [c_int, c_int, c_int]),
         "gpe_adjoint_lattice": (c_int, [c_void_p, c_int, c_double, c_void_p, c_void_p, c_size_t, P(c_double),
                                         P(c_double)]),
+        "gpe_adjoint_workspace_size_ex": (c_size_t, [c_int, c_int, c_int, c_int]),
+        "gpe_adjoint_lattice_ex": (c_int, [c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,
+                                           P(c_double), P(c_double)]),
         "gpe_destroy": (None, [c_void_p]),
         "gpe_last_error": (c_char_p, [c_void_p]),
         "gpe_status_string": (c_char_p, [c_int]),
@@ -254,6 +258,23 @@ def gpe_adjoint_lattice(ctx, nsteps: int, dt: float, phi_ptr: int, ws_ptr: int, 
     grad = (c_double * max(nctrl, 1))()
     _check(ctx, load().gpe_adjoint_lattice(ctx, int(nsteps), float(dt), c_void_p(phi_ptr), c_void_p(ws_ptr),
                                            ws_bytes, ctypes.byref(J), grad))
+    return J.value, [grad[i] for i in range(nctrl)]
+
+
+GPE_ADJ_CHECKPOINT, GPE_ADJ_REVERSE = 0, 1
+
+
+def gpe_adjoint_workspace_size_ex(nx: int, ny: int, nsteps: int, variant: int) -> int:
+    return load().gpe_adjoint_workspace_size_ex(nx, ny, nsteps, variant)
+
+
+def gpe_adjoint_lattice_ex(ctx, nsteps: int, dt: float, variant: int, phi_ptr: int, ws_ptr: int, ws_bytes: int,
+                           nctrl: int):
+    """gpe_adjoint_lattice with the reverse-sweep variant (GPE_ADJ_CHECKPOINT or GPE_ADJ_REVERSE)."""
+    J = c_double()
+    grad = (c_double * max(nctrl, 1))()
+    _check(ctx, load().gpe_adjoint_lattice_ex(ctx, int(nsteps), float(dt), int(variant), c_void_p(phi_ptr),
+                                              c_void_p(ws_ptr), ws_bytes, ctypes.byref(J), grad))
     return J.value, [grad[i] for i in range(nctrl)]
 
 

@@ -122,3 +122,91 @@ def test_adjoint_passes_are_profiled_per_kind():
     assert abi.gpe_profile_read_kind(s.ctx, abi.GPE_PASS_ADJ_ROW) == (0.0, 0)     # reset by the read
     with pytest.raises(abi.GPEError):
         abi.gpe_profile_read_kind(s.ctx, 5)
+
+
+# ------------------------------------------------------------------ reverse sweep without checkpoints
+def run_gpu_reverse(p, psi0, phi, steps, dt):
+    from paper_2404_14401_b300 import Simulation
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    s.set_psi(np.asarray(psi0, dtype=np.complex64))
+    J, grad = s.adjoint_lattice(phi, steps, dt, reverse=True)
+    return s, J, np.array(grad)
+
+
+@pytest.mark.parametrize("g", [0.0, 20.0])
+def test_reverse_sweep_matches_oracle(g):
+    """States recovered by stepping backward in time give the oracle's J and
+    gradient within the checkpointed tolerances; J, computed before the
+    reverse sweep, is the checkpointed call's bit for bit."""
+    p, psi0, phi, steps, dt = case(g=g)
+    s, J, grad = run_gpu_reverse(p, psi0, phi, steps, dt)
+    Jr, gr = oracle.adjoint(p, psi0.astype(np.complex64).astype(np.complex128), phi, steps, dt)
+    close(J, grad, Jr, gr)
+    _, Jc, _ = run_gpu(p, psi0, phi, steps, dt)
+    assert J == Jc
+    assert s.sync() == 0
+
+
+def test_reverse_sweep_leaves_the_state_of_single_steps():
+    from paper_2404_14401_b300 import Simulation
+    p, psi0, phi, steps, dt = case(steps=10)
+    s, _, _ = run_gpu_reverse(p, psi0, phi, steps, dt)
+    ref = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    ref.set_potential(p)
+    ref.set_psi(np.asarray(psi0, dtype=np.complex64))
+    for _ in range(steps):
+        ref.step(1, dt, False)
+    assert np.array_equal(s.get_psi(), ref.get_psi())
+    assert abs(s.t - steps * dt) < 1e-15
+
+
+def test_reverse_sweep_on_the_control_workload_grid():
+    """512^2, 400 steps of the adjoint-control workload: the gradient from the
+    reverse sweep against the checkpointed one.  The recovered states carry the
+    FP32 rounding of up to 400 steps taken back (a few 1e-5 at most if every
+    step's rounding added up), so the bound is 1e-3 of the largest component."""
+    w = gi.adjoint_control(n=512, L=20.0, steps=400, npts=40, seed=13)
+    p, dt = w["params"], w["dt"]
+    psi0 = w["psi0"]()
+    phi = w["phi"]()
+    _, Jc, gc = run_gpu(p, psi0, phi, 400, dt)
+    _, J, g = run_gpu_reverse(p, psi0, phi, 400, dt)
+    assert J == Jc
+    assert np.max(np.abs(g - gc)) < 1e-3 * np.max(np.abs(gc))
+
+
+def test_reverse_sweep_workspace_and_errors():
+    from paper_2404_14401_b300 import Simulation, gpe as abi
+    n = 4000
+    ck = abi.gpe_adjoint_workspace_size_ex(512, 512, n, abi.GPE_ADJ_CHECKPOINT)
+    rv = abi.gpe_adjoint_workspace_size_ex(512, 512, n, abi.GPE_ADJ_REVERSE)
+    assert ck == abi.gpe_adjoint_workspace_size(512, 512, n)
+    assert rv < 4 * 512 * 512 * 8 + 64 * 1024 < ck
+    assert abi.gpe_adjoint_workspace_size_ex(512, 512, n, 2) == 0
+    p, psi0, phi, steps, dt = case(steps=4)
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    f = torch.from_numpy(phi.astype(np.complex64)).cuda()
+    need = abi.gpe_adjoint_workspace_size_ex(p["nx"], p["ny"], steps, abi.GPE_ADJ_REVERSE)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(abi.GPEError) as e:
+        abi.gpe_adjoint_lattice_ex(s.ctx, steps, dt, 2, f.data_ptr(), ws.data_ptr(), need, len(p["ctrl_v"]))
+    assert e.value.status == abi.GPE_EINVAL
+    with pytest.raises(abi.GPEError) as e:
+        abi.gpe_adjoint_lattice_ex(s.ctx, steps, dt, abi.GPE_ADJ_REVERSE, f.data_ptr(), ws.data_ptr(), need - 256,
+                                   len(p["ctrl_v"]))
+    assert e.value.status == abi.GPE_ENOMEM
+
+
+def test_autograd_function_with_the_reverse_sweep():
+    from paper_2404_14401_b300 import Simulation
+    from paper_2404_14401_b300.adjoint import lattice_control_objective
+    p, psi0, phi, steps, dt = case(steps=12, npts=6)
+    sim = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    v = torch.tensor(p["ctrl_v"], dtype=torch.float64, requires_grad=True)
+    J = lattice_control_objective(v, sim, p, np.asarray(psi0, dtype=np.complex64), phi, steps, dt, reverse=True)
+    J.backward()
+    _, Jc, gc = run_gpu_reverse(p, psi0, phi, steps, dt)
+    assert J.detach().item() == Jc
+    assert np.array_equal(v.grad.numpy(), gc)
