@@ -533,15 +533,26 @@ def run_ours(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(local_rank) if rank == 0 else None
     time.sleep(0.4 if clocks else 0.0)
+    # the timed steps as 5 consecutive runs (events between them, no sync), so
+    # that the median and the mean of 5 runs can be reported beside the total
+    nrun = 5 if args.steps >= 5 else 1
+    cuts = [args.steps * i // nrun for i in range(nrun + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nrun - 1)]
     torch.cuda.synchronize()
     barrier()
     e0.record(stream)
-    Simulation.step_many(sims, args.steps, dt)
+    for i in range(nrun):
+        Simulation.step_many(sims, cuts[i + 1] - cuts[i], dt)
+        if i < nrun - 1:
+            ev[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
+    marks = [e0] + ev + [e1]
+    run_rates = [n * n * B * world * (cuts[i + 1] - cuts[i]) / (marks[i].elapsed_time(marks[i + 1]) * 1e-3)
+                 for i in range(nrun)]
     launches = sum(s.launches for s in sims) - launches0
     ms = max_over_ranks(ms, world, dev)
     status = [s.sync() for s in sims]
@@ -640,6 +651,11 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": total_pts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": f"one job of {e2e_steps} steps: pinned h2d of every psi, gpe_step_many, d2h of every psi + observables"},
+        "runs": {"count": nrun, "steps_each": [cuts[i + 1] - cuts[i] for i in range(nrun)],
+                 "median": statistics.median(run_rates), "mean": statistics.fmean(run_rates),
+                 "values": run_rates, "unit": UNIT,
+                 "note": "the timed steps split into consecutive gpe_step_many calls, timed by events between them; "
+                         "value is the whole timed region"},
         "gpu_launches": launches,
         "clocks": clk,
         "check": {"norm": obs["norm"], "energy": obs["energy"], "status": status,
