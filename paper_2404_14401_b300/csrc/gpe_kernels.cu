@@ -15,6 +15,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/gpe.h"
 #include "gpe_fft.cuh"
 #include "gpe_internal.h"
@@ -1256,6 +1258,20 @@ __global__ void timeout_probe_kernel(DevScalars *sc, int spins)
 }
 
 // ------------------------------------------------------------------ launchers
+// Opt func in to `bytes` of dynamic shared memory once per device (function
+// attributes belong to the device's context), safe from several host threads.
+template <class F> static cudaError_t smem_opt_in(F *func, int bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 int row_rows_per_cta(int nx, int ny)
 {
     const int E = nx >= 16 ? 16 : nx;
@@ -1278,16 +1294,12 @@ template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cuda
     const int rpc = row_rows_per_cta(N, a.ny);
     const int threads = rpc * C::TP;
     const size_t smem = (size_t)rpc * C::PS * sizeof(float2) + (size_t)C::TWN * sizeof(float4);
-    static bool attr = false;
-    if (!attr) {
-        const int rpc_max = 256 / C::TP > 1 ? 256 / C::TP : 1;
-        const int smem_max = rpc_max * C::PS * (int)sizeof(float2) + C::TWN * (int)sizeof(float4);
-        if (smem_max > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(row_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 smem_max);
-            if (e != cudaSuccess) return e;
-        }
-        attr = true;
+    constexpr int rpc_max = 256 / C::TP > 1 ? 256 / C::TP : 1;
+    constexpr int smem_max = rpc_max * C::PS * (int)sizeof(float2) + C::TWN * (int)sizeof(float4);
+    if constexpr (smem_max > 48 * 1024) {
+        static std::atomic<unsigned long long> attr{0};
+        const cudaError_t e = smem_opt_in(row_kernel<N, MODE>, smem_max, attr);
+        if (e != cudaSuccess) return e;
     }
     row_kernel<N, MODE><<<a.ny / rpc, threads, smem, s>>>(a);
     return cudaGetLastError();
@@ -1334,14 +1346,10 @@ static cudaError_t col_launch(const PassArgs &a, const CUtensorMap &map, cudaStr
     constexpr int W = col_w(N), G = col_g(N);
     constexpr size_t smem = (G == W ? (size_t)W * C::PS : (size_t)N * W + (size_t)G * C::PS) * sizeof(float2) +
                             (size_t)C::TWN * sizeof(float4) + 128;
-    static bool attr = false;
-    if (!attr) {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(col_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        attr = true;
+    if constexpr (smem > 48 * 1024) {
+        static std::atomic<unsigned long long> attr{0};
+        const cudaError_t e = smem_opt_in(col_kernel<N, MODE>, (int)smem, attr);
+        if (e != cudaSuccess) return e;
     }
     col_kernel<N, MODE><<<a.nx / W, G * C::TP, smem, s>>>(a, map);
     return cudaGetLastError();
@@ -1380,13 +1388,17 @@ cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cuda
     }
 }
 
+// SM count of the current device (cached per device; 148 if it cannot be read)
 static int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    std::atomic<int> &c = cache[dev & 63];
+    int n = c.load(std::memory_order_relaxed);
+    if (n <= 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        c.store(n, std::memory_order_relaxed);
     }
     return n;
 }
@@ -1394,13 +1406,9 @@ static int sm_count()
 template <int N> static cudaError_t row_group_launch(const PassArgs &a, cudaStream_t s)
 {
     using C = RowGroupCfg<N>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(row_group_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_opt_in(row_group_kernel<N>, (int)C::SMEM, attr);
+    if (e != cudaSuccess) return e;
     const int items = a.ny / C::RG;
     int grid = sm_count();
     if (grid * C::NG > items) grid = (items + C::NG - 1) / C::NG;
@@ -1423,13 +1431,9 @@ cudaError_t launch_row_group(const PassArgs &a, cudaStream_t s)
 template <int N> static cudaError_t row_stream_launch(const PassArgs &a, cudaStream_t s)
 {
     using C = RowStreamCfg<N>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(row_stream_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_opt_in(row_stream_kernel<N>, (int)C::SMEM, attr);
+    if (e != cudaSuccess) return e;
     const int items = a.ny / C::RPC;
     int grid = C::CTAS_PER_SM * sm_count();
     if (grid > items) grid = items;
@@ -1451,13 +1455,9 @@ cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s)
 template <int N, int MODE> static cudaError_t col_stream_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     using C = ColStreamCfg<N>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(col_stream_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_opt_in(col_stream_kernel<N, MODE>, (int)C::SMEM, attr);
+    if (e != cudaSuccess) return e;
     const int items = a.nx / C::W;
     int grid = C::CTAS_PER_SM * sm_count();
     if (grid > items) grid = items;

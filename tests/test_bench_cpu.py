@@ -57,7 +57,8 @@ def test_traffic_record_is_keyed_by_the_kernel_sources():
     h = bench.kernel_source_hash()
     assert len(h) == 16 and all(c in "0123456789abcdef" for c in h)
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    rows = [dict(x.split("=", 1) for x in line.split() if "=" in x) for line in open(path) if line.strip()]
+    rows = [dict(x.split("=", 1) for x in line.split() if "=" in x) for line in open(path)
+            if line.strip() and not line.startswith("#")]
     assert rows
     for kv in rows:
         assert {"kernel", "grid", "src", "dram_bytes_per_launch"} <= set(kv)
