@@ -93,6 +93,7 @@ int lanes_for(gpe_ctx *const *ctxs, int count)
 struct Lanes {
     cudaStream_t s[kLanes];
     cudaEvent_t ev[kLanes];        // fork / join of the other lanes into a capture on lane 0
+    std::mutex mu;                 // one gpe_step_many at a time enqueues on these lanes
 };
 Lanes *lanes_for_current_device()
 {
@@ -795,6 +796,11 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
     // while passes of different contexts overlap on the GPU.
     Lanes *L = (count > 1 && !getenv("GPE_SERIAL_MANY")) ? lanes_for_current_device() : nullptr;
     const int nl = L ? lanes_for(ctxs, count) : 0;
+    // the lanes are shared by every caller on the device: work of two host
+    // threads must not interleave on them (a graph capture on lane 0 would
+    // take in the other thread's launches)
+    std::unique_lock<std::mutex> lane_lock;
+    if (L) lane_lock = std::unique_lock<std::mutex>(L->mu);
     std::vector<cudaStream_t> own(count);
     for (int i = 0; i < count; ++i) own[i] = ctxs[i]->stream;
     gpe_status st = GPE_OK;

@@ -382,6 +382,53 @@ def test_lockstep_lanes_match_single_context_stepping(imag):
         assert np.array_equal(s.get_psi(), ref)
 
 
+def test_step_many_from_two_host_threads_matches_one_context_alone():
+    """Two host threads stepping their own batches of small grids at once (the
+    graph-replay path on the shared lanes) give each context's single-stream
+    result bit for bit."""
+    import threading
+    from paper_2404_14401_b300 import Simulation
+    w = gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"])
+    dt = 5e-4
+
+    def batch(seed):
+        out = []
+        for b in range(4):
+            s = sim_for(p)
+            s.set_psi(c64(gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=seed + b)))
+            out.append(s)
+        return out
+
+    batches = [batch(60), batch(70)]
+    alone = []
+    for seed in (60, 70):
+        for s in batch(seed):
+            for _ in range(3):
+                s.step(12, dt)
+            alone.append(s.get_psi())
+    errors = []
+
+    def run(sims):
+        try:
+            for _ in range(3):
+                Simulation.step_many(sims, 12, dt)
+            for s in sims:
+                s.sync()
+        except Exception as e:          # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(b,)) for b in batches]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    got = [s.get_psi() for b in batches for s in b]
+    for g, ref in zip(got, alone):
+        assert np.array_equal(g, ref)
+
+
 # ------------------------------------------------------------------ graph replay
 # With two or more contexts and no time-dependent control, gpe_step_many
 # captures one interior lockstep step into a CUDA graph and replays it.  The
