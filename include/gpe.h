@@ -237,17 +237,25 @@ gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax,
  * variant (a CTA per group of rows or per TMA tile of columns).  A context
  * starts with every applicable variant on.  The bits select them: */
 enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
+/* Bits 3-4 (value << GPE_VARIANT_ROW_TILE_SHIFT, value 0..2): on rows of
+ * 256 points and more the one-shot row pass runs 2^-value of its default
+ * rows per CTA (256 threads' worth, at least one warp), so that a small grid
+ * spreads over more SMs; shorter rows ignore it. */
+enum { GPE_VARIANT_ROW_TILE_SHIFT = 3 };
 int gpe_get_pass_variants(const gpe_ctx *ctx);                /* -1 for a null context */
-gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants); /* GPE_EINVAL outside 0..7 */
+gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants); /* GPE_EINVAL outside 0..23 */
 /* Autotuner: times every applicable variant of the interior row pass
- * (potential phase + T_x) and column pass (T_y) of a step of dt in `mode`
- * on a copy of psi in scratch_dev (>= nx*ny*8 bytes, 256-byte aligned,
- * borrowed; psi itself is not changed), `reps` launches each after one
- * warm-up, with CUDA events on the context's stream, and selects the fastest
- * row and column variants for this context.  variants_out receives the bits;
- * times_out (5 doubles or NULL) the mean milliseconds of the row pass
- * one-shot / grouped / streaming and the column pass one-shot / streaming,
- * NaN where a variant does not apply.  Synchronises the stream.  Errors:
+ * (potential phase + T_x; the one-shot pass at row-tile values 0 and 1, the
+ * half tile kept unless at least 3% slower; a persistent variant replaces
+ * the one-shot pass only when at least 3% faster) and column pass (T_y)
+ * of a step of dt in `mode` on a copy of psi in scratch_dev (>= nx*ny*8
+ * bytes, 256-byte aligned, borrowed; psi itself is not changed), `reps`
+ * launches each after one warm-up, with CUDA events on the context's
+ * stream, and selects the fastest row and column variants for this context.
+ * variants_out receives the bits; times_out (5 doubles or NULL) the mean
+ * milliseconds of the row pass one-shot (its kept tile) / grouped /
+ * streaming and the column pass one-shot / streaming, NaN where a variant
+ * does not apply.  Synchronises the stream.  Errors:
  * GPE_EINVAL, GPE_ECUDA. */
 gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, size_t scratch_bytes, int reps,
                     int *variants_out, double *times_out);

@@ -56,6 +56,7 @@ struct gpe_ctx {
     int stream_passes;       // use the persistent streaming row pass where it applies
     int stream_cols;         // use the persistent streaming column pass where it applies
     int group_rows;          // use the grouped persistent row pass where it applies
+    int row_tile_shift;      // one-shot row pass: 2^-shift of the default rows per CTA (0..2)
     long long launches;
     cudaEvent_t ev_fork, ev_join;   // ordering of gpe_step_many's lanes with this context's stream
     // per-pass event timing (gpe_profile)
@@ -307,7 +308,8 @@ gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd,
         return timed_launch(c, 0, [&] { return launch_row_stream(a, c->stream); }, "row pass");
     if (mode == ROW_PT && c->group_rows && row_group_ok(c->nx, c->ny))
         return timed_launch(c, 0, [&] { return launch_row_group(a, c->stream); }, "row pass");
-    return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream); }, "row pass");
+    const int ts = mode == ROW_PT ? c->row_tile_shift : 0;
+    return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream, ts); }, "row pass");
 }
 
 gpe_status run_col(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag)
@@ -373,6 +375,7 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->stream_passes = getenv("GPE_NO_STREAM_PASSES") ? 0 : 1;
     c->stream_cols = c->stream_passes;
     c->group_rows = getenv("GPE_NO_GROUP_ROWS") ? 0 : 1;
+    c->row_tile_shift = 0;
     c->launches = 0;
     c->prof = false;
     for (int k = 0; k < GPE_PASS_KINDS; ++k) {
@@ -1030,15 +1033,16 @@ int gpe_get_pass_variants(const gpe_ctx *c)
 {
     if (!c) return -1;
     return (c->group_rows ? GPE_VARIANT_GROUP_ROWS : 0) | (c->stream_passes ? GPE_VARIANT_STREAM_ROWS : 0) |
-           (c->stream_cols ? GPE_VARIANT_STREAM_COLS : 0);
+           (c->stream_cols ? GPE_VARIANT_STREAM_COLS : 0) | (c->row_tile_shift << GPE_VARIANT_ROW_TILE_SHIFT);
 }
 
 gpe_status gpe_set_pass_variants(gpe_ctx *c, int v)
 {
-    if (!c || v < 0 || v > 7) return GPE_EINVAL;
+    if (!c || v < 0 || v >= (3 << GPE_VARIANT_ROW_TILE_SHIFT)) return GPE_EINVAL;
     c->group_rows = (v & GPE_VARIANT_GROUP_ROWS) != 0;
     c->stream_passes = (v & GPE_VARIANT_STREAM_ROWS) != 0;
     c->stream_cols = (v & GPE_VARIANT_STREAM_COLS) != 0;
+    c->row_tile_shift = v >> GPE_VARIANT_ROW_TILE_SHIFT;
     return GPE_OK;
 }
 
@@ -1074,7 +1078,24 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
     };
     double t[5];
     for (double &x : t) x = NAN;
-    gpe_status st = time_it([&] { return launch_row(ROW_PT, a, c->stream); }, &t[0]);
+    // one-shot row pass at its default and at half its default rows per CTA;
+    // the half tile is kept unless it is at least 3% slower.  In the
+    // phase-diagram sweep under gpe_step_many (256^2 .. 1024^2) every size
+    // ran best at the half tile: 35.2 against 33.0 G pt*steps/s at the
+    // default and 33.1 at the quarter tile (value 2, which is left to
+    // gpe_set_pass_variants), while alone the two larger tiles timed within
+    // a few percent of each other.
+    int shift = 0;
+    gpe_status st = GPE_OK;
+    for (int k = 0; k < 2 && st == GPE_OK; ++k) {
+        if (k > 0 && row_rows_per_cta(c->nx, c->ny, k) == row_rows_per_cta(c->nx, c->ny, k - 1)) break;
+        double ms = NAN;
+        st = time_it([&] { return launch_row(ROW_PT, a, c->stream, k); }, &ms);
+        if (st == GPE_OK && (k == 0 || ms <= 1.03 * t[0])) {
+            t[0] = ms;
+            shift = k;
+        }
+    }
     if (st == GPE_OK && row_group_ok(c->nx, c->ny))
         st = time_it([&] { return launch_row_group(a, c->stream); }, &t[1]);
     if (st == GPE_OK && row_stream_ok(c->nx, c->ny))
@@ -1085,10 +1106,15 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
     c->ev_free.push_back(e0);
     c->ev_free.push_back(e1);
     if (st != GPE_OK) return st;
+    // a persistent row variant replaces the one-shot pass only when at least
+    // 3% faster: on near ties the one-shot pass, whose CTAs the hardware
+    // schedules freely, overlapped better with other grids' passes under
+    // gpe_step_many (1024^2 in the phase-diagram sweep)
     int best = 0;
     for (int k = 1; k < 3; ++k)
-        if (t[k] == t[k] && t[k] < t[best]) best = k;
+        if (t[k] == t[k] && t[k] < 0.97 * t[best]) best = k;
     int v = best == 1 ? GPE_VARIANT_GROUP_ROWS : best == 2 ? GPE_VARIANT_STREAM_ROWS : 0;
+    if (best == 0) v |= shift << GPE_VARIANT_ROW_TILE_SHIFT;
     if (t[4] == t[4] && t[4] < t[3]) v |= GPE_VARIANT_STREAM_COLS;
     TRY(gpe_set_pass_variants(c, v));
     *variants_out = v;

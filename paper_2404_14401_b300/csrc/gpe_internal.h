@@ -98,7 +98,9 @@ struct PassArgs {
 };
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
-cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s);
+// tile_shift: the one-shot row pass takes 2^-tile_shift of its default rows
+// per CTA (0, 1 or 2; see row_rows_per_cta)
+cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shift = 0);
 cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
 cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s);
 cudaError_t launch_col_stream(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
@@ -119,6 +121,6 @@ cudaError_t launch_adj_overlap(const float2 *psi, const float2 *phi, const Table
 cudaError_t launch_adj_terminal(float2 *lam, const float2 *psi, const float2 *phi, const PassArgs &a, float c_re,
                                 float c_im, float dxdy, cudaStream_t s);
 int col_tile_width(int nx, int ny);
-int row_rows_per_cta(int nx, int ny);
+int row_rows_per_cta(int nx, int ny, int tile_shift = 0);
 
 }  // namespace gpe

@@ -1272,11 +1272,16 @@ template <class F> static cudaError_t smem_opt_in(F *func, int bytes, std::atomi
     return e;
 }
 
-int row_rows_per_cta(int nx, int ny)
+// Rows per CTA of the one-shot row pass: 256 threads' worth, divided by
+// 2^tile_shift for rows of 256 points and more (the tuner's smaller tiles
+// spread a small grid over more SMs), never below one warp's worth nor above
+// the grid.
+int row_rows_per_cta(int nx, int ny, int tile_shift)
 {
     const int E = nx >= 16 ? 16 : nx;
     const int tp = nx / E;
-    int rpc = 256 / tp;
+    int rpc = (256 / tp) >> (nx >= 256 ? tile_shift : 0);
+    if (rpc * tp < 32) rpc = (32 + tp - 1) / tp;
     if (rpc < 1) rpc = 1;
     if (rpc > ny) rpc = ny;
     return rpc;
@@ -1288,10 +1293,10 @@ int col_tile_width(int nx, int ny)
     return col_w(ny);
 }
 
-template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cudaStream_t s)
+template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cudaStream_t s, int tile_shift)
 {
     using C = RowCfg<N>;
-    const int rpc = row_rows_per_cta(N, a.ny);
+    const int rpc = row_rows_per_cta(N, a.ny, tile_shift);
     const int threads = rpc * C::TP;
     const size_t smem = (size_t)rpc * C::PS * sizeof(float2) + (size_t)C::TWN * sizeof(float4);
     constexpr int rpc_max = 256 / C::TP > 1 ? 256 / C::TP : 1;
@@ -1305,36 +1310,36 @@ template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cuda
     return cudaGetLastError();
 }
 
-template <int N> static cudaError_t row_dispatch_mode(int mode, const PassArgs &a, cudaStream_t s)
+template <int N> static cudaError_t row_dispatch_mode(int mode, const PassArgs &a, cudaStream_t s, int ts)
 {
     switch (mode) {
-    case ROW_PT: return row_launch<N, ROW_PT>(a, s);
-    case ROW_PHASE: return row_launch<N, ROW_PHASE>(a, s);
-    case ROW_PHASE_R: return row_launch<N, ROW_PHASE_R>(a, s);
-    case ROW_REDUCE_R: return row_launch<N, ROW_REDUCE_R>(a, s);
-    case ROW_SCALE: return row_launch<N, ROW_SCALE>(a, s);
-    case ROW_FFT_F: return row_launch<N, ROW_FFT_F>(a, s);
-    case ROW_FFT_I: return row_launch<N, ROW_FFT_I>(a, s);
-    case ROW_OBS: return row_launch<N, ROW_OBS>(a, s);
-    case ROW_ADJ: return row_launch<N, ROW_ADJ>(a, s);
+    case ROW_PT: return row_launch<N, ROW_PT>(a, s, ts);
+    case ROW_PHASE: return row_launch<N, ROW_PHASE>(a, s, ts);
+    case ROW_PHASE_R: return row_launch<N, ROW_PHASE_R>(a, s, ts);
+    case ROW_REDUCE_R: return row_launch<N, ROW_REDUCE_R>(a, s, ts);
+    case ROW_SCALE: return row_launch<N, ROW_SCALE>(a, s, ts);
+    case ROW_FFT_F: return row_launch<N, ROW_FFT_F>(a, s, ts);
+    case ROW_FFT_I: return row_launch<N, ROW_FFT_I>(a, s, ts);
+    case ROW_OBS: return row_launch<N, ROW_OBS>(a, s, ts);
+    case ROW_ADJ: return row_launch<N, ROW_ADJ>(a, s, ts);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s)
+cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shift)
 {
     switch (a.nx) {
-    case 8: return row_dispatch_mode<8>(mode, a, s);
-    case 16: return row_dispatch_mode<16>(mode, a, s);
-    case 32: return row_dispatch_mode<32>(mode, a, s);
-    case 64: return row_dispatch_mode<64>(mode, a, s);
-    case 128: return row_dispatch_mode<128>(mode, a, s);
-    case 256: return row_dispatch_mode<256>(mode, a, s);
-    case 512: return row_dispatch_mode<512>(mode, a, s);
-    case 1024: return row_dispatch_mode<1024>(mode, a, s);
-    case 2048: return row_dispatch_mode<2048>(mode, a, s);
-    case 4096: return row_dispatch_mode<4096>(mode, a, s);
-    case 8192: return row_dispatch_mode<8192>(mode, a, s);
+    case 8: return row_dispatch_mode<8>(mode, a, s, tile_shift);
+    case 16: return row_dispatch_mode<16>(mode, a, s, tile_shift);
+    case 32: return row_dispatch_mode<32>(mode, a, s, tile_shift);
+    case 64: return row_dispatch_mode<64>(mode, a, s, tile_shift);
+    case 128: return row_dispatch_mode<128>(mode, a, s, tile_shift);
+    case 256: return row_dispatch_mode<256>(mode, a, s, tile_shift);
+    case 512: return row_dispatch_mode<512>(mode, a, s, tile_shift);
+    case 1024: return row_dispatch_mode<1024>(mode, a, s, tile_shift);
+    case 2048: return row_dispatch_mode<2048>(mode, a, s, tile_shift);
+    case 4096: return row_dispatch_mode<4096>(mode, a, s, tile_shift);
+    case 8192: return row_dispatch_mode<8192>(mode, a, s, tile_shift);
     default: return cudaErrorInvalidValue;
     }
 }

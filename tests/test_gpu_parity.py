@@ -478,12 +478,40 @@ def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     assert np.isnan(ms["row_streaming"]) != (nx == 4096)
     assert np.isnan(ms["col_streaming"]) != (ny == 4096)
     rows = [ms["row_one_shot"], ms["row_grouped"], ms["row_streaming"]]
-    best = int(np.nanargmin(rows))
+    best = 0                                    # a persistent variant must be 3% faster
+    for k in (1, 2):
+        if not np.isnan(rows[k]) and rows[k] < 0.97 * rows[best]:
+            best = k
     assert (v & abi.GPE_VARIANT_GROUP_ROWS != 0) == (best == 1)
     assert (v & abi.GPE_VARIANT_STREAM_ROWS != 0) == (best == 2)
     assert (v & abi.GPE_VARIANT_STREAM_COLS != 0) == (not np.isnan(ms["col_streaming"])
                                                        and ms["col_streaming"] < ms["col_one_shot"])
+    assert r["row_tile"] in (0, 1) and (r["row_tile"] == 0 or best == 0)
     # stepping with the chosen variants still matches the oracle
     s.step(20, w["dt"], False)
     ref, _ = oracle.evolve(p, psi0.astype(np.complex128), 20, w["dt"], False)
     assert rel_l2(s.get_psi(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("nx,ny,imag", [(256, 256, False), (512, 128, True), (1024, 64, True), (2048, 32, False)])
+def test_row_tiles_give_identical_steps(nx, ny, imag):
+    """The one-shot row pass with 1/2 and 1/4 of its default rows per CTA
+    (more, smaller CTAs) computes every row the same way: bit for bit the
+    same trajectory, in real and imaginary time."""
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-2, seed=61))
+    dt = 2e-3 if imag else 5e-4
+    out = []
+    for tile in (0, 1, 2):
+        s = sim_for(p)
+        s.variants = tile << abi.GPE_VARIANT_ROW_TILE_SHIFT        # one-shot passes only
+        assert s.variants == tile << abi.GPE_VARIANT_ROW_TILE_SHIFT
+        s.set_psi(psi0)
+        s.step(15, dt, imag)
+        assert s.sync() == 0
+        out.append(s.get_psi())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    with pytest.raises(abi.GPEError):
+        s.variants = 3 << abi.GPE_VARIANT_ROW_TILE_SHIFT
