@@ -379,6 +379,7 @@ def adjoint_leg(dev, with_oracle):
     sim = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
     sim.set_potential(p)
     sim.set_psi(psi0)
+    tuned = sim.tune(dt)                                  # pass variants and row tile of this grid
     sim.adjoint_lattice(phi, 64, dt)                      # warm-up (tables, modules)
     sim.set_psi(psi0)
     sim.t = 0.0
@@ -396,7 +397,7 @@ def adjoint_leg(dev, with_oracle):
     out = {"workload": f"adjoint control {n}x{n}, {steps} real-time steps, {len(p['ctrl_v'])} lattice control "
                        "points, J = E(psi_T) + |<phi|psi_T>|^2",
            "value": n * n * steps / wall, "unit": "pt*steps/s (checkpointed forward + reverse sweep)",
-           "wall_s": wall, "J": J, "grad_norm": float(np.linalg.norm(grad)),
+           "wall_s": wall, "J": J, "grad_norm": float(np.linalg.norm(grad)), "pass_variants": tuned,
            "adjoint_row_pass_ms": rms / max(rn, 1), "adjoint_col_pass_ms": cms / max(cn, 1),
            "roofline": {"bound": "hbm", "kernel": f"{'row' if dom == 'ROW_ADJ' else 'col'}_kernel<{n},{dom}>",
                         "achieved": alg / (dom_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",

@@ -678,7 +678,7 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         ar.gout = gdev + 2 * s + 1;
         ar.L0x = (float)c->pot.lat_V0x;
         ar.L0y = (float)c->pot.lat_V0y;
-        TRY(timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream); },
+        TRY(timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream, c->row_tile_shift); },
                          "adjoint row pass"));
         PassArgs ac = pass_args(c, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0);
         ac.psi = lam;
