@@ -238,10 +238,10 @@ gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax,
  * starts with every applicable variant on.  The bits select them: */
 enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
 /* Bits 3-4 (value << GPE_VARIANT_ROW_TILE_SHIFT, value 0..2): on rows of
- * 256 points and more the one-shot row pass of a step (and the adjoint's
- * row pass) runs 2^-value of its default rows per CTA (256 threads' worth,
- * at least one warp), so that a small grid spreads over more SMs; shorter
- * rows ignore it. */
+ * 256 points and more the one-shot row passes of the context's steps,
+ * observables and adjoint run 2^-value of their default rows per CTA (256
+ * threads' worth, at least one warp), so that a small grid spreads over more
+ * SMs; shorter rows ignore it. */
 enum { GPE_VARIANT_ROW_TILE_SHIFT = 3 };
 int gpe_get_pass_variants(const gpe_ctx *ctx);                /* -1 for a null context */
 gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants); /* GPE_EINVAL outside 0..23 */

@@ -308,7 +308,7 @@ gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd,
         return timed_launch(c, 0, [&] { return launch_row_stream(a, c->stream); }, "row pass");
     if (mode == ROW_PT && c->group_rows && row_group_ok(c->nx, c->ny))
         return timed_launch(c, 0, [&] { return launch_row_group(a, c->stream); }, "row pass");
-    const int ts = mode == ROW_PT ? c->row_tile_shift : 0;
+    const int ts = c->row_tile_shift;
     return timed_launch(c, 0, [&] { return launch_row(mode, a, c->stream, ts); }, "row pass");
 }
 
