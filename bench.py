@@ -62,7 +62,8 @@ def config(args, world):
             "trajectories_per_gpu": args.batch,
             "resident_bytes_per_gpu": 8 * args.size * args.size * args.batch,
             "l2": "inputs larger than L2 (psi of all trajectories > 126 MB), no flush",
-            "schedule": "lockstep over trajectories, passes of two trajectories overlap on two library streams",
+            "schedule": "lockstep over trajectories, one library stream per trajectory (passes of different "
+                        "trajectories overlap)",
             "parallelism": f"replicas x{world}"}
 
 
@@ -241,7 +242,7 @@ def cufft_baseline(psis, p, dt, steps, dev):
 def sweep_leg(dev, steps=40):
     """The batched phase-diagram sweep (384 cavity instances: 128 at 256^2,
     192 at 512^2, 64 at 1024^2, imaginary time): lockstep gpe_step_many over
-    all instances (two library streams, interior steps replayed from a CUDA
+    all instances (16 library streams, interior steps replayed from a CUDA
     graph) against the plain per-instance loop of gpe_step on one stream."""
     import numpy as np
     import torch

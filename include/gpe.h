@@ -131,11 +131,11 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * schedule -- e.g. a batch of trajectories of a parameter sweep (Sec. 5.3
  * phase diagram), possibly of different sizes.  With count > 1 the passes
  * run on streams owned by the library ("lanes", created on first use per
- * device: 2 when the grids average 2^20 points or more, up to 8 below), so
- * that passes of different contexts overlap on the GPU; each context's steps
- * are ordered after the work already on its own stream, and its stream waits
- * for them, so callers see the same ordering as with gpe_step.  For batches
- * of small grids with no time-dependent control and no profiling, the
+ * device: one per context, at most 16), so that passes of different contexts
+ * overlap on the GPU; each context's steps are ordered after the work
+ * already on its own stream, and its stream waits for them, so callers see
+ * the same ordering as with gpe_step.  For batches of grids of at most 2^20
+ * points on average with no time-dependent control and no profiling, the
  * interior steps 1 .. n-2 are captured once into a CUDA graph and replayed
  * (same results bit for bit, one host launch per step).  Calls from several
  * host threads on one device take turns on the lanes.  Contexts must be on

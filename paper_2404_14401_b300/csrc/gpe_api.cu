@@ -73,23 +73,27 @@ namespace {
 bool pow2_in_range(int n) { return n >= 8 && n <= 8192 && (n & (n - 1)) == 0; }
 
 // Streams of the library on which gpe_step_many runs contexts side by side
-// (created on first use per device, kept until the process exits).  Two
-// lanes let the passes of one large trajectory fill the SMs that the other's
-// pass leaves idle at its end, and hide the gaps between launches; grids
-// below 2^20 points launch too few CTAs to fill the GPU alone, so batches of
-// them use up to kLanes lanes.
-constexpr int kLanes = 8;
+// (created on first use per device, kept until the process exits): one lane
+// per context up to kLanes.  Passes of different contexts then fill the SMs
+// that one pass leaves idle (its tail, or all but a few SMs for a small
+// grid) and hide the gaps between launches.  Measured: the phase-diagram
+// sweep (384 grids of 256^2 .. 1024^2) ran at 35.1 G pt*steps/s on 8 lanes,
+// 41.0 on 16, 40.9 on 32 and 38.9 on 64; 8 trajectories of 2048^2 at 72.2
+// on 2 lanes and 73.4 on 8.
+constexpr int kLanes = 16;
+// Batches of grids of at most 2^20 points on average are "small": their
+// interior steps are replayed from a CUDA graph (one host launch per step).
 bool small_grids(gpe_ctx *const *ctxs, int count)
 {
     double pts = 0.0;
     for (int i = 0; i < count; ++i) pts += (double)ctxs[i]->nx * ctxs[i]->ny;
-    return pts / count < (double)(1 << 20);
+    return pts / count <= (double)(1 << 20);
 }
 int lanes_for(gpe_ctx *const *ctxs, int count)
 {
+    (void)ctxs;
     if (count < 2) return 0;
-    const int want = small_grids(ctxs, count) ? kLanes : 2;
-    return count < want ? count : want;
+    return count < kLanes ? count : kLanes;
 }
 struct Lanes {
     cudaStream_t s[kLanes];
@@ -822,9 +826,10 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
     // short enough for the host's launch rate to matter, one of them is
     // captured into a CUDA graph (every lane, every context) and the graph is
     // replayed for the others: one host launch per step instead of one per
-    // pass.  (For large grids the free-running lanes overlap better than the
-    // per-step joins of graph replays: 72.1 against 71.4 G pt*steps/s at
-    // 2048^2 x 8.)  Profiling contexts keep per-pass launches (their events).
+    // pass.  (At 2048^2 x 8 on 8 lanes replays and free-running lanes
+    // measured alike, 73.4 and 73.3 G pt*steps/s, and on 2 lanes the replays'
+    // per-step joins cost 1%; large batches keep per-pass launches.)
+    // Profiling contexts keep per-pass launches (their events).
     bool graph = L && nl >= 2 && n >= 4 && small_grids(ctxs, count) && !getenv("GPE_NO_GRAPH");
     for (int i = 0; i < count && graph; ++i) graph = !ctxs[i]->prof && ctxs[i]->ctrl_t.empty();
     int s = 0;
