@@ -644,7 +644,11 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes,
-                     "avg_launch_ms": dom_ms, "row_pass_ms": row_ms, "col_pass_ms": col_ms},
+                     "avg_launch_ms": dom_ms, "row_pass_ms": row_ms, "col_pass_ms": col_ms,
+                     "step_achieved": 32 * n * n * B / (ms / args.steps * 1e-3) / 1e9,
+                     "step_frac": 32 * n * n * B / (ms / args.steps * 1e-3) / 1e9 / peak,
+                     "step_note": "whole timed step (all passes of all trajectories, overlapped on the lanes) "
+                                  "at 32 B/point algorithmic, this rank"},
         "cpu_baseline": cpu,
         "cufft_baseline": cufft,
         "adjoint": adj,
