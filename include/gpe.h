@@ -110,7 +110,10 @@ size_t gpe_workspace_size(int nx, int ny);
 /* Create a context.  psi_dev: complex64 [ny][nx], 16-byte aligned, borrowed
  * for the context's life.  workspace_dev: >= gpe_workspace_size bytes,
  * 256-byte aligned, borrowed.  stream: a cudaStream_t (NULL = legacy default).
- * m > 0, Lx, Ly > 0.  The context starts at t = 0 with no potential.
+ * m > 0, Lx, Ly > 0.  The context starts at t = 0 with no potential.  The
+ * device current at this call is the context's device: every later call that
+ * launches work on the context must be made with that device current (the
+ * call returns GPE_EINVAL otherwise, before launching anything).
  * Errors: GPE_EINVAL (sizes/pointers/alignment), GPE_ENOMEM (workspace too
  * small), GPE_ECUDA. *out is NULL on failure. */
 gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g,

@@ -53,6 +53,7 @@ struct gpe_ctx {
     int kin_mode;
     bool kin_valid;
     int spins;
+    int device;              // the CUDA device current at gpe_create; every launch checks it
     int stream_passes;       // use the persistent streaming row pass where it applies
     int stream_cols;         // use the persistent streaming column pass where it applies
     int group_rows;          // use the grouped persistent row pass where it applies
@@ -289,6 +290,11 @@ cudaEvent_t take_event(gpe_ctx *c)
 // Launch one pass, bracketed by events when profiling (kind 0 row, 1 column).
 template <class F> gpe_status timed_launch(gpe_ctx *c, int kind, F &&launch, const char *what)
 {
+    // the context's pointers, tables and tensor map are on its own device: a
+    // kernel launched with another device current would address foreign memory
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+        return fail(c, GPE_EINVAL, "%s: the context is on device %d, the current device is %d", what, c->device, dev);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof) {
         e0 = take_event(c);
@@ -366,7 +372,10 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     const Layout L = layout(nx, ny);
     if (ws_bytes < L.total) return GPE_ENOMEM;
 
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return GPE_ECUDA;
     gpe_ctx *c = new gpe_ctx();
+    c->device = dev;
     c->nx = nx; c->ny = ny; c->Lx = Lx; c->Ly = Ly; c->m = m; c->g = g;
     c->psi = (float2 *)psi_dev;
     c->ws = (unsigned char *)workspace_dev;
@@ -791,8 +800,13 @@ static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, 
 gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode)
 {
     if (!ctxs || count < 1) return GPE_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GPE_ECUDA;
     for (int i = 0; i < count; ++i) {
         TRY(step_check(ctxs[i], n, dt, mode));
+        if (ctxs[i]->device != dev)
+            return fail(ctxs[i], GPE_EINVAL, "gpe_step_many: context on device %d, current device %d",
+                        ctxs[i]->device, dev);
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return fail(ctxs[i], GPE_EINVAL, "gpe_step_many: repeated context");
     }
