@@ -309,7 +309,10 @@ size_t gpe_adjoint_workspace_size_ex(int nx, int ny, int nsteps, int variant);
 gpe_status gpe_adjoint_lattice_ex(gpe_ctx *ctx, int nsteps, double dt, int variant, const void *phi_dev,
                                   void *adj_ws, size_t adj_ws_bytes, double *J_out, double *grad_out);
 
-/* Release the context (host memory only; borrowed memory is untouched). */
+/* Release the context (host memory only; borrowed memory is untouched).
+ * It does not wait for work already enqueued on the context's stream: keep
+ * psi, the workspace and any borrowed V array valid until that work is done
+ * (gpe_sync, or a synchronisation of the stream). */
 void gpe_destroy(gpe_ctx *ctx);
 
 /* Message for the last error on ctx (never NULL). */

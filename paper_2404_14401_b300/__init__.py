@@ -30,12 +30,29 @@ class Simulation:
         ws = abi.gpe_workspace_size(nx, ny)
         if ws == 0:
             raise GPEError(abi.GPE_EINVAL, f"unsupported grid {nx}x{ny}")
-        self.psi = torch.zeros((ny, nx), dtype=torch.complex64, device=self.device)
-        self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.psi = self._borrow(torch.zeros((ny, nx), dtype=torch.complex64, device=self.device))
+        self.ws = self._borrow(torch.empty(ws, dtype=torch.uint8, device=self.device))
         self._keep = []
         self._ctrl = None
+        self._order_after_current()
         self.ctx = abi.gpe_create(nx, ny, Lx, Ly, m, g, self.psi.data_ptr(), self.ws.data_ptr(), ws,
                                   self.stream.cuda_stream)
+
+    def _order_after_current(self):
+        """Make the context's stream wait for the work torch enqueued on the
+        current stream (allocations, fills, uploads) before it uses them."""
+        cur = self.torch.cuda.current_stream(self.device)
+        if self.stream != cur:
+            self.stream.wait_stream(cur)
+
+    def _borrow(self, t):
+        """A device tensor the context will use on its stream: when that stream
+        is not the one the tensor was allocated on, tell torch's caching
+        allocator, so that the memory is not handed out again before the
+        context's work on it has finished."""
+        if self.stream != self.torch.cuda.current_stream(self.device):
+            t.record_stream(self.stream)
+        return t
 
     # ------------------------------------------------------------ set-up
     def set_potential(self, p: dict):
@@ -50,7 +67,8 @@ class Simulation:
         keep = []
         self._ctrl = None
         if p.get("Varr") is not None:
-            V = torch.as_tensor(np.asarray(p["Varr"], dtype=np.float32)).to(self.device)
+            V = self._borrow(torch.as_tensor(np.asarray(p["Varr"], dtype=np.float32)).to(self.device))
+            self._order_after_current()
             keep.append(V)
             pot.V = V.data_ptr()
         if p.get("ctrl_t") is not None:
@@ -72,7 +90,8 @@ class Simulation:
             abi.gpe_set_psi(self.ctx, h.data_ptr(), False)
             self.sync()
         else:
-            t = psi.to(device=self.device, dtype=torch.complex64).contiguous()
+            t = self._borrow(psi.to(device=self.device, dtype=torch.complex64).contiguous())
+            self._order_after_current()
             abi.gpe_set_psi(self.ctx, t.data_ptr(), True)
             self._tmp = t
 
@@ -94,7 +113,7 @@ class Simulation:
         """Kapitza-Dirac readout: fractions of the momentum distribution in the
         windows |k - 2 n k0| < k0 along `axis`, n = -nmax..nmax."""
         torch = self.torch
-        scratch = torch.empty(8 * self.nx * self.ny, dtype=torch.uint8, device=self.device)
+        scratch = self._borrow(torch.empty(8 * self.nx * self.ny, dtype=torch.uint8, device=self.device))
         return np.array(abi.gpe_momentum_populations(self.ctx, axis, k0, nmax, scratch.data_ptr(), scratch.numel()))
 
     def tune(self, dt: float, imag: bool = False, reps: int = 5) -> dict:
@@ -102,7 +121,7 @@ class Simulation:
         of psi and keep the fastest (gpe_tune).  Returns the chosen variant bits
         and the per-variant milliseconds."""
         torch = self.torch
-        scratch = torch.empty(8 * self.nx * self.ny, dtype=torch.uint8, device=self.device)
+        scratch = self._borrow(torch.empty(8 * self.nx * self.ny, dtype=torch.uint8, device=self.device))
         v, t = abi.gpe_tune(self.ctx, dt, abi.GPE_IMAG if imag else abi.GPE_REAL, scratch.data_ptr(),
                             scratch.numel(), reps)
         keys = ("row_one_shot", "row_grouped", "row_streaming", "col_one_shot", "col_streaming")
@@ -127,11 +146,12 @@ class Simulation:
         [ny][nx]."""
         torch = self.torch
         phi_t = torch.as_tensor(np.asarray(phi, dtype=np.complex64) if isinstance(phi, np.ndarray) else phi)
-        phi_t = phi_t.to(device=self.device, dtype=torch.complex64).contiguous()
+        phi_t = self._borrow(phi_t.to(device=self.device, dtype=torch.complex64).contiguous())
+        self._order_after_current()
         variant = abi.GPE_ADJ_REVERSE if reverse else abi.GPE_ADJ_CHECKPOINT
         nbytes = abi.gpe_adjoint_workspace_size_ex(self.nx, self.ny, nsteps, variant)
         if getattr(self, "_adj_ws", None) is None or self._adj_ws.numel() < nbytes:
-            self._adj_ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._adj_ws = self._borrow(torch.empty(nbytes, dtype=torch.uint8, device=self.device))
         nctrl = 0 if self._ctrl is None else len(self._ctrl)
         return abi.gpe_adjoint_lattice_ex(self.ctx, nsteps, dt, variant, phi_t.data_ptr(), self._adj_ws.data_ptr(),
                                           self._adj_ws.numel(), nctrl)

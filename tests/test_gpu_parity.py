@@ -429,6 +429,27 @@ def test_step_many_from_two_host_threads_matches_one_context_alone():
         assert np.array_equal(g, ref)
 
 
+def test_context_on_its_own_stream_matches_the_default_stream():
+    """A context created on a side stream (its tensors then tell torch's
+    allocator about that stream) steps exactly as one on the current stream."""
+    from paper_2404_14401_b300 import Simulation
+    w = gi.lattice_real_time(n=128, L=20.0)
+    p = dict(w["params"])
+    psi0 = c64(gi.gaussian_state(128, 128, 20.0, 20.0, 1.5, 1e-2, seed=62))
+    a = sim_for(p)
+    a.set_psi(psi0)
+    a.step(25, w["dt"])
+    side = torch.cuda.Stream()
+    b = Simulation(128, 128, p["Lx"], p["Ly"], p["m"], p["g"], stream=side)
+    b.set_potential(p)
+    b.set_psi(psi0)
+    b.step(25, w["dt"])
+    assert b.sync() == 0
+    assert np.array_equal(a.get_psi(), b.get_psi())
+    b.close()
+    side.synchronize()
+
+
 # ------------------------------------------------------------------ graph replay
 # With two or more contexts and no time-dependent control, gpe_step_many
 # captures one interior lockstep step into a CUDA graph and replays it.  The
