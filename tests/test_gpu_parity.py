@@ -382,6 +382,36 @@ def test_lockstep_lanes_match_single_context_stepping(imag):
         assert np.array_equal(s.get_psi(), ref)
 
 
+def test_throughput_configuration_in_lockstep_matches_single_stepping_and_oracle():
+    """The launch configuration the benchmark times: 8 trajectories of the
+    2048^2 real-time lattice workload stepped in lockstep by gpe_step_many
+    (one lane each).  Every trajectory equals its single-context stepping bit
+    for bit, and one of them matches the oracle element by element."""
+    from paper_2404_14401_b300 import Simulation
+    w = gi.lattice_real_time(n=2048, L=40.0)
+    p, dt, n = w["params"], w["dt"], 10
+    base = w["psi0"]()
+    states = []
+    for b in range(8):
+        z = gi.normal(100 + b, 2 * 2048 * 2048).reshape(2, 2048, 2048)
+        x = base * (1 + 1e-3 * (z[0] + 1j * z[1]))
+        states.append(c64(x / np.sqrt(np.sum(np.abs(x) ** 2) * (40.0 / 2048) ** 2)))
+    sims = []
+    for x in states:
+        s = sim_for(p)
+        s.set_psi(x)
+        sims.append(s)
+    Simulation.step_many(sims, n, dt)
+    for s, x in zip(sims, states):
+        assert s.sync() == 0
+        one = sim_for(p)
+        one.set_psi(x)
+        one.step(n, dt)
+        assert np.array_equal(s.get_psi(), one.get_psi())
+    ref, _ = oracle.evolve(p, states[3].astype(np.complex128), n, dt, False)
+    assert rel_l2(sims[3].get_psi(), ref) < state_tol(n)
+
+
 def test_step_many_from_two_host_threads_matches_one_context_alone():
     """Two host threads stepping their own batches of small grids at once (the
     graph-replay path on the shared lanes) give each context's single-stream
