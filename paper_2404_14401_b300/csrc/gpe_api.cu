@@ -845,7 +845,10 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
     // per-step joins cost 1%; large batches keep per-pass launches.)
     // Profiling contexts keep per-pass launches (their events).
     bool graph = L && nl >= 2 && n >= 4 && small_grids(ctxs, count) && !getenv("GPE_NO_GRAPH");
-    for (int i = 0; i < count && graph; ++i) graph = !ctxs[i]->prof && ctxs[i]->ctrl_t.empty();
+    // time enters a pass only through a control table and the cavity probe
+    // (Sec. 5.4): with either, consecutive steps have different arguments
+    for (int i = 0; i < count && graph; ++i)
+        graph = !ctxs[i]->prof && ctxs[i]->ctrl_t.empty() && ctxs[i]->pot.probe_omega == 0.0;
     int s = 0;
     if (graph && st == GPE_OK) {
         for (int i = 0; i < count && st == GPE_OK; ++i) st = step_part(ctxs[i], 0, n, dt, mode);

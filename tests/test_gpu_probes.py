@@ -76,3 +76,22 @@ def test_bragg_probe_cavity_field_matches_oracle():
         assert abs(a - b) < 1e-5 * abs(b) + 1e-7, (t, a, b)
         assert abs(a - complex(q["alpha_re"], q["alpha_im"])) > 1e-3 * abs(b)
     assert float(np.linalg.norm(s.get_psi() - ref) / np.linalg.norm(ref)) < 1e-5
+
+
+def test_probed_batch_in_lockstep_matches_single_stepping():
+    """A batch of small cavity grids under the probe, stepped by gpe_step_many:
+    the probe makes every step's cavity-field update depend on time, so the
+    batch must not replay one captured step; each context equals its own
+    single-context stepping bit for bit."""
+    from paper_2404_14401_b300 import Simulation
+    w = gi.bragg_probe(n=64, L=12.0, steps=30)
+    p, dt = w["params"], w["dt"]
+    psi0 = w["psi0"]().astype(np.complex64)
+    etas = (1.0, 1.5, 2.0)
+    batch = [sim(dict(p, eta=e), psi0) for e in etas]
+    Simulation.step_many(batch, 30, dt)
+    for e, s in zip(etas, batch):
+        one = sim(dict(p, eta=e), psi0)
+        one.step(30, dt, False)
+        assert s.sync() == 0
+        assert np.array_equal(s.get_psi(), one.get_psi())
