@@ -2,7 +2,8 @@
 accumulations against the FP64 oracle, and what FP32 accumulation would
 cost instead.
 
-Three dynamics (the survey's workloads at sizes the oracle finishes in
+Three dynamics (the imaginary-time trap, real-time lattice and cavity-ramp
+workloads, at sizes the oracle finishes in
 seconds) report, for the final state, the relative error of every
 observable the library returns (norm, E_kin, E_pot, E_int, E, mu, O, B,
 alpha).  For the sums over the grid (norm, E_pot, E_int, O, B) the same GPU
