@@ -456,6 +456,23 @@ def oracle_sample(n, budget_s=16.0, min_steps=1):
     return n * n * k / secs, k, secs, oracle.threads()
 
 
+def oracle_sample_single_thread(n, budget_s=6.0):
+    """The same oracle sample on one host thread (a child process started with
+    OMP_NUM_THREADS=1; it touches no GPU).  Returns a dict, or None if the
+    child failed."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "v, k, secs, thr = bench.oracle_sample(%d, budget_s=%r); "
+            "print(json.dumps({'value': v, 'steps': k, 'secs': secs, 'cores': thr}))" % (ROOT, n, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, env=env)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+    return {"value": d["value"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+            "sample": f"one {n}x{n} trajectory, {d['steps']} FP64 split steps ({d['secs']:.1f} s), one thread"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -629,7 +646,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu:
         v, k, secs, thr = oracle_sample(n)
         cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"one {n}x{n} trajectory of the workload, {k} FP64 split steps ({secs:.1f} s)"}
+               "sample": f"one {n}x{n} trajectory of the workload, {k} FP64 split steps ({secs:.1f} s)",
+               "single_thread": oracle_sample_single_thread(n)}
 
     if rank != 0:
         return
