@@ -387,7 +387,11 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->spins = 1 << 24;
     c->stream_passes = getenv("GPE_NO_STREAM_PASSES") ? 0 : 1;
     c->stream_cols = c->stream_passes;
-    c->group_rows = getenv("GPE_NO_GROUP_ROWS") ? 0 : 1;
+    // the grouped row pass by default only for 2048-point rows: at 1024 (and
+    // below) the one-shot pass, whose CTAs share SMs with other passes,
+    // measured faster under gpe_step_many (1024^2 x 8: 71.8 against 64.2 G
+    // pt*steps/s), at 2048 the grouped pass (73.2 against 72.2)
+    c->group_rows = (getenv("GPE_NO_GROUP_ROWS") || nx != 2048) ? 0 : 1;
     c->row_tile_shift = 0;
     c->launches = 0;
     c->prof = false;

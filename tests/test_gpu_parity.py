@@ -331,19 +331,29 @@ def test_streaming_and_one_shot_passes_agree_bitwise(nx, ny, monkeypatch):
 # items, so both buffers and the store/reload hand-over are exercised.
 @pytest.mark.parametrize("nx,ny,imag", [(512, 16, False), (1024, 8, True), (2048, 8, False),
                                         (2048, 64, True), (512, 4096, False)])
-def test_grouped_and_one_shot_row_passes_agree_bitwise(nx, ny, imag, monkeypatch):
+def test_grouped_and_one_shot_row_passes_agree_bitwise(nx, ny, imag):
+    from paper_2404_14401_b300 import gpe as abi
     w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
     psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=15))
     outs = []
-    for env in (None, "1"):
-        if env:
-            monkeypatch.setenv("GPE_NO_GROUP_ROWS", env)
+    for grouped in (True, False):
         s = sim_for(p)
+        base = s.variants & ~abi.GPE_VARIANT_GROUP_ROWS            # the column variant stays as it is
+        s.variants = base | (abi.GPE_VARIANT_GROUP_ROWS if grouped else 0)
         s.set_psi(psi0)
         s.step(10, 2e-3 if imag else w["dt"], imag)
         outs.append(s.get_psi())
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_default_row_variant_is_grouped_only_for_2048_point_rows():
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.lattice_real_time(n=64, L=16.0)
+    for nx in (256, 512, 1024, 2048, 4096):
+        s = sim_for(dict(w["params"], nx=nx, ny=16, Lx=box(nx), Ly=box(16)))
+        assert bool(s.variants & abi.GPE_VARIANT_GROUP_ROWS) == (nx == 2048)
+        assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
 
 
 
