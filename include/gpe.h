@@ -238,10 +238,10 @@ gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax,
  * tables in shared memory, TMA double buffering), rows and columns of 4096
  * points a streaming persistent variant; every grid has the one-shot
  * variant (a CTA per group of rows or per TMA tile of columns).  A context
- * starts with the streaming variants on where they apply and the grouped
- * row pass on for 2048-point rows only (at 1024 points and below the
- * one-shot pass overlapped better with other grids' passes under
- * gpe_step_many).  The bits select them: */
+ * starts with the streaming variants on where they apply, the grouped row
+ * pass on for 2048-point rows only, and the half row tile (below) for 512-
+ * and 1024-point rows: with those the passes of other grids overlapped best
+ * under gpe_step_many.  The bits select them: */
 enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
 /* Bits 3-4 (value << GPE_VARIANT_ROW_TILE_SHIFT, value 0..2): on rows of
  * 256 points and more the one-shot row passes of the context's steps,

@@ -392,7 +392,11 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // measured faster under gpe_step_many (1024^2 x 8: 71.8 against 64.2 G
     // pt*steps/s), at 2048 the grouped pass (73.2 against 72.2)
     c->group_rows = (getenv("GPE_NO_GROUP_ROWS") || nx != 2048) ? 0 : 1;
-    c->row_tile_shift = 0;
+    // half-height one-shot row tiles for 512- and 1024-point rows: 8 grids of
+    // 1024^2 under gpe_step_many ran at 77.2 against 72.5 G pt*steps/s, of
+    // 512^2 at 56.0 against 53.8; at 2048 the half tile was slower (65.7
+    // against 71.7) and at 256 the same
+    c->row_tile_shift = (nx == 512 || nx == 1024) ? 1 : 0;
     c->launches = 0;
     c->prof = false;
     for (int k = 0; k < GPE_PASS_KINDS; ++k) {

@@ -347,13 +347,14 @@ def test_grouped_and_one_shot_row_passes_agree_bitwise(nx, ny, imag):
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_default_row_variant_is_grouped_only_for_2048_point_rows():
+def test_default_row_variants_follow_the_row_length():
     from paper_2404_14401_b300 import gpe as abi
     w = gi.lattice_real_time(n=64, L=16.0)
     for nx in (256, 512, 1024, 2048, 4096):
         s = sim_for(dict(w["params"], nx=nx, ny=16, Lx=box(nx), Ly=box(16)))
         assert bool(s.variants & abi.GPE_VARIANT_GROUP_ROWS) == (nx == 2048)
         assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
+        assert s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT == (1 if nx in (512, 1024) else 0)
 
 
 
