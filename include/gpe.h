@@ -139,8 +139,9 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * already on its own stream, and its stream waits for them, so callers see
  * the same ordering as with gpe_step.  For batches of grids of at most 2^20
  * points on average with no time-dependent control or probe and no profiling, the
- * interior steps 1 .. n-2 are captured once into a CUDA graph and replayed
- * (same results bit for bit, one host launch per step).  Calls from several
+ * interior steps 1 .. n-2 are captured into a CUDA graph of up to 8 steps
+ * (fewer for large batches) and replayed (same results bit for bit, one host
+ * launch per graph).  Calls from several
  * host threads on one device take turns on the lanes.  Contexts must be on
  * the current device.  Same argument rules and errors as gpe_step; contexts
  * must be distinct.  Environment: GPE_SERIAL_MANY (no lanes: the contexts'
