@@ -137,7 +137,7 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * device: one per context, at most 16), so that passes of different contexts
  * overlap on the GPU; each context's steps are ordered after the work
  * already on its own stream, and its stream waits for them, so callers see
- * the same ordering as with gpe_step.  For batches of grids of at most 2^20
+ * the same ordering as with gpe_step.  For batches of grids of at most 2^22
  * points on average with no time-dependent control or probe and no profiling, the
  * interior steps 1 .. n-2 are captured into a CUDA graph of up to 8 steps
  * (fewer for large batches) and replayed (same results bit for bit, one host

@@ -82,13 +82,14 @@ bool pow2_in_range(int n) { return n >= 8 && n <= 8192 && (n & (n - 1)) == 0; }
 // 41.0 on 16, 40.9 on 32 and 38.9 on 64; 8 trajectories of 2048^2 at 72.2
 // on 2 lanes and 73.4 on 8.
 constexpr int kLanes = 16;
-// Batches of grids of at most 2^20 points on average are "small": their
-// interior steps are replayed from a CUDA graph (one host launch per step).
+// Batches of grids of at most 2^22 points (2048^2) on average replay their
+// interior steps from CUDA graphs: 8 grids of 2048^2 ran at 74.0 G pt*steps/s
+// with 8-step graphs against 73.4 without, 2 of 4096^2 at 51.5 against 51.8.
 bool small_grids(gpe_ctx *const *ctxs, int count)
 {
     double pts = 0.0;
     for (int i = 0; i < count; ++i) pts += (double)ctxs[i]->nx * ctxs[i]->ny;
-    return pts / count <= (double)(1 << 20);
+    return pts / count <= (double)(1 << 22);
 }
 int lanes_for(gpe_ctx *const *ctxs, int count)
 {
@@ -861,13 +862,11 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
     }
     for (int i = 0; i < count && st == GPE_OK; ++i) st = step_prologue(ctxs[i], dt, mode);
     // Interior steps (0 < s < n-1) are identical when no context has a
-    // time-dependent control.  For batches of small grids, whose passes are
-    // short enough for the host's launch rate to matter, up to kGraphSteps of
-    // them are captured into a CUDA graph (every lane, every context) and the
-    // graph is replayed for the others: one host launch per graph instead of
-    // one per pass.  (At 2048^2 x 8 on 8 lanes replays and free-running lanes
-    // measured alike, 73.4 and 73.3 G pt*steps/s, and on 2 lanes the replays'
-    // per-step joins cost 1%; large batches keep per-pass launches.)
+    // time-dependent control.  For batches of grids up to 2048^2, up to
+    // kGraphSteps of them are captured into a CUDA graph (every lane, every
+    // context) and the graph is replayed for the others: one host launch per
+    // graph instead of one per pass, and fewer points where every lane waits
+    // for the slowest.
     // Profiling contexts keep per-pass launches (their events).
     bool graph = L && nl >= 2 && n >= 4 && small_grids(ctxs, count) && !getenv("GPE_NO_GRAPH");
     // time enters a pass only through a control table and the cavity probe
