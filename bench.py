@@ -63,7 +63,7 @@ def config(args, world):
             "resident_bytes_per_gpu": 8 * args.size * args.size * args.batch,
             "l2": "inputs larger than L2 (psi of all trajectories > 126 MB), no flush",
             "schedule": "lockstep over trajectories, one library stream per trajectory (passes of different "
-                        "trajectories overlap)",
+                        "trajectories overlap), interior steps replayed from 8-step CUDA graphs",
             "parallelism": f"replicas x{world}"}
 
 
