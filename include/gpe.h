@@ -307,9 +307,10 @@ gpe_status gpe_adjoint_lattice(gpe_ctx *ctx, int nsteps, double dt, const void *
  * recovered states carry the rounding of the steps taken back, so the
  * gradient differs from the checkpointed one by about that much (the
  * reverse sweep costs the same passes as the recomputation it replaces).
- * Workspace (gpe_adjoint_workspace_size_ex): 3 copies of psi, the kinetic
- * factors of -dt and 2 nsteps + 1 doubles, independent of the number of
- * steps apart from those doubles.  Returns 0 / GPE_EINVAL for an unknown
+ * Workspace (gpe_adjoint_workspace_size_ex): 2 copies of psi (psi_T and
+ * lambda), the kinetic factors of -dt and 2 nsteps + 1 doubles, independent
+ * of the number of steps apart from those doubles; the step back overwrites
+ * the context's psi after the row adjoint pass of that step has read it.  Returns 0 / GPE_EINVAL for an unknown
  * variant; otherwise as gpe_adjoint_workspace_size / gpe_adjoint_lattice. */
 typedef enum { GPE_ADJ_CHECKPOINT = 0, GPE_ADJ_REVERSE = 1 } gpe_adjoint_variant;
 size_t gpe_adjoint_workspace_size_ex(int nx, int ny, int nsteps, int variant);

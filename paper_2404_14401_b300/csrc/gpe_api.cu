@@ -560,8 +560,8 @@ gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
 // Layout of the adjoint workspace for n steps: S = ceil(sqrt(n)) steps per
 // segment, K = ceil(n / S) segments.  Checkpoints psi_{kS} (k < K) and psi_n,
 // the S + 1 states of one segment, lambda, and the 2n + 1 per-phase dJ/dv.
-// GPE_ADJ_REVERSE keeps no checkpoints: ck holds psi_T only, st one state,
-// and kx / ky the kinetic factors of -dt for the backward steps.
+// GPE_ADJ_REVERSE keeps no checkpoints: ck holds psi_T only, and kx / ky the
+// kinetic factors of -dt for the backward steps (st is not used).
 struct AdjLayout {
     int S, K, variant;
     size_t P, ck, st, lam, g, kx, ky, total;
@@ -575,8 +575,8 @@ static AdjLayout adj_layout(int nx, int ny, int n, int variant = GPE_ADJ_CHECKPO
     if (variant == GPE_ADJ_REVERSE) {
         L.S = n;
         L.K = 0;
-        L.st = L.ck + L.P;
-        L.lam = L.st + L.P;
+        L.st = 0;
+        L.lam = L.ck + L.P;
         L.kx = L.lam + L.P;
         L.ky = L.kx + align256(sizeof(float2) * (size_t)nx);
         L.g = L.ky + align256(sizeof(float2) * (size_t)ny);
@@ -691,22 +691,25 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
 
     // adjoint passes of step s: the row pass with the step's end state psi_{s+1},
     // the column pass with its initial state psi_s
-    auto adjoint_step = [&](int s, const float2 *psi_s, const float2 *psi_s1) -> gpe_status {
-        const double ts = t0 + s * dt, te = ts + dt;
+    auto adjoint_row = [&](int s, const float2 *psi_s1) -> gpe_status {
+        const double te = t0 + s * dt + dt;
         PassArgs ar = pass_args(c, phase_at(c, te, 0.5 * dt), red_at(c, te), 0, 0);
         ar.psi = lam;
         ar.psi2 = psi_s1;
         ar.gout = gdev + 2 * s + 1;
         ar.L0x = (float)c->pot.lat_V0x;
         ar.L0y = (float)c->pot.lat_V0y;
-        TRY(timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream, c->row_tile_shift); },
-                         "adjoint row pass"));
+        return timed_launch(c, GPE_PASS_ADJ_ROW, [&] { return launch_row(ROW_ADJ, ar, c->stream, c->row_tile_shift); },
+                            "adjoint row pass");
+    };
+    auto adjoint_col = [&](int s, const float2 *psi_s) -> gpe_status {
+        const double ts = t0 + s * dt;
         PassArgs ac = pass_args(c, phase_at(c, ts, 0.5 * dt), red_at(c, ts), 0, 0);
         ac.psi = lam;
         ac.psi2 = psi_s;
         ac.gout = gdev + 2 * s;
-        ac.L0x = ar.L0x;
-        ac.L0y = ar.L0y;
+        ac.L0x = (float)c->pot.lat_V0x;
+        ac.L0y = (float)c->pot.lat_V0y;
         TRY(timed_launch(c, GPE_PASS_ADJ_COL, [&] { return launch_col(COL_ADJ, ac, lam_map, c->stream); },
                          "adjoint column pass"));
         return GPE_OK;
@@ -723,10 +726,12 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         TRY(timed_launch(c, 2, [&] {
             return launch_kinetic_tables(Tb, c->nx, c->ny, c->Lx, c->Ly, c->m, -dt, 0, c->stream);
         }, "kinetic tables"));
+        // the row pass reads psi_{s+1} before the step back overwrites it, so
+        // the context's psi is the only state buffer
         for (int s = n - 1; s >= 0; --s) {
-            TRY(copy_d2d(c, st, c->psi));                         // psi_{s+1}
+            TRY(adjoint_row(s, c->psi));                          // with psi_{s+1}
             TRY(step_backward(c, dt, kx, ky));                    // psi <- psi_s, t <- t_s
-            TRY(adjoint_step(s, c->psi, st));
+            TRY(adjoint_col(s, c->psi));                          // with psi_s
         }
     }
 
@@ -741,8 +746,10 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
             TRY(gpe_step(c, 1, dt, GPE_REAL));
             TRY(copy_d2d(c, st + (size_t)i * P, c->psi));
         }
-        for (int s = s1 - 1; s >= s0; --s)
-            TRY(adjoint_step(s, st + (size_t)(s - s0) * P, st + (size_t)(s + 1 - s0) * P));
+        for (int s = s1 - 1; s >= s0; --s) {
+            TRY(adjoint_row(s, st + (size_t)(s + 1 - s0) * P));
+            TRY(adjoint_col(s, st + (size_t)(s - s0) * P));
+        }
     }
     // leave the context at the final state and time, as gpe_step would
     TRY(copy_d2d(c, c->psi, psiT));
