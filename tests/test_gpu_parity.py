@@ -522,6 +522,29 @@ def test_graph_replay_matches_per_pass_launches(imag, monkeypatch):
     assert runs[0][1] == runs[1][1]
 
 
+@pytest.mark.parametrize("steps", [4, 11, 30])
+def test_one_context_graph_replay_matches_per_pass_launches(steps, monkeypatch):
+    """gpe_step on one small grid replays its interior steps from graphs of up
+    to 8 steps on a library lane (4 steps: one 2-step graph; 11: one 8-step
+    graph and a leftover step; 30: three replays and leftovers); state and
+    launch count equal those of per-pass launches on the context's stream."""
+    w = gi.cavity_ramp(n=64, L=16.0, steps=400, dt=2e-4)
+    p = dict(w["params"], ctrl_target=0, eta=2.0, ctrl_t=None, ctrl_v=None)     # a cavity, no control
+    psi0 = c64(gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=63, checker=0.3, kc=p["kc"]))
+    runs = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("GPE_NO_GRAPH", env)
+        s = sim_for(p)
+        s.set_psi(psi0)
+        l0 = s.launches
+        s.step(steps, 2e-4, False)
+        assert s.sync() == 0
+        runs.append((s.get_psi(), s.launches - l0, s.t))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1] and runs[0][2] == runs[1][2]
+
+
 # ------------------------------------------------------------------ autotuner
 @pytest.mark.parametrize("nx,ny", [(2048, 64), (4096, 64), (64, 4096), (128, 128)])
 def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
