@@ -679,7 +679,8 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32), f64 reductions",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "dtype_note": "complex64 state, FFT and phase arithmetic in f32; grid reductions and the cavity field in f64",
         "data": "synthetic (seeded Gaussian relaxed in imaginary time, + seeded noise)",
         "config": dict(config(args, world), pass_variants=tune),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
