@@ -14,11 +14,18 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                   lattice momentum-basis exact evolution, 2nd order in dt
   evolve (imag)   pinned: harmonic ground state E = 1, Thomas-Fermi mu,
                   virial identity, unit norm
+  potential array pinned: a trap written into V_scale * V[y][x] gives the
+                  analytic-trap trajectory to 1e-12 on a non-square grid
+                  (transposed, shifted or unscaled arrays fail)
   cavity alpha    pinned: eta = 0 gives alpha = 0 and the plain GPE;
                   symmetric density gives O = 0; alpha formula against a
-                  direct quadrature of Eqs. (14)-(15) on a known density.
-                  The full self-consistent trajectory is parity-only
-                  (no closed form): "parity unpinned" for that trajectory.
+                  direct quadrature of Eqs. (14)-(15) on a known density;
+                  the update order in imaginary time (alpha from the density
+                  at the start of each half phase) against a plain numpy
+                  restatement of two steps on 8x8, to 1e-14.
+                  The full self-consistent trajectory over many steps has
+                  no closed form: its pieces are pinned, the trajectory as
+                  a whole is compared with the GPU only.
   observables     pinned: E = mu = 1 for the oscillator ground state,
                   kinetic energy of a Gaussian in closed form
   momentum pops   pinned: plane-wave superpositions give |c_n|^2 exactly;
