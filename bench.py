@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-control leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched phase-diagram sweep leg")
     ap.add_argument("--no-grids", action="store_true", help="skip the grid-size leg (1024^2 .. 8192^2)")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-trajectory 1024^2 / 2048^2 leg")
     return ap.parse_args()
 
 
@@ -63,7 +64,8 @@ def config(args, world):
             "resident_bytes_per_gpu": 8 * args.size * args.size * args.batch,
             "l2": "inputs larger than L2 (psi of all trajectories > 126 MB), no flush",
             "schedule": "lockstep over trajectories, one library stream per trajectory (passes of different "
-                        "trajectories overlap), interior steps replayed from 8-step CUDA graphs",
+                        "trajectories overlap), interior steps replayed from 8-step CUDA graphs, instantiated "
+                        "before the warm-up and kept by the library across calls",
             "parallelism": f"replicas x{world}"}
 
 
@@ -384,6 +386,51 @@ def grids_leg(dev):
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs", "cases": out, "cavity_512": cav}
 
 
+# ------------------------------------------------------------------ single-trajectory leg
+def single_leg(dev, steps=400):
+    """One trajectory of the real-time throughput configuration at 1024^2 and
+    2048^2 (psi0 relaxed in imaginary time as in the main leg), stepped alone
+    by gpe_step on one context: the per-grid rate that the batched headline
+    does not show.  The 8 MB / 32 MB state fits in L2, so between the timed
+    runs a 256 MB buffer is written to flush it; each run's device time is
+    taken with CUDA events and the median of 5 runs is reported."""
+    import numpy as np
+    import torch
+
+    import gpe_inputs as gi
+    from paper_2404_14401_b300 import Simulation
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = []
+    for n in (1024, 2048):
+        w = workload(n)
+        p, dt = w["params"], w["dt"]
+        s = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
+        s.set_potential(p)
+        s.set_psi(w["psi0"]().astype(np.complex64))
+        s.step(2000, 1e-3, imag=True)
+        s.t = 0.0
+        s.step(steps, dt)                               # builds and keeps this call's graph; warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rates = []
+        for _ in range(5):
+            flush.fill_(1)
+            e0.record()
+            s.step(steps, dt)
+            e1.record()
+            torch.cuda.synchronize()
+            rates.append(n * n * steps / (e0.elapsed_time(e1) * 1e-3))
+        med = statistics.median(rates)
+        out.append({"grid": [n, n], "trajectories": 1, "steps_per_run": steps, "value": med, "unit": UNIT,
+                    "ms_per_step": n * n / med * 1e3, "runs": rates, "status": s.sync(),
+                    "l2": "state fits in L2; a 256 MB write flushes it before each run"})
+        del s
+    del flush
+    torch.cuda.empty_cache()
+    return {"workload": "real-time lattice GPE (box 40, V0 = 5, k = 2 pi, g = 500, dt = 5e-4), one trajectory "
+                        "per grid, gpe_step", "cases": out}
+
+
 # ------------------------------------------------------------------ adjoint leg
 def adjoint_leg(dev, with_oracle):
     """The adjoint-control workload (512^2, 4000 real-time steps, 200 lattice
@@ -566,7 +613,17 @@ def run_ours(args, rank, world, local_rank):
     tune = dict(sims[0].tune(dt), used=v0)
     sims[0].variants = v0                         # gpe_tune applies its pick; keep the defaults
 
-    # warm-up, then exactly `steps` lockstep steps of all trajectories
+    # the timed steps run as up to 5 consecutive gpe_step_many calls (events
+    # between them, no sync), so that the median and the mean of 5 runs can be
+    # reported beside the total.  Each call replays its interior steps from a
+    # CUDA graph that the library instantiates on first use and keeps: one
+    # untimed call of each length makes them here, like an FFT plan, so that
+    # the timed calls replay them.  Then the warm-up, then exactly `steps`
+    # lockstep steps of all trajectories.
+    nrun = 5 if args.steps >= 5 else 1
+    cuts = [args.steps * i // nrun for i in range(nrun + 1)]
+    for k in sorted(set(cuts[i + 1] - cuts[i] for i in range(nrun))):
+        Simulation.step_many(sims, k, dt)
     Simulation.step_many(sims, args.warmup, dt)
     torch.cuda.synchronize()
     barrier()
@@ -575,10 +632,6 @@ def run_ours(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(local_rank) if rank == 0 else None
     time.sleep(0.4 if clocks else 0.0)
-    # the timed steps as 5 consecutive runs (events between them, no sync), so
-    # that the median and the mean of 5 runs can be reported beside the total
-    nrun = 5 if args.steps >= 5 else 1
-    cuts = [args.steps * i // nrun for i in range(nrun + 1)]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(nrun - 1)]
     torch.cuda.synchronize()
     barrier()
@@ -661,6 +714,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_grids:
         grids = grids_leg(dev)
 
+    single = None
+    if rank == 0 and not args.no_single:
+        single = single_leg(dev)
+
     adj = None
     if rank == 0 and not args.no_adjoint:
         adj = adjoint_leg(dev, not args.no_cpu)
@@ -692,7 +749,9 @@ def run_ours(args, rank, world, local_rank):
                      "step_note": "whole timed step (all passes of all trajectories, overlapped on the lanes) "
                                   "at 32 B/point algorithmic, this rank"},
         "cpu_baseline": cpu,
+        "ours_over_cufft": None if cufft is None else cufft["ours_over_cufft"],
         "cufft_baseline": cufft,
+        "single_trajectory": single,
         "adjoint": adj,
         "sweep": sweep,
         "grids": grids,

@@ -144,7 +144,11 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * points on average with no time-dependent control or probe and no profiling, the
  * interior steps 1 .. n-2 are captured into a CUDA graph of up to 8 steps
  * (fewer for large batches) and replayed (same results bit for bit, one host
- * launch per graph).  Calls from several
+ * launch per graph).  The instantiated graph is kept (the 8 most recently
+ * used per device) and replayed again by later calls on the same contexts,
+ * in the same order, with the same dt, mode and step count per graph, as
+ * long as none of the contexts has changed its potential, pass variants or
+ * wait limit since; gpe_destroy releases the graphs of its context.  Calls from several
  * host threads on one device take turns on the lanes.  Contexts must be on
  * the current device.  Same argument rules and errors as gpe_step; contexts
  * must be distinct.  Environment: GPE_SERIAL_MANY (no lanes: the contexts'
@@ -172,8 +176,22 @@ double gpe_get_time(const gpe_ctx *ctx);
  * same row/column kernels as gpe_step with the phases switched off. */
 gpe_status gpe_fft2(gpe_ctx *ctx, int sign);
 
-/* Wait for the stream; return and clear the latched device status. */
+/* Wait for the stream; return and clear the latched device status (and the
+ * counters the reducing passes use to find their last CTA). */
 gpe_status gpe_sync(gpe_ctx *ctx);
+
+/* Bound on every device wait of this context's kernels: the number of polls
+ * of a TMA barrier before the kernel gives up, latches GPE_ETIMEOUT and goes
+ * on without storing its results (default 2^24, far longer than any copy
+ * takes).  A CTA whose wait ran out still lets the copies it issued land (a
+ * fixed number of further polls) and still adds zero partial sums to the
+ * pass's reductions, so the context stays usable: after gpe_sync has
+ * returned and cleared the status, later calls compute correctly from the
+ * state psi then holds (rows or tiles of the failed pass keep their old
+ * values).  0 makes every wait give up at once, to test that path.
+ * Errors: GPE_EINVAL for a null context or a negative limit. */
+gpe_status gpe_set_wait_limit(gpe_ctx *ctx, int spins);
+int gpe_get_wait_limit(const gpe_ctx *ctx);              /* -1 for a null context */
 
 /* Run one kernel whose bounded barrier wait is given nothing to wait for,
  * so it must run out after about `spins` polls and latch GPE_ETIMEOUT

@@ -1,6 +1,13 @@
-"""Build the sm_103a CUDA library libgpe.so in-tree (nvcc, no GPU needed)."""
+"""Build the sm_103a CUDA library libgpe.so in-tree (nvcc, no GPU needed).
+
+Each .cu file is compiled to an object in parallel (separate nvcc processes;
+gpe_kernels.cu in KERNEL_PARTS parts, each emitting a share of the kernel
+instantiations), then the objects are linked into the shared library.  No relocatable device
+code: the files share no device functions.
+"""
 from __future__ import annotations
 
+import concurrent.futures
 import os
 import subprocess
 
@@ -9,9 +16,10 @@ SRC = [os.path.join(HERE, "csrc", f) for f in ("gpe_api.cu", "gpe_kernels.cu", "
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("gpe_fft.cuh", "gpe_internal.h")] + [
     os.path.join(os.path.dirname(HERE), "include", "gpe.h")]
 LIB = os.path.join(HERE, "libgpe.so")
+OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-         "-diag-suppress", "128"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "128"]
+KERNEL_PARTS = 5                                   # parts of gpe_kernels.cu compiled side by side
 
 
 def nvcc() -> str:
@@ -28,13 +36,28 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in DEPS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libgpe.so for sm_103a if missing or older than its sources."""
+def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compile libgpe.so for sm_103a if missing or older than its sources.
+    `extra`: further nvcc flags (for example a -D switch of a debug build)."""
     if force or stale():
-        cmd = [nvcc(), *ARCH, *FLAGS, *SRC, "-o", LIB]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        subprocess.run(cmd, check=True)
+        os.makedirs(OBJDIR, exist_ok=True)
+        flags = [*ARCH, *FLAGS, *extra] + (["-Xptxas=-v"] if verbose else [])
+        jobs = []                                   # (source, object, extra flags)
+        for f in SRC:
+            base = os.path.basename(f)[:-3]
+            if base == "gpe_kernels":               # compiled in parts (GPE_PART in the file)
+                jobs += [(f, os.path.join(OBJDIR, f"{base}_p{k}.o"), [f"-DGPE_PART={k}"]) for k in range(KERNEL_PARTS)]
+            else:
+                jobs.append((f, os.path.join(OBJDIR, base + ".o"), []))
+        objs = [o for _, o, _ in jobs]
+        with concurrent.futures.ThreadPoolExecutor(len(jobs)) as ex:
+            runs = [ex.submit(subprocess.run, [nvcc(), *flags, *x, "-c", f, "-o", o], check=True)
+                    for f, o, x in jobs]
+            for r in runs:
+                r.result()
+        tmp = LIB + ".tmp"
+        subprocess.run([nvcc(), *ARCH, "-shared", *objs, "-o", tmp], check=True)
+        os.replace(tmp, LIB)
     return LIB
 
 

@@ -22,11 +22,13 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -59,6 +61,8 @@ struct gpe_ctx {
     int group_rows;          // use the grouped persistent row pass where it applies
     int row_tile_shift;      // one-shot row pass: 2^-shift of the default rows per CTA (0..2)
     long long launches;
+    unsigned long long uid;          // unique over the process (never reused, unlike the pointer)
+    unsigned long long version;      // bumped by every call that changes the passes' arguments
     cudaEvent_t ev_fork, ev_join;   // ordering of gpe_step_many's lanes with this context's stream
     // per-pass event timing (gpe_profile)
     bool prof;
@@ -96,19 +100,35 @@ int lanes_for(gpe_ctx *const *ctxs, int count)
     (void)ctxs;
     return count < kLanes ? count : kLanes;
 }
+// An instantiated graph of K interior lockstep steps, kept across
+// gpe_step_many calls: its kernel arguments are fixed by the contexts (each
+// by its uid and version), dt, the mode, K and the lane count, so a later call
+// with the same key replays it without capturing again.
+struct GraphEntry {
+    std::vector<unsigned long long> key;   // uid, version per context, in order
+    double dt;
+    int mode, K, nl;
+    cudaGraphExec_t exec;
+    std::vector<long long> launches;       // kernels each context launches per replay
+    unsigned long long used;               // LRU stamp
+};
+constexpr size_t kGraphCache = 8;
 struct Lanes {
     cudaStream_t s[kLanes];
     cudaEvent_t ev[kLanes];        // fork / join of the other lanes into a capture on lane 0
     std::mutex mu;                 // one gpe_step_many at a time enqueues on these lanes
+    std::vector<GraphEntry> graphs;   // guarded by mu
+    unsigned long long clock = 0;
 };
+Lanes *g_lanes[64];                // per device, created on first use
+std::mutex g_lanes_mu;
 Lanes *lanes_for_current_device()
 {
     constexpr int kMaxDev = 64;
-    static std::mutex mu;
-    static Lanes *lanes[kMaxDev] = {};
+    Lanes **lanes = g_lanes;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
-    std::lock_guard<std::mutex> lock(mu);
+    std::lock_guard<std::mutex> lock(g_lanes_mu);
     if (!lanes[dev]) {
         Lanes *L = new Lanes;
         for (int i = 0; i < kLanes; ++i)
@@ -398,6 +418,11 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // against 71.7) and at 256 the same
     c->row_tile_shift = (nx == 512 || nx == 1024) ? 1 : 0;
     c->launches = 0;
+    {
+        static std::atomic<unsigned long long> next_uid{1};
+        c->uid = next_uid.fetch_add(1);
+    }
+    c->version = 0;
     c->prof = false;
     for (int k = 0; k < GPE_PASS_KINDS; ++k) {
         c->prof_ms[k] = 0.0;
@@ -453,6 +478,7 @@ gpe_status gpe_set_potential(gpe_ctx *c, const gpe_potential *p)
         return fail(c, GPE_EINVAL, "probe parameters must be finite");
     if (p->V && ((uintptr_t)p->V & 3u)) return fail(c, GPE_EINVAL, "potential array misaligned");
     c->pot = *p;
+    c->version++;
     c->ctrl_t.assign(p->ctrl_t, p->ctrl_t + p->nctrl);
     c->ctrl_v.assign(p->ctrl_v, p->ctrl_v + p->nctrl);
     c->pot.ctrl_t = nullptr;
@@ -768,34 +794,35 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     return GPE_OK;
 }
 
-// Capture step 1 of every context (on both lanes) into a graph and launch it
-// for steps 1 .. n-2.  The contexts' streams are the lanes at this point.
-// Interior steps captured per graph: fewer graph boundaries (where every lane
-// waits for the slowest), but the capture and instantiation, paid once per
-// gpe_step_many call, grow with the graph.  Up to kGraphSteps steps while
-// the graph stays within about 64 contexts' steps: 8 grids of 1024^2 ran at
-// 81.2 G pt*steps/s with 4 steps per graph against 77.1 with 1, while the
-// 384-grid sweep (40 steps per call) lost 11% to instantiating 4-step graphs.
+// Capture K interior steps of every context (on every lane) into a graph and
+// launch it for steps 1 .. R K (R = (n-2) / K replays).  The contexts'
+// streams are the lanes at this point.  Interior steps per graph: fewer graph
+// boundaries (where every lane waits for the slowest), but the capture and
+// instantiation grow with the graph.  Up to kGraphSteps steps while the graph
+// stays within about 64 contexts' steps: 8 grids of 1024^2 ran at 81.2 G
+// pt*steps/s with 4 steps per graph against 77.1 with 1, while the 384-grid
+// sweep (40 steps per call) lost 11% to instantiating 4-step graphs.  The
+// instantiated graph is kept (per device, the kGraphCache most recently used)
+// and replayed again by later calls with the same contexts, unchanged since
+// (uid, version), dt, mode, K and lane count, so a run split into many calls
+// pays the capture once.
 constexpr int kGraphSteps = 8;
 constexpr int kGraphContextSteps = 64;
 
-static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode, Lanes *L,
-                                        int nl, int *done)
+static GraphEntry *find_graph(Lanes *L, const std::vector<unsigned long long> &key, double dt, int mode, int K,
+                              int nl)
 {
-    *done = 0;
-    int K = kGraphContextSteps / count;                              // interior steps per replay
-    if (K > kGraphSteps) K = kGraphSteps;
-    if (K > n - 2) K = n - 2;
-    if (K < 1) K = 1;
-    const int R = (n - 2) / K;                                       // replays
+    for (GraphEntry &g : L->graphs)
+        if (g.dt == dt && g.mode == mode && g.K == K && g.nl == nl && g.key == key) return &g;
+    return nullptr;
+}
+
+static gpe_status capture_graph(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode, Lanes *L, int nl,
+                                int K, GraphEntry *out)
+{
     gpe_ctx *c0 = ctxs[0];
     std::vector<long long> before(count);
     for (int i = 0; i < count; ++i) before[i] = ctxs[i]->launches;
-    // the graph runs on lane 0: order it after the work already on every lane
-    for (int l = 1; l < nl; ++l) {
-        TRY(cuda_check(c0, cudaEventRecord(L->ev[l], L->s[l]), "pre-capture join"));
-        TRY(cuda_check(c0, cudaStreamWaitEvent(L->s[0], L->ev[l], 0), "pre-capture join"));
-    }
     TRY(cuda_check(c0, cudaStreamBeginCapture(L->s[0], cudaStreamCaptureModeThreadLocal), "begin capture"));
     gpe_status st = cuda_check(c0, cudaEventRecord(L->ev[0], L->s[0]), "capture fork");
     for (int l = 1; l < nl && st == GPE_OK; ++l)
@@ -808,25 +835,98 @@ static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, 
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(L->s[0], &g);   // always end the capture
+    // the captured launches were only recorded, not run: count them per replay
+    out->launches.resize(count);
+    for (int i = 0; i < count; ++i) {
+        out->launches[i] = ctxs[i]->launches - before[i];
+        ctxs[i]->launches = before[i];
+    }
     if (st != GPE_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
     TRY(cuda_check(c0, e, "end capture"));
-    cudaGraphExec_t x = nullptr;
-    st = cuda_check(c0, cudaGraphInstantiate(&x, g, 0), "graph instantiate");
+    out->exec = nullptr;
+    st = cuda_check(c0, cudaGraphInstantiate(&out->exec, g, 0), "graph instantiate");
     cudaGraphDestroy(g);
-    if (st != GPE_OK) return st;
-    for (int r = 0; r < R && st == GPE_OK; ++r) st = cuda_check(c0, cudaGraphLaunch(x, L->s[0]), "graph launch");
+    return st;
+}
+
+static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode, Lanes *L,
+                                        int nl, int *done)
+{
+    *done = 0;
+    int K = kGraphContextSteps / count;                              // interior steps per replay
+    if (K > kGraphSteps) K = kGraphSteps;
+    if (K > n - 2) K = n - 2;
+    if (K < 1) K = 1;
+    const int R = (n - 2) / K;                                       // replays
+    gpe_ctx *c0 = ctxs[0];
+    // the graph runs on lane 0: order it after the work already on every lane
+    for (int l = 1; l < nl; ++l) {
+        TRY(cuda_check(c0, cudaEventRecord(L->ev[l], L->s[l]), "pre-capture join"));
+        TRY(cuda_check(c0, cudaStreamWaitEvent(L->s[0], L->ev[l], 0), "pre-capture join"));
+    }
+    std::vector<unsigned long long> key(2 * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+        key[2 * i] = ctxs[i]->uid;
+        key[2 * i + 1] = ctxs[i]->version;
+    }
+    GraphEntry *g = find_graph(L, key, dt, (int)mode, K, nl);
+    if (!g) {
+        GraphEntry e;
+        e.key = key;
+        e.dt = dt;
+        e.mode = (int)mode;
+        e.K = K;
+        e.nl = nl;
+        e.exec = nullptr;
+        e.used = 0;
+        TRY(capture_graph(ctxs, count, n, dt, mode, L, nl, K, &e));
+        if (L->graphs.size() >= kGraphCache) {
+            // release the least recently used graph (its pending launches complete first)
+            size_t lru = 0;
+            for (size_t i = 1; i < L->graphs.size(); ++i)
+                if (L->graphs[i].used < L->graphs[lru].used) lru = i;
+            cudaGraphExecDestroy(L->graphs[lru].exec);
+            L->graphs.erase(L->graphs.begin() + (long)lru);
+        }
+        L->graphs.push_back(std::move(e));
+        g = &L->graphs.back();
+    }
+    g->used = ++L->clock;
+    gpe_status st = GPE_OK;
+    for (int r = 0; r < R && st == GPE_OK; ++r) st = cuda_check(c0, cudaGraphLaunch(g->exec, L->s[0]), "graph launch");
     // the other lanes' next work follows the last replay
     if (st == GPE_OK) st = cuda_check(c0, cudaEventRecord(L->ev[0], L->s[0]), "replay join");
     for (int l = 1; l < nl && st == GPE_OK; ++l)
         st = cuda_check(c0, cudaStreamWaitEvent(L->s[l], L->ev[0], 0), "replay join");
-    cudaGraphExecDestroy(x);                                   // released once the launches complete
-    // the capture counted K steps of launches; the replays ran R K of them
-    for (int i = 0; i < count; ++i) ctxs[i]->launches += (ctxs[i]->launches - before[i]) * (long long)(R - 1);
+    for (int i = 0; i < count; ++i) ctxs[i]->launches += g->launches[i] * (long long)R;
     if (st == GPE_OK) *done = R * K;
     return st;
+}
+
+// Drop the cached graphs that step context `uid` (at its destruction).
+static void forget_graphs(int device, unsigned long long uid)
+{
+    Lanes *L = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_lanes_mu);
+        if (device >= 0 && device < 64) L = g_lanes[device];
+    }
+    if (!L) return;
+    std::lock_guard<std::mutex> lock(L->mu);
+    for (size_t i = 0; i < L->graphs.size();) {
+        const std::vector<unsigned long long> &k = L->graphs[i].key;
+        bool hit = false;
+        for (size_t j = 0; j < k.size(); j += 2) hit = hit || k[j] == uid;
+        if (hit) {
+            cudaGraphExecDestroy(L->graphs[i].exec);
+            L->graphs.erase(L->graphs.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
 }
 
 gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode)
@@ -994,10 +1094,27 @@ gpe_status gpe_sync(gpe_ctx *c)
     int st = 0;
     TRY(cuda_check(c, cudaMemcpyAsync(&st, &c->T.sc->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
                    "copy"));
-    TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->status, 0, sizeof(int), c->stream), "memset"));
+    // clear the status word and, with it, the last-CTA counters: every CTA of
+    // a reducing pass takes its turn at the counter even when its wait ran
+    // out, so they are back at zero after each pass; resetting them here
+    // as well makes a cleared context start from a known state
+    static_assert(offsetof(DevScalars, status) == offsetof(DevScalars, ticket) + 2 * sizeof(unsigned int),
+                  "ticket[2] and status are adjacent");
+    TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->ticket[0], 0, 2 * sizeof(unsigned int) + sizeof(int), c->stream),
+                   "memset"));
     TRY(cuda_check(c, cudaStreamSynchronize(c->stream), "sync"));
     return st ? fail(c, (gpe_status)st, "device status %s", gpe_status_string((gpe_status)st)) : GPE_OK;
 }
+
+gpe_status gpe_set_wait_limit(gpe_ctx *c, int spins)
+{
+    if (!c || spins < 0) return GPE_EINVAL;
+    c->spins = spins;
+    c->version++;
+    return GPE_OK;
+}
+
+int gpe_get_wait_limit(const gpe_ctx *c) { return c ? c->spins : -1; }
 
 gpe_status gpe_debug_timeout_probe(gpe_ctx *c, int spins)
 {
@@ -1099,6 +1216,7 @@ gpe_status gpe_set_pass_variants(gpe_ctx *c, int v)
     c->stream_passes = (v & GPE_VARIANT_STREAM_ROWS) != 0;
     c->stream_cols = (v & GPE_VARIANT_STREAM_COLS) != 0;
     c->row_tile_shift = v >> GPE_VARIANT_ROW_TILE_SHIFT;
+    c->version++;
     return GPE_OK;
 }
 
@@ -1228,6 +1346,7 @@ void gpe_destroy(gpe_ctx *c)
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
+    forget_graphs(c->device, c->uid);
     delete c;
 }
 

@@ -102,6 +102,11 @@ struct PassArgs {
 // per CTA (0, 1 or 2; see row_rows_per_cta)
 cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shift = 0);
 cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
+// the same for rows / columns of at most 256 points (lo) and more (hi)
+cudaError_t launch_row_lo(int mode, const PassArgs &a, cudaStream_t s, int tile_shift);
+cudaError_t launch_row_hi(int mode, const PassArgs &a, cudaStream_t s, int tile_shift);
+cudaError_t launch_col_lo(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
+cudaError_t launch_col_hi(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
 cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s);
 cudaError_t launch_col_stream(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
 bool row_stream_ok(int nx, int ny);

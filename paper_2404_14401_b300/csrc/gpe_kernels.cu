@@ -21,6 +21,18 @@
 #include "gpe_fft.cuh"
 #include "gpe_internal.h"
 
+// GPE_PART selects which launchers (and so which kernel instantiations) this
+// compilation emits, so that the build can compile the file in parts side by
+// side: 0 tables and readout kernels, shared host helpers and the pass
+// dispatchers; 1 row passes of 8..256 points; 2 row passes of 512..8192
+// points (one-shot, grouped, streaming); 3 column passes of 8..256 points;
+// 4 column passes of 512..8192 points (one-shot, streaming).  Undefined:
+// everything.
+#ifndef GPE_PART
+#define GPE_PART -1
+#endif
+#define GPE_IN_PART(k) (GPE_PART < 0 || GPE_PART == (k))
+
 namespace gpe {
 
 // ------------------------------------------------------------------ TMA / mbarrier
@@ -57,6 +69,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     for (int i = 0; i < spins; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+// After a wait has run out: give a bulk copy already issued towards this CTA's
+// shared memory a fixed number of polls to land, whatever the caller's wait
+// limit, so that the CTA does not reuse or release shared memory that the copy
+// may still write.  If even this runs out the CTA goes on (nothing better is
+// possible without waiting forever).
+constexpr int kDrainSpins = 1 << 22;
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity)
+{
+    return mbar_wait_bounded(bar, parity, kDrainSpins);
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
 {
@@ -166,7 +188,7 @@ __device__ __forceinline__ bool last_block_total(const double *part, unsigned in
 // Norm, overlaps, renormalisation scale and cavity field from the sums
 // S0 = sum |psi|^2, S1 = sum cos(kc x)cos(kc y)|psi|^2, S2 = sum cos^2(kc x)|psi|^2
 // (Sec. 3.3 normalisation; Eqs. 14-15).  One thread, FP64.
-__device__ void finalize_fields(const double *S, const RedArgs &r, DevScalars *sc)
+[[maybe_unused]] static __device__ void finalize_fields(const double *S, const RedArgs &r, DevScalars *sc)
 {
     const double norm = S[0] * r.dxdy;
     const double O = S[1] / S[0], B = S[2] / S[0];
@@ -400,10 +422,15 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
     float2 v[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = __ldcs(&row[j + r * TP]);    // streamed: keep the tables in L1
+    // live: the twiddle table arrived in time.  A CTA whose wait ran out lets
+    // the copy land, then runs on without storing anything and adds zero
+    // partial sums, so that every reduction still counts all of its CTAs.
+    bool live = true;
     if constexpr (FFT && C::TWN > 0) {
         if (!__syncthreads_and(mbar_wait_bounded(&twbar, 0, a.spins))) {
             if (threadIdx.x == 0) latch_status(T.sc, GPE_ETIMEOUT);
-            return;
+            mbar_drain(&twbar, 0);
+            live = false;
         }
     }
 
@@ -483,6 +510,9 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
             const float kx = (float)(e < N / 2 ? e : e - N);   // in units of 2 pi / Lx
             q[6] += kx * kx * (v[r].x * v[r].x + v[r].y * v[r].y);
         }
+        if (!live)
+#pragma unroll
+            for (int i = 0; i < 7; ++i) q[i] = 0.f;
         block_sum<7>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
         double S[7];
         if (last_block_total<7>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0)
@@ -520,9 +550,10 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
         fft_pencil<N, E, false>(v, sb, j, 1, stw);
         kinetic_axis<E, TP, true>(v, T.kinx, j, a.sx, 0);
         fft_pencil<N, E, true>(v, sb, j, 1, stw);
+        if (live)
 #pragma unroll
-        for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
-        float q1[1] = {2.f * a.ph.h * gq};
+            for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
+        float q1[1] = {live ? 2.f * a.ph.h * gq : 0.f};
         block_sum<1>(q1, T.part_row + (size_t)blockIdx.x * NQ, red);
         double S[1];
         if (last_block_total<1>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0) *a.gout = S[0];
@@ -531,8 +562,9 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 
     constexpr bool STORE = !(MODE == ROW_REDUCE_R || MODE == ROW_OBS);
     if constexpr (STORE) {
+        if (live)
 #pragma unroll
-        for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
+            for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
     }
 }
 
@@ -619,11 +651,13 @@ __global__ void __launch_bounds__(RowGroupCfg<N>::THREADS, 1) row_group_kernel(c
     }
     const float cs = a.use_c ? (float)T.sc->c : 1.f;
     if (!__syncthreads_and(mbar_wait_bounded(&tbar, 0, a.spins))) {
+        // let the table copies and each group's first item land before the
+        // CTA exits; nothing is stored
         if (threadIdx.x == 0) {
             latch_status(T.sc, GPE_ETIMEOUT);
-            mbar_wait_bounded(&tbar, 0, a.spins);
+            mbar_drain(&tbar, 0);
         }
-        if (leader && first < nitems) mbar_wait_bounded(&full[g][0], 0, a.spins);
+        if (leader && first < nitems) mbar_drain(&full[g][0], 0);
         return;
     }
 
@@ -634,9 +668,11 @@ __global__ void __launch_bounds__(RowGroupCfg<N>::THREADS, 1) row_group_kernel(c
         float2 *buf = buf0 + b * C::BUF;
         const int next = item + gstride;
         if (!group_all(mbar_wait_bounded(&full[g][b], (parity >> b) & 1u, a.spins), 1 + g, C::GT)) {
+            // only this buffer's load is in flight (the next one is issued
+            // after this wait); let it land, then stop this group
             if (leader) {
                 latch_status(T.sc, GPE_ETIMEOUT);
-                mbar_wait_bounded(&full[g][b], (parity >> b) & 1u, a.spins);
+                mbar_drain(&full[g][b], (parity >> b) & 1u);
             }
             break;
         }
@@ -758,11 +794,13 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
         if constexpr (C::TWN > 0) stage_twiddles_async<N>(stw, T.twy, &bar);
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + (size_t)r0 * W, &map, &bar, 2 * c0, r0);
     }
+    // ok: the tile (and twiddles) arrived in time.  Otherwise the copies are
+    // given time to land, the CTA runs on without storing and adds zero
+    // partial sums, so that every reduction still counts all of its CTAs.
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins));
     if (!ok) {
         if (threadIdx.x == 0) latch_status(T.sc, GPE_ETIMEOUT);
-        mbar_wait_bounded(&bar, 0, a.spins);        // give copies in flight a last chance
-        return;
+        mbar_drain(&bar, 0);
     }
 
     constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
@@ -851,6 +889,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
         if constexpr (!INPLACE) __syncthreads();
     }
 
+    if (!ok) q[0] = q[1] = q[2] = 0.f;
     if constexpr (MODE == COL_OBS) {
         float q1[1] = {q[0]};
         block_sum<1>(q1, T.part_col + (size_t)blockIdx.x * NQ, red);
@@ -863,7 +902,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     // make the generic-proxy tile writes visible to the TMA engine, then store
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && ok) {
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, tile + (size_t)r0 * W, 2 * c0, r0);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
@@ -937,12 +976,16 @@ __global__ void __launch_bounds__(256, 2) row_stream_kernel(const PassArgs a, in
             mbar_expect_tx(&bar[b ^ 1], BYTES);
             bulk_load_1d(buf0 + (b ^ 1) * C::BUF, a.psi + (size_t)next * RPC * N, BYTES, &bar[b ^ 1]);
         }
-        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], (parity >> b) & 1u, a.spins));
+        const uint32_t pb = (parity >> b) & 1u;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], pb, a.spins));
         parity ^= 1u << b;
         if (!ok) {
+            // both loads may be in flight (this item's and the next one's,
+            // issued above): let them land before the CTA stops
             if (threadIdx.x == 0) {
                 latch_status(T.sc, GPE_ETIMEOUT);
-                if (next < nitems) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, a.spins);
+                mbar_drain(&bar[b], pb);
+                if (next < nitems) mbar_drain(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u);
             }
             break;
         }
@@ -1032,12 +1075,16 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
             mbar_expect_tx(&bar[b ^ 1], (uint32_t)(N * W * 8));
             for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(nb + r0 * W, &map, &bar[b ^ 1], 2 * next * W, r0);
         }
-        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], (parity >> b) & 1u, a.spins));
+        const uint32_t pb = (parity >> b) & 1u;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[b], pb, a.spins));
         parity ^= 1u << b;
         if (!ok) {
+            // both loads may be in flight (this item's and the next one's,
+            // issued above): let them land before the CTA stops
             if (threadIdx.x == 0) {
                 latch_status(T.sc, GPE_ETIMEOUT);
-                if (next < nitems) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, a.spins);
+                mbar_drain(&bar[b], pb);
+                if (next < nitems) mbar_drain(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u);
             }
             break;
         }
@@ -1091,11 +1138,12 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
     if (threadIdx.x == 0) bulk_wait_read_all();
 }
 
+#if GPE_IN_PART(0)
 // ------------------------------------------------------------------ tables
 // Entry i of the per-stage twiddle table of an n-point axis (fft_tw_offset
 // layout): W_{NS R}^{r k} = exp(-2 pi i r k / (NS R)) as {re_hi, im_hi, re_lo,
 // im_lo}, hi = float(x), lo = float(x - hi).  Entries past the table are 1.
-__device__ float4 twiddle_entry(int i, int n)
+static __device__ float4 twiddle_entry(int i, int n)
 {
     long long num = 0, den = 1;
     for (int s = 1; s < fft_stages(n); ++s) {
@@ -1257,10 +1305,13 @@ __global__ void timeout_probe_kernel(DevScalars *sc, int spins)
     if (!ok && threadIdx.x == 0) latch_status(sc, GPE_ETIMEOUT);
 }
 
+#endif  // GPE_IN_PART(0)
+
 // ------------------------------------------------------------------ launchers
 // Opt func in to `bytes` of dynamic shared memory once per device (function
 // attributes belong to the device's context), safe from several host threads.
-template <class F> static cudaError_t smem_opt_in(F *func, int bytes, std::atomic<unsigned long long> &done)
+template <class F> [[maybe_unused]] static cudaError_t smem_opt_in(F *func, int bytes,
+                                                                   std::atomic<unsigned long long> &done)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1272,6 +1323,7 @@ template <class F> static cudaError_t smem_opt_in(F *func, int bytes, std::atomi
     return e;
 }
 
+#if GPE_IN_PART(0)
 // Rows per CTA of the one-shot row pass: 256 threads' worth, divided by
 // 2^tile_shift for rows of 256 points and more (the tuner's smaller tiles
 // spread a small grid over more SMs), never below one warp's worth nor above
@@ -1292,6 +1344,24 @@ int col_tile_width(int nx, int ny)
     (void)nx;
     return col_w(ny);
 }
+
+bool row_group_ok(int nx, int ny) { return (nx == 512 || nx == 1024 || nx == 2048) && ny % (2048 / nx) == 0; }
+
+// Streaming row pass for ROW_PT when the grid has enough rows; false = not applicable.
+bool row_stream_ok(int nx, int ny) { return nx == 4096 && ny >= 8; }
+
+bool col_stream_ok(int nx, int ny) { return ny == 4096 && nx >= 8 * col_w(ny); }
+
+cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shift)
+{
+    return a.nx <= 256 ? launch_row_lo(mode, a, s, tile_shift) : launch_row_hi(mode, a, s, tile_shift);
+}
+
+cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    return a.ny <= 256 ? launch_col_lo(mode, a, map, s) : launch_col_hi(mode, a, map, s);
+}
+#endif  // GPE_IN_PART(0)
 
 template <int N, int MODE> static cudaError_t row_launch(const PassArgs &a, cudaStream_t s, int tile_shift)
 {
@@ -1326,7 +1396,8 @@ template <int N> static cudaError_t row_dispatch_mode(int mode, const PassArgs &
     }
 }
 
-cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shift)
+#if GPE_IN_PART(1)
+cudaError_t launch_row_lo(int mode, const PassArgs &a, cudaStream_t s, int tile_shift)
 {
     switch (a.nx) {
     case 8: return row_dispatch_mode<8>(mode, a, s, tile_shift);
@@ -1335,6 +1406,15 @@ cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shi
     case 64: return row_dispatch_mode<64>(mode, a, s, tile_shift);
     case 128: return row_dispatch_mode<128>(mode, a, s, tile_shift);
     case 256: return row_dispatch_mode<256>(mode, a, s, tile_shift);
+    default: return cudaErrorInvalidValue;
+    }
+}
+#endif
+
+#if GPE_IN_PART(2)
+cudaError_t launch_row_hi(int mode, const PassArgs &a, cudaStream_t s, int tile_shift)
+{
+    switch (a.nx) {
     case 512: return row_dispatch_mode<512>(mode, a, s, tile_shift);
     case 1024: return row_dispatch_mode<1024>(mode, a, s, tile_shift);
     case 2048: return row_dispatch_mode<2048>(mode, a, s, tile_shift);
@@ -1343,6 +1423,7 @@ cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shi
     default: return cudaErrorInvalidValue;
     }
 }
+#endif
 
 template <int N, int MODE>
 static cudaError_t col_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
@@ -1375,7 +1456,8 @@ template <int N> static cudaError_t col_dispatch_mode(int mode, const PassArgs &
     }
 }
 
-cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+#if GPE_IN_PART(3)
+cudaError_t launch_col_lo(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     switch (a.ny) {
     case 8: return col_dispatch_mode<8>(mode, a, map, s);
@@ -1384,6 +1466,15 @@ cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cuda
     case 64: return col_dispatch_mode<64>(mode, a, map, s);
     case 128: return col_dispatch_mode<128>(mode, a, map, s);
     case 256: return col_dispatch_mode<256>(mode, a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+#endif
+
+#if GPE_IN_PART(4)
+cudaError_t launch_col_hi(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    switch (a.ny) {
     case 512: return col_dispatch_mode<512>(mode, a, map, s);
     case 1024: return col_dispatch_mode<1024>(mode, a, map, s);
     case 2048: return col_dispatch_mode<2048>(mode, a, map, s);
@@ -1392,9 +1483,10 @@ cudaError_t launch_col(int mode, const PassArgs &a, const CUtensorMap &map, cuda
     default: return cudaErrorInvalidValue;
     }
 }
+#endif
 
 // SM count of the current device (cached per device; 148 if it cannot be read)
-static int sm_count()
+[[maybe_unused]] static int sm_count()
 {
     static std::atomic<int> cache[64];
     int dev = 0;
@@ -1408,6 +1500,7 @@ static int sm_count()
     return n;
 }
 
+#if GPE_IN_PART(2)
 template <int N> static cudaError_t row_group_launch(const PassArgs &a, cudaStream_t s)
 {
     using C = RowGroupCfg<N>;
@@ -1426,8 +1519,6 @@ template <int N> static cudaError_t row_group_launch(const PassArgs &a, cudaStre
     row_group_kernel<N><<<grid, C::THREADS, C::SMEM, s>>>(a, items);
     return cudaGetLastError();
 }
-
-bool row_group_ok(int nx, int ny) { return (nx == 512 || nx == 1024 || nx == 2048) && ny % (2048 / nx) == 0; }
 
 cudaError_t launch_row_group(const PassArgs &a, cudaStream_t s)
 {
@@ -1452,9 +1543,6 @@ template <int N> static cudaError_t row_stream_launch(const PassArgs &a, cudaStr
     return cudaGetLastError();
 }
 
-// Streaming row pass for ROW_PT when the grid has enough rows; false = not applicable.
-bool row_stream_ok(int nx, int ny) { return nx == 4096 && ny >= 8; }
-
 cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s)
 {
     switch (a.nx) {
@@ -1462,7 +1550,9 @@ cudaError_t launch_row_stream(const PassArgs &a, cudaStream_t s)
     default: return cudaErrorInvalidValue;
     }
 }
+#endif  // GPE_IN_PART(2)
 
+#if GPE_IN_PART(4)
 template <int N, int MODE> static cudaError_t col_stream_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     using C = ColStreamCfg<N>;
@@ -1475,8 +1565,6 @@ template <int N, int MODE> static cudaError_t col_stream_launch(const PassArgs &
     col_stream_kernel<N, MODE><<<grid, C::THREADS, C::SMEM, s>>>(a, map, items);
     return cudaGetLastError();
 }
-
-bool col_stream_ok(int nx, int ny) { return ny == 4096 && nx >= 8 * col_w(ny); }
 
 template <int N> static cudaError_t col_stream_mode(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
@@ -1495,7 +1583,9 @@ cudaError_t launch_col_stream(int mode, const PassArgs &a, const CUtensorMap &ma
     default: return cudaErrorInvalidValue;
     }
 }
+#endif  // GPE_IN_PART(4)
 
+#if GPE_IN_PART(0)
 cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m, double wx,
                           double wy, double lkx, double lky, double kc, cudaStream_t s)
 {
@@ -1550,5 +1640,6 @@ cudaError_t launch_timeout_probe(DevScalars *sc, int spins, cudaStream_t s)
     timeout_probe_kernel<<<1, 32, 0, s>>>(sc, spins);
     return cudaGetLastError();
 }
+#endif  // GPE_IN_PART(0)
 
 }  // namespace gpe

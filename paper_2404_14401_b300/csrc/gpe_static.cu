@@ -70,6 +70,11 @@ extern "C" gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, d
     if (!psi_dev || !out || ((uintptr_t)psi_dev & 15u)) return GPE_EINVAL;
     if (!pow2_between(nx, 8, 8192) || !pow2_between(ny, 8, 8192)) return GPE_EINVAL;
     if (nx > GPE_STATIC_MAX_N || ny > GPE_STATIC_MAX_N) return GPE_ENOMEM;   // beyond the fixed scratch
+    // one partial-sum slot per CTA of the reducing row pass: refuse a launch
+    // with more CTAs than the scratch has slots (the bound above keeps it at
+    // most GPE_STATIC_MAX_N / 2 with today's row tiling; this check keeps the
+    // call safe if that tiling changes)
+    if (ny / row_rows_per_cta(nx, ny, 0) > kMaxBlocks) return GPE_ENOMEM;
     if (!(Lx > 0.0) || !(Ly > 0.0)) return GPE_EINVAL;
     unsigned char *base = nullptr;
     if (scratch_on_current_device(&base) != GPE_OK) return GPE_ECUDA;

@@ -21,7 +21,7 @@ GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 
 EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", "gpe_step_many",
            "gpe_observables", "gpe_set_psi", "gpe_get_psi", "gpe_set_time", "gpe_get_time", "gpe_fft2",
-           "gpe_sync", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_profile_read_kind", "gpe_launch_count",
+           "gpe_sync", "gpe_set_wait_limit", "gpe_get_wait_limit", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_profile_read_kind", "gpe_launch_count",
            "gpe_overlaps_static", "gpe_momentum_populations", "gpe_get_pass_variants", "gpe_set_pass_variants", "gpe_tune",
            "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_adjoint_workspace_size_ex",
            "gpe_adjoint_lattice_ex", "gpe_destroy",
@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
         "gpe_get_time": (c_double, [c_void_p]),
         "gpe_fft2": (c_int, [c_void_p, c_int]),
         "gpe_sync": (c_int, [c_void_p]),
+        "gpe_set_wait_limit": (c_int, [c_void_p, c_int]),
+        "gpe_get_wait_limit": (c_int, [c_void_p]),
         "gpe_debug_timeout_probe": (c_int, [c_void_p, c_int]),
         "gpe_overlaps_static": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p,
                                         P(c_double)]),
@@ -204,6 +206,14 @@ def gpe_fft2(ctx, sign: int):
 def gpe_sync(ctx) -> int:
     """Wait for the stream; returns (does not raise) the latched device status."""
     return load().gpe_sync(ctx)
+
+
+def gpe_set_wait_limit(ctx, spins: int):
+    _check(ctx, load().gpe_set_wait_limit(ctx, int(spins)))
+
+
+def gpe_get_wait_limit(ctx) -> int:
+    return load().gpe_get_wait_limit(ctx)
 
 
 def gpe_debug_timeout_probe(ctx, spins: int):

@@ -102,12 +102,8 @@ def test_imaginary_time_harmonic_trap_matches_oracle(g):
     s, got, obs, ref, _ = run_both(p, w["psi0"](), 2000, w["dt"], True)
     assert rel_l2(got, ref) < 1e-4
     ro = oracle.observables(p, ref, t=s.t)
-    for k in ("energy", "mu"):
+    for k in ("energy", "mu", "ekin", "epot"):
         assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
-    # E_kin and E_pot alone are first order in the state error, which imaginary
-    # time lets reach ~eps32 / (gap dtau) ~ 2e-5 along the slowest mode
-    for k in ("ekin", "epot"):
-        assert abs(obs[k] - ro[k]) < 1e-4 * abs(ro[k]), k
     assert abs(obs["norm"] - 1.0) < 1e-6
     if g == 0.0:
         assert abs(obs["energy"] - 1.0) < 2e-4                # closed form E = 1
@@ -127,12 +123,13 @@ def test_imaginary_then_real_time_switches_kinetic_factors():
 
 
 def cavity_close(obs, ro):
-    """alpha and O from FP64 sums of FP32 products: 1e-6 absolute plus 1e-5 relative."""
+    """O, B and alpha (FP64 sums of FP32 products, alpha formed in FP64):
+    relative 1e-5, the bound stated for the observables."""
     a_gpu = complex(obs["alpha_re"], obs["alpha_im"])
     a_ref = complex(ro["alpha_re"], ro["alpha_im"])
-    assert abs(obs["O"] - ro["O"]) < 1e-6 + 1e-5 * abs(ro["O"])
-    assert abs(obs["B"] - ro["B"]) < 1e-6 + 1e-5 * abs(ro["B"])
-    assert abs(a_gpu - a_ref) < 1e-5 + 1e-5 * abs(a_ref)
+    assert abs(obs["O"] - ro["O"]) < 1e-5 * abs(ro["O"])
+    assert abs(obs["B"] - ro["B"]) < 1e-5 * abs(ro["B"])
+    assert abs(a_gpu - a_ref) < 1e-5 * abs(a_ref)
 
 
 def test_cavity_ramp_matches_oracle():
@@ -223,6 +220,41 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     assert s.sync() == abi.GPE_OK                             # latched status was cleared
     s.step(10, 1e-3, True)
     assert abs(s.observables()["norm"] - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("spins", [0, 1])
+def test_real_pass_waits_run_out_and_reductions_recover(spins):
+    """The bounded waits of real passes run out: with limit 0 every TMA wait
+    gives up at once, with limit 1 after one poll (so some CTAs may finish and
+    others not).  The context latches GPE_ETIMEOUT (limit 0 always), every
+    CTA still takes its turn at the reduction counters, and after gpe_sync the
+    observables and further steps match the oracle from the state psi then
+    holds.  The cavity keeps a reducing pass in every step."""
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.cavity_ramp(n=64, L=16.0, steps=40, dt=2e-4)
+    p = dict(w["params"], ctrl_target=0, eta=2.0, ctrl_t=None, ctrl_v=None)
+    psi0 = c64(gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-2, seed=64, checker=0.3, kc=p["kc"]))
+    s = sim_for(p)
+    s.set_psi(psi0)
+    assert abi.gpe_get_wait_limit(s.ctx) == 1 << 24
+    abi.gpe_set_wait_limit(s.ctx, spins)
+    s.step(3, 2e-4)
+    st = s.sync()
+    assert st in (abi.GPE_OK, abi.GPE_ETIMEOUT)
+    if spins == 0:
+        assert st == abi.GPE_ETIMEOUT
+    assert s.sync() == abi.GPE_OK                              # status and counters cleared
+    abi.gpe_set_wait_limit(s.ctx, 1 << 24)
+    cur, t0 = s.get_psi(), s.t
+    assert np.all(np.isfinite(cur))
+    obs = s.observables()
+    ro = oracle.observables(p, cur.astype(np.complex128), t=t0)
+    for k in ("norm", "energy", "O", "B"):
+        assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+    s.step(20, 2e-4)
+    assert s.sync() == abi.GPE_OK
+    ref, _ = oracle.evolve(p, cur.astype(np.complex128), 20, 2e-4, False, t0=t0)
+    assert rel_l2(s.get_psi(), ref) < state_tol(20)
 
 
 @pytest.mark.parametrize("n", [1024, 2048])
