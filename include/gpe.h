@@ -155,6 +155,43 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * own streams, one pass at a time) and GPE_NO_GRAPH (no graph replay). */
 gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode);
 
+/* ---- Persistent batch: n lockstep steps of many contexts in one launch ----
+ * The same steps as gpe_step_many (Sec. 3.1, Eqs. 3-4; imaginary time Sec.
+ * 3.3; cavity Sec. 5.3) -- e.g. the instances of a phase-diagram sweep (Sec.
+ * 5.3, Fig. 5(b)), of uneven sizes -- run as ONE kernel launch per call
+ * instead of one launch per pass and context.  Every pass of every context is
+ * cut into items of 256 threads' work (whole rows; TMA-loaded tiles of whole
+ * columns), all items form one queue in lockstep order, and the CTAs of one
+ * persistent launch take them in order; an item waits (bounded) until the
+ * previous pass of its context is complete, whose last item sums the pass's
+ * FP64 partial sums in a fixed order and updates 1/sqrt(norm) and alpha.  The
+ * results equal those of gpe_step_many within the propagator's tolerances
+ * (not bit for bit: the items group the reductions differently).
+ *
+ * gpe_batch_workspace_size: device bytes a batch of these contexts needs
+ * (descriptors, counters, copies of the control points); 0 for bad input.
+ * gpe_batch_create: binds `count` distinct contexts, in order, to ws (>= that
+ * size, 256-byte aligned, borrowed for the batch's life; the caller must not
+ * write it meanwhile) and writes the descriptors there; waits for the first
+ * context's stream.  Every context must be on the current device, with nx, ny
+ * powers of two in 64..2048 (and each axis at least 256 / (other axis / 16)
+ * points: a row or column item is never cut).  The contexts must outlive the
+ * batch; a context's later gpe_set_potential / gpe_set_pass_variants /
+ * gpe_set_wait_limit is picked up by the next gpe_batch_step.
+ * gpe_batch_step: enqueues n >= 0 steps of dt in `mode` for every context on
+ * the first context's stream (ordered after the work on every context's
+ * stream, which all wait for the launch), advancing each context's time by
+ * n dt.  Every context must have a cavity or none; with a control table or a
+ * probe, all must be at the same time.  A bounded wait that runs out ends the
+ * launch and latches GPE_ETIMEOUT in that context's status (gpe_sync).  The
+ * launch is counted in the first context's gpe_launch_count.
+ * Errors: GPE_EINVAL, GPE_ENOMEM (workspace too small), GPE_ECUDA. */
+typedef struct gpe_batch gpe_batch;
+size_t gpe_batch_workspace_size(gpe_ctx *const *ctxs, int count);
+gpe_status gpe_batch_create(gpe_ctx *const *ctxs, int count, void *ws, size_t ws_bytes, gpe_batch **out);
+gpe_status gpe_batch_step(gpe_batch *batch, int n, double dt, gpe_mode mode);
+void gpe_batch_destroy(gpe_batch *batch);
+
 /* Compute the observables of psi at the current time; waits for the stream.
  * Returns the latched device status if it is not GPE_OK (out is filled). */
 gpe_status gpe_observables(gpe_ctx *ctx, gpe_obs *out);

@@ -193,3 +193,35 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """A persistent batch over Simulations (gpe_batch_create): each step() is one
+    kernel launch for n lockstep steps of every simulation.  Owns the batch
+    workspace (a torch allocation on the first simulation's device); the
+    simulations must outlive it."""
+
+    def __init__(self, sims):
+        torch = sims[0].torch
+        self.sims = list(sims)
+        ctxs = [s.ctx for s in self.sims]
+        nbytes = abi.gpe_batch_workspace_size(ctxs)
+        if nbytes == 0:
+            raise GPEError(abi.GPE_EINVAL, "empty batch")
+        self.ws = self.sims[0]._borrow(torch.empty(nbytes, dtype=torch.uint8, device=self.sims[0].device))
+        self.sims[0]._order_after_current()
+        self.batch = abi.gpe_batch_create(ctxs, self.ws.data_ptr(), nbytes)
+
+    def step(self, n: int, dt: float, imag: bool = False):
+        abi.gpe_batch_step(self.batch, self.sims[0].ctx, n, dt, abi.GPE_IMAG if imag else abi.GPE_REAL)
+
+    def close(self):
+        if getattr(self, "batch", None):
+            abi.gpe_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

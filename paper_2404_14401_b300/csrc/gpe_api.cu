@@ -193,8 +193,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // TMA view of a [ny][nx] complex64 array as float32 [ny][2 nx] with box
-// W complex columns x BR rows (the column pass's tile)
-gpe_status encode_map(gpe_ctx *c, void *base, CUtensorMap *out)
+// w complex columns x BR rows (a column pass's tile)
+gpe_status encode_map_w(gpe_ctx *c, void *base, int w, CUtensorMap *out);
+gpe_status encode_map(gpe_ctx *c, void *base, CUtensorMap *out) { return encode_map_w(c, base, c->W, out); }
+gpe_status encode_map_w(gpe_ctx *c, void *base, int w, CUtensorMap *out)
 {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
@@ -209,7 +211,7 @@ gpe_status encode_map(gpe_ctx *c, void *base, CUtensorMap *out)
     const int BR = c->ny < 256 ? c->ny : 256;
     cuuint64_t dims[2] = {(cuuint64_t)2 * c->nx, (cuuint64_t)c->ny};
     cuuint64_t strides[1] = {(cuuint64_t)2 * c->nx * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)(2 * c->W), (cuuint32_t)BR};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * w), (cuuint32_t)BR};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1351,5 +1353,271 @@ void gpe_destroy(gpe_ctx *c)
 }
 
 const char *gpe_last_error(const gpe_ctx *c) { return c ? c->err : "null context"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- persistent batch
+// A batch binds contexts (in order) to a caller-provided device workspace that
+// holds the kernel's descriptors, prefix sums, control points and counters.
+struct gpe_batch {
+    std::vector<gpe_ctx *> ctxs;
+    std::vector<unsigned long long> key;      // uid, version per context at the last upload
+    unsigned char *ws;
+    size_t ws_bytes;
+    int device;
+    std::vector<cudaStream_t> streams;        // distinct context streams other than the first
+    cudaEvent_t ev;
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t counters, rpre, cpre, desc, ctrl, total;
+};
+
+BatchLayout batch_layout(int count, size_t ctrl_points)
+{
+    BatchLayout L;
+    size_t o = 0;
+    L.counters = o; o = align256(o + sizeof(unsigned int) * (2 + 2 * (size_t)count));
+    L.rpre = o;     o = align256(o + sizeof(int) * ((size_t)count + 1));
+    L.cpre = o;     o = align256(o + sizeof(int) * ((size_t)count + 1));
+    L.desc = o;     o = align256(o + sizeof(BatchCtx) * (size_t)count);
+    L.ctrl = o;     o = align256(o + 2 * sizeof(double) * ctrl_points);
+    L.total = o;
+    return L;
+}
+
+size_t ctrl_points_of(gpe_ctx *const *ctxs, int count)
+{
+    size_t n = 0;
+    for (int i = 0; i < count; ++i) n += ctxs[i]->ctrl_t.size();
+    return n;
+}
+
+bool time_dependent(const gpe_ctx *c) { return !c->ctrl_t.empty() || c->pot.probe_omega != 0.0; }
+
+// Write the descriptors of every context into the batch workspace (pageable
+// copies on the first context's stream, which the call then waits for).
+gpe_status batch_upload(gpe_batch *b)
+{
+    const int count = (int)b->ctxs.size();
+    gpe_ctx *c0 = b->ctxs[0];
+    const BatchLayout L = batch_layout(count, ctrl_points_of(b->ctxs.data(), count));
+    std::vector<BatchCtx> d(count);
+    std::vector<int> rpre(count + 1, 0), cpre(count + 1, 0);
+    std::vector<double> ctrl;
+    const double *ctrl_dev = (const double *)(b->ws + L.ctrl);
+    for (int i = 0; i < count; ++i) {
+        gpe_ctx *c = b->ctxs[i];
+        BatchCtx &e = d[i];
+        memset(&e, 0, sizeof(e));
+        e.cpi = batch_rows_per_item(c->ny);
+        e.rpi = batch_rows_per_item(c->nx);
+        TRY(encode_map_w(c, c->psi, e.cpi, &e.map));
+        e.psi = c->psi;
+        e.T = c->T;
+        e.V = c->pot.V;
+        e.V_scale = (float)c->pot.V_scale;
+        e.g = (float)c->g;
+        e.sx = (float)(1.0 / c->nx);
+        e.sy = (float)(1.0 / c->ny);
+        e.nx = c->nx;
+        e.ny = c->ny;
+        e.row_items = c->ny / e.rpi;
+        e.col_items = c->nx / e.cpi;
+        const gpe_potential &p = c->pot;
+        e.lat_V0x = p.lat_V0x;
+        e.lat_V0y = p.lat_V0y;
+        e.eta = p.eta;
+        e.U0 = p.U0;
+        e.dc = p.dc;
+        e.kappa = p.kappa;
+        e.N = p.N;
+        e.dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
+        e.probe_omega = p.probe_omega;
+        e.probe_delta = p.probe_delta;
+        e.probe_phi = p.probe_phi;
+        e.cavity = p.cavity;
+        e.pump_lattice = p.pump_lattice;
+        e.ctrl_target = p.ctrl_target;
+        e.nctrl = (int)c->ctrl_t.size();
+        if (e.nctrl > 0) {
+            e.ctrl_t = ctrl_dev + ctrl.size();
+            ctrl.insert(ctrl.end(), c->ctrl_t.begin(), c->ctrl_t.end());
+            e.ctrl_v = ctrl_dev + ctrl.size();
+            ctrl.insert(ctrl.end(), c->ctrl_v.begin(), c->ctrl_v.end());
+        }
+        rpre[i + 1] = rpre[i] + e.row_items;
+        cpre[i + 1] = cpre[i] + e.col_items;
+    }
+    const cudaStream_t s = c0->stream;
+    TRY(cuda_check(c0, cudaMemcpyAsync(b->ws + L.desc, d.data(), sizeof(BatchCtx) * count, cudaMemcpyHostToDevice, s),
+                   "batch upload"));
+    TRY(cuda_check(c0, cudaMemcpyAsync(b->ws + L.rpre, rpre.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
+                                       s), "batch upload"));
+    TRY(cuda_check(c0, cudaMemcpyAsync(b->ws + L.cpre, cpre.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
+                                       s), "batch upload"));
+    if (!ctrl.empty())
+        TRY(cuda_check(c0, cudaMemcpyAsync(b->ws + L.ctrl, ctrl.data(), sizeof(double) * ctrl.size(),
+                                           cudaMemcpyHostToDevice, s), "batch upload"));
+    TRY(cuda_check(c0, cudaStreamSynchronize(s), "batch upload"));
+    for (int i = 0; i < count; ++i) {
+        b->key[2 * i] = b->ctxs[i]->uid;
+        b->key[2 * i + 1] = b->ctxs[i]->version;
+    }
+    return GPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gpe_batch_workspace_size(gpe_ctx *const *ctxs, int count)
+{
+    if (!ctxs || count < 1) return 0;
+    for (int i = 0; i < count; ++i)
+        if (!ctxs[i]) return 0;
+    return batch_layout(count, ctrl_points_of(ctxs, count)).total;
+}
+
+gpe_status gpe_batch_create(gpe_ctx *const *ctxs, int count, void *ws, size_t ws_bytes, gpe_batch **out)
+{
+    if (!out) return GPE_EINVAL;
+    *out = nullptr;
+    if (!ctxs || count < 1) return GPE_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) return GPE_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(ctxs[i], GPE_EINVAL, "gpe_batch_create: repeated context");
+        if (!batch_supported(ctxs[i]->nx, ctxs[i]->ny))
+            return fail(ctxs[i], GPE_EINVAL, "gpe_batch_create: grid %dx%d not supported in a batch (64..2048 per axis)",
+                        ctxs[i]->nx, ctxs[i]->ny);
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(ctxs[i], GPE_EINVAL, "gpe_batch_create: contexts on different devices");
+    }
+    if (!ws || ((uintptr_t)ws & 255u)) return fail(ctxs[0], GPE_EINVAL, "gpe_batch_create: workspace not 256-byte aligned");
+    if (ws_bytes < gpe_batch_workspace_size(ctxs, count))
+        return fail(ctxs[0], GPE_ENOMEM, "gpe_batch_create: workspace of %zu bytes, %zu needed", ws_bytes,
+                    gpe_batch_workspace_size(ctxs, count));
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != ctxs[0]->device)
+        return fail(ctxs[0], GPE_EINVAL, "gpe_batch_create: the contexts' device is not current");
+    gpe_batch *b = new gpe_batch();
+    b->ctxs.assign(ctxs, ctxs + count);
+    b->key.assign(2 * (size_t)count, 0);
+    b->ws = (unsigned char *)ws;
+    b->ws_bytes = ws_bytes;
+    b->device = dev;
+    b->ev = nullptr;
+    for (int i = 1; i < count; ++i) {
+        bool seen = ctxs[i]->stream == ctxs[0]->stream;
+        for (cudaStream_t t : b->streams) seen = seen || t == ctxs[i]->stream;
+        if (!seen) b->streams.push_back(ctxs[i]->stream);
+    }
+    gpe_status st = cuda_check(ctxs[0], cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming), "event");
+    if (st == GPE_OK) st = batch_upload(b);
+    if (st != GPE_OK) {
+        if (b->ev) cudaEventDestroy(b->ev);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_step(gpe_batch *b, int n, double dt, gpe_mode mode)
+{
+    if (!b) return GPE_EINVAL;
+    const int count = (int)b->ctxs.size();
+    gpe_ctx *c0 = b->ctxs[0];
+    for (int i = 0; i < count; ++i) TRY(step_check(b->ctxs[i], n, dt, mode));
+    if (n == 0) return GPE_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return fail(c0, GPE_EINVAL, "gpe_batch_step: the batch's device is not current");
+    const int cavity = c0->pot.cavity ? 1 : 0;
+    bool timed = false;
+    for (int i = 0; i < count; ++i) {
+        gpe_ctx *c = b->ctxs[i];
+        if ((c->pot.cavity ? 1 : 0) != cavity)
+            return fail(c, GPE_EINVAL, "gpe_batch_step: every context of a batch has a cavity, or none");
+        if (c->prof) return fail(c, GPE_EINVAL, "gpe_batch_step: profiling contexts step through gpe_step_many");
+        timed = timed || time_dependent(c);
+    }
+    for (int i = 1; i < count && timed; ++i)
+        if (b->ctxs[i]->t != c0->t)
+            return fail(b->ctxs[i], GPE_EINVAL, "gpe_batch_step: with a control table or a probe, every context "
+                                                "of the batch must be at the same time");
+    // the descriptors follow the contexts' settings (potential, variants, wait limit)
+    bool stale = false;
+    for (int i = 0; i < count; ++i) stale = stale || b->key[2 * i + 1] != b->ctxs[i]->version;
+    if (stale) TRY(batch_upload(b));
+    // kinetic factors of (dt, mode) on each context's stream
+    const int imag = mode == GPE_IMAG;
+    for (int i = 0; i < count; ++i) {
+        gpe_ctx *c = b->ctxs[i];
+        if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
+            TRY(timed_launch(c, 2, [&] {
+                return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
+            }, "kinetic tables"));
+            c->kin_valid = true;
+            c->kin_dt = dt;
+            c->kin_mode = (int)mode;
+        }
+    }
+    // the launch runs on the first context's stream, after the others' work
+    const cudaStream_t s = c0->stream;
+    for (cudaStream_t t : b->streams) {
+        TRY(cuda_check(c0, cudaEventRecord(b->ev, t), "batch fork"));
+        TRY(cuda_check(c0, cudaStreamWaitEvent(s, b->ev, 0), "batch fork"));
+    }
+    const BatchLayout L = batch_layout(count, ctrl_points_of(b->ctxs.data(), count));
+    int R = 0, C = 0;
+    for (int i = 0; i < count; ++i) {
+        R += b->ctxs[i]->ny / batch_rows_per_item(b->ctxs[i]->nx);
+        C += b->ctxs[i]->nx / batch_rows_per_item(b->ctxs[i]->ny);
+    }
+    // a launch's queue stays below 2^31 items: longer runs take several launches
+    const long long per_step = batch_queue_length(1, imag, cavity, R, C);
+    const int max_steps = (int)((1LL << 31) / (per_step > 0 ? per_step : 1)) - 2;
+    unsigned int *cnt = (unsigned int *)(b->ws + L.counters);
+    for (int done = 0; done < n;) {
+        const int m = n - done < max_steps ? n - done : max_steps;
+        BatchArgs a;
+        memset(&a, 0, sizeof(a));
+        a.ctx = (const BatchCtx *)(b->ws + L.desc);
+        a.row_prefix = (const int *)(b->ws + L.rpre);
+        a.col_prefix = (const int *)(b->ws + L.cpre);
+        a.head = cnt;
+        a.epoch = cnt + 2;
+        a.done = cnt + 2 + count;
+        a.count = count;
+        a.n = m;
+        a.imag = imag;
+        a.cavity = cavity;
+        a.spins = c0->spins;
+        a.dt = dt;
+        a.t0 = c0->t;
+        a.total = (unsigned int)batch_queue_length(m, imag, cavity, R, C);
+        TRY(cuda_check(c0, cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * (2 + 2 * (size_t)count), s), "batch memset"));
+        TRY(cuda_check(c0, launch_batch(a, s), "batch launch"));
+        c0->launches++;
+        for (int i = 0; i < count; ++i) b->ctxs[i]->t += m * dt;
+        done += m;
+    }
+    for (cudaStream_t t : b->streams) {
+        TRY(cuda_check(c0, cudaEventRecord(b->ev, s), "batch join"));
+        TRY(cuda_check(c0, cudaStreamWaitEvent(t, b->ev, 0), "batch join"));
+    }
+    return GPE_OK;
+}
+
+void gpe_batch_destroy(gpe_batch *b)
+{
+    if (!b) return;
+    if (b->ev) cudaEventDestroy(b->ev);
+    delete b;
+}
 
 }  // extern "C"

@@ -97,6 +97,46 @@ struct PassArgs {
     float L0x, L0y;
 };
 
+// ---- Persistent batch (gpe_batch.cu): one launch steps many contexts.
+// Every pass of every context is cut into items of 256 threads' work (a group
+// of whole rows, or a tile of whole columns); the items of all passes of all
+// contexts form one queue in lockstep order (pass q of every context before
+// pass q + 1 of any), which the CTAs of one launch take in order from a
+// global counter.  An item of pass q of context i waits until pass q - 1 of
+// context i is complete (a per-context counter), so the queue order makes
+// every wait end: all earlier items are held by running CTAs.
+constexpr int BATCH_THREADS = 256;
+struct BatchCtx {                 // 128-byte aligned by its tensor map
+    CUtensorMap map;               // TMA view of psi as float32 [ny][2 nx], box 2 cpi x min(ny, 256)
+    float2 *psi;
+    Tables T;
+    const float *V;
+    float V_scale, g, sx, sy;
+    int nx, ny;
+    int rpi, row_items;            // rows per row item (256 threads' worth), items per row pass
+    int cpi, col_items;            // columns per column item, items per column pass
+    // potential parameters for the per-pass phase and reduction arguments,
+    // evaluated on the device as the host scheduler does (phase_at, red_at)
+    double lat_V0x, lat_V0y, eta, U0, dc, kappa, N, dxdy, probe_omega, probe_delta, probe_phi;
+    int cavity, pump_lattice, ctrl_target, nctrl;
+    const double *ctrl_t, *ctrl_v; // the context's control points, copied into the batch workspace
+};
+struct BatchArgs {
+    const BatchCtx *ctx;           // count descriptors
+    const int *row_prefix;         // count + 1 prefix sums of row items
+    const int *col_prefix;         // count + 1 prefix sums of column items
+    unsigned int *head;            // [0] next queue index, [1] abort flag (cleared before the launch)
+    unsigned int *epoch;           // per context: passes of this launch completed
+    unsigned int *done;            // per context: items of the current pass completed
+    int count, n, imag, cavity, spins;
+    double dt, t0;
+    unsigned int total;            // items in the queue
+};
+cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s);
+int batch_supported(int nx, int ny);      // 1 if a context of this size can join a batch
+int batch_rows_per_item(int n);           // rows (of n points) in a row item; columns of length n in a column item
+long long batch_queue_length(int n, int imag, int cavity, int row_items, int col_items);
+
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
 // tile_shift: the one-shot row pass takes 2^-tile_shift of its default rows
 // per CTA (0, 1 or 2; see row_rows_per_cta)

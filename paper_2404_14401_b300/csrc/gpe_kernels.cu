@@ -18,6 +18,7 @@
 #include <atomic>
 
 #include "../../include/gpe.h"
+#include "gpe_device.cuh"
 #include "gpe_fft.cuh"
 #include "gpe_internal.h"
 
@@ -34,354 +35,6 @@
 #define GPE_IN_PART(k) (GPE_PART < 0 || GPE_PART == (k))
 
 namespace gpe {
-
-// ------------------------------------------------------------------ TMA / mbarrier
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Poll the barrier at most `spins` times; false if it never completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int spins)
-{
-    for (int i = 0; i < spins; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-// After a wait has run out: give a bulk copy already issued towards this CTA's
-// shared memory a fixed number of polls to land, whatever the caller's wait
-// limit, so that the CTA does not reuse or release shared memory that the copy
-// may still write.  If even this runs out the CTA goes on (nothing better is
-// possible without waiting forever).
-constexpr int kDrainSpins = 1 << 22;
-__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity)
-{
-    return mbar_wait_bounded(bar, parity, kDrainSpins);
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_store_1d(void *dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void latch_status(DevScalars *sc, int code) { atomicCAS(&sc->status, 0, code); }
-
-// ------------------------------------------------------------------ reductions
-// Sum K per-thread FP32 partials over the CTA in FP64 with a fixed shuffle
-// tree and a fixed warp order; thread 0 writes them to dst[0..K).
-template <int K>
-__device__ __forceinline__ void block_sum(const float (&q)[K], double *__restrict__ dst, double *red)
-{
-    double d[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) d[i] = (double)q[i];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int width = blockDim.x < 32 ? blockDim.x : 32;
-    const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
-    for (int off = width >> 1; off > 0; off >>= 1)
-#pragma unroll
-        for (int i = 0; i < K; ++i) d[i] += __shfl_down_sync(mask, d[i], off);
-    if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < K; ++i) red[warp * NQ + i] = d[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red[w * NQ + i];
-            dst[i] = s;
-        }
-    }
-}
-
-// After every CTA has stored its partials: the CTA that arrives last sums
-// them in block order (deterministic whatever CTA is last) into out[0..K).
-// Returns true in the last CTA (all threads), with out valid after a barrier.
-template <int K>
-__device__ __forceinline__ bool last_block_total(const double *part, unsigned int *ticket, double *out,
-                                                 double *red)
-{
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    double acc[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-#pragma unroll
-        for (int i = 0; i < K; ++i) acc[i] += __ldcg(&part[(size_t)b * NQ + i]);
-    // fixed-order tree over threads (reuse block_sum on doubles via red)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int width = blockDim.x < 32 ? blockDim.x : 32;
-    const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
-    for (int off = width >> 1; off > 0; off >>= 1)
-#pragma unroll
-        for (int i = 0; i < K; ++i) acc[i] += __shfl_down_sync(mask, acc[i], off);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < K; ++i) red[warp * NQ + i] = acc[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red[w * NQ + i];
-            out[i] = s;
-        }
-        *ticket = 0u;
-    }
-    return true;
-}
-
-// Norm, overlaps, renormalisation scale and cavity field from the sums
-// S0 = sum |psi|^2, S1 = sum cos(kc x)cos(kc y)|psi|^2, S2 = sum cos^2(kc x)|psi|^2
-// (Sec. 3.3 normalisation; Eqs. 14-15).  One thread, FP64.
-[[maybe_unused]] static __device__ void finalize_fields(const double *S, const RedArgs &r, DevScalars *sc)
-{
-    const double norm = S[0] * r.dxdy;
-    const double O = S[1] / S[0], B = S[2] / S[0];
-    sc->norm = norm;
-    sc->O = O;
-    sc->B = B;
-    sc->c = 1.0 / sqrt(norm);
-    if (!isfinite(norm) || !(norm > 0.0) || !isfinite(O) || !isfinite(B)) {
-        latch_status(sc, GPE_ENONFINITE);
-        return;
-    }
-    if (r.cavity) {
-        const double dr = r.dc - r.U0 * B, di = r.kappa;
-        const double den = dr * dr + di * di;
-        if (!(den > 1e-24)) {
-            latch_status(sc, GPE_EILLCOND);
-            sc->alpha_re = 0.0;
-            sc->alpha_im = 0.0;
-            return;
-        }
-        // alpha = (num + probe) / (dr + i di), probe = Omega_c exp(i (Delta_p t + phi))
-        double ps = 0.0, pc = 0.0;
-        if (r.probe_omega != 0.0) sincos(r.probe_delta * r.t + r.probe_phi, &ps, &pc);
-        const double a = r.N * r.eta * O + r.probe_omega * pc, b = r.probe_omega * ps;
-        sc->alpha_re = (a * dr + b * di) / den;
-        sc->alpha_im = (b * dr - a * di) / den;
-    } else {
-        sc->alpha_re = 0.0;
-        sc->alpha_im = 0.0;
-    }
-}
-
-// ------------------------------------------------------------------ pointwise pieces
-// Per-CTA potential coefficients.  V at a point is
-//   F + t.x + A t.y + (B t.z + C) t.z
-// where t is the coordinate-table entry {trap, cos^2(k_lat .), cos(kc .), .}
-// of the axis that varies along the pencil and F, A, B, C fold in the fixed
-// axis: row pencils vary x (A = lattice x depth, B = U0|alpha|^2, C = 2 eta
-// Re(alpha) cos(kc y)); column pencils vary y (A = lattice y depth, B = pump
-// depth eta^2/U0, C = 2 eta Re(alpha) cos(kc x)).  Eqs. (9)-(13).
-struct PotCoefs {
-    float F, A, B, C;
-};
-
-__device__ __forceinline__ void alpha_terms(const PassArgs &a, float &acx2, float &acxcy)
-{
-    acx2 = 0.f;
-    acxcy = 0.f;
-    if (a.ph.use_alpha) {
-        const double ar = a.T.sc->alpha_re, ai = a.T.sc->alpha_im;
-        acx2 = (float)((double)a.ph.U0 * (ar * ar + ai * ai));     // V_c amplitude, Eq. (12)
-        acxcy = (float)((double)a.ph.two_eta * ar);                 // V_i amplitude, Eq. (13)
-    }
-}
-
-// row pencil at fixed y (yt = ytab[y])
-__device__ __forceinline__ PotCoefs row_coefs(const PassArgs &a, float4 yt)
-{
-    float acx2, acxcy;
-    alpha_terms(a, acx2, acxcy);
-    return PotCoefs{yt.x + a.ph.a_laty * yt.y + a.ph.a_pump * yt.z * yt.z, a.ph.a_latx, acx2, acxcy * yt.z};
-}
-
-// column pencil at fixed x (xt = xtab[x])
-__device__ __forceinline__ PotCoefs col_coefs(const PassArgs &a, float4 xt)
-{
-    float acx2, acxcy;
-    alpha_terms(a, acx2, acxcy);
-    return PotCoefs{xt.x + a.ph.a_latx * xt.y + acx2 * xt.z * xt.z, a.ph.a_laty, a.ph.a_pump, acxcy * xt.z};
-}
-
-__device__ __forceinline__ float pot_at(const PotCoefs &p, float4 t)
-{
-    return p.F + t.x + p.A * t.y + (p.B * t.z + p.C) * t.z;
-}
-
-// psi <- exp(-i theta) psi (real time) or exp(-theta) psi (imaginary time),
-// theta = (V + g |psi|^2) h (Sec. 3.1, Sec. 3.3).  Real time multiplies by
-// 1 + d with d = exp(-i theta) - 1 = -2 sin^2(theta/2) - 2 i sin(theta/2)
-// cos(theta/2): small phases keep their relative precision and |1 + d| = 1
-// up to unbiased rounding.  For |theta| <= 1, sin and cos of w = theta/2 come
-// from their Taylor series in w^2 (remainders w^11/11! and w^10/10! below
-// 3e-10); larger phases use sincosf.
-__device__ __forceinline__ float2 phase_mul(float2 q, float V, float g, float h, int imag)
-{
-    const float n = q.x * q.x + q.y * q.y;
-    const float th = (V + g * n) * h;
-    if (imag) {
-        const float f = expf(-th);
-        return make_float2(q.x * f, q.y * f);
-    }
-    const float w = 0.5f * th;
-    float s, c;
-    if (fabsf(th) <= 1.f) {
-        const float v = w * w;
-        float ps = fmaf(v, 1.f / 362880.f, -1.f / 5040.f);     // sin w = w (1 - v/3! + v^2/5! - ...)
-        ps = fmaf(v, ps, 1.f / 120.f);
-        ps = fmaf(v, ps, -1.f / 6.f);
-        s = fmaf(w * v, ps, w);
-        float pc = fmaf(v, 1.f / 40320.f, -1.f / 720.f);       // cos w = 1 - v/2! + v^2/4! - ...
-        pc = fmaf(v, pc, 1.f / 24.f);
-        pc = fmaf(v, pc, -0.5f);
-        c = fmaf(v, pc, 1.f);
-    } else {
-        sincosf(w, &s, &c);
-    }
-    const float dr = -2.f * s * s, di = -2.f * s * c;
-    return make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
-}
-
-// psi <- exp(-i theta) psi for a given theta (real time), in the same 1 + d
-// form as phase_mul; used by the adjoint passes, whose theta comes from the
-// forward state rather than from the value being rotated.
-__device__ __forceinline__ float2 phase_rot(float2 q, float th)
-{
-    const float w = 0.5f * th;
-    float s, c;
-    if (fabsf(th) <= 1.f) {
-        const float v = w * w;
-        float ps = fmaf(v, 1.f / 362880.f, -1.f / 5040.f);
-        ps = fmaf(v, ps, 1.f / 120.f);
-        ps = fmaf(v, ps, -1.f / 6.f);
-        s = fmaf(w * v, ps, w);
-        float pc = fmaf(v, 1.f / 40320.f, -1.f / 720.f);
-        pc = fmaf(v, pc, 1.f / 24.f);
-        pc = fmaf(v, pc, -0.5f);
-        c = fmaf(v, pc, 1.f);
-    } else {
-        sincosf(w, &s, &c);
-    }
-    const float dr = -2.f * s * s, di = -2.f * s * c;
-    return make_float2(q.x + (q.x * dr - q.y * di), q.y + (q.x * di + q.y * dr));
-}
-
-// Adjoint of one real-time half phase at one point (discrete adjoint of
-// psi' = exp(-i theta) psi, theta = h (V + g |psi|^2)): lam = mu + 2 h g
-// Im(conj(mu) psi) psi with mu = exp(+i theta) lam'; returns Im(conj(mu) psi),
-// whose 2 h L(r) multiple is dJ/dv at this point.  `psi` is the phase's input.
-__device__ __forceinline__ float phase_adjoint(float2 &lam, float2 psi, float V, float g, float h)
-{
-    const float th = (V + g * (psi.x * psi.x + psi.y * psi.y)) * h;
-    const float2 mu = phase_rot(lam, -th);
-    const float q = mu.x * psi.y - mu.y * psi.x;
-    const float f = 2.f * h * g * q;
-    lam = make_float2(fmaf(f, psi.x, mu.x), fmaf(f, psi.y, mu.y));
-    return q;
-}
-
-// one axis of the kinetic propagator in k-space: real time psi <- s (psi + psi D)
-// with D = exp(-i k^2 dt / 2m) - 1, imaginary time psi <- s K psi with
-// K = exp(-k^2 dtau / 2m); s = 1/n exact (the inverse FFT's normalisation).
-// CONJ: the adjoint (conjugate) propagator, D -> conj(D).
-template <int E, int TP, bool CONJ = false>
-__device__ __forceinline__ void kinetic_axis(float2 (&v)[E], const float2 *__restrict__ D, int j, float s, int imag)
-{
-    if (imag) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const float f = __ldg(&D[j + r * TP]).x * s;
-            v[r] = make_float2(v[r].x * f, v[r].y * f);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            float2 d = __ldg(&D[j + r * TP]);
-            if constexpr (CONJ) d.y = -d.y;
-            const float2 p = v[r];
-            const float2 pd = cmul(p, d);
-            v[r] = make_float2((p.x + pd.x) * s, (p.y + pd.y) * s);
-        }
-    }
-}
-
-// Copy an axis' twiddle table into shared memory (every thread of the CTA;
-// visible to the first twiddled stage through the barrier of the stage-0
-// exchange that precedes it).
-template <int N>
-__device__ __forceinline__ void stage_twiddles(float4 *__restrict__ dst, const float4 *__restrict__ src)
-{
-    for (int i = threadIdx.x; i < fft_tw_count(N); i += blockDim.x) dst[i] = __ldg(&src[i]);
-}
-
-// Asynchronous variant: one bulk copy of the table into shared memory whose
-// bytes complete on `bar`.  The caller (thread 0) has already armed `bar` with
-// a single arrive.expect_tx covering these bytes (a barrier of count 1 takes
-// exactly one arrival per phase).
-template <int N> __host__ __device__ constexpr uint32_t twiddle_bytes() { return (uint32_t)(fft_tw_count(N) * 16); }
-template <int N>
-__device__ __forceinline__ void stage_twiddles_async(float4 *__restrict__ dst, const float4 *__restrict__ src,
-                                                     uint64_t *bar)
-{
-    bulk_load_1d(dst, src, twiddle_bytes<N>(), bar);
-}
 
 // ------------------------------------------------------------------ row pass
 template <int N> struct RowCfg {

@@ -24,7 +24,8 @@ EXPORTS = ("gpe_workspace_size", "gpe_create", "gpe_set_potential", "gpe_step", 
            "gpe_sync", "gpe_set_wait_limit", "gpe_get_wait_limit", "gpe_debug_timeout_probe", "gpe_profile", "gpe_profile_read", "gpe_profile_read_kind", "gpe_launch_count",
            "gpe_overlaps_static", "gpe_momentum_populations", "gpe_get_pass_variants", "gpe_set_pass_variants", "gpe_tune",
            "gpe_adjoint_workspace_size", "gpe_adjoint_lattice", "gpe_adjoint_workspace_size_ex",
-           "gpe_adjoint_lattice_ex", "gpe_destroy",
+           "gpe_adjoint_lattice_ex", "gpe_batch_workspace_size", "gpe_batch_create", "gpe_batch_step",
+           "gpe_batch_destroy", "gpe_destroy",
            "gpe_last_error", "gpe_status_string")
 
 
@@ -103,6 +104,10 @@ def load() -> ctypes.CDLL:
         "gpe_adjoint_workspace_size_ex": (c_size_t, [c_int, c_int, c_int, c_int]),
         "gpe_adjoint_lattice_ex": (c_int, [c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,
                                            P(c_double), P(c_double)]),
+        "gpe_batch_workspace_size": (c_size_t, [P(c_void_p), c_int]),
+        "gpe_batch_create": (c_int, [P(c_void_p), c_int, c_void_p, c_size_t, P(c_void_p)]),
+        "gpe_batch_step": (c_int, [c_void_p, c_int, c_double, c_int]),
+        "gpe_batch_destroy": (None, [c_void_p]),
         "gpe_destroy": (None, [c_void_p]),
         "gpe_last_error": (c_char_p, [c_void_p]),
         "gpe_status_string": (c_char_p, [c_int]),
@@ -287,6 +292,33 @@ def gpe_adjoint_lattice_ex(ctx, nsteps: int, dt: float, variant: int, phi_ptr: i
     _check(ctx, load().gpe_adjoint_lattice_ex(ctx, int(nsteps), float(dt), int(variant), c_void_p(phi_ptr),
                                               c_void_p(ws_ptr), ws_bytes, ctypes.byref(J), grad))
     return J.value, [grad[i] for i in range(nctrl)]
+
+
+def _ctx_array(ctxs):
+    arr = (c_void_p * len(ctxs))()
+    for i, c in enumerate(ctxs):
+        arr[i] = c.value if isinstance(c, c_void_p) else c
+    return arr
+
+
+def gpe_batch_workspace_size(ctxs) -> int:
+    return load().gpe_batch_workspace_size(_ctx_array(ctxs), len(ctxs))
+
+
+def gpe_batch_create(ctxs, ws_ptr: int, ws_bytes: int) -> c_void_p:
+    b = c_void_p()
+    _check(ctxs[0] if ctxs else None, load().gpe_batch_create(_ctx_array(ctxs), len(ctxs), c_void_p(ws_ptr), ws_bytes,
+                                                              ctypes.byref(b)))
+    return b
+
+
+def gpe_batch_step(batch, ctx0, n: int, dt: float, mode: int):
+    """ctx0: the batch's first context (for the error message)."""
+    _check(ctx0, load().gpe_batch_step(batch, int(n), float(dt), int(mode)))
+
+
+def gpe_batch_destroy(batch):
+    load().gpe_batch_destroy(batch)
 
 
 def gpe_destroy(ctx):
