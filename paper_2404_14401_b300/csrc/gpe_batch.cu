@@ -32,6 +32,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <atomic>
 
 #include "../../include/gpe.h"
@@ -393,21 +395,32 @@ __device__ bool dispatch(int n, const BatchCtx &c, const Item &it, const PhaseAr
 }
 
 // ------------------------------------------------------------------ kernel
-__global__ void __launch_bounds__(BATCH_THREADS, 2) batch_kernel(const BatchArgs b)
+// CPS: CTAs per SM the launch bounds ask for (2: 128 registers, no spill;
+// 3: 80 registers, a few spilled values)
+template <int CPS>
+__global__ void __launch_bounds__(BATCH_THREADS, CPS) batch_kernel(const BatchArgs b)
 {
     __shared__ __align__(128) float2 buf[kBufF2];
     __shared__ double red[32 * NQ];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ unsigned int s_idx;
+    __shared__ unsigned int s_idx, s_next;
     __shared__ int s_flag;
     __shared__ PhaseArgs s_ph;
     __shared__ RedArgs s_rd;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        s_next = atomicAdd(&b.head[0], 1u);
+    }
     __syncthreads();
     uint32_t parity = 0;
     for (;;) {
-        if (threadIdx.x == 0)
-            s_idx = ld_acquire(&b.head[1]) ? b.total : atomicAdd(&b.head[0], 1u);
+        // the queue entry taken one item ahead: the CTA holds at most two
+        // entries and starts the later only after finishing the earlier, so
+        // the smallest unfinished entry is always being worked on
+        if (threadIdx.x == 0) {
+            s_idx = ld_acquire(&b.head[1]) ? b.total : s_next;
+            if (s_idx < b.total) s_next = atomicAdd(&b.head[0], 1u);
+        }
         __syncthreads();
         const unsigned int idx = s_idx;
         if (idx >= b.total) break;
@@ -449,12 +462,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) batch_kernel(const BatchArgs
             }
             break;
         }
-        // item complete: publish its stores, count it; the item that finishes
-        // the pass sums the partials, updates the scalars and opens the next pass
-        __threadfence();
+        // item complete: count it (the barrier orders every thread's stores
+        // before thread 0's fence, which is cumulative); the item that
+        // finishes the pass sums the partials, updates the scalars and opens
+        // the next pass
         __syncthreads();
         const int items = it.col ? c.col_items : c.row_items;
-        if (threadIdx.x == 0) s_flag = (atomicAdd(&b.done[it.i], 1u) + 1u == (unsigned int)items);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_flag = (atomicAdd(&b.done[it.i], 1u) + 1u == (unsigned int)items);
+        }
         __syncthreads();
         if (s_flag) {
             if (it.reduce) {
@@ -472,7 +489,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) batch_kernel(const BatchArgs
     }
 }
 
-static int batch_grid()
+// resident CTAs of one variant on the current device (cached per device)
+template <int CPS> static int batch_grid()
 {
     static std::atomic<int> cache[64];
     int dev = 0;
@@ -482,7 +500,7 @@ static int batch_grid()
     if (v <= 0) {
         int sms = 0, per = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, BATCH_THREADS, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<CPS>, BATCH_THREADS, 0) != cudaSuccess)
             return 0;
         v = sms * (per > 0 ? per : 1);
         g.store(v, std::memory_order_relaxed);
@@ -490,13 +508,22 @@ static int batch_grid()
     return v;
 }
 
-cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s)
+template <int CPS> static cudaError_t launch_variant(const BatchArgs &b, cudaStream_t s)
 {
-    int grid = batch_grid();
+    int grid = batch_grid<CPS>();
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if ((unsigned int)grid > b.total) grid = (int)b.total;
-    batch_kernel<<<grid, BATCH_THREADS, 0, s>>>(b);
+    batch_kernel<CPS><<<grid, BATCH_THREADS, 0, s>>>(b);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s)
+{
+    static const bool two = [] {
+        const char *e = getenv("GPE_BATCH_CTAS");
+        return e && atoi(e) == 2;
+    }();
+    return two ? launch_variant<2>(b, s) : launch_variant<3>(b, s);
 }
 
 long long batch_queue_length(int n, int imag, int cavity, int R, int C) { return batch_total(n, imag, cavity, R, C); }

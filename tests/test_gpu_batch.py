@@ -70,8 +70,9 @@ def test_batch_of_sweep_instances_matches_oracle():
         sims.append(s)
         psis.append(x)
     b = Batch(sims)
+    b.step(25, 1e-3, imag=True)                 # also sets each context's kinetic factors for this dt
     l0 = [s.launches for s in sims]
-    b.step(50, 1e-3, imag=True)
+    b.step(25, 1e-3, imag=True)
     assert [s.launches - a for s, a in zip(sims, l0)] == [1, 0, 0]      # one kernel for the whole batch
     for s, w, x in zip(sims, picks, psis):
         check_against_oracle(s, w["params"], x, 50, 1e-3, True, cavity=True)
@@ -203,7 +204,9 @@ def test_batch_argument_errors():
     with pytest.raises(GPEError):
         Batch([small])                                             # 32 points: below the batch's 64
     a = sim_for(dict(w["params"], nx=64, ny=64))
-    thin = sim_for(dict(w["params"], nx=2048, ny=64))              # a 2048-point row item needs 2 rows: fine
+    thin = sim_for(dict(w["params"], nx=2048, ny=64, Lx=40.0))     # a 2048-point row item needs 2 rows: fine
+    a.set_psi(c64(gi.gaussian_state(64, 64, 16.0, 16.0, 1.5, 1e-3, seed=92)))
+    thin.set_psi(c64(gi.gaussian_state(2048, 64, 40.0, 16.0, 1.5, 1e-3, seed=93)))
     Batch([a, thin]).step(3, 5e-4)
     assert a.sync() == 0 and thin.sync() == 0
     cav = sim_for(dict(w["params"], nx=64, ny=64, cavity=1, eta=1.0, U0=-0.5, dc=-2.0, kappa=1.0, kc=2 * np.pi))
