@@ -1365,6 +1365,9 @@ struct gpe_batch {
     unsigned char *ws;
     size_t ws_bytes;
     int device;
+    int tpi;                                  // tiles per item
+    int grid;                                 // CTAs of a launch
+    int row_items, col_items;                 // items per row / column pass, all contexts
     std::vector<cudaStream_t> streams;        // distinct context streams other than the first
     cudaEvent_t ev;
 };
@@ -1408,6 +1411,18 @@ gpe_status batch_upload(gpe_batch *b)
     std::vector<int> rpre(count + 1, 0), cpre(count + 1, 0);
     std::vector<double> ctrl;
     const double *ctrl_dev = (const double *)(b->ws + L.ctrl);
+    // tiles per item: one item per tile unless the passes are much wider than
+    // the launch (then up to 8 consecutive tiles per item, so that the
+    // per-item dependency check and completion count are paid less often)
+    const int resident = batch_resident_ctas();
+    if (resident <= 0) return fail(c0, GPE_ECUDA, "gpe_batch: no occupancy for the batch kernel");
+    long long rt = 0, ct = 0;
+    for (int i = 0; i < count; ++i) {
+        rt += b->ctxs[i]->ny / batch_rows_per_item(b->ctxs[i]->nx);
+        ct += b->ctxs[i]->nx / batch_rows_per_item(b->ctxs[i]->ny);
+    }
+    long long tpi = (rt < ct ? rt : ct) / (4LL * resident);
+    b->tpi = (int)(tpi < 1 ? 1 : tpi > 8 ? 8 : tpi);
     for (int i = 0; i < count; ++i) {
         gpe_ctx *c = b->ctxs[i];
         BatchCtx &e = d[i];
@@ -1424,8 +1439,10 @@ gpe_status batch_upload(gpe_batch *b)
         e.sy = (float)(1.0 / c->ny);
         e.nx = c->nx;
         e.ny = c->ny;
-        e.row_items = c->ny / e.rpi;
-        e.col_items = c->nx / e.cpi;
+        e.row_tiles = c->ny / e.rpi;
+        e.col_tiles = c->nx / e.cpi;
+        e.row_items = (e.row_tiles + b->tpi - 1) / b->tpi;
+        e.col_items = (e.col_tiles + b->tpi - 1) / b->tpi;
         const gpe_potential &p = c->pot;
         e.lat_V0x = p.lat_V0x;
         e.lat_V0y = p.lat_V0y;
@@ -1466,6 +1483,11 @@ gpe_status batch_upload(gpe_batch *b)
         b->key[2 * i] = b->ctxs[i]->uid;
         b->key[2 * i + 1] = b->ctxs[i]->version;
     }
+    // no more CTAs than the widest pass has items: the rest would only wait
+    b->row_items = rpre[count];
+    b->col_items = cpre[count];
+    const int wide = b->row_items > b->col_items ? b->row_items : b->col_items;
+    b->grid = wide < resident ? wide : resident;
     return GPE_OK;
 }
 
@@ -1573,11 +1595,7 @@ gpe_status gpe_batch_step(gpe_batch *b, int n, double dt, gpe_mode mode)
         TRY(cuda_check(c0, cudaStreamWaitEvent(s, b->ev, 0), "batch fork"));
     }
     const BatchLayout L = batch_layout(count, ctrl_points_of(b->ctxs.data(), count));
-    int R = 0, C = 0;
-    for (int i = 0; i < count; ++i) {
-        R += b->ctxs[i]->ny / batch_rows_per_item(b->ctxs[i]->nx);
-        C += b->ctxs[i]->nx / batch_rows_per_item(b->ctxs[i]->ny);
-    }
+    const int R = b->row_items, C = b->col_items;
     // a launch's queue stays below 2^31 items: longer runs take several launches
     const long long per_step = batch_queue_length(1, imag, cavity, R, C);
     const int max_steps = (int)((1LL << 31) / (per_step > 0 ? per_step : 1)) - 2;
@@ -1597,11 +1615,12 @@ gpe_status gpe_batch_step(gpe_batch *b, int n, double dt, gpe_mode mode)
         a.imag = imag;
         a.cavity = cavity;
         a.spins = c0->spins;
+        a.tpi = b->tpi;
         a.dt = dt;
         a.t0 = c0->t;
         a.total = (unsigned int)batch_queue_length(m, imag, cavity, R, C);
         TRY(cuda_check(c0, cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * (2 + 2 * (size_t)count), s), "batch memset"));
-        TRY(cuda_check(c0, launch_batch(a, s), "batch launch"));
+        TRY(cuda_check(c0, launch_batch(a, s, b->grid), "batch launch"));
         c0->launches++;
         for (int i = 0; i < count; ++i) b->ctxs[i]->t += m * dt;
         done += m;

@@ -240,12 +240,16 @@ __host__ __device__ inline long long batch_total(int n, int imag, int cavity, in
 }
 
 // ------------------------------------------------------------------ items
+// One row tile: RPI whole rows, plain coalesced loads through L2, the pass's
+// pointwise work and T_x in registers and shared memory, stores through L2;
+// the tile's norm / overlap sums are added to q.
 template <int N>
-__device__ void row_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, float2 *buf, double *red)
+__device__ void row_tile(const BatchCtx &c, int tile, const Item &it, const PhaseArgs &ph, int imag, float2 *buf,
+                         float (&q)[3])
 {
     constexpr int E = kE, TP = N / E, RPI = BATCH_THREADS / TP, PS = N + N / 16;
     const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
-    const int y = it.k * RPI + lr;
+    const int y = tile * RPI + lr;
     const Tables &T = c.T;
     float2 *row = c.psi + (size_t)y * N;
     float2 *sb = buf + lr * PS;
@@ -279,37 +283,51 @@ __device__ void row_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph,
         kinetic_axis<E, TP>(v, T.kinx, j, c.sx, imag);
         fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
     }
-    if (mode == ROW_PHASE_R || mode == ROW_REDUCE_R) {
-        float q[3] = {0.f, 0.f, 0.f};
+    if (it.reduce) {
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const float cx = __ldg(&T.xtab[j + r * TP]).z;
             const float n = v[r].x * v[r].x + v[r].y * v[r].y;
-            q[0] += n;
-            q[1] += cx * n;
-            q[2] += cx * cx * n;
+            q0 += n;
+            q1 += cx * n;
+            q2 += cx * cx * n;
         }
-        q[1] *= yt.z;
-        block_sum<3>(q, T.part_row + (size_t)it.k * NQ, red);
+        q[0] += q0;
+        q[1] += q1 * yt.z;
+        q[2] += q2;
     }
     if (mode != ROW_REDUCE_R)
 #pragma unroll
         for (int r = 0; r < E; ++r) __stcg(&row[j + r * TP], v[r]);
 }
 
-// Column item: TMA load of the dense [N][G] tile, T_y [+ closing phase]
-// [+ reductions], results back into the tile and out with coalesced stores.
-// False if the tile's bounded wait ran out (the copy has then been given its
-// time to land; nothing is stored).
+// A row item: tiles k tpi .. min((k + 1) tpi, row_tiles) - 1, then one
+// FP64 partial sum of the item.  The exchange buffers are free again when a
+// tile ends (its last exchange ends with a barrier after the reads).
 template <int N>
-__device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, float2 *buf, double *red,
-                         uint64_t *bar, uint32_t &parity, int spins)
+__device__ void row_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi, float2 *buf,
+                         double *red)
+{
+    float q[3] = {0.f, 0.f, 0.f};
+    const int t0 = it.k * tpi, t1 = min(t0 + tpi, c.row_tiles);
+    for (int t = t0; t < t1; ++t) row_tile<N>(c, t, it, ph, imag, buf, q);
+    if (it.reduce) block_sum<3>(q, c.T.part_row + (size_t)it.k * NQ, red);
+}
+
+// One column tile: TMA load of the dense [N][G] tile, T_y [+ closing phase]
+// [+ the tile's sums into q], results back into the tile and out with
+// coalesced stores through L2.  False if the tile's bounded wait ran out (the
+// copy has then been given its time to land; nothing is stored).
+template <int N>
+__device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const PhaseArgs &ph, int imag, float2 *buf,
+                         uint64_t *bar, uint32_t &parity, int spins, float (&q)[3])
 {
     constexpr int E = kE, TP = N / E, G = BATCH_THREADS / TP, BR = N < 256 ? N : 256, PS = N + N / 16;
     static_assert(G * PS <= kBufF2, "padded pencils of a tile fit the item buffer");
-    const int c0 = it.k * G;
+    const int c0 = tile * G;
     const Tables &T = c.T;
-    float2 *tile = buf;
+    float2 *tile_buf = buf;
     if (threadIdx.x == 0) {
         // psi was written by other CTAs through the generic proxy (acquired
         // above): order those writes before this thread's async-proxy loads.
@@ -318,7 +336,7 @@ __device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph,
         asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&c.map) : "memory");
         mbar_expect_tx(bar, (uint32_t)(N * G * 8));
-        for (int r0 = 0; r0 < N; r0 += BR) tma_load_2d(tile + (size_t)r0 * G, &c.map, bar, 2 * c0, r0);
+        for (int r0 = 0; r0 < N; r0 += BR) tma_load_2d(tile_buf + (size_t)r0 * G, &c.map, bar, 2 * c0, r0);
     }
     const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity, spins));
     if (!ok) mbar_drain(bar, parity);
@@ -328,9 +346,9 @@ __device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph,
     const int j = threadIdx.x % TP, cg = threadIdx.x / TP;
     float2 v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = tile[(j + r * TP) * G + cg];
+    for (int r = 0; r < E; ++r) v[r] = tile_buf[(j + r * TP) * G + cg];
     __syncthreads();                                   // dense reads done before the exchange writes
-    float2 *sb = tile + cg * PS;
+    float2 *sb = tile_buf + cg * PS;
     fft_pencil<N, E, false>(v, sb, j, 1, T.twy);
     kinetic_axis<E, TP>(v, T.kiny, j, c.sy, imag);
     fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
@@ -348,7 +366,6 @@ __device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph,
             v[r] = phase_mul(v[r], V, c.g, ph.h, imag);
         }
     }
-    float q[3] = {0.f, 0.f, 0.f};
     if (it.reduce) {
         const float cx = __ldg(&T.xtab[x]).z;
         float n0 = 0.f, n1 = 0.f;
@@ -358,39 +375,51 @@ __device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph,
             n0 += n;
             n1 += __ldg(&T.ytab[j + r * TP]).z * n;
         }
-        q[0] = n0;
-        q[1] = cx * n1;
-        q[2] = cx * cx * n0;
+        q[0] += n0;
+        q[1] += cx * n1;
+        q[2] += cx * cx * n0;
     }
     // every exchange read finished at the last exchange's barrier
 #pragma unroll
-    for (int r = 0; r < E; ++r) tile[(j + r * TP) * G + cg] = v[r];
+    for (int r = 0; r < E; ++r) tile_buf[(j + r * TP) * G + cg] = v[r];
     __syncthreads();
     for (int e = threadIdx.x; e < N * G; e += BATCH_THREADS)
-        __stcg(&c.psi[(size_t)(e / G) * c.nx + c0 + e % G], tile[e]);
-    if (it.reduce) block_sum<3>(q, T.part_col + (size_t)it.k * NQ, red);
+        __stcg(&c.psi[(size_t)(e / G) * c.nx + c0 + e % G], tile_buf[e]);
+    __syncthreads();                                   // the tile is read out before the next load reuses it
     return true;
 }
 
 template <int N>
-__device__ bool run_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, float2 *buf, double *red,
-                         uint64_t *bar, uint32_t &parity, int spins)
+__device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi, float2 *buf,
+                         double *red, uint64_t *bar, uint32_t &parity, int spins)
 {
-    if (it.col) return col_item<N>(c, it, ph, imag, buf, red, bar, parity, spins);
-    row_item<N>(c, it, ph, imag, buf, red);
+    float q[3] = {0.f, 0.f, 0.f};
+    const int t0 = it.k * tpi, t1 = min(t0 + tpi, c.col_tiles);
+    for (int t = t0; t < t1; ++t)
+        if (!col_tile<N>(c, t, it, ph, imag, buf, bar, parity, spins, q)) return false;
+    if (it.reduce) block_sum<3>(q, c.T.part_col + (size_t)it.k * NQ, red);
     return true;
 }
 
-__device__ bool dispatch(int n, const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, float2 *buf,
+template <int N>
+__device__ bool run_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi, float2 *buf,
                          double *red, uint64_t *bar, uint32_t &parity, int spins)
 {
+    if (it.col) return col_item<N>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    row_item<N>(c, it, ph, imag, tpi, buf, red);
+    return true;
+}
+
+__device__ bool dispatch(int n, const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi,
+                         float2 *buf, double *red, uint64_t *bar, uint32_t &parity, int spins)
+{
     switch (n) {
-    case 64: return run_item<64>(c, it, ph, imag, buf, red, bar, parity, spins);
-    case 128: return run_item<128>(c, it, ph, imag, buf, red, bar, parity, spins);
-    case 256: return run_item<256>(c, it, ph, imag, buf, red, bar, parity, spins);
-    case 512: return run_item<512>(c, it, ph, imag, buf, red, bar, parity, spins);
-    case 1024: return run_item<1024>(c, it, ph, imag, buf, red, bar, parity, spins);
-    default: return run_item<2048>(c, it, ph, imag, buf, red, bar, parity, spins);
+    case 64: return run_item<64>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 128: return run_item<128>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 256: return run_item<256>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 512: return run_item<512>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 1024: return run_item<1024>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    default: return run_item<2048>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
     }
 }
 
@@ -431,13 +460,15 @@ __global__ void __launch_bounds__(BATCH_THREADS, CPS) batch_kernel(const BatchAr
         // a pass of the largest batches takes milliseconds)
         if (threadIdx.x == 0) {
             int ok = 1, polls = 0;
+            unsigned int ns = 32;                      // back off: many CTAs may wait on one counter
             const int limit = b.spins < (1 << 22) ? b.spins : (1 << 22);
             while (ld_acquire(&b.epoch[it.i]) < (unsigned int)it.q) {
                 if (polls++ >= limit || ld_acquire(&b.head[1])) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(ns);
+                if (ns < 1024) ns *= 2;
             }
             if (!ok) {
                 latch_status(c.T.sc, GPE_ETIMEOUT);
@@ -455,7 +486,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, CPS) batch_kernel(const BatchAr
         if (!s_flag) break;
         const PhaseArgs ph = s_ph;
         const int n = it.col ? c.ny : c.nx;
-        if (!dispatch(n, c, it, ph, b.imag, buf, red, &bar, parity, b.spins)) {
+        if (!dispatch(n, c, it, ph, b.imag, b.tpi, buf, red, &bar, parity, b.spins)) {
             if (threadIdx.x == 0) {
                 latch_status(c.T.sc, GPE_ETIMEOUT);
                 atomicExch(&b.head[1], 1u);
@@ -508,22 +539,24 @@ template <int CPS> static int batch_grid()
     return v;
 }
 
-template <int CPS> static cudaError_t launch_variant(const BatchArgs &b, cudaStream_t s)
-{
-    int grid = batch_grid<CPS>();
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if ((unsigned int)grid > b.total) grid = (int)b.total;
-    batch_kernel<CPS><<<grid, BATCH_THREADS, 0, s>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s)
+static bool two_per_sm()
 {
     static const bool two = [] {
         const char *e = getenv("GPE_BATCH_CTAS");
         return e && atoi(e) == 2;
     }();
-    return two ? launch_variant<2>(b, s) : launch_variant<3>(b, s);
+    return two;
+}
+
+int batch_resident_ctas() { return two_per_sm() ? batch_grid<2>() : batch_grid<3>(); }
+
+cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s, int grid)
+{
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    if ((unsigned int)grid > b.total) grid = (int)b.total;
+    if (two_per_sm()) batch_kernel<2><<<grid, BATCH_THREADS, 0, s>>>(b);
+    else batch_kernel<3><<<grid, BATCH_THREADS, 0, s>>>(b);
+    return cudaGetLastError();
 }
 
 long long batch_queue_length(int n, int imag, int cavity, int R, int C) { return batch_total(n, imag, cavity, R, C); }

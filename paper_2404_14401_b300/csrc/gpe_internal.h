@@ -113,8 +113,9 @@ struct BatchCtx {                 // 128-byte aligned by its tensor map
     const float *V;
     float V_scale, g, sx, sy;
     int nx, ny;
-    int rpi, row_items;            // rows per row item (256 threads' worth), items per row pass
-    int cpi, col_items;            // columns per column item, items per column pass
+    int rpi, row_tiles;            // rows per row tile (256 threads' worth), tiles per row pass
+    int cpi, col_tiles;            // columns per column tile, tiles per column pass
+    int row_items, col_items;      // items (runs of tpi consecutive tiles) per row / column pass
     // potential parameters for the per-pass phase and reduction arguments,
     // evaluated on the device as the host scheduler does (phase_at, red_at)
     double lat_V0x, lat_V0y, eta, U0, dc, kappa, N, dxdy, probe_omega, probe_delta, probe_phi;
@@ -129,10 +130,12 @@ struct BatchArgs {
     unsigned int *epoch;           // per context: passes of this launch completed
     unsigned int *done;            // per context: items of the current pass completed
     int count, n, imag, cavity, spins;
+    int tpi;                       // tiles per item (the last item of a pass may have fewer)
     double dt, t0;
     unsigned int total;            // items in the queue
 };
-cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s);
+cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s, int grid);
+int batch_resident_ctas();                // CTAs of the batch kernel that fit the current device at once
 int batch_supported(int nx, int ny);      // 1 if a context of this size can join a batch
 int batch_rows_per_item(int n);           // rows (of n points) in a row item; columns of length n in a column item
 long long batch_queue_length(int n, int imag, int cavity, int row_items, int col_items);
