@@ -48,7 +48,9 @@ typedef enum {
     GPE_ECUDA = 3,       /* a CUDA runtime/driver call failed; see gpe_last_error */
     GPE_ETIMEOUT = 4,    /* a bounded device wait (TMA barrier) ran out          */
     GPE_ENONFINITE = 5,  /* NaN/Inf found in a norm or cavity reduction          */
-    GPE_EILLCOND = 6     /* |Delta_c - U0 B + i kappa| below 1e-12 (Eq. 14)      */
+    GPE_EILLCOND = 6,    /* |Delta_c - U0 B + i kappa| below 1e-12 (Eq. 14)      */
+    GPE_EBOUNDS = 7      /* debug bounds-check build only: an index check failed
+                            (the access was skipped, nothing trapped)           */
 } gpe_status;
 
 typedef enum { GPE_REAL = 0, GPE_IMAG = 1 } gpe_mode;

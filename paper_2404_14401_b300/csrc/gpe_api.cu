@@ -372,6 +372,7 @@ const char *gpe_status_string(gpe_status s)
     case GPE_ETIMEOUT: return "GPE_ETIMEOUT";
     case GPE_ENONFINITE: return "GPE_ENONFINITE";
     case GPE_EILLCOND: return "GPE_EILLCOND";
+    case GPE_EBOUNDS: return "GPE_EBOUNDS";
     default: return "GPE_UNKNOWN";
     }
 }

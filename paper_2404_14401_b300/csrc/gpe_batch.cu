@@ -249,13 +249,14 @@ __device__ void row_tile(const BatchCtx &c, int tile, const Item &it, const Phas
 {
     constexpr int E = kE, TP = N / E, RPI = BATCH_THREADS / TP, PS = N + N / 16;
     const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
-    const int y = tile * RPI + lr;
     const Tables &T = c.T;
+    const bool inb = check_index((long long)tile * RPI + lr, c.ny, T.sc);   // bounds-check build
+    const int y = inb ? tile * RPI + lr : 0;
     float2 *row = c.psi + (size_t)y * N;
     float2 *sb = buf + lr * PS;
     float2 v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = __ldcg(&row[j + r * TP]);
+    for (int r = 0; r < E; ++r) v[r] = inb ? __ldcg(&row[j + r * TP]) : make_float2(0.f, 0.f);
     const float4 yt = __ldg(&T.ytab[y]);
     const int mode = it.mode;
     if (mode == ROW_PT || mode == ROW_PHASE || mode == ROW_PHASE_R) {
@@ -283,7 +284,7 @@ __device__ void row_tile(const BatchCtx &c, int tile, const Item &it, const Phas
         kinetic_axis<E, TP>(v, T.kinx, j, c.sx, imag);
         fft_pencil<N, E, true>(v, sb, j, 1, T.twx);
     }
-    if (it.reduce) {
+    if (it.reduce && inb) {
         float q0 = 0.f, q1 = 0.f, q2 = 0.f;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -297,7 +298,7 @@ __device__ void row_tile(const BatchCtx &c, int tile, const Item &it, const Phas
         q[1] += q1 * yt.z;
         q[2] += q2;
     }
-    if (mode != ROW_REDUCE_R)
+    if (mode != ROW_REDUCE_R && inb)
 #pragma unroll
         for (int r = 0; r < E; ++r) __stcg(&row[j + r * TP], v[r]);
 }
@@ -325,8 +326,9 @@ __device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const Phas
 {
     constexpr int E = kE, TP = N / E, G = BATCH_THREADS / TP, BR = N < 256 ? N : 256, PS = N + N / 16;
     static_assert(G * PS <= kBufF2, "padded pencils of a tile fit the item buffer");
-    const int c0 = tile * G;
     const Tables &T = c.T;
+    const bool inb = check_index((long long)tile * G + G - 1, c.nx, T.sc);  // bounds-check build
+    const int c0 = inb ? tile * G : 0;
     float2 *tile_buf = buf;
     if (threadIdx.x == 0) {
         // psi was written by other CTAs through the generic proxy (acquired
@@ -366,7 +368,7 @@ __device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const Phas
             v[r] = phase_mul(v[r], V, c.g, ph.h, imag);
         }
     }
-    if (it.reduce) {
+    if (it.reduce && inb) {
         const float cx = __ldg(&T.xtab[x]).z;
         float n0 = 0.f, n1 = 0.f;
 #pragma unroll
@@ -383,7 +385,7 @@ __device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const Phas
 #pragma unroll
     for (int r = 0; r < E; ++r) tile_buf[(j + r * TP) * G + cg] = v[r];
     __syncthreads();
-    for (int e = threadIdx.x; e < N * G; e += BATCH_THREADS)
+    for (int e = threadIdx.x; e < N * G && inb; e += BATCH_THREADS)
         __stcg(&c.psi[(size_t)(e / G) * c.nx + c0 + e % G], tile_buf[e]);
     __syncthreads();                                   // the tile is read out before the next load reuses it
     return true;

@@ -90,6 +90,40 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 __device__ __forceinline__ void latch_status(DevScalars *sc, int code) { atomicCAS(&sc->status, 0, code); }
 
+// ------------------------------------------------------------------ debug bounds checks
+// The bounds-check build (GPE_DEBUG_BOUNDS=1) checks, in every pass kernel,
+// the global row / column index of each thread's accesses and the extent of
+// each CTA's shared-memory regions against their buffers.  A failed check
+// latches GPE_EBOUNDS and the access is skipped (loads give zero, stores are
+// dropped): nothing traps and the context stays usable.  In the normal build
+// every check is true at compile time and costs nothing.
+#ifndef GPE_DEBUG_BOUNDS
+#define GPE_DEBUG_BOUNDS 0
+#endif
+
+// bytes of dynamic shared memory this launch was given
+__device__ __forceinline__ uint32_t dyn_smem_bytes()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+// true if 0 <= i < n; otherwise (bounds-check build) latch GPE_EBOUNDS
+__device__ __forceinline__ bool check_index(long long i, long long n, DevScalars *sc)
+{
+#if GPE_DEBUG_BOUNDS
+    if (i >= 0 && i < n) return true;
+    latch_status(sc, GPE_EBOUNDS);
+    return false;
+#else
+    (void)i;
+    (void)n;
+    (void)sc;
+    return true;
+#endif
+}
+
 // ------------------------------------------------------------------ reductions
 // Sum K per-thread FP32 partials over the CTA in FP64 with a fixed shuffle
 // tree and a fixed warp order; thread 0 writes them to dst[0..K).

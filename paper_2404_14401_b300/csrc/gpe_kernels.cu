@@ -56,17 +56,21 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 
     const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
     const int rpc = blockDim.x / TP;
-    const int y = blockIdx.x * rpc + lr;
-    float2 *row = a.psi + (size_t)y * N;
-    float2 *sb = smem + lr * C::PS;
     const Tables &T = a.T;
+    // this thread's row of the grid, and its pencil's exchange buffer within
+    // the launch's shared memory (checked in the bounds-check build)
+    const bool inb = check_index((long long)blockIdx.x * rpc + lr, a.ny, T.sc) &&
+                     check_index((long long)C::TWN * 16 + (long long)(lr + 1) * C::PS * 8 - 1, dyn_smem_bytes(), T.sc);
+    const int y = inb ? blockIdx.x * rpc + lr : 0;
+    float2 *row = a.psi + (size_t)y * N;
+    float2 *sb = smem + (inb ? lr : 0) * C::PS;
     constexpr bool FFT = (MODE == ROW_PT || MODE == ROW_FFT_F || MODE == ROW_FFT_I || MODE == ROW_OBS ||
                           MODE == ROW_ADJ);
     __shared__ __align__(8) uint64_t twbar;
     if constexpr (FFT && C::TWN > 0) {
         if (threadIdx.x == 0) mbar_init(&twbar, 1);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && check_index((long long)C::TWN * 16 - 1, dyn_smem_bytes(), T.sc)) {
             mbar_expect_tx(&twbar, twiddle_bytes<N>());
             stage_twiddles_async<N>(stw, T.twx, &twbar);
         }
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 
     float2 v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = __ldcs(&row[j + r * TP]);    // streamed: keep the tables in L1
+    for (int r = 0; r < E; ++r) v[r] = inb ? __ldcs(&row[j + r * TP]) : make_float2(0.f, 0.f);   // streamed
     // live: the twiddle table arrived in time.  A CTA whose wait ran out lets
     // the copy land, then runs on without storing anything and adds zero
     // partial sums, so that every reduction still counts all of its CTAs.
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
             live = false;
         }
     }
-
+    const bool keep = live && inb;              // this thread's results may be stored
     if constexpr (MODE == ROW_SCALE) {
         const float c = (float)T.sc->c;
 #pragma unroll
@@ -127,6 +131,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
             q[2] += cx * cx * n;
         }
         q[1] *= yt.z;
+        if (!inb) q[0] = q[1] = q[2] = 0.f;
         block_sum<3>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
         double S[3];
         if (last_block_total<3>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0)
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
             const float kx = (float)(e < N / 2 ? e : e - N);   // in units of 2 pi / Lx
             q[6] += kx * kx * (v[r].x * v[r].x + v[r].y * v[r].y);
         }
-        if (!live)
+        if (!keep)
 #pragma unroll
             for (int i = 0; i < 7; ++i) q[i] = 0.f;
         block_sum<7>(q, T.part_row + (size_t)blockIdx.x * NQ, red);
@@ -203,10 +208,10 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
         fft_pencil<N, E, false>(v, sb, j, 1, stw);
         kinetic_axis<E, TP, true>(v, T.kinx, j, a.sx, 0);
         fft_pencil<N, E, true>(v, sb, j, 1, stw);
-        if (live)
+        if (keep)
 #pragma unroll
             for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
-        float q1[1] = {live ? 2.f * a.ph.h * gq : 0.f};
+        float q1[1] = {keep ? 2.f * a.ph.h * gq : 0.f};
         block_sum<1>(q1, T.part_row + (size_t)blockIdx.x * NQ, red);
         double S[1];
         if (last_block_total<1>(T.part_row, &T.sc->ticket[0], S, red) && threadIdx.x == 0) *a.gout = S[0];
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(N >= 8192 ? 512 : 256) row_kernel(const PassAr
 
     constexpr bool STORE = !(MODE == ROW_REDUCE_R || MODE == ROW_OBS);
     if constexpr (STORE) {
-        if (live)
+        if (keep)
 #pragma unroll
             for (int r = 0; r < E; ++r) __stcs(&row[j + r * TP], v[r]);
     }
@@ -298,7 +303,12 @@ __global__ void __launch_bounds__(RowGroupCfg<N>::THREADS, 1) row_group_kernel(c
         bulk_load_1d(smraw + C::OFF_X, T.xtab, N * 16, &tbar);
         bulk_load_1d(smraw + C::OFF_K, T.kinx, N * 8, &tbar);
     }
-    if (leader && first < nitems) {
+    // an item's rows lie in the grid and its buffers in the launch's shared
+    // memory (bounds-check build; a failed check issues no copy, so the
+    // group's bounded wait runs out and the group stops)
+    const bool bufs_ok = check_index((long long)C::OFF_B + (long long)(g + 1) * 2 * C::BUF * 8 - 1, dyn_smem_bytes(),
+                                     T.sc);
+    if (leader && first < nitems && bufs_ok && check_index((long long)(first + 1) * RG - 1, a.ny, T.sc)) {
         mbar_expect_tx(&full[g][0], C::ITEM_BYTES);
         bulk_load_1d(buf0, a.psi + (size_t)first * RG * N, C::ITEM_BYTES, &full[g][0]);
     }
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(RowGroupCfg<N>::THREADS, 1) row_group_kernel(c
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = buf[lr * N + j + r * TP];
-        if (leader && next < nitems) {
+        if (leader && next < nitems && check_index((long long)(next + 1) * RG - 1, a.ny, T.sc)) {
             bulk_wait_read_all();                    // the store of the other buffer has read it
             mbar_expect_tx(&full[g][b ^ 1], C::ITEM_BYTES);
             bulk_load_1d(buf0 + (b ^ 1) * C::BUF, a.psi + (size_t)next * RG * N, C::ITEM_BYTES, &full[g][b ^ 1]);
@@ -435,8 +445,12 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     float2 *pen = INPLACE ? tile : tile + N * W;
     float4 *stw = reinterpret_cast<float4 *>(tile + (INPLACE ? W * C::PS : N * W + G * C::PS));
 
-    const int c0 = blockIdx.x * W;
     const Tables &T = a.T;
+    // the tile's columns lie in the grid and its buffers in the launch's
+    // shared memory (checked in the bounds-check build; TMA itself clips)
+    const bool inb = check_index((long long)blockIdx.x * W + W - 1, a.nx, T.sc) &&
+                     check_index((long long)((unsigned char *)(stw + C::TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
+    const int c0 = inb ? blockIdx.x * W : 0;
     const float4 *tw = C::TWN ? stw : T.twy;
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -542,7 +556,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
         if constexpr (!INPLACE) __syncthreads();
     }
 
-    if (!ok) q[0] = q[1] = q[2] = 0.f;
+    if (!ok || !inb) q[0] = q[1] = q[2] = 0.f;
     if constexpr (MODE == COL_OBS) {
         float q1[1] = {q[0]};
         block_sum<1>(q1, T.part_col + (size_t)blockIdx.x * NQ, red);
@@ -555,7 +569,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     // make the generic-proxy tile writes visible to the TMA engine, then store
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x == 0 && ok) {
+    if (threadIdx.x == 0 && ok && inb) {
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, tile + (size_t)r0 * W, 2 * c0, r0);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
@@ -613,7 +627,9 @@ __global__ void __launch_bounds__(256, 2) row_stream_kernel(const PassArgs a, in
         mbar_init(&bar[1], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < nitems) {
+    if (threadIdx.x == 0 && (int)blockIdx.x < nitems &&
+        check_index((long long)(blockIdx.x + 1) * RPC - 1, a.ny, T.sc) &&
+        check_index((long long)((unsigned char *)(buf0 + 2 * C::BUF) - smraw) - 1, dyn_smem_bytes(), T.sc)) {
         mbar_expect_tx(&bar[0], BYTES);
         bulk_load_1d(buf0, a.psi + (size_t)blockIdx.x * RPC * N, BYTES, &bar[0]);
     }
@@ -624,7 +640,7 @@ __global__ void __launch_bounds__(256, 2) row_stream_kernel(const PassArgs a, in
         const int b = it & 1;
         float2 *buf = buf0 + b * C::BUF;
         const int next = item + gridDim.x;
-        if (threadIdx.x == 0 && next < nitems) {
+        if (threadIdx.x == 0 && next < nitems && check_index((long long)(next + 1) * RPC - 1, a.ny, T.sc)) {
             bulk_wait_read_all();                     // the other buffer's last store has read it
             mbar_expect_tx(&bar[b ^ 1], BYTES);
             bulk_load_1d(buf0 + (b ^ 1) * C::BUF, a.psi + (size_t)next * RPC * N, BYTES, &bar[b ^ 1]);
@@ -709,7 +725,9 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
         mbar_init(&bar[1], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < nitems) {
+    if (threadIdx.x == 0 && (int)blockIdx.x < nitems &&
+        check_index((long long)(blockIdx.x + 1) * W - 1, a.nx, T.sc) &&
+        check_index((long long)((unsigned char *)(buf0 + 2 * C::BUF) - smraw) - 1, dyn_smem_bytes(), T.sc)) {
         mbar_expect_tx(&bar[0], (uint32_t)(N * W * 8));
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(buf0 + r0 * W, &map, &bar[0], 2 * blockIdx.x * W, r0);
     }
@@ -722,7 +740,7 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
         const int b = it & 1;
         float2 *buf = buf0 + b * C::BUF;
         const int next = item + gridDim.x;
-        if (threadIdx.x == 0 && next < nitems) {
+        if (threadIdx.x == 0 && next < nitems && check_index((long long)(next + 1) * W - 1, a.nx, T.sc)) {
             bulk_wait_read_all();
             float2 *nb = buf0 + (b ^ 1) * C::BUF;
             mbar_expect_tx(&bar[b ^ 1], (uint32_t)(N * W * 8));

@@ -15,7 +15,7 @@ from . import build as _build
 c_int, c_double, c_size_t, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, ctypes.c_size_t,
                                                   ctypes.c_void_p, ctypes.c_char_p)
 
-GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EILLCOND = range(7)
+GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EILLCOND, GPE_EBOUNDS = range(8)
 GPE_REAL, GPE_IMAG = 0, 1
 GPE_CTRL_NONE, GPE_CTRL_LATTICE, GPE_CTRL_ETA = 0, 1, 2
 
@@ -59,7 +59,8 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libgpe.so, or with GPE_LIBRARY=debug the bounds-check build libgpe_debug.so."""
+    return _build.DEBUG_LIB if os.environ.get("GPE_LIBRARY") == "debug" else _build.LIB
 
 
 def load() -> ctypes.CDLL:
@@ -67,9 +68,10 @@ def load() -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        _build.build()
-    L = ctypes.CDLL(_build.LIB)
+    path = lib_path()
+    if not os.path.exists(path):
+        _build.build(debug=path == _build.DEBUG_LIB)
+    L = ctypes.CDLL(path)
     P = ctypes.POINTER
     sig = {
         "gpe_workspace_size": (c_size_t, [c_int, c_int]),

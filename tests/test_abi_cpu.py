@@ -68,3 +68,20 @@ def test_null_context_calls_fail_cleanly():
     assert lib.gpe_step(None, 1, 0.1, 0) == abi.GPE_EINVAL
     assert lib.gpe_sync(None) == abi.GPE_EINVAL
     assert lib.gpe_last_error(None) == b"null context"
+
+
+def test_bounds_check_build_compiles_and_exports_the_same_entry_points():
+    """The debug bounds-check build (-DGPE_DEBUG_BOUNDS=1: kernels check their
+    global indices and shared-memory regions and latch GPE_EBOUNDS instead of
+    making an out-of-bounds access) builds for sm_103a and exports the same
+    C ABI as the normal library."""
+    from paper_2404_14401_b300 import build
+    from paper_2404_14401_b300 import gpe as abi
+    path = build.build(debug=True)
+    assert path == build.DEBUG_LIB and os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    for n in header_functions():
+        assert hasattr(lib, n), n
+    lib.gpe_status_string.restype = ctypes.c_char_p
+    assert lib.gpe_status_string(abi.GPE_EBOUNDS) == b"GPE_EBOUNDS"
+    assert abi.status_string(abi.GPE_EBOUNDS) == "GPE_EBOUNDS"
