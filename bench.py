@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched phase-diagram sweep leg")
     ap.add_argument("--no-grids", action="store_true", help="skip the grid-size leg (1024^2 .. 8192^2)")
     ap.add_argument("--no-single", action="store_true", help="skip the single-trajectory 1024^2 / 2048^2 leg")
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
+                    help="only run `--steps` real-time steps of the lattice workload on one N x N grid (psi built on "
+                         "the device, no relaxation) and exit: a small case for ncu captures of the passes")
+    ap.add_argument("--ncu-sweep", type=int, default=0, metavar="K",
+                    help="only run `--steps` persistent-batch steps of the first K sweep instances of each size and "
+                         "exit: a small case for ncu captures of the batch kernel")
     return ap.parse_args()
 
 
@@ -806,8 +812,47 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def ncu_case(args):
+    """A short, self-contained workload for ncu: no timing, no JSON line."""
+    import numpy as np
+    import torch
+
+    import gpe_inputs as gi
+    from paper_2404_14401_b300 import Batch, Simulation
+    if args.ncu_case:
+        n = args.ncu_case
+        w = gi.lattice_real_time(n=n, L=40.0)
+        p = w["params"]
+        x = (torch.arange(n, device="cuda", dtype=torch.float64) - n // 2) * (p["Lx"] / n)
+        psi = torch.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / (2 * 1.5 ** 2))
+        psi = (psi / torch.sqrt(torch.sum(psi ** 2) * (p["Lx"] / n) ** 2)).to(torch.complex64)
+        s = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"])
+        s.set_potential(p)
+        s.set_psi(psi)
+        s.step(args.steps, w["dt"])
+        status = s.sync()
+    else:
+        ws = gi.phase_diagram_sweep()
+        picks = [w for n in (256, 512, 1024) for w in [v for v in ws if v["params"]["nx"] == n][:args.ncu_sweep]]
+        sims = []
+        for w in picks:
+            p = w["params"]
+            s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+            s.set_potential(p)
+            s.set_psi(torch.from_numpy(w["psi0"]().astype(np.complex64)).cuda())
+            sims.append(s)
+        Batch(sims).step(args.steps, picks[0]["dt"], imag=True)
+        status = max(s.sync() for s in sims)
+    print(json.dumps({"ncu_case": args.ncu_case or f"sweep x{args.ncu_sweep}", "steps": args.steps, "status": status}))
+    if status:
+        sys.exit(1)
+
+
 def main():
     args = parse()
+    if args.ncu_case or args.ncu_sweep:
+        ncu_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
