@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched phase-diagram sweep leg")
     ap.add_argument("--no-grids", action="store_true", help="skip the grid-size leg (1024^2 .. 8192^2)")
     ap.add_argument("--no-single", action="store_true", help="skip the single-trajectory 1024^2 / 2048^2 leg")
-    ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
-                    help="only run `--steps` real-time steps of the lattice workload on one N x N grid (psi built on "
-                         "the device, no relaxation) and exit: a small case for ncu captures of the passes")
+    ap.add_argument("--ncu-case", default="", metavar="NX[xNY]",
+                    help="only run `--steps` real-time steps of the lattice workload on one NX x NY grid (psi built "
+                         "on the device, no relaxation) and exit: a small case for ncu captures of the passes")
     ap.add_argument("--ncu-sweep", type=int, default=0, metavar="K",
                     help="only run `--steps` persistent-batch steps of the first K sweep instances of each size and "
                          "exit: a small case for ncu captures of the batch kernel")
@@ -676,12 +676,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(nrun - 1)]
+    torch.cuda.nvtx.range_push("gpe_timed_steps")      # lets ncu restrict a capture to the timed launches
     e0.record(stream)
     for i in range(nrun):
         Simulation.step_many(sims, cuts[i + 1] - cuts[i], dt)
         if i < nrun - 1:
             ev[i].record(stream)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop() if clocks else None
@@ -820,13 +822,14 @@ def ncu_case(args):
     import gpe_inputs as gi
     from paper_2404_14401_b300 import Batch, Simulation
     if args.ncu_case:
-        n = args.ncu_case
-        w = gi.lattice_real_time(n=n, L=40.0)
-        p = w["params"]
-        x = (torch.arange(n, device="cuda", dtype=torch.float64) - n // 2) * (p["Lx"] / n)
-        psi = torch.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / (2 * 1.5 ** 2))
-        psi = (psi / torch.sqrt(torch.sum(psi ** 2) * (p["Lx"] / n) ** 2)).to(torch.complex64)
-        s = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"])
+        nx, ny = (int(v) for v in (args.ncu_case + "x" + args.ncu_case).split("x")[:2])
+        w = gi.lattice_real_time(n=nx, L=40.0)
+        p = dict(w["params"], nx=nx, ny=ny, Lx=0.02 * nx, Ly=0.02 * ny)
+        x = (torch.arange(nx, device="cuda", dtype=torch.float64) - nx // 2) * (p["Lx"] / nx)
+        y = (torch.arange(ny, device="cuda", dtype=torch.float64) - ny // 2) * (p["Ly"] / ny)
+        psi = torch.exp(-(x[None, :] ** 2 + y[:, None] ** 2) / (2 * 1.5 ** 2))
+        psi = (psi / torch.sqrt(torch.sum(psi ** 2) * (p["Lx"] / nx) * (p["Ly"] / ny))).to(torch.complex64)
+        s = Simulation(nx, ny, p["Lx"], p["Ly"], p["m"], p["g"])
         s.set_potential(p)
         s.set_psi(psi)
         s.step(args.steps, w["dt"])
