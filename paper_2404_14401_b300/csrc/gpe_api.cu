@@ -1367,6 +1367,7 @@ struct gpe_batch {
     size_t ws_bytes;
     int device;
     int tpi;                                  // tiles per item
+    int bt;                                   // threads per CTA and per tile (256 or 64)
     int grid;                                 // CTAs of a launch
     int row_items, col_items;                 // items per row / column pass, all contexts
     std::vector<cudaStream_t> streams;        // distinct context streams other than the first
@@ -1412,24 +1413,38 @@ gpe_status batch_upload(gpe_batch *b)
     std::vector<int> rpre(count + 1, 0), cpre(count + 1, 0);
     std::vector<double> ctrl;
     const double *ctrl_dev = (const double *)(b->ws + L.ctrl);
+    // tile width: 256-thread tiles, unless even the widest pass would leave
+    // most of the launch idle (a single small grid) and every context fits
+    // 64-thread tiles (rows of at most 1024 points, columns of at most 512):
+    // then 4 times as many, smaller tiles spread a pass over more SMs
+    auto tiles = [&](int bt, long long &rt, long long &ct) {
+        rt = ct = 0;
+        for (int i = 0; i < count; ++i) {
+            rt += b->ctxs[i]->ny / batch_rows_per_item(b->ctxs[i]->nx, bt);
+            ct += b->ctxs[i]->nx / batch_rows_per_item(b->ctxs[i]->ny, bt);
+        }
+    };
+    long long rt = 0, ct = 0;
+    tiles(256, rt, ct);
+    bool small_ok = true;
+    for (int i = 0; i < count; ++i) small_ok = small_ok && batch_supported(b->ctxs[i]->nx, b->ctxs[i]->ny, 64);
+    const char *forced = getenv("GPE_BATCH_THREADS");
+    if (forced) b->bt = (atoi(forced) == 64 && small_ok) ? 64 : 256;
+    else b->bt = (small_ok && (rt > ct ? rt : ct) < batch_resident_ctas(256)) ? 64 : 256;
+    if (b->bt == 64) tiles(64, rt, ct);
     // tiles per item: one item per tile unless the passes are much wider than
     // the launch (then up to 8 consecutive tiles per item, so that the
     // per-item dependency check and completion count are paid less often)
-    const int resident = batch_resident_ctas();
+    const int resident = batch_resident_ctas(b->bt);
     if (resident <= 0) return fail(c0, GPE_ECUDA, "gpe_batch: no occupancy for the batch kernel");
-    long long rt = 0, ct = 0;
-    for (int i = 0; i < count; ++i) {
-        rt += b->ctxs[i]->ny / batch_rows_per_item(b->ctxs[i]->nx);
-        ct += b->ctxs[i]->nx / batch_rows_per_item(b->ctxs[i]->ny);
-    }
     long long tpi = (rt < ct ? rt : ct) / (4LL * resident);
     b->tpi = (int)(tpi < 1 ? 1 : tpi > 8 ? 8 : tpi);
     for (int i = 0; i < count; ++i) {
         gpe_ctx *c = b->ctxs[i];
         BatchCtx &e = d[i];
         memset(&e, 0, sizeof(e));
-        e.cpi = batch_rows_per_item(c->ny);
-        e.rpi = batch_rows_per_item(c->nx);
+        e.cpi = batch_rows_per_item(c->ny, b->bt);
+        e.rpi = batch_rows_per_item(c->nx, b->bt);
         TRY(encode_map_w(c, c->psi, e.cpi, &e.map));
         e.psi = c->psi;
         e.T = c->T;
@@ -1513,7 +1528,7 @@ gpe_status gpe_batch_create(gpe_ctx *const *ctxs, int count, void *ws, size_t ws
         if (!ctxs[i]) return GPE_EINVAL;
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return fail(ctxs[i], GPE_EINVAL, "gpe_batch_create: repeated context");
-        if (!batch_supported(ctxs[i]->nx, ctxs[i]->ny))
+        if (!batch_supported(ctxs[i]->nx, ctxs[i]->ny, 256))
             return fail(ctxs[i], GPE_EINVAL, "gpe_batch_create: grid %dx%d not supported in a batch (64..2048 per axis)",
                         ctxs[i]->nx, ctxs[i]->ny);
         if (ctxs[i]->device != ctxs[0]->device)
@@ -1617,6 +1632,7 @@ gpe_status gpe_batch_step(gpe_batch *b, int n, double dt, gpe_mode mode)
         a.cavity = cavity;
         a.spins = c0->spins;
         a.tpi = b->tpi;
+        a.bt = b->bt;
         a.dt = dt;
         a.t0 = c0->t;
         a.total = (unsigned int)batch_queue_length(m, imag, cavity, R, C);

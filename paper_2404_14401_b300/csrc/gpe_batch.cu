@@ -32,8 +32,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <stdlib.h>
-
 #include <atomic>
 
 #include "../../include/gpe.h"
@@ -44,14 +42,18 @@
 namespace gpe {
 
 constexpr int kE = 16;                                        // elements per thread
-constexpr int kBufF2 = BATCH_THREADS * kE + BATCH_THREADS;    // padded pencils of one item (float2)
+// padded pencils of one tile of BT threads (float2)
+template <int BT> __host__ __device__ constexpr int buf_f2() { return BT * kE + BT; }
 
-int batch_rows_per_item(int n) { return n >= 16 ? BATCH_THREADS / (n / kE) : 0; }
+int batch_rows_per_item(int n, int bt) { return n >= 16 && bt >= n / kE ? bt / (n / kE) : 0; }
 
-int batch_supported(int nx, int ny)
+int batch_supported(int nx, int ny, int bt)
 {
     auto ok = [](int n) { return n >= 64 && n <= 2048 && (n & (n - 1)) == 0; };
-    return ok(nx) && ok(ny) && batch_rows_per_item(nx) <= ny && batch_rows_per_item(ny) <= nx;
+    const int rpi = batch_rows_per_item(nx, bt), cpi = batch_rows_per_item(ny, bt);
+    // a row tile holds whole rows; a column tile at least 2 whole columns (a
+    // TMA box row of 16 bytes) and at most the grid's width
+    return ok(nx) && ok(ny) && rpi >= 1 && rpi <= ny && cpi >= 2 && cpi <= nx;
 }
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
@@ -243,11 +245,11 @@ __host__ __device__ inline long long batch_total(int n, int imag, int cavity, in
 // One row tile: RPI whole rows, plain coalesced loads through L2, the pass's
 // pointwise work and T_x in registers and shared memory, stores through L2;
 // the tile's norm / overlap sums are added to q.
-template <int N>
+template <int N, int BT>
 __device__ void row_tile(const BatchCtx &c, int tile, const Item &it, const PhaseArgs &ph, int imag, float2 *buf,
                          float (&q)[3])
 {
-    constexpr int E = kE, TP = N / E, RPI = BATCH_THREADS / TP, PS = N + N / 16;
+    constexpr int E = kE, TP = N / E, RPI = BT / TP, PS = N + N / 16;
     const int lr = threadIdx.x / TP, j = threadIdx.x % TP;
     const Tables &T = c.T;
     const bool inb = check_index((long long)tile * RPI + lr, c.ny, T.sc);   // bounds-check build
@@ -306,13 +308,13 @@ __device__ void row_tile(const BatchCtx &c, int tile, const Item &it, const Phas
 // A row item: tiles k tpi .. min((k + 1) tpi, row_tiles) - 1, then one
 // FP64 partial sum of the item.  The exchange buffers are free again when a
 // tile ends (its last exchange ends with a barrier after the reads).
-template <int N>
+template <int N, int BT>
 __device__ void row_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi, float2 *buf,
                          double *red)
 {
     float q[3] = {0.f, 0.f, 0.f};
     const int t0 = it.k * tpi, t1 = min(t0 + tpi, c.row_tiles);
-    for (int t = t0; t < t1; ++t) row_tile<N>(c, t, it, ph, imag, buf, q);
+    for (int t = t0; t < t1; ++t) row_tile<N, BT>(c, t, it, ph, imag, buf, q);
     if (it.reduce) block_sum<3>(q, c.T.part_row + (size_t)it.k * NQ, red);
 }
 
@@ -320,12 +322,12 @@ __device__ void row_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph,
 // [+ the tile's sums into q], results back into the tile and out with
 // coalesced stores through L2.  False if the tile's bounded wait ran out (the
 // copy has then been given its time to land; nothing is stored).
-template <int N>
+template <int N, int BT>
 __device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const PhaseArgs &ph, int imag, float2 *buf,
                          uint64_t *bar, uint32_t &parity, int spins, float (&q)[3])
 {
-    constexpr int E = kE, TP = N / E, G = BATCH_THREADS / TP, BR = N < 256 ? N : 256, PS = N + N / 16;
-    static_assert(G * PS <= kBufF2, "padded pencils of a tile fit the item buffer");
+    constexpr int E = kE, TP = N / E, G = BT / TP, BR = N < 256 ? N : 256, PS = N + N / 16;
+    static_assert(G >= 2 && G * PS <= buf_f2<BT>(), "a tile is 2 or more columns and fits the item buffer");
     const Tables &T = c.T;
     const bool inb = check_index((long long)tile * G + G - 1, c.nx, T.sc);  // bounds-check build
     const int c0 = inb ? tile * G : 0;
@@ -385,53 +387,65 @@ __device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const Phas
 #pragma unroll
     for (int r = 0; r < E; ++r) tile_buf[(j + r * TP) * G + cg] = v[r];
     __syncthreads();
-    for (int e = threadIdx.x; e < N * G && inb; e += BATCH_THREADS)
+    for (int e = threadIdx.x; e < N * G && inb; e += BT)
         __stcg(&c.psi[(size_t)(e / G) * c.nx + c0 + e % G], tile_buf[e]);
     __syncthreads();                                   // the tile is read out before the next load reuses it
     return true;
 }
 
-template <int N>
+template <int N, int BT>
 __device__ bool col_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi, float2 *buf,
                          double *red, uint64_t *bar, uint32_t &parity, int spins)
 {
     float q[3] = {0.f, 0.f, 0.f};
     const int t0 = it.k * tpi, t1 = min(t0 + tpi, c.col_tiles);
     for (int t = t0; t < t1; ++t)
-        if (!col_tile<N>(c, t, it, ph, imag, buf, bar, parity, spins, q)) return false;
+        if (!col_tile<N, BT>(c, t, it, ph, imag, buf, bar, parity, spins, q)) return false;
     if (it.reduce) block_sum<3>(q, c.T.part_col + (size_t)it.k * NQ, red);
     return true;
 }
 
-template <int N>
+// N: the pencil length of the item's pass (nx for a row pass, ny for a
+// column pass).  The 64-thread variant holds rows of at most 1024 points and
+// columns of at most 512 (a column tile is at least 2 columns); sizes outside
+// a variant are never queued (batch_supported), the branches only keep the
+// instantiations valid.
+template <int N, int BT>
 __device__ bool run_item(const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi, float2 *buf,
                          double *red, uint64_t *bar, uint32_t &parity, int spins)
 {
-    if (it.col) return col_item<N>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
-    row_item<N>(c, it, ph, imag, tpi, buf, red);
+    if (it.col) {
+        if constexpr (BT / (N / kE) >= 2) return col_item<N, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+        else return false;
+    }
+    if constexpr (BT / (N / kE) >= 1) row_item<N, BT>(c, it, ph, imag, tpi, buf, red);
+    else return false;
     return true;
 }
 
+template <int BT>
 __device__ bool dispatch(int n, const BatchCtx &c, const Item &it, const PhaseArgs &ph, int imag, int tpi,
                          float2 *buf, double *red, uint64_t *bar, uint32_t &parity, int spins)
 {
     switch (n) {
-    case 64: return run_item<64>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
-    case 128: return run_item<128>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
-    case 256: return run_item<256>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
-    case 512: return run_item<512>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
-    case 1024: return run_item<1024>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
-    default: return run_item<2048>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 64: return run_item<64, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 128: return run_item<128, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 256: return run_item<256, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 512: return run_item<512, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    case 1024: return run_item<1024, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
+    default: return run_item<2048, BT>(c, it, ph, imag, tpi, buf, red, bar, parity, spins);
     }
 }
 
 // ------------------------------------------------------------------ kernel
-// CPS: CTAs per SM the launch bounds ask for (2: 128 registers, no spill;
-// 3: 80 registers, a few spilled values)
-template <int CPS>
-__global__ void __launch_bounds__(BATCH_THREADS, CPS) batch_kernel(const BatchArgs b)
+// BT: threads per CTA and per tile (256 for batches that fill the GPU with
+// such tiles, 64 for narrow ones); CPS: CTAs per SM the launch bounds ask for
+// (256 threads: 3 per SM at 80 registers; with 2 per SM, 128 registers and no
+// spill, the sweep ran 12% slower)
+template <int BT, int CPS>
+__global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchArgs b)
 {
-    __shared__ __align__(128) float2 buf[kBufF2];
+    __shared__ __align__(128) float2 buf[buf_f2<BT>()];
     __shared__ double red[32 * NQ];
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned int s_idx, s_next;
@@ -488,7 +502,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, CPS) batch_kernel(const BatchAr
         if (!s_flag) break;
         const PhaseArgs ph = s_ph;
         const int n = it.col ? c.ny : c.nx;
-        if (!dispatch(n, c, it, ph, b.imag, b.tpi, buf, red, &bar, parity, b.spins)) {
+        if (!dispatch<BT>(n, c, it, ph, b.imag, b.tpi, buf, red, &bar, parity, b.spins)) {
             if (threadIdx.x == 0) {
                 latch_status(c.T.sc, GPE_ETIMEOUT);
                 atomicExch(&b.head[1], 1u);
@@ -523,7 +537,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, CPS) batch_kernel(const BatchAr
 }
 
 // resident CTAs of one variant on the current device (cached per device)
-template <int CPS> static int batch_grid()
+template <int BT, int CPS> static int batch_grid()
 {
     static std::atomic<int> cache[64];
     int dev = 0;
@@ -533,7 +547,7 @@ template <int CPS> static int batch_grid()
     if (v <= 0) {
         int sms = 0, per = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<CPS>, BATCH_THREADS, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<BT, CPS>, BT, 0) != cudaSuccess)
             return 0;
         v = sms * (per > 0 ? per : 1);
         g.store(v, std::memory_order_relaxed);
@@ -541,23 +555,16 @@ template <int CPS> static int batch_grid()
     return v;
 }
 
-static bool two_per_sm()
-{
-    static const bool two = [] {
-        const char *e = getenv("GPE_BATCH_CTAS");
-        return e && atoi(e) == 2;
-    }();
-    return two;
-}
+constexpr int kSmallCps = 8;                       // 64-thread CTAs per SM (128 registers at most)
 
-int batch_resident_ctas() { return two_per_sm() ? batch_grid<2>() : batch_grid<3>(); }
+int batch_resident_ctas(int bt) { return bt == 64 ? batch_grid<64, kSmallCps>() : batch_grid<256, 3>(); }
 
 cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s, int grid)
 {
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if ((unsigned int)grid > b.total) grid = (int)b.total;
-    if (two_per_sm()) batch_kernel<2><<<grid, BATCH_THREADS, 0, s>>>(b);
-    else batch_kernel<3><<<grid, BATCH_THREADS, 0, s>>>(b);
+    if (b.bt == 64) batch_kernel<64, kSmallCps><<<grid, 64, 0, s>>>(b);
+    else batch_kernel<256, 3><<<grid, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -98,14 +98,14 @@ struct PassArgs {
 };
 
 // ---- Persistent batch (gpe_batch.cu): one launch steps many contexts.
-// Every pass of every context is cut into items of 256 threads' work (a group
-// of whole rows, or a tile of whole columns); the items of all passes of all
+// Every pass of every context is cut into tiles of one CTA's work (256 or 64
+// threads: a group of whole rows, or of whole columns); the items (runs of
+// consecutive tiles) of all passes of all
 // contexts form one queue in lockstep order (pass q of every context before
 // pass q + 1 of any), which the CTAs of one launch take in order from a
 // global counter.  An item of pass q of context i waits until pass q - 1 of
 // context i is complete (a per-context counter), so the queue order makes
 // every wait end: all earlier items are held by running CTAs.
-constexpr int BATCH_THREADS = 256;
 struct BatchCtx {                 // 128-byte aligned by its tensor map
     CUtensorMap map;               // TMA view of psi as float32 [ny][2 nx], box 2 cpi x min(ny, 256)
     float2 *psi;
@@ -113,7 +113,7 @@ struct BatchCtx {                 // 128-byte aligned by its tensor map
     const float *V;
     float V_scale, g, sx, sy;
     int nx, ny;
-    int rpi, row_tiles;            // rows per row tile (256 threads' worth), tiles per row pass
+    int rpi, row_tiles;            // rows per row tile (one CTA's worth), tiles per row pass
     int cpi, col_tiles;            // columns per column tile, tiles per column pass
     int row_items, col_items;      // items (runs of tpi consecutive tiles) per row / column pass
     // potential parameters for the per-pass phase and reduction arguments,
@@ -131,13 +131,14 @@ struct BatchArgs {
     unsigned int *done;            // per context: items of the current pass completed
     int count, n, imag, cavity, spins;
     int tpi;                       // tiles per item (the last item of a pass may have fewer)
+    int bt;                        // threads per CTA and per tile: 256 or 64
     double dt, t0;
     unsigned int total;            // items in the queue
 };
 cudaError_t launch_batch(const BatchArgs &b, cudaStream_t s, int grid);
-int batch_resident_ctas();                // CTAs of the batch kernel that fit the current device at once
-int batch_supported(int nx, int ny);      // 1 if a context of this size can join a batch
-int batch_rows_per_item(int n);           // rows (of n points) in a row item; columns of length n in a column item
+int batch_resident_ctas(int bt);          // CTAs of a batch-kernel variant that fit the current device at once
+int batch_supported(int nx, int ny, int bt);   // 1 if a context of this size can join a batch of bt-thread tiles
+int batch_rows_per_item(int n, int bt);   // rows (of n points) in a row tile; columns of length n in a column tile
 long long batch_queue_length(int n, int imag, int cavity, int row_items, int col_items);
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
