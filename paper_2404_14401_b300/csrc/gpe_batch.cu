@@ -358,19 +358,30 @@ __device__ bool col_tile(const BatchCtx &c, int tile, const Item &it, const Phas
     fft_pencil<N, E, true>(v, sb, j, 1, T.twy);
     const int mode = it.mode, x = c0 + cg;
     if (mode == COL_T_PR) {
+        // closing half phase and its reduction in one loop (one y-table read per point)
         float acx2, acxcy;
         if (ph.use_alpha) alpha_amps(ph, __ldcg(&T.sc->alpha_re), __ldcg(&T.sc->alpha_im), acx2, acxcy);
         else alpha_amps(ph, 0.0, 0.0, acx2, acxcy);
-        const PotCoefs pc = col_coefs_from(ph, acx2, acxcy, __ldg(&T.xtab[x]));
+        const float4 xt = __ldg(&T.xtab[x]);
+        const PotCoefs pc = col_coefs_from(ph, acx2, acxcy, xt);
+        float n0 = 0.f, n1 = 0.f;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int yi = j + r * TP;
-            float V = pot_at(pc, __ldg(&T.ytab[yi]));
+            const float4 yt = __ldg(&T.ytab[yi]);
+            float V = pot_at(pc, yt);
             if (c.V) V += c.V_scale * __ldg(&c.V[(size_t)yi * c.nx + x]);
             v[r] = phase_mul(v[r], V, c.g, ph.h, imag);
+            const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+            n0 += n;
+            n1 += yt.z * n;
         }
-    }
-    if (it.reduce && inb) {
+        if (inb) {
+            q[0] += n0;
+            q[1] += xt.z * n1;
+            q[2] += xt.z * xt.z * n0;
+        }
+    } else if (it.reduce && inb) {
         const float cx = __ldg(&T.xtab[x]).z;
         float n0 = 0.f, n1 = 0.f;
 #pragma unroll

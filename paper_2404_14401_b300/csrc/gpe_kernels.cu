@@ -519,18 +519,27 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
         }
 
         if constexpr (MODE == COL_T_PR) {
+            // closing half phase and the reduction of its result in one loop:
+            // each y-table entry is read once (through L1, which the large
+            // shared-memory carve-out of this pass leaves small)
             const float4 xt = __ldg(&T.xtab[c0 + c]);
             const PotCoefs pc = col_coefs(a, xt);
+            float n0 = 0.f, n1 = 0.f;
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const int yi = j + r * TP;
-                float V = pot_at(pc, __ldg(&T.ytab[yi]));
+                const float4 yt = __ldg(&T.ytab[yi]);
+                float V = pot_at(pc, yt);
                 if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
                 v[r] = phase_mul(v[r], V, a.g, a.ph.h, a.imag);
+                const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+                n0 += n;
+                n1 += yt.z * n;
             }
-        }
-
-        if constexpr (REDUCE) {
+            q[0] += n0;
+            q[1] += xt.z * n1;
+            q[2] += xt.z * xt.z * n0;
+        } else if constexpr (REDUCE) {
             const float cx = __ldg(&T.xtab[c0 + c]).z;
             float n0 = 0.f, n1 = 0.f;
 #pragma unroll
@@ -772,16 +781,25 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
         kinetic_axis<E, TP>(v, T.kiny, j, a.sy, a.imag);
         fft_pencil<N, E, true>(v, sb, j, 1, tw);
         if constexpr (MODE == COL_T_PR) {
-            const PotCoefs pc = col_coefs(a, __ldg(&T.xtab[c0 + c]));
+            // closing half phase and its reduction in one loop (one y-table read per point)
+            const float4 xt = __ldg(&T.xtab[c0 + c]);
+            const PotCoefs pc = col_coefs(a, xt);
+            float n0 = 0.f, n1 = 0.f;
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const int yi = j + r * TP;
-                float V = pot_at(pc, __ldg(&T.ytab[yi]));
+                const float4 yt = __ldg(&T.ytab[yi]);
+                float V = pot_at(pc, yt);
                 if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
                 v[r] = phase_mul(v[r], V, a.g, a.ph.h, a.imag);
+                const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+                n0 += n;
+                n1 += yt.z * n;
             }
-        }
-        if constexpr (REDUCE) {
+            q[0] += n0;
+            q[1] += xt.z * n1;
+            q[2] += xt.z * xt.z * n0;
+        } else if constexpr (REDUCE) {
             const float cx = __ldg(&T.xtab[c0 + c]).z;
             float n0 = 0.f, n1 = 0.f;
 #pragma unroll
