@@ -486,6 +486,11 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchArgs b)
         // min(spins, 2^22) polls of about 64 ns plus an L2 round trip each;
         // a pass of the largest batches takes milliseconds)
         if (threadIdx.x == 0) {
+            // the pass's arguments do not depend on the previous pass: work
+            // them out while it may still be running
+            if (it.h != 0.0) s_ph = phase_dev(c, it.tp, it.h);
+            else memset(&s_ph, 0, sizeof(s_ph));
+            s_rd = red_dev(c, it.tr);
             int ok = 1, polls = 0;
             unsigned int ns = 32;                      // back off: many CTAs may wait on one counter
             const int limit = b.spins < (1 << 22) ? b.spins : (1 << 22);
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchArgs b)
                     break;
                 }
                 __nanosleep(ns);
-                if (ns < 1024) ns *= 2;
+                if (ns < 256) ns *= 2;
             }
             if (!ok) {
                 latch_status(c.T.sc, GPE_ETIMEOUT);
@@ -503,11 +508,6 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchArgs b)
             }
             __threadfence();
             s_flag = ok;
-            if (ok) {
-                if (it.h != 0.0) s_ph = phase_dev(c, it.tp, it.h);
-                else memset(&s_ph, 0, sizeof(s_ph));
-                s_rd = red_dev(c, it.tr);
-            }
         }
         __syncthreads();
         if (!s_flag) break;

@@ -420,6 +420,17 @@ __host__ __device__ constexpr int col_g(int n)
     return g > col_w(n) ? col_w(n) : g;
 }
 
+// Twiddle entries a column pass of mode MODE stages in shared memory.  The
+// modes that also read the y-table at every point (the reductions, the
+// closing phase, the adjoint phase) read the twiddles through L1 instead:
+// three CTAs that each staged a 2048-point table (32.6 KB) left L1 about
+// 22 KB, too little for the y-table (32 KB) beside the kinetic factors, and
+// the closing-phase pass then ran at 62% L1 hits against 98% for T_y alone.
+template <int N, int MODE> __host__ __device__ constexpr int col_twn()
+{
+    return (MODE == COL_T_R || MODE == COL_T_PR || MODE == COL_ADJ) ? 0 : ColCfg<N>::TWN;
+}
+
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
 {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
@@ -437,7 +448,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     col_kernel(const PassArgs a, const __grid_constant__ CUtensorMap map)
 {
     using C = ColCfg<N>;
-    constexpr int E = C::E, TP = C::TP, W = col_w(N), G = col_g(N);
+    constexpr int E = C::E, TP = C::TP, W = col_w(N), G = col_g(N), TWN = col_twn<N, MODE>();
     constexpr bool INPLACE = (G == W);   // exchange buffers may overlay the dense tile
     extern __shared__ unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -452,16 +463,16 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
     // the tile's columns lie in the grid and its buffers in the launch's
     // shared memory (checked in the bounds-check build; TMA itself clips)
     const bool inb = check_index((long long)blockIdx.x * W + W - 1, a.nx, T.sc) &&
-                     check_index((long long)((unsigned char *)(stw + C::TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
+                     check_index((long long)((unsigned char *)(stw + TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
     const int c0 = inb ? blockIdx.x * W : 0;
-    const float4 *tw = C::TWN ? stw : T.twy;
+    const float4 *tw = TWN ? stw : T.twy;
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         // one arrival per phase: the tile and the twiddle table share it
-        mbar_expect_tx(&bar, (uint32_t)(N * W * 8) + (C::TWN > 0 ? twiddle_bytes<N>() : 0u));
-        if constexpr (C::TWN > 0) stage_twiddles_async<N>(stw, T.twy, &bar);
+        mbar_expect_tx(&bar, (uint32_t)(N * W * 8) + (TWN > 0 ? twiddle_bytes<N>() : 0u));
+        if constexpr (TWN > 0) stage_twiddles_async<N>(stw, T.twy, &bar);
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + (size_t)r0 * W, &map, &bar, 2 * c0, r0);
     }
     // ok: the tile (and twiddles) arrived in time.  Otherwise the copies are
@@ -1123,7 +1134,7 @@ static cudaError_t col_launch(const PassArgs &a, const CUtensorMap &map, cudaStr
     using C = ColCfg<N>;
     constexpr int W = col_w(N), G = col_g(N);
     constexpr size_t smem = (G == W ? (size_t)W * C::PS : (size_t)N * W + (size_t)G * C::PS) * sizeof(float2) +
-                            (size_t)C::TWN * sizeof(float4) + 128;
+                            (size_t)col_twn<N, MODE>() * sizeof(float4) + 128;
     if constexpr (smem > 48 * 1024) {
         static std::atomic<unsigned long long> attr{0};
         const cudaError_t e = smem_opt_in(col_kernel<N, MODE>, (int)smem, attr);
