@@ -298,10 +298,12 @@ gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax,
  * of 512..2048-point rows has a grouped persistent variant (one CTA per SM,
  * tables in shared memory, TMA double buffering), rows and columns of 4096
  * points a streaming persistent variant; every grid has the one-shot
- * variant (a CTA per group of rows or per TMA tile of columns).  A context
- * starts with the streaming variants on where they apply, the grouped row
- * pass on for 2048-point rows only, and the half row tile (below) for 512-
- * and 1024-point rows: with those the passes of other grids overlapped best
+ * variant (a CTA per group of rows or per TMA tile of columns), and the
+ * column passes of 512..2048-point columns a pencil-pair form (bit 5).  A
+ * context starts with the streaming variants on where they apply, the
+ * grouped row pass on for 2048-point rows only, the half row tile (below)
+ * for 512- and 1024-point rows and the pencil-pair column passes for
+ * 2048-point columns: with those the passes of other grids overlapped best
  * under gpe_step_many.  The bits select them: */
 enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
 /* Bits 3-4 (value << GPE_VARIANT_ROW_TILE_SHIFT, value 0..2): on rows of
@@ -310,8 +312,15 @@ enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STRE
  * threads' worth, at least one warp), so that a small grid spreads over more
  * SMs; shorter rows ignore it. */
 enum { GPE_VARIANT_ROW_TILE_SHIFT = 3 };
+/* Bit 5: the column passes (T_y [+ closing phase] [+ reductions]) of
+ * 512..2048-point columns as pencil pairs: both columns of a 2-column tile
+ * in one packed f32x2 transform, each table entry read once for both (equal
+ * to the one-pencil passes to FP32 rounding).  On by default for 2048-point
+ * columns, where it measured faster. */
+enum { GPE_VARIANT_PAIR_COLS = 32 };
 int gpe_get_pass_variants(const gpe_ctx *ctx);                /* -1 for a null context */
-gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants); /* GPE_EINVAL outside 0..23 */
+/* GPE_EINVAL for bits other than those above or a row-tile value above 2 */
+gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants);
 /* Autotuner: times every applicable variant of the interior row pass
  * (potential phase + T_x; the one-shot pass at row-tile values 0 and 1, the
  * half tile kept unless at least 3% slower; a persistent variant replaces
@@ -322,7 +331,9 @@ gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants); /* GPE_EINVAL outs
  * stream, and selects the fastest row and column variants for this context.
  * variants_out receives the bits; times_out (5 doubles or NULL) the mean
  * milliseconds of the row pass one-shot (its kept tile) / grouped /
- * streaming and the column pass one-shot / streaming, NaN where a variant
+ * streaming and the column pass one-shot (the faster of the one-pencil and
+ * pencil-pair forms; the pair bit is set when it is the pair) / streaming,
+ * NaN where a variant
  * does not apply.  Synchronises the stream.  Errors:
  * GPE_EINVAL, GPE_ECUDA. */
 gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, size_t scratch_bytes, int reps,

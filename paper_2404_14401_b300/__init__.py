@@ -125,7 +125,7 @@ class Simulation:
         v, t = abi.gpe_tune(self.ctx, dt, abi.GPE_IMAG if imag else abi.GPE_REAL, scratch.data_ptr(),
                             scratch.numel(), reps)
         keys = ("row_one_shot", "row_grouped", "row_streaming", "col_one_shot", "col_streaming")
-        return {"variants": v, "row_tile": v >> abi.GPE_VARIANT_ROW_TILE_SHIFT,
+        return {"variants": v, "row_tile": (v >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3,
                 "ms": {k: (None if x != x else x) for k, x in zip(keys, t)}}
 
     @property

@@ -12,8 +12,9 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = [os.path.join(HERE, "csrc", f) for f in ("gpe_api.cu", "gpe_kernels.cu", "gpe_batch.cu", "gpe_static.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("gpe_fft.cuh", "gpe_device.cuh", "gpe_internal.h")] + [
+SRC = [os.path.join(HERE, "csrc", f) for f in ("gpe_api.cu", "gpe_kernels.cu", "gpe_batch.cu", "gpe_static.cu",
+                                                       "gpe_pair.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("gpe_fft.cuh", "gpe_fft2.cuh", "gpe_device.cuh", "gpe_internal.h")] + [
     os.path.join(os.path.dirname(HERE), "include", "gpe.h")]
 LIB = os.path.join(HERE, "libgpe.so")
 DEBUG_LIB = os.path.join(HERE, "libgpe_debug.so")  # -DGPE_DEBUG_BOUNDS=1: index checks that latch GPE_EBOUNDS

@@ -59,6 +59,7 @@ struct gpe_ctx {
     int stream_passes;       // use the persistent streaming row pass where it applies
     int stream_cols;         // use the persistent streaming column pass where it applies
     int group_rows;          // use the grouped persistent row pass where it applies
+    int pair_cols;           // use the pencil-pair column pass (T_y) where it applies
     int row_tile_shift;      // one-shot row pass: 2^-shift of the default rows per CTA (0..2)
     long long launches;
     unsigned long long uid;          // unique over the process (never reused, unlike the pointer)
@@ -349,6 +350,8 @@ gpe_status run_col(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd,
     const PassArgs a = pass_args(c, ph, rd, imag, 0);
     if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR) && c->stream_cols && col_stream_ok(c->nx, c->ny))
         return timed_launch(c, 1, [&] { return launch_col_stream(mode, a, c->map, c->stream); }, "column pass");
+    if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR) && c->pair_cols && col_pair_ok(c->nx, c->ny))
+        return timed_launch(c, 1, [&] { return launch_col_pair(mode, a, c->map, c->stream); }, "column pass");
     return timed_launch(c, 1, [&] { return launch_col(mode, a, c->map, c->stream); }, "column pass");
 }
 
@@ -409,7 +412,9 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->kin_valid = false;
     c->spins = 1 << 24;
     c->stream_passes = getenv("GPE_NO_STREAM_PASSES") ? 0 : 1;
-    c->stream_cols = c->stream_passes;
+    // the streaming column pass by default where it measured faster (4096);
+    // at 2048 the autotuner may choose it
+    c->stream_cols = c->stream_passes && ny == 4096;
     // the grouped row pass by default only for 2048-point rows: at 1024 (and
     // below) the one-shot pass, whose CTAs share SMs with other passes,
     // measured faster under gpe_step_many (1024^2 x 8: 71.8 against 64.2 G
@@ -420,6 +425,11 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // 512^2 at 56.0 against 53.8; at 2048 the half tile was slower (65.7
     // against 71.7) and at 256 the same
     c->row_tile_shift = (nx == 512 || nx == 1024) ? 1 : 0;
+    // the pencil-pair column passes by default for 2048-point columns (8 x
+    // 2048^2 under gpe_step_many: 69.7 against 67.6 G pt*steps/s; the T_y
+    // pass alone 33.7 against 36.0 us); at 512 and 1024 both forms timed
+    // alike
+    c->pair_cols = (ny == 2048 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
     c->launches = 0;
     {
         static std::atomic<unsigned long long> next_uid{1};
@@ -1209,16 +1219,20 @@ int gpe_get_pass_variants(const gpe_ctx *c)
 {
     if (!c) return -1;
     return (c->group_rows ? GPE_VARIANT_GROUP_ROWS : 0) | (c->stream_passes ? GPE_VARIANT_STREAM_ROWS : 0) |
-           (c->stream_cols ? GPE_VARIANT_STREAM_COLS : 0) | (c->row_tile_shift << GPE_VARIANT_ROW_TILE_SHIFT);
+           (c->stream_cols ? GPE_VARIANT_STREAM_COLS : 0) | (c->row_tile_shift << GPE_VARIANT_ROW_TILE_SHIFT) |
+           (c->pair_cols ? GPE_VARIANT_PAIR_COLS : 0);
 }
 
 gpe_status gpe_set_pass_variants(gpe_ctx *c, int v)
 {
-    if (!c || v < 0 || v >= (3 << GPE_VARIANT_ROW_TILE_SHIFT)) return GPE_EINVAL;
+    const int known = GPE_VARIANT_GROUP_ROWS | GPE_VARIANT_STREAM_ROWS | GPE_VARIANT_STREAM_COLS |
+                      (3 << GPE_VARIANT_ROW_TILE_SHIFT) | GPE_VARIANT_PAIR_COLS;
+    if (!c || v < 0 || (v & ~known) || ((v >> GPE_VARIANT_ROW_TILE_SHIFT) & 3) > 2) return GPE_EINVAL;
     c->group_rows = (v & GPE_VARIANT_GROUP_ROWS) != 0;
+    c->pair_cols = (v & GPE_VARIANT_PAIR_COLS) != 0;
     c->stream_passes = (v & GPE_VARIANT_STREAM_ROWS) != 0;
     c->stream_cols = (v & GPE_VARIANT_STREAM_COLS) != 0;
-    c->row_tile_shift = v >> GPE_VARIANT_ROW_TILE_SHIFT;
+    c->row_tile_shift = (v >> GPE_VARIANT_ROW_TILE_SHIFT) & 3;
     c->version++;
     return GPE_OK;
 }
@@ -1278,6 +1292,9 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
     if (st == GPE_OK && row_stream_ok(c->nx, c->ny))
         st = time_it([&] { return launch_row_stream(a, c->stream); }, &t[2]);
     if (st == GPE_OK) st = time_it([&] { return launch_col(COL_T, a, wmap, c->stream); }, &t[3]);
+    double t_pair = NAN;
+    if (st == GPE_OK && col_pair_ok(c->nx, c->ny))
+        st = time_it([&] { return launch_col_pair(COL_T, a, wmap, c->stream); }, &t_pair);
     if (st == GPE_OK && col_stream_ok(c->nx, c->ny))
         st = time_it([&] { return launch_col_stream(COL_T, a, wmap, c->stream); }, &t[4]);
     c->ev_free.push_back(e0);
@@ -1292,7 +1309,11 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
         if (t[k] == t[k] && t[k] < 0.97 * t[best]) best = k;
     int v = best == 1 ? GPE_VARIANT_GROUP_ROWS : best == 2 ? GPE_VARIANT_STREAM_ROWS : 0;
     if (best == 0) v |= shift << GPE_VARIANT_ROW_TILE_SHIFT;
+    // the one-shot column pass: the faster of the one-pencil and pair forms
+    const bool pair = t_pair == t_pair && t_pair < t[3];
+    if (pair) t[3] = t_pair;
     if (t[4] == t[4] && t[4] < t[3]) v |= GPE_VARIANT_STREAM_COLS;
+    else if (pair) v |= GPE_VARIANT_PAIR_COLS;
     TRY(gpe_set_pass_variants(c, v));
     *variants_out = v;
     if (times_out)

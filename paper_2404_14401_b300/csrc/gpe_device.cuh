@@ -11,6 +11,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/gpe.h"
 #include "gpe_fft.cuh"
 #include "gpe_internal.h"
@@ -69,6 +71,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
 }
 
 __device__ __forceinline__ void bulk_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
@@ -422,6 +432,36 @@ __device__ __forceinline__ void stage_twiddles_async(float4 *__restrict__ dst, c
                                                      uint64_t *bar)
 {
     bulk_load_1d(dst, src, twiddle_bytes<N>(), bar);
+}
+
+// Opt func in to `bytes` of dynamic shared memory once per device (function
+// attributes belong to the device's context), safe from several host threads.
+template <class F> [[maybe_unused]] static cudaError_t smem_opt_in(F *func, int bytes,
+                                                                   std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+// SM count of the current device (cached per device; 148 if it cannot be read)
+[[maybe_unused]] static int sm_count()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    std::atomic<int> &c = cache[dev & 63];
+    int n = c.load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        c.store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 }  // namespace gpe

@@ -157,6 +157,10 @@ bool row_stream_ok(int nx, int ny);
 bool row_group_ok(int nx, int ny);
 cudaError_t launch_row_group(const PassArgs &a, cudaStream_t s);
 bool col_stream_ok(int nx, int ny);
+// pencil-pair column pass (gpe_pair.cu): COL_T, COL_T_R, COL_T_PR on 2-column
+// tiles of 512..2048-point columns
+bool col_pair_ok(int nx, int ny);
+cudaError_t launch_col_pair(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
 cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m,
                           double wx, double wy, double lkx, double lky, double kc, cudaStream_t s);
 cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly,

@@ -420,23 +420,15 @@ __host__ __device__ constexpr int col_g(int n)
     return g > col_w(n) ? col_w(n) : g;
 }
 
-// Twiddle entries a column pass of mode MODE stages in shared memory.  The
-// modes that also read the y-table at every point (the reductions, the
-// closing phase, the adjoint phase) read the twiddles through L1 instead:
-// three CTAs that each staged a 2048-point table (32.6 KB) left L1 about
-// 22 KB, too little for the y-table (32 KB) beside the kinetic factors, and
-// the closing-phase pass then ran at 62% L1 hits against 98% for T_y alone.
+// Twiddle entries a column pass of mode MODE stages in shared memory: the
+// whole table in every mode.  Reading it through L1 instead in the modes
+// that also read the y-table at every point (so that L1 keeps room for the
+// y-table) measured slower at 2048^2: closing phase + norm 76.7 against 67.0
+// us, cavity overlaps 61.8 against 55.8 us.
 template <int N, int MODE> __host__ __device__ constexpr int col_twn()
 {
-    return (MODE == COL_T_R || MODE == COL_T_PR || MODE == COL_ADJ) ? 0 : ColCfg<N>::TWN;
-}
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
-{
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(smem_u32(src)), "r"(x), "r"(y)
-                 : "memory");
+    (void)MODE;
+    return ColCfg<N>::TWN;
 }
 
 // Column pass over a tile of W columns: TMA load of the dense [N][W] tile,
@@ -531,8 +523,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
 
         if constexpr (MODE == COL_T_PR) {
             // closing half phase and the reduction of its result in one loop:
-            // each y-table entry is read once (through L1, which the large
-            // shared-memory carve-out of this pass leaves small)
+            // each y-table entry is read once
             const float4 xt = __ldg(&T.xtab[c0 + c]);
             const PotCoefs pc = col_coefs(a, xt);
             float n0 = 0.f, n1 = 0.f;
@@ -1011,20 +1002,6 @@ __global__ void timeout_probe_kernel(DevScalars *sc, int spins)
 #endif  // GPE_IN_PART(0)
 
 // ------------------------------------------------------------------ launchers
-// Opt func in to `bytes` of dynamic shared memory once per device (function
-// attributes belong to the device's context), safe from several host threads.
-template <class F> [[maybe_unused]] static cudaError_t smem_opt_in(F *func, int bytes,
-                                                                   std::atomic<unsigned long long> &done)
-{
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
-    return e;
-}
 
 #if GPE_IN_PART(0)
 // Rows per CTA of the one-shot row pass: 256 threads' worth, divided by
@@ -1053,7 +1030,10 @@ bool row_group_ok(int nx, int ny) { return (nx == 512 || nx == 1024 || nx == 204
 // Streaming row pass for ROW_PT when the grid has enough rows; false = not applicable.
 bool row_stream_ok(int nx, int ny) { return nx == 4096 && ny >= 8; }
 
-bool col_stream_ok(int nx, int ny) { return ny == 4096 && nx >= 8 * col_w(ny); }
+// Streaming column pass: 4096-point columns (the default there) and 2048 (a
+// variant the autotuner may pick: the twiddles staged once per CTA instead
+// of once per 2-column tile, at 2 CTAs per SM instead of 3)
+bool col_stream_ok(int nx, int ny) { return (ny == 2048 || ny == 4096) && nx >= 8 * col_w(ny); }
 
 cudaError_t launch_row(int mode, const PassArgs &a, cudaStream_t s, int tile_shift)
 {
@@ -1188,20 +1168,6 @@ cudaError_t launch_col_hi(int mode, const PassArgs &a, const CUtensorMap &map, c
 }
 #endif
 
-// SM count of the current device (cached per device; 148 if it cannot be read)
-[[maybe_unused]] static int sm_count()
-{
-    static std::atomic<int> cache[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-    std::atomic<int> &c = cache[dev & 63];
-    int n = c.load(std::memory_order_relaxed);
-    if (n <= 0) {
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-        c.store(n, std::memory_order_relaxed);
-    }
-    return n;
-}
 
 #if GPE_IN_PART(2)
 template <int N> static cudaError_t row_group_launch(const PassArgs &a, cudaStream_t s)
@@ -1282,6 +1248,7 @@ template <int N> static cudaError_t col_stream_mode(int mode, const PassArgs &a,
 cudaError_t launch_col_stream(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
     switch (a.ny) {
+    case 2048: return col_stream_mode<2048>(mode, a, map, s);
     case 4096: return col_stream_mode<4096>(mode, a, map, s);
     default: return cudaErrorInvalidValue;
     }

@@ -1,0 +1,255 @@
+// gpe_pair.cu -- pencil-pair variant of the column pass (sm_103a).
+//
+// The column pass of Sec. 3.1's split step (T_y = F_y^-1 K_y F_y on every
+// column, Eq. 3, optionally followed by the closing half phase and the FP64
+// reductions of Eqs. 14-15) on a TMA tile of two columns, transformed as one
+// pencil pair by the packed f32x2 FFT of gpe_fft2.cuh: each thread holds the
+// same 16 elements of both columns, so every add and multiply of the
+// transform, the kinetic factor and the phase is one f32x2 instruction for
+// the two columns, and each twiddle, kinetic-factor and y-table entry is
+// loaded once for both.  Against the one-pencil pass (gpe_kernels.cu) that
+// halves the twiddle reads from shared memory and the table reads through
+// L1, and removes the stride-2 dense tile accesses; the CTA has half the
+// threads (N/16 for a 2-column tile), each with twice the registers.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/gpe.h"
+#include "gpe_device.cuh"
+#include "gpe_fft2.cuh"
+#include "gpe_internal.h"
+
+namespace gpe {
+
+template <int N> struct ColPairCfg {
+    static constexpr int E = 16, TP = N / E;       // threads per 2-column tile
+    static constexpr int BR = N < 256 ? N : 256;   // rows per TMA box (the context's tensor map)
+    static constexpr int SLOTS = pad8_len(N);      // 16-byte exchange slots, overlaying the dense tile
+    static constexpr int TWN = fft_tw_count(N);    // twiddles staged in shared memory
+    static constexpr uint32_t TW_BYTES = (uint32_t)TWN * 16u;
+    static constexpr size_t SMEM = (size_t)SLOTS * 16 + TW_BYTES + 128;
+    // CTAs per SM the registers are sized for: as many as the shared memory
+    // holds (3 at 2048), at most 16
+    static constexpr int BY_SMEM = (int)((224u * 1024u) / (SMEM + 1024));
+    static constexpr int MIN_CTAS = BY_SMEM < 16 ? BY_SMEM : 16;
+};
+
+// V at the same y of two columns (coefficients pa, pb; y-table entry t), in
+// the order of pot_at
+__device__ __forceinline__ float2 pot_at2(const PotCoefs &pa, const PotCoefs &pb, float4 t)
+{
+    const float2 f = add2(make_float2(pa.F, pb.F), bc2(t.x));
+    const float2 u = fma2(bc2(pa.A), bc2(t.y), f);
+    const float2 w = fma2(bc2(pa.B), bc2(t.z), make_float2(pa.C, pb.C));
+    return fma2(w, bc2(t.z), u);
+}
+
+// phase_mul on a packed pair of points: exp(-i theta) (real time, the 1 + d
+// form with the Taylor series of sin and cos of theta/2 for |theta| <= 1) or
+// exp(-theta) (imaginary time), theta = (V + g |psi|^2) h
+__device__ __forceinline__ void phase_mul2(float2 &x, float2 &y, float2 V, float g, float h, int imag)
+{
+    const float2 n = fma2(x, x, mul2(y, y));
+    const float2 th = mul2(fma2(bc2(g), n, V), bc2(h));
+    if (imag) {
+        const float2 f = make_float2(expf(-th.x), expf(-th.y));
+        x = mul2(x, f);
+        y = mul2(y, f);
+        return;
+    }
+    if (!(fabsf(th.x) <= 1.f && fabsf(th.y) <= 1.f)) {
+        // lane by lane, as phase_mul does for one point
+        const float2 r0 = phase_mul(make_float2(x.x, y.x), V.x, g, h, 0);
+        const float2 r1 = phase_mul(make_float2(x.y, y.y), V.y, g, h, 0);
+        x = make_float2(r0.x, r1.x);
+        y = make_float2(r0.y, r1.y);
+        return;
+    }
+    const float2 w = mul2(bc2(0.5f), th);
+    const float2 v = mul2(w, w);
+    float2 ps = fma2(v, bc2(1.f / 362880.f), bc2(-1.f / 5040.f));
+    ps = fma2(v, ps, bc2(1.f / 120.f));
+    ps = fma2(v, ps, bc2(-1.f / 6.f));
+    const float2 s = fma2(mul2(w, v), ps, w);
+    float2 pc = fma2(v, bc2(1.f / 40320.f), bc2(-1.f / 720.f));
+    pc = fma2(v, pc, bc2(1.f / 24.f));
+    pc = fma2(v, pc, bc2(-0.5f));
+    const float2 c = fma2(v, pc, bc2(1.f));
+    const float2 m2s = mul2(bc2(-2.f), s);
+    const float2 dr = mul2(m2s, s), di = mul2(m2s, c);
+    const float2 nx = add2(x, fma2(x, dr, mul2(y, make_float2(-di.x, -di.y))));
+    y = add2(y, fma2(x, di, mul2(y, dr)));
+    x = nx;
+}
+
+// T_y's kinetic factor on the pair: real time (p + p d) / N with the 1 + D
+// form of the table, imaginary time p e^{-k^2 dt/2m} / N
+template <int E, int TP>
+__device__ __forceinline__ void kinetic_pair(float2 (&X)[E], float2 (&Y)[E], const float2 *__restrict__ D, int j,
+                                             float s, int imag)
+{
+    if (imag) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 f = bc2(__ldg(&D[j + r * TP]).x * s);
+            X[r] = mul2(X[r], f);
+            Y[r] = mul2(Y[r], f);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 d = __ldg(&D[j + r * TP]);
+            const float2 pdx = fma2(X[r], bc2(d.x), mul2(Y[r], bc2(-d.y)));
+            const float2 pdy = fma2(X[r], bc2(d.y), mul2(Y[r], bc2(d.x)));
+            X[r] = mul2(add2(X[r], pdx), bc2(s));
+            Y[r] = mul2(add2(Y[r], pdy), bc2(s));
+        }
+    }
+}
+
+// Column pass over a 2-column tile as one pencil pair.  MODE: COL_T (T_y),
+// COL_T_R (T_y, then the norm and cavity overlaps of the result reduced in
+// FP64, Eqs. 14-15), COL_T_PR (T_y, the closing half phase, the reductions).
+template <int N, int MODE>
+__global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
+    col_pair_kernel(const PassArgs a, const __grid_constant__ CUtensorMap map)
+{
+    using C = ColPairCfg<N>;
+    constexpr int E = C::E, TP = C::TP;
+    constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double red[32 * NQ];
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *tile = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));   // [N] {A, B} rows
+    float4 *stw = tile + C::SLOTS;
+    const Tables &T = a.T;
+    const bool inb = check_index((long long)blockIdx.x * 2 + 1, a.nx, T.sc) &&
+                     check_index((long long)((unsigned char *)(stw + C::TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
+    const int c0 = inb ? blockIdx.x * 2 : 0;
+
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, (uint32_t)N * 16u + C::TW_BYTES);
+        bulk_load_1d(stw, T.twy, C::TW_BYTES, &bar);
+        for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + r0, &map, &bar, 2 * c0, r0);
+    }
+    // the tile and the twiddles arrived in time.  Otherwise the copies are
+    // given time to land, the CTA stores nothing and adds zero partial sums,
+    // so that every reduction still counts all of its CTAs.
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins));
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            latch_status(T.sc, GPE_ETIMEOUT);
+            mbar_drain(&bar, 0);
+        }
+        if constexpr (!REDUCE) return;
+    }
+
+    const int j = threadIdx.x;
+    float2 X[E], Y[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const float4 t = tile[j + r * TP];          // {re_A, im_A, re_B, im_B}
+        X[r] = make_float2(t.x, t.z);
+        Y[r] = make_float2(t.y, t.w);
+    }
+    __syncthreads();                                // dense reads done before the exchange writes
+
+    fft_pair<N, E, false>(X, Y, tile, j, stw);
+    kinetic_pair<E, TP>(X, Y, T.kiny, j, a.sy, a.imag);
+    fft_pair<N, E, true>(X, Y, tile, j, stw);
+
+    float q[3] = {0.f, 0.f, 0.f};
+    if constexpr (REDUCE) {
+        // per column: n0 = sum |psi|^2, n1 = sum cos(kc y) |psi|^2 (after the
+        // closing phase in COL_T_PR; each y-table entry read once for both)
+        const float4 xa = __ldg(&T.xtab[c0]), xb = __ldg(&T.xtab[c0 + 1]);
+        PotCoefs pa{}, pb{};
+        if constexpr (MODE == COL_T_PR) {
+            pa = col_coefs(a, xa);
+            pb = col_coefs(a, xb);
+        }
+        float2 n0 = make_float2(0.f, 0.f), n1 = n0;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int yi = j + r * TP;
+            const float4 yt = __ldg(&T.ytab[yi]);
+            if constexpr (MODE == COL_T_PR) {
+                float2 V = pot_at2(pa, pb, yt);
+                if (a.V) {
+                    const float2 va = make_float2(__ldg(&a.V[(size_t)yi * a.nx + c0]), __ldg(&a.V[(size_t)yi * a.nx + c0 + 1]));
+                    V = fma2(bc2(a.V_scale), va, V);
+                }
+                phase_mul2(X[r], Y[r], V, a.g, a.ph.h, a.imag);
+            }
+            const float2 n = fma2(X[r], X[r], mul2(Y[r], Y[r]));
+            n0 = add2(n0, n);
+            n1 = fma2(bc2(yt.z), n, n1);
+        }
+        q[0] = n0.x + n0.y;
+        q[1] = xa.z * n1.x + xb.z * n1.y;
+        q[2] = xa.z * xa.z * n0.x + xb.z * xb.z * n0.y;
+    }
+
+    // every exchange read finished at the last stage's barrier
+#pragma unroll
+    for (int r = 0; r < E; ++r) tile[j + r * TP] = make_float4(X[r].x, Y[r].x, X[r].y, Y[r].y);
+    fence_proxy_async();                            // generic-proxy writes visible to the TMA store
+    __syncthreads();
+    if (threadIdx.x == 0 && ok && inb) {
+        for (int r0 = 0; r0 < N; r0 += C::BR) tma_store_2d(&map, tile + r0, 2 * c0, r0);
+        bulk_commit();
+    }
+    if constexpr (REDUCE) {
+        if (!ok || !inb) q[0] = q[1] = q[2] = 0.f;
+        block_sum<3>(q, T.part_col + (size_t)blockIdx.x * NQ, red);
+        double S[3];
+        if (last_block_total<3>(T.part_col, &T.sc->ticket[1], S, red) && threadIdx.x == 0)
+            finalize_fields(S, a.red, T.sc);
+    }
+    if (threadIdx.x == 0) bulk_wait_read_all();     // the tile is read before the CTA exits
+}
+
+template <int N, int MODE>
+static cudaError_t col_pair_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    using C = ColPairCfg<N>;
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_opt_in(col_pair_kernel<N, MODE>, (int)C::SMEM, attr);
+    if (e != cudaSuccess) return e;
+    col_pair_kernel<N, MODE><<<a.nx / 2, C::TP, C::SMEM, s>>>(a, map);
+    return cudaGetLastError();
+}
+
+template <int N> static cudaError_t col_pair_mode(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    switch (mode) {
+    case COL_T: return col_pair_launch<N, COL_T>(a, map, s);
+    case COL_T_R: return col_pair_launch<N, COL_T_R>(a, map, s);
+    case COL_T_PR: return col_pair_launch<N, COL_T_PR>(a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Columns of 512..2048 points in tiles of 2 (the context's tensor map box).
+bool col_pair_ok(int nx, int ny) { return (ny == 512 || ny == 1024 || ny == 2048) && nx >= 2; }
+
+cudaError_t launch_col_pair(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
+{
+    if (!col_pair_ok(a.nx, a.ny)) return cudaErrorInvalidValue;
+    switch (a.ny) {
+    case 512: return col_pair_mode<512>(mode, a, map, s);
+    case 1024: return col_pair_mode<1024>(mode, a, map, s);
+    case 2048: return col_pair_mode<2048>(mode, a, map, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gpe

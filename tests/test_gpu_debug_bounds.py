@@ -6,8 +6,9 @@ the access) instead of making an out-of-bounds access.  A child process
 loads that library (GPE_LIBRARY=debug) and runs cases through every pass
 kernel family -- the one-shot row and column passes on short pencils (the
 32 x 256 and 64 x 64 grids among them), the grouped, streaming, adjoint and
-readout passes and the persistent batch -- each checked against the FP64
-oracle and for a clean device status.
+readout passes, the pencil-pair column passes (2048-point columns by
+default, 512 by choice) and the persistent batch -- each checked against
+the FP64 oracle and for a clean device status.
 """
 import os
 import subprocess
@@ -41,12 +42,16 @@ w = gi.lattice_real_time(n=64, L=16.0)
 h = gi.harmonic_trap(n=64, L=10.0, g=100.0)
 cav = dict(cavity=1, eta=2.0, U0=-0.5, dc=-2.0, kappa=1.0, kc=2 * np.pi, Nat=1.0, pump_lattice=1)
 cases = [(32, 256, w, False, {}), (64, 64, w, False, {}), (64, 64, h, True, cav), (8, 8, h, True, {}),
-         (2048, 8, w, False, {}), (4096, 64, w, False, {}), (64, 4096, h, True, {}), (128, 128, w, False, cav)]
+         (2048, 8, w, False, {}), (4096, 64, w, False, {}), (64, 4096, h, True, {}), (128, 128, w, False, cav),
+         (8, 2048, w, False, {}), (16, 2048, h, True, cav), (8, 512, h, True, {})]
+pair = {(8, 512)}                       # pencil-pair column passes also off their default column length
 for nx, ny, ww, imag, extra in cases:
     p = dict(ww["params"], nx=nx, ny=ny, Lx=max(0.02 * nx, 8.0), Ly=max(0.02 * ny, 8.0), **extra)
     x = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.2, 1e-2, seed=nx + ny, checker=0.2, kc=2 * np.pi)
     x = x.astype(np.complex64)
     s = sim(p)
+    if (nx, ny) in pair:
+        s.variants = s.variants | abi.GPE_VARIANT_PAIR_COLS
     s.set_psi(x)
     dt = 1e-3 if imag else 5e-4
     s.step(20, dt, imag)

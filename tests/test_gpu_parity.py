@@ -68,8 +68,11 @@ def test_fft2_passes_match_oracle(nx, ny):
 
 
 # ------------------------------------------------------------------ split steps
-def run_both(p, psi0, n, dt, imag, t0=0.0):
+def run_both(p, psi0, n, dt, imag, t0=0.0, streaming=False):
     s = sim_for(p)
+    if streaming:                       # the streaming passes where they apply (not the default at 2048)
+        from paper_2404_14401_b300 import gpe as abi
+        s.variants = s.variants | abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS
     s.set_psi(c64(psi0))
     s.t = t0
     s.step(n, dt, imag)
@@ -331,9 +334,10 @@ def test_grids_larger_than_l2_match_oracle_and_conserve(n):
 
 # ------------------------------------------------------------------ streaming passes
 # Axes of 4096 points run the persistent, double-buffered row (nx = 4096) and
-# column (ny = 4096) passes; these cases cover their imaginary-time, cavity and
-# real-time paths against the oracle and against the one-shot passes.
-STREAM_SHAPES = [(4096, 64), (64, 4096)]
+# column (ny = 4096) passes by default, 2048-point columns when the autotuner
+# picks them; these cases cover their imaginary-time, cavity and real-time
+# paths against the oracle and against the one-shot passes.
+STREAM_SHAPES = [(4096, 64), (64, 4096), (64, 2048)]
 
 
 def box(n):
@@ -345,7 +349,7 @@ def test_streaming_imaginary_time_matches_oracle(nx, ny):
     w = gi.harmonic_trap(n=64, L=10.0, g=100.0)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
     psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=11)
-    s, got, obs, ref, _ = run_both(p, psi0, 40, 2e-3, True)
+    s, got, obs, ref, _ = run_both(p, psi0, 40, 2e-3, True, streaming=True)
     assert rel_l2(got, ref) < 1e-5
     ro = oracle.observables(p, ref, t=s.t)
     assert abs(obs["energy"] - ro["energy"]) < 1e-5 * abs(ro["energy"])
@@ -357,7 +361,7 @@ def test_streaming_cavity_real_time_matches_oracle(nx, ny):
     w = gi.cavity_ramp(n=64, L=16.0, steps=40, dt=2e-4)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny), ctrl_v=np.array([1.0, 4.0]))
     psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-2, seed=12, checker=0.3, kc=p["kc"])
-    s, got, obs, ref, _ = run_both(p, psi0, 40, 2e-4, False)
+    s, got, obs, ref, _ = run_both(p, psi0, 40, 2e-4, False, streaming=True)
     assert rel_l2(got, ref) < 1e-5
     cavity_close(obs, oracle.observables(p, ref, t=s.t))
 
@@ -367,7 +371,7 @@ def test_streaming_real_time_matches_oracle(nx, ny):
     w = gi.lattice_real_time(n=64, L=16.0)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
     psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=13)
-    s, got, obs, ref, _ = run_both(p, psi0, 30, 5e-4, False)
+    s, got, obs, ref, _ = run_both(p, psi0, 30, 5e-4, False, streaming=True)
     assert rel_l2(got, ref) < 1e-5
 
 
@@ -376,11 +380,16 @@ def test_streaming_and_one_shot_passes_agree_bitwise(nx, ny, monkeypatch):
     w = gi.lattice_real_time(n=64, L=16.0)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
     psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=14))
+    from paper_2404_14401_b300 import gpe as abi
     outs = []
     for env in (None, "1"):
         if env:
             monkeypatch.setenv("GPE_NO_STREAM_PASSES", env)
         s = sim_for(p)
+        if not env:
+            s.variants = s.variants | abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS
+        else:
+            assert s.variants & (abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS) == 0
         s.set_psi(psi0)
         s.step(10, w["dt"], False)
         outs.append(s.get_psi())
@@ -418,7 +427,11 @@ def test_default_row_variants_follow_the_row_length():
         s = sim_for(dict(w["params"], nx=nx, ny=16, Lx=box(nx), Ly=box(16)))
         assert bool(s.variants & abi.GPE_VARIANT_GROUP_ROWS) == (nx == 2048)
         assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
-        assert s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT == (1 if nx in (512, 1024) else 0)
+        assert (s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3 == (1 if nx in (512, 1024) else 0)
+        assert not s.variants & abi.GPE_VARIANT_PAIR_COLS                  # 16-point columns
+    for ny in (512, 1024, 2048, 4096):                  # pencil-pair column passes for 2048-point columns
+        s = sim_for(dict(w["params"], nx=64, ny=ny, Lx=box(64), Ly=box(ny)))
+        assert bool(s.variants & abi.GPE_VARIANT_PAIR_COLS) == (ny == 2048)
 
 
 
@@ -610,7 +623,7 @@ def test_one_context_graph_replay_matches_per_pass_launches(steps, monkeypatch):
 
 
 # ------------------------------------------------------------------ autotuner
-@pytest.mark.parametrize("nx,ny", [(2048, 64), (4096, 64), (64, 4096), (128, 128)])
+@pytest.mark.parametrize("nx,ny", [(2048, 64), (4096, 64), (64, 4096), (128, 128), (64, 2048), (64, 512)])
 def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     from paper_2404_14401_b300 import gpe as abi
     w = gi.lattice_real_time(n=64, L=16.0)
@@ -625,7 +638,7 @@ def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     group_ok = nx in (512, 1024, 2048)
     assert np.isnan(ms["row_grouped"]) != group_ok
     assert np.isnan(ms["row_streaming"]) != (nx == 4096)
-    assert np.isnan(ms["col_streaming"]) != (ny == 4096)
+    assert np.isnan(ms["col_streaming"]) != (ny in (2048, 4096) and nx >= 16)
     rows = [ms["row_one_shot"], ms["row_grouped"], ms["row_streaming"]]
     best = 0                                    # a persistent variant must be 3% faster
     for k in (1, 2):
@@ -635,6 +648,8 @@ def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     assert (v & abi.GPE_VARIANT_STREAM_ROWS != 0) == (best == 2)
     assert (v & abi.GPE_VARIANT_STREAM_COLS != 0) == (not np.isnan(ms["col_streaming"])
                                                        and ms["col_streaming"] < ms["col_one_shot"])
+    if ny not in (512, 1024, 2048) or v & abi.GPE_VARIANT_STREAM_COLS:
+        assert not v & abi.GPE_VARIANT_PAIR_COLS       # no pair form here, or the streaming pass won
     assert r["row_tile"] in (0, 1) and (r["row_tile"] == 0 or best == 0)
     # stepping with the chosen variants still matches the oracle
     s.step(20, w["dt"], False)
