@@ -144,10 +144,13 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * already on its own stream, and its stream waits for them, so callers see
  * the same ordering as with gpe_step.  For batches of grids of at most 2^22
  * points on average with no time-dependent control or probe and no profiling, the
- * interior steps 1 .. n-2 are captured into a CUDA graph of up to 8 steps
- * (fewer for large batches) and replayed (same results bit for bit, one host
- * launch per graph).  The instantiated graph is kept (the 8 most recently
- * used per device) and replayed again by later calls on the same contexts,
+ * interior steps 1 .. n-2 are captured into CUDA graphs of up to 8 steps
+ * (fewer for large batches), one per lane, and replayed (same results bit
+ * for bit, one host launch per lane and graph; each lane replays on its own
+ * stream, so a context whose earlier work on its stream -- an upload, say
+ * -- finishes first also starts its steps first).  The instantiated graphs
+ * are kept (those of the 8 most recently used batches per device) and
+ * replayed again by later calls on the same contexts,
  * in the same order, with the same dt, mode and step count per graph, as
  * long as none of the contexts has changed its potential, pass variants or
  * wait limit since; gpe_destroy releases the graphs of its context.  Calls from several

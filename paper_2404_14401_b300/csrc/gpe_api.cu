@@ -101,22 +101,29 @@ int lanes_for(gpe_ctx *const *ctxs, int count)
     (void)ctxs;
     return count < kLanes ? count : kLanes;
 }
-// An instantiated graph of K interior lockstep steps, kept across
-// gpe_step_many calls: its kernel arguments are fixed by the contexts (each
-// by its uid and version), dt, the mode, K and the lane count, so a later call
-// with the same key replays it without capturing again.
+// Instantiated graphs of K interior lockstep steps, one per lane (the steps
+// of the contexts on that lane), kept across gpe_step_many calls: their
+// kernel arguments are fixed by the contexts (each by its uid and version),
+// dt, the mode, K and the lane count, so a later call with the same key
+// replays them without capturing again.  Each lane replays its own graph on
+// its own stream: no lane waits for another between replays.
 struct GraphEntry {
     std::vector<unsigned long long> key;   // uid, version per context, in order
     double dt;
     int mode, K, nl;
-    cudaGraphExec_t exec;
+    std::vector<cudaGraphExec_t> exec;     // per lane
     std::vector<long long> launches;       // kernels each context launches per replay
     unsigned long long used;               // LRU stamp
 };
+static void destroy_graphs(GraphEntry &e)
+{
+    for (cudaGraphExec_t x : e.exec)
+        if (x) cudaGraphExecDestroy(x);
+    e.exec.clear();
+}
 constexpr size_t kGraphCache = 8;
 struct Lanes {
     cudaStream_t s[kLanes];
-    cudaEvent_t ev[kLanes];        // fork / join of the other lanes into a capture on lane 0
     std::mutex mu;                 // one gpe_step_many at a time enqueues on these lanes
     std::vector<GraphEntry> graphs;   // guarded by mu
     unsigned long long clock = 0;
@@ -135,12 +142,6 @@ Lanes *lanes_for_current_device()
         for (int i = 0; i < kLanes; ++i)
             if (cudaStreamCreateWithFlags(&L->s[i], cudaStreamNonBlocking) != cudaSuccess) {
                 for (int k = 0; k < i; ++k) cudaStreamDestroy(L->s[k]);
-                delete L;
-                return nullptr;
-            }
-        for (int i = 0; i < kLanes; ++i)
-            if (cudaEventCreateWithFlags(&L->ev[i], cudaEventDisableTiming) != cudaSuccess) {
-                for (int k = 0; k < kLanes; ++k) cudaStreamDestroy(L->s[k]);
                 delete L;
                 return nullptr;
             }
@@ -836,32 +837,27 @@ static gpe_status capture_graph(gpe_ctx *const *ctxs, int count, int n, double d
     gpe_ctx *c0 = ctxs[0];
     std::vector<long long> before(count);
     for (int i = 0; i < count; ++i) before[i] = ctxs[i]->launches;
-    TRY(cuda_check(c0, cudaStreamBeginCapture(L->s[0], cudaStreamCaptureModeThreadLocal), "begin capture"));
-    gpe_status st = cuda_check(c0, cudaEventRecord(L->ev[0], L->s[0]), "capture fork");
-    for (int l = 1; l < nl && st == GPE_OK; ++l)
-        st = cuda_check(c0, cudaStreamWaitEvent(L->s[l], L->ev[0], 0), "capture fork");
-    for (int k = 1; k <= K && st == GPE_OK; ++k)
-        for (int i = 0; i < count && st == GPE_OK; ++i) st = step_part(ctxs[i], k, n, dt, mode);
-    for (int l = 1; l < nl && st == GPE_OK; ++l) {
-        st = cuda_check(c0, cudaEventRecord(L->ev[l], L->s[l]), "capture join");
-        if (st == GPE_OK) st = cuda_check(c0, cudaStreamWaitEvent(L->s[0], L->ev[l], 0), "capture join");
+    out->exec.assign(nl, nullptr);
+    gpe_status st = GPE_OK;
+    for (int l = 0; l < nl && st == GPE_OK; ++l) {
+        // the steps of lane l's contexts (i = l, l + nl, ...), captured on that lane
+        st = cuda_check(c0, cudaStreamBeginCapture(L->s[l], cudaStreamCaptureModeThreadLocal), "begin capture");
+        if (st != GPE_OK) break;
+        for (int k = 1; k <= K && st == GPE_OK; ++k)
+            for (int i = l; i < count && st == GPE_OK; i += nl) st = step_part(ctxs[i], k, n, dt, mode);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(L->s[l], &g);   // always end the capture
+        if (st == GPE_OK) st = cuda_check(c0, e, "end capture");
+        if (st == GPE_OK) st = cuda_check(c0, cudaGraphInstantiate(&out->exec[l], g, 0), "graph instantiate");
+        if (g) cudaGraphDestroy(g);
     }
-    cudaGraph_t g = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(L->s[0], &g);   // always end the capture
     // the captured launches were only recorded, not run: count them per replay
     out->launches.resize(count);
     for (int i = 0; i < count; ++i) {
         out->launches[i] = ctxs[i]->launches - before[i];
         ctxs[i]->launches = before[i];
     }
-    if (st != GPE_OK) {
-        if (g) cudaGraphDestroy(g);
-        return st;
-    }
-    TRY(cuda_check(c0, e, "end capture"));
-    out->exec = nullptr;
-    st = cuda_check(c0, cudaGraphInstantiate(&out->exec, g, 0), "graph instantiate");
-    cudaGraphDestroy(g);
+    if (st != GPE_OK) destroy_graphs(*out);
     return st;
 }
 
@@ -875,11 +871,6 @@ static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, 
     if (K < 1) K = 1;
     const int R = (n - 2) / K;                                       // replays
     gpe_ctx *c0 = ctxs[0];
-    // the graph runs on lane 0: order it after the work already on every lane
-    for (int l = 1; l < nl; ++l) {
-        TRY(cuda_check(c0, cudaEventRecord(L->ev[l], L->s[l]), "pre-capture join"));
-        TRY(cuda_check(c0, cudaStreamWaitEvent(L->s[0], L->ev[l], 0), "pre-capture join"));
-    }
     std::vector<unsigned long long> key(2 * (size_t)count);
     for (int i = 0; i < count; ++i) {
         key[2 * i] = ctxs[i]->uid;
@@ -893,15 +884,14 @@ static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, 
         e.mode = (int)mode;
         e.K = K;
         e.nl = nl;
-        e.exec = nullptr;
         e.used = 0;
         TRY(capture_graph(ctxs, count, n, dt, mode, L, nl, K, &e));
         if (L->graphs.size() >= kGraphCache) {
-            // release the least recently used graph (its pending launches complete first)
+            // release the least recently used graphs (their pending launches complete first)
             size_t lru = 0;
             for (size_t i = 1; i < L->graphs.size(); ++i)
                 if (L->graphs[i].used < L->graphs[lru].used) lru = i;
-            cudaGraphExecDestroy(L->graphs[lru].exec);
+            destroy_graphs(L->graphs[lru]);
             L->graphs.erase(L->graphs.begin() + (long)lru);
         }
         L->graphs.push_back(std::move(e));
@@ -909,11 +899,9 @@ static gpe_status replay_interior_steps(gpe_ctx *const *ctxs, int count, int n, 
     }
     g->used = ++L->clock;
     gpe_status st = GPE_OK;
-    for (int r = 0; r < R && st == GPE_OK; ++r) st = cuda_check(c0, cudaGraphLaunch(g->exec, L->s[0]), "graph launch");
-    // the other lanes' next work follows the last replay
-    if (st == GPE_OK) st = cuda_check(c0, cudaEventRecord(L->ev[0], L->s[0]), "replay join");
-    for (int l = 1; l < nl && st == GPE_OK; ++l)
-        st = cuda_check(c0, cudaStreamWaitEvent(L->s[l], L->ev[0], 0), "replay join");
+    for (int r = 0; r < R && st == GPE_OK; ++r)
+        for (int l = 0; l < nl && st == GPE_OK; ++l)
+            st = cuda_check(c0, cudaGraphLaunch(g->exec[l], L->s[l]), "graph launch");
     for (int i = 0; i < count; ++i) ctxs[i]->launches += g->launches[i] * (long long)R;
     if (st == GPE_OK) *done = R * K;
     return st;
@@ -934,7 +922,7 @@ static void forget_graphs(int device, unsigned long long uid)
         bool hit = false;
         for (size_t j = 0; j < k.size(); j += 2) hit = hit || k[j] == uid;
         if (hit) {
-            cudaGraphExecDestroy(L->graphs[i].exec);
+            destroy_graphs(L->graphs[i]);
             L->graphs.erase(L->graphs.begin() + (long)i);
         } else {
             ++i;
@@ -962,10 +950,11 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
     // while passes of different contexts overlap on the GPU.
     // Interior steps (0 < s < n-1) are identical when no context has a
     // time-dependent control.  For batches of grids up to 2048^2 (one context
-    // included), up to kGraphSteps of them are captured into a CUDA graph
-    // (every lane, every context) and the graph is replayed for the others:
-    // one host launch per graph instead of one per pass, and fewer points
-    // where every lane waits for the slowest.  Profiling contexts keep
+    // included), up to kGraphSteps of them are captured into a CUDA graph per
+    // lane (the steps of that lane's contexts) and each lane replays its
+    // graph for the others on its own stream: one host launch per lane and
+    // replay instead of one per pass, and no lane waits for another (a lane
+    // whose contexts' inputs arrive first starts first).  Profiling contexts keep
     // per-pass launches (their events); time enters a pass only through a
     // control table and the cavity probe (Sec. 5.4), with either of which
     // consecutive steps have different arguments.

@@ -568,10 +568,47 @@ def test_context_on_its_own_stream_matches_the_default_stream():
     side.synchronize()
 
 
+def test_step_many_on_contexts_with_their_own_streams_and_uploads():
+    """Lockstep steps of contexts on streams of their own, each uploaded from
+    pinned host memory on its stream just before the call (each lane starts
+    after its own context's upload), then each read back: bit for bit the
+    trajectories of the same contexts on the current stream, twice in a row
+    (the second call replays the per-lane graphs of the first)."""
+    import torch
+    from paper_2404_14401_b300 import Simulation
+    from paper_2404_14401_b300 import gpe as abi
+    w = gi.lattice_real_time(n=64, L=16.0)
+    shapes = [(256, 256), (512, 128), (128, 512), (256, 256)]
+    ref, got = [], []
+    for own in (False, True):
+        sims, hosts = [], []
+        for k, (nx, ny) in enumerate(shapes):
+            p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+            s = Simulation(nx, ny, p["Lx"], p["Ly"], p["m"], p["g"], stream=torch.cuda.Stream() if own else None)
+            s.set_potential(p)
+            hosts.append(torch.from_numpy(c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3,
+                                                                   seed=300 + k))).pin_memory())
+            sims.append(s)
+        outs = []
+        for call in range(2):
+            for s, h in zip(sims, hosts):
+                abi.gpe_set_psi(s.ctx, h.data_ptr(), False)
+            Simulation.step_many(sims, 20, 5e-4)
+            outs.append([s.get_psi() for s in sims])
+            assert all(s.sync() == 0 for s in sims)
+        (got if own else ref).append(outs)
+    for a_call, b_call in zip(ref[0], got[0]):
+        for a, b in zip(a_call, b_call):
+            assert np.array_equal(a, b)
+    for a, b in zip(got[0][0], got[0][1]):
+        assert np.array_equal(a, b)                     # same upload, same steps
+
+
 # ------------------------------------------------------------------ graph replay
 # With two or more contexts and no time-dependent control, gpe_step_many
-# captures one interior lockstep step into a CUDA graph and replays it.  The
-# result and the launch count must equal those of per-pass launches.
+# captures the interior lockstep steps of each lane into a CUDA graph and
+# replays it.  The result and the launch count must equal those of per-pass
+# launches.
 @pytest.mark.parametrize("imag", [False, True])
 def test_graph_replay_matches_per_pass_launches(imag, monkeypatch):
     from paper_2404_14401_b300 import Simulation
