@@ -349,9 +349,11 @@ gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd,
 gpe_status run_col(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag)
 {
     const PassArgs a = pass_args(c, ph, rd, imag, 0);
-    if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR) && c->stream_cols && col_stream_ok(c->nx, c->ny))
+    if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR || mode == COL_T_P) && c->stream_cols &&
+        col_stream_ok(c->nx, c->ny))
         return timed_launch(c, 1, [&] { return launch_col_stream(mode, a, c->map, c->stream); }, "column pass");
-    if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR) && c->pair_cols && col_pair_ok(c->nx, c->ny))
+    if ((mode == COL_T || mode == COL_T_R || mode == COL_T_PR || mode == COL_T_P) && c->pair_cols &&
+        col_pair_ok(c->nx, c->ny))
         return timed_launch(c, 1, [&] { return launch_col_pair(mode, a, c->map, c->stream); }, "column pass");
     return timed_launch(c, 1, [&] { return launch_col(mode, a, c->map, c->stream); }, "column pass");
 }
@@ -551,7 +553,7 @@ gpe_status step_part(gpe_ctx *c, int s, int n, double dt, gpe_mode mode)
         if (cav)
             TRY(run_col(c, COL_T_R, none, red_at(c, te), 0));
         else if (s == n - 1)
-            TRY(run_col(c, COL_T_PR, phase_at(c, te, 0.5 * dt), red_at(c, te), 0));
+            TRY(run_col(c, COL_T_P, phase_at(c, te, 0.5 * dt), red_at(c, te), 0));
         else
             TRY(run_col(c, COL_T, none, red_at(c, te), 0));
     } else {

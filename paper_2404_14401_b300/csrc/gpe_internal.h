@@ -75,7 +75,8 @@ enum ColMode {
     COL_FFT_F = 3,      // F_y only
     COL_FFT_I = 4,      // F_y^-1 (with 1/ny)
     COL_OBS = 5,        // F_y, sum ky^2 |.|^2, no store
-    COL_ADJ = 6         // T_y^H, then the adjoint of an opening half phase (psi2 = its input); reduce dJ/dv
+    COL_ADJ = 6,        // T_y^H, then the adjoint of an opening half phase (psi2 = its input); reduce dJ/dv
+    COL_T_P = 7         // T_y, potential phase, store (no reductions: the last real-time step without cavity)
 };
 
 struct PassArgs {

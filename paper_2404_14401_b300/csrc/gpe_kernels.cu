@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
             fft_pencil<N, E, false>(v, sb, j, 1, tw);
         }
 
-        if constexpr (MODE == COL_T || MODE == COL_T_R || MODE == COL_T_PR) {
+        if constexpr (MODE == COL_T || MODE == COL_T_R || MODE == COL_T_PR || MODE == COL_T_P) {
             kinetic_axis<E, TP>(v, T.kiny, j, a.sy, a.imag);
             fft_pencil<N, E, true>(v, sb, j, 1, tw);
         }
@@ -521,9 +521,9 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
             q[0] += 2.f * a.ph.h * gq;
         }
 
-        if constexpr (MODE == COL_T_PR) {
-            // closing half phase and the reduction of its result in one loop:
-            // each y-table entry is read once
+        if constexpr (MODE == COL_T_PR || MODE == COL_T_P) {
+            // closing half phase [and the reduction of its result] in one
+            // loop: each y-table entry is read once
             const float4 xt = __ldg(&T.xtab[c0 + c]);
             const PotCoefs pc = col_coefs(a, xt);
             float n0 = 0.f, n1 = 0.f;
@@ -534,9 +534,11 @@ __global__ void __launch_bounds__(col_g(N) * ColCfg<N>::TP, N >= 4096 ? 1 : 3)
                 float V = pot_at(pc, yt);
                 if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
                 v[r] = phase_mul(v[r], V, a.g, a.ph.h, a.imag);
-                const float n = v[r].x * v[r].x + v[r].y * v[r].y;
-                n0 += n;
-                n1 += yt.z * n;
+                if constexpr (REDUCE) {
+                    const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+                    n0 += n;
+                    n1 += yt.z * n;
+                }
             }
             q[0] += n0;
             q[1] += xt.z * n1;
@@ -782,8 +784,8 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
         fft_pencil<N, E, false>(v, sb, j, 1, tw);
         kinetic_axis<E, TP>(v, T.kiny, j, a.sy, a.imag);
         fft_pencil<N, E, true>(v, sb, j, 1, tw);
-        if constexpr (MODE == COL_T_PR) {
-            // closing half phase and its reduction in one loop (one y-table read per point)
+        if constexpr (MODE == COL_T_PR || MODE == COL_T_P) {
+            // closing half phase [and its reduction] in one loop (one y-table read per point)
             const float4 xt = __ldg(&T.xtab[c0 + c]);
             const PotCoefs pc = col_coefs(a, xt);
             float n0 = 0.f, n1 = 0.f;
@@ -794,9 +796,11 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
                 float V = pot_at(pc, yt);
                 if (a.V) V += a.V_scale * __ldg(&a.V[(size_t)yi * a.nx + c0 + c]);
                 v[r] = phase_mul(v[r], V, a.g, a.ph.h, a.imag);
-                const float n = v[r].x * v[r].x + v[r].y * v[r].y;
-                n0 += n;
-                n1 += yt.z * n;
+                if constexpr (REDUCE) {
+                    const float n = v[r].x * v[r].x + v[r].y * v[r].y;
+                    n0 += n;
+                    n1 += yt.z * n;
+                }
             }
             q[0] += n0;
             q[1] += xt.z * n1;
@@ -1131,6 +1135,7 @@ template <int N> static cudaError_t col_dispatch_mode(int mode, const PassArgs &
     case COL_T: return col_launch<N, COL_T>(a, map, s);
     case COL_T_R: return col_launch<N, COL_T_R>(a, map, s);
     case COL_T_PR: return col_launch<N, COL_T_PR>(a, map, s);
+    case COL_T_P: return col_launch<N, COL_T_P>(a, map, s);
     case COL_FFT_F: return col_launch<N, COL_FFT_F>(a, map, s);
     case COL_FFT_I: return col_launch<N, COL_FFT_I>(a, map, s);
     case COL_OBS: return col_launch<N, COL_OBS>(a, map, s);
@@ -1241,6 +1246,7 @@ template <int N> static cudaError_t col_stream_mode(int mode, const PassArgs &a,
     case COL_T: return col_stream_launch<N, COL_T>(a, map, s);
     case COL_T_R: return col_stream_launch<N, COL_T_R>(a, map, s);
     case COL_T_PR: return col_stream_launch<N, COL_T_PR>(a, map, s);
+    case COL_T_P: return col_stream_launch<N, COL_T_P>(a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -113,7 +113,8 @@ __device__ __forceinline__ void kinetic_pair(float2 (&X)[E], float2 (&Y)[E], con
 
 // Column pass over a 2-column tile as one pencil pair.  MODE: COL_T (T_y),
 // COL_T_R (T_y, then the norm and cavity overlaps of the result reduced in
-// FP64, Eqs. 14-15), COL_T_PR (T_y, the closing half phase, the reductions).
+// FP64, Eqs. 14-15), COL_T_PR (T_y, the closing half phase, the reductions),
+// COL_T_P (T_y, the closing half phase).
 template <int N, int MODE>
 __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     col_pair_kernel(const PassArgs a, const __grid_constant__ CUtensorMap map)
@@ -167,6 +168,20 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     fft_pair<N, E, true>(X, Y, tile, j, stw);
 
     float q[3] = {0.f, 0.f, 0.f};
+    if constexpr (MODE == COL_T_P) {
+        // the closing half phase alone (each y-table entry read once for both columns)
+        const PotCoefs pa = col_coefs(a, __ldg(&T.xtab[c0])), pb = col_coefs(a, __ldg(&T.xtab[c0 + 1]));
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int yi = j + r * TP;
+            float2 V = pot_at2(pa, pb, __ldg(&T.ytab[yi]));
+            if (a.V) {
+                const float2 va = make_float2(__ldg(&a.V[(size_t)yi * a.nx + c0]), __ldg(&a.V[(size_t)yi * a.nx + c0 + 1]));
+                V = fma2(bc2(a.V_scale), va, V);
+            }
+            phase_mul2(X[r], Y[r], V, a.g, a.ph.h, a.imag);
+        }
+    }
     if constexpr (REDUCE) {
         // per column: n0 = sum |psi|^2, n1 = sum cos(kc y) |psi|^2 (after the
         // closing phase in COL_T_PR; each y-table entry read once for both)
@@ -234,6 +249,7 @@ template <int N> static cudaError_t col_pair_mode(int mode, const PassArgs &a, c
     case COL_T: return col_pair_launch<N, COL_T>(a, map, s);
     case COL_T_R: return col_pair_launch<N, COL_T_R>(a, map, s);
     case COL_T_PR: return col_pair_launch<N, COL_T_PR>(a, map, s);
+    case COL_T_P: return col_pair_launch<N, COL_T_P>(a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }
