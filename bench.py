@@ -167,11 +167,9 @@ def row_kernel_name(n):
 
 def col_kernel_name(n):
     """Kernel of the interior real-time column pass for an n x n grid with a
-    context's default variants (streaming pass for 4096-point columns,
-    pencil-pair pass for 2048, one-shot one-pencil pass otherwise)."""
-    if n == 4096:
-        return f"col_stream_kernel<{n},COL_T>"
-    if n == 2048:
+    context's default variants (pencil-pair pass for columns of 2048 points
+    and more, one-shot one-pencil pass otherwise)."""
+    if n >= 2048:
         return f"col_pair_kernel<{n},COL_T>"
     return f"col_kernel<{n},COL_T>"
 

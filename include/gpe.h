@@ -302,12 +302,13 @@ gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax,
  * tables in shared memory, TMA double buffering), rows and columns of 4096
  * points a streaming persistent variant; every grid has the one-shot
  * variant (a CTA per group of rows or per TMA tile of columns), and the
- * column passes of 512..2048-point columns a pencil-pair form (bit 5).  A
- * context starts with the streaming variants on where they apply, the
+ * column passes of 512..8192-point columns a pencil-pair form (bit 5).  A
+ * context starts with the streaming row pass on where it applies, the
  * grouped row pass on for 2048-point rows only, the half row tile (below)
  * for 512- and 1024-point rows and the pencil-pair column passes for
- * 2048-point columns: with those the passes of other grids overlapped best
- * under gpe_step_many.  The bits select them: */
+ * columns of 2048 points and more (the streaming column pass off): with
+ * those the passes of other grids overlapped best under gpe_step_many.  The
+ * bits select them: */
 enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
 /* Bits 3-4 (value << GPE_VARIANT_ROW_TILE_SHIFT, value 0..2): on rows of
  * 256 points and more the one-shot row passes of the context's steps,
@@ -316,10 +317,10 @@ enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STRE
  * SMs; shorter rows ignore it. */
 enum { GPE_VARIANT_ROW_TILE_SHIFT = 3 };
 /* Bit 5: the column passes (T_y [+ closing phase] [+ reductions]) of
- * 512..2048-point columns as pencil pairs: both columns of a 2-column tile
+ * 512..8192-point columns as pencil pairs: both columns of a 2-column tile
  * in one packed f32x2 transform, each table entry read once for both (equal
- * to the one-pencil passes to FP32 rounding).  On by default for 2048-point
- * columns, where it measured faster. */
+ * to the one-pencil passes to FP32 rounding).  On by default for columns
+ * of 2048 points and more, where it measured faster. */
 enum { GPE_VARIANT_PAIR_COLS = 32 };
 int gpe_get_pass_variants(const gpe_ctx *ctx);                /* -1 for a null context */
 /* GPE_EINVAL for bits other than those above or a row-tile value above 2 */

@@ -415,9 +415,9 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->kin_valid = false;
     c->spins = 1 << 24;
     c->stream_passes = getenv("GPE_NO_STREAM_PASSES") ? 0 : 1;
-    // the streaming column pass by default where it measured faster (4096);
-    // at 2048 the autotuner may choose it
-    c->stream_cols = c->stream_passes && ny == 4096;
+    // the streaming column pass by default nowhere: the pencil-pair pass
+    // (below) measured faster at 4096 and 2048; the autotuner may choose it
+    c->stream_cols = 0;
     // the grouped row pass by default only for 2048-point rows: at 1024 (and
     // below) the one-shot pass, whose CTAs share SMs with other passes,
     // measured faster under gpe_step_many (1024^2 x 8: 71.8 against 64.2 G
@@ -428,11 +428,12 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // 512^2 at 56.0 against 53.8; at 2048 the half tile was slower (65.7
     // against 71.7) and at 256 the same
     c->row_tile_shift = (nx == 512 || nx == 1024) ? 1 : 0;
-    // the pencil-pair column passes by default for 2048-point columns (8 x
-    // 2048^2 under gpe_step_many: 69.7 against 67.6 G pt*steps/s; the T_y
-    // pass alone 33.7 against 36.0 us); at 512 and 1024 both forms timed
-    // alike
-    c->pair_cols = (ny == 2048 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
+    // the pencil-pair column passes by default for columns of 2048 points and
+    // more (8 x 2048^2 under gpe_step_many: 69.7 against 67.6 G pt*steps/s,
+    // the T_y pass alone 33.7 against 36.0 us; 4096^2: 126 against 183 us
+    // for the streaming pass; 8192^2: 888 against 943 us); at 512 and 1024
+    // the one-pencil pass was as fast or faster
+    c->pair_cols = (ny >= 2048 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
     c->launches = 0;
     {
         static std::atomic<unsigned long long> next_uid{1};

@@ -29,13 +29,20 @@ template <int N> struct ColPairCfg {
     static constexpr int E = 16, TP = N / E;       // threads per 2-column tile
     static constexpr int BR = N < 256 ? N : 256;   // rows per TMA box (the context's tensor map)
     static constexpr int SLOTS = pad8_len(N);      // 16-byte exchange slots, overlaying the dense tile
-    static constexpr int TWN = fft_tw_count(N);    // twiddles staged in shared memory
+    // twiddles staged in shared memory up to 2048-point columns; the 4096-
+    // and 8192-point tables (65 and 131 KB) are read through L1 instead, so
+    // that two CTAs (one at 8192) fit on an SM
+    static constexpr bool TW_L1 = N >= 4096;
+    static constexpr int TWN = TW_L1 ? 0 : fft_tw_count(N);
     static constexpr uint32_t TW_BYTES = (uint32_t)TWN * 16u;
     static constexpr size_t SMEM = (size_t)SLOTS * 16 + TW_BYTES + 128;
     // CTAs per SM the registers are sized for: as many as the shared memory
-    // holds (3 at 2048), at most 16
+    // holds (3 at 2048), but no fewer than 128 registers per thread (2 at
+    // 4096), at most 16
     static constexpr int BY_SMEM = (int)((224u * 1024u) / (SMEM + 1024));
-    static constexpr int MIN_CTAS = BY_SMEM < 16 ? BY_SMEM : 16;
+    static constexpr int BY_REGS = 65536 / (TP * 128);
+    static constexpr int CAP = BY_REGS < 16 ? BY_REGS : 16;
+    static constexpr int MIN_CTAS = BY_SMEM < CAP ? BY_SMEM : CAP;
 };
 
 // V at the same y of two columns (coefficients pa, pb; y-table entry t), in
@@ -138,7 +145,7 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar, (uint32_t)N * 16u + C::TW_BYTES);
-        bulk_load_1d(stw, T.twy, C::TW_BYTES, &bar);
+        if constexpr (!C::TW_L1) bulk_load_1d(stw, T.twy, C::TW_BYTES, &bar);
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + r0, &map, &bar, 2 * c0, r0);
     }
     // the tile and the twiddles arrived in time.  Otherwise the copies are
@@ -163,9 +170,10 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     }
     __syncthreads();                                // dense reads done before the exchange writes
 
-    fft_pair<N, E, false>(X, Y, tile, j, stw);
+    const float4 *tw = C::TW_L1 ? T.twy : stw;
+    fft_pair<N, E, false>(X, Y, tile, j, tw);
     kinetic_pair<E, TP>(X, Y, T.kiny, j, a.sy, a.imag);
-    fft_pair<N, E, true>(X, Y, tile, j, stw);
+    fft_pair<N, E, true>(X, Y, tile, j, tw);
 
     float q[3] = {0.f, 0.f, 0.f};
     if constexpr (MODE == COL_T_P) {
@@ -254,8 +262,11 @@ template <int N> static cudaError_t col_pair_mode(int mode, const PassArgs &a, c
     }
 }
 
-// Columns of 512..2048 points in tiles of 2 (the context's tensor map box).
-bool col_pair_ok(int nx, int ny) { return (ny == 512 || ny == 1024 || ny == 2048) && nx >= 2; }
+// Columns of 512..8192 points in tiles of 2 (the context's tensor map box).
+bool col_pair_ok(int nx, int ny)
+{
+    return (ny == 512 || ny == 1024 || ny == 2048 || ny == 4096 || ny == 8192) && nx >= 2;
+}
 
 cudaError_t launch_col_pair(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {
@@ -264,6 +275,8 @@ cudaError_t launch_col_pair(int mode, const PassArgs &a, const CUtensorMap &map,
     case 512: return col_pair_mode<512>(mode, a, map, s);
     case 1024: return col_pair_mode<1024>(mode, a, map, s);
     case 2048: return col_pair_mode<2048>(mode, a, map, s);
+    case 4096: return col_pair_mode<4096>(mode, a, map, s);
+    case 8192: return col_pair_mode<8192>(mode, a, map, s);
     default: return cudaErrorInvalidValue;
     }
 }

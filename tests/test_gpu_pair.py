@@ -48,7 +48,7 @@ def box(n):
 
 # the narrowest grid (8 columns: 4 tiles), wide and square grids, and every
 # column length the pair pass takes
-PAIR_SHAPES = [(8, 512), (16, 1024), (64, 2048), (256, 512), (128, 1024), (512, 512)]
+PAIR_SHAPES = [(8, 512), (16, 1024), (64, 2048), (256, 512), (128, 1024), (512, 512), (8, 4096), (8, 8192)]
 
 
 @pytest.mark.parametrize("nx,ny", PAIR_SHAPES)
@@ -88,7 +88,7 @@ def test_pair_columns_1000_real_time_steps_hold_the_norm():
     assert abs(obs["norm"] - oracle.observables(p, ref)["norm"]) < 1e-6
 
 
-@pytest.mark.parametrize("nx,ny", [(64, 2048), (2048, 2048), (256, 512), (8, 1024)])
+@pytest.mark.parametrize("nx,ny", [(64, 2048), (2048, 2048), (256, 512), (8, 1024), (16, 4096)])
 def test_pair_and_one_pencil_columns_agree(nx, ny):
     """The same 12 real-time steps with and without the pair pass: equal to
     FP32 rounding; the launch count is the same (one column pass per step)."""
@@ -143,7 +143,7 @@ def check_against_oracle(p, psi0, n, dt, imag, cavity=False):
             assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
 
 
-@pytest.mark.parametrize("nx,ny", [(16, 2048), (64, 512), (32, 1024)])
+@pytest.mark.parametrize("nx,ny", [(16, 2048), (64, 512), (32, 1024), (8, 4096)])
 def test_pair_columns_imaginary_time_match_oracle(nx, ny):
     """Imaginary time: every column pass applies the closing half phase and
     reduces the norm (the pair form of T_y + phase + reductions)."""
@@ -152,7 +152,7 @@ def test_pair_columns_imaginary_time_match_oracle(nx, ny):
     check_against_oracle(p, gi.gaussian_state(nx, ny, 10.0, p["Ly"], 1.5, 1e-3, seed=250 + ny), 40, 2e-3, True)
 
 
-@pytest.mark.parametrize("nx,ny", [(16, 2048), (64, 512)])
+@pytest.mark.parametrize("nx,ny", [(16, 2048), (64, 512), (8, 4096)])
 def test_pair_columns_cavity_real_time_match_oracle(nx, ny):
     """Real time with the self-consistent cavity: every column pass reduces
     the norm and the overlaps O, B for the next alpha (T_y + reductions)."""

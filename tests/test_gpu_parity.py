@@ -429,9 +429,10 @@ def test_default_row_variants_follow_the_row_length():
         assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
         assert (s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3 == (1 if nx in (512, 1024) else 0)
         assert not s.variants & abi.GPE_VARIANT_PAIR_COLS                  # 16-point columns
-    for ny in (512, 1024, 2048, 4096):                  # pencil-pair column passes for 2048-point columns
+    for ny in (512, 1024, 2048, 4096, 8192):            # pencil-pair column passes from 2048 points on
         s = sim_for(dict(w["params"], nx=64, ny=ny, Lx=box(64), Ly=box(ny)))
-        assert bool(s.variants & abi.GPE_VARIANT_PAIR_COLS) == (ny == 2048)
+        assert bool(s.variants & abi.GPE_VARIANT_PAIR_COLS) == (ny >= 2048)
+        assert not s.variants & abi.GPE_VARIANT_STREAM_COLS
 
 
 
@@ -685,7 +686,7 @@ def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     assert (v & abi.GPE_VARIANT_STREAM_ROWS != 0) == (best == 2)
     assert (v & abi.GPE_VARIANT_STREAM_COLS != 0) == (not np.isnan(ms["col_streaming"])
                                                        and ms["col_streaming"] < ms["col_one_shot"])
-    if ny not in (512, 1024, 2048) or v & abi.GPE_VARIANT_STREAM_COLS:
+    if ny not in (512, 1024, 2048, 4096, 8192) or v & abi.GPE_VARIANT_STREAM_COLS:
         assert not v & abi.GPE_VARIANT_PAIR_COLS       # no pair form here, or the streaming pass won
     assert r["row_tile"] in (0, 1) and (r["row_tile"] == 0 or best == 0)
     # stepping with the chosen variants still matches the oracle
