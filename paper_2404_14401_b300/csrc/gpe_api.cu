@@ -60,6 +60,7 @@ struct gpe_ctx {
     int stream_cols;         // use the persistent streaming column pass where it applies
     int group_rows;          // use the grouped persistent row pass where it applies
     int pair_cols;           // use the pencil-pair column pass (T_y) where it applies
+    int pair_rows;           // use the pencil-pair row pass where it applies
     int row_tile_shift;      // one-shot row pass: 2^-shift of the default rows per CTA (0..2)
     long long launches;
     unsigned long long uid;          // unique over the process (never reused, unlike the pointer)
@@ -338,6 +339,8 @@ template <class F> gpe_status timed_launch(gpe_ctx *c, int kind, F &&launch, con
 gpe_status run_row(gpe_ctx *c, int mode, const PhaseArgs &ph, const RedArgs &rd, int imag, int use_c)
 {
     const PassArgs a = pass_args(c, ph, rd, imag, use_c);
+    if (mode == ROW_PT && c->pair_rows && row_pair_ok(c->nx, c->ny))
+        return timed_launch(c, 0, [&] { return launch_row_pair(a, c->stream); }, "row pass");
     if (mode == ROW_PT && c->stream_passes && row_stream_ok(c->nx, c->ny))
         return timed_launch(c, 0, [&] { return launch_row_stream(a, c->stream); }, "row pass");
     if (mode == ROW_PT && c->group_rows && row_group_ok(c->nx, c->ny))
@@ -434,6 +437,11 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // for the streaming pass; 8192^2: 888 against 943 us); at 512 and 1024
     // the one-pencil pass was as fast or faster
     c->pair_cols = (ny >= 2048 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
+    // the pencil-pair row pass by default for 4096-point rows (157 against
+    // 182 us for the streaming pass at 4096^2); at 2048 the grouped pass and
+    // at 8192 the one-shot pass measured faster (44 against 47, 940 against
+    // 972 us)
+    c->pair_rows = (nx == 4096 && !getenv("GPE_NO_PAIR_ROWS")) ? 1 : 0;
     c->launches = 0;
     {
         static std::atomic<unsigned long long> next_uid{1};
@@ -1212,16 +1220,17 @@ int gpe_get_pass_variants(const gpe_ctx *c)
     if (!c) return -1;
     return (c->group_rows ? GPE_VARIANT_GROUP_ROWS : 0) | (c->stream_passes ? GPE_VARIANT_STREAM_ROWS : 0) |
            (c->stream_cols ? GPE_VARIANT_STREAM_COLS : 0) | (c->row_tile_shift << GPE_VARIANT_ROW_TILE_SHIFT) |
-           (c->pair_cols ? GPE_VARIANT_PAIR_COLS : 0);
+           (c->pair_cols ? GPE_VARIANT_PAIR_COLS : 0) | (c->pair_rows ? GPE_VARIANT_PAIR_ROWS : 0);
 }
 
 gpe_status gpe_set_pass_variants(gpe_ctx *c, int v)
 {
     const int known = GPE_VARIANT_GROUP_ROWS | GPE_VARIANT_STREAM_ROWS | GPE_VARIANT_STREAM_COLS |
-                      (3 << GPE_VARIANT_ROW_TILE_SHIFT) | GPE_VARIANT_PAIR_COLS;
+                      (3 << GPE_VARIANT_ROW_TILE_SHIFT) | GPE_VARIANT_PAIR_COLS | GPE_VARIANT_PAIR_ROWS;
     if (!c || v < 0 || (v & ~known) || ((v >> GPE_VARIANT_ROW_TILE_SHIFT) & 3) > 2) return GPE_EINVAL;
     c->group_rows = (v & GPE_VARIANT_GROUP_ROWS) != 0;
     c->pair_cols = (v & GPE_VARIANT_PAIR_COLS) != 0;
+    c->pair_rows = (v & GPE_VARIANT_PAIR_ROWS) != 0;
     c->stream_passes = (v & GPE_VARIANT_STREAM_ROWS) != 0;
     c->stream_cols = (v & GPE_VARIANT_STREAM_COLS) != 0;
     c->row_tile_shift = (v >> GPE_VARIANT_ROW_TILE_SHIFT) & 3;
@@ -1279,6 +1288,11 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
             shift = k;
         }
     }
+    // the pencil-pair row pass (one-shot, one CTA per row pair) competes with
+    // the one-pencil one-shot pass for slot 0
+    double t_rpair = NAN;
+    if (st == GPE_OK && row_pair_ok(c->nx, c->ny))
+        st = time_it([&] { return launch_row_pair(a, c->stream); }, &t_rpair);
     if (st == GPE_OK && row_group_ok(c->nx, c->ny))
         st = time_it([&] { return launch_row_group(a, c->stream); }, &t[1]);
     if (st == GPE_OK && row_stream_ok(c->nx, c->ny))
@@ -1296,11 +1310,13 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
     // 3% faster: on near ties the one-shot pass, whose CTAs the hardware
     // schedules freely, overlapped better with other grids' passes under
     // gpe_step_many (1024^2 in the phase-diagram sweep)
+    const bool rpair = t_rpair == t_rpair && t_rpair < t[0];
+    if (rpair) t[0] = t_rpair;
     int best = 0;
     for (int k = 1; k < 3; ++k)
         if (t[k] == t[k] && t[k] < 0.97 * t[best]) best = k;
     int v = best == 1 ? GPE_VARIANT_GROUP_ROWS : best == 2 ? GPE_VARIANT_STREAM_ROWS : 0;
-    if (best == 0) v |= shift << GPE_VARIANT_ROW_TILE_SHIFT;
+    if (best == 0) v |= rpair ? GPE_VARIANT_PAIR_ROWS : shift << GPE_VARIANT_ROW_TILE_SHIFT;
     // the one-shot column pass: the faster of the one-pencil and pair forms
     const bool pair = t_pair == t_pair && t_pair < t[3];
     if (pair) t[3] = t_pair;

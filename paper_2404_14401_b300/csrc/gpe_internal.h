@@ -162,6 +162,9 @@ bool col_stream_ok(int nx, int ny);
 // tiles of 512..2048-point columns
 bool col_pair_ok(int nx, int ny);
 cudaError_t launch_col_pair(int mode, const PassArgs &a, const CUtensorMap &map, cudaStream_t s);
+// pencil-pair row pass (gpe_pair.cu): ROW_PT on pairs of 2048..8192-point rows
+bool row_pair_ok(int nx, int ny);
+cudaError_t launch_row_pair(const PassArgs &a, cudaStream_t s);
 cudaError_t launch_tables(const Tables &T, int nx, int ny, double Lx, double Ly, double m,
                           double wx, double wy, double lkx, double lky, double kc, cudaStream_t s);
 cudaError_t launch_kinetic_tables(const Tables &T, int nx, int ny, double Lx, double Ly,

@@ -1,4 +1,4 @@
-// gpe_pair.cu -- pencil-pair variant of the column pass (sm_103a).
+// gpe_pair.cu -- pencil-pair variants of the column and row passes (sm_103a).
 //
 // The column pass of Sec. 3.1's split step (T_y = F_y^-1 K_y F_y on every
 // column, Eq. 3, optionally followed by the closing half phase and the FP64
@@ -240,6 +240,128 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     if (threadIdx.x == 0) bulk_wait_read_all();     // the tile is read before the CTA exits
 }
 
+// ------------------------------------------------------------------ row pass
+// Row pass ROW_PT ([scale c] potential phase, T_x = F_x^-1 K_x F_x) on two
+// consecutive rows as one pencil pair: one CTA of N/16 threads per row pair,
+// the two rows (contiguous in psi) brought in with one bulk copy and written
+// back with one; the coordinate table and kinetic factors of each x are read
+// once for both rows.  Twiddles as in the column pass of the same length.
+template <int N> struct RowPairCfg {
+    static constexpr int E = 16, TP = N / E;
+    static constexpr int SLOTS = pad8_len(N);      // 16-byte exchange slots, overlaying the two dense rows
+    static constexpr bool TW_L1 = N >= 4096;
+    static constexpr int TWN = TW_L1 ? 0 : fft_tw_count(N);
+    static constexpr uint32_t TW_BYTES = (uint32_t)TWN * 16u;
+    static constexpr uint32_t ROW_BYTES = 2u * N * 8u;
+    static constexpr size_t SMEM = (size_t)SLOTS * 16 + TW_BYTES + 128;
+    static constexpr int BY_SMEM = (int)((224u * 1024u) / (SMEM + 1024));
+    static constexpr int BY_REGS = 65536 / (TP * 128);
+    static constexpr int CAP = BY_REGS < 16 ? BY_REGS : 16;
+    static constexpr int MIN_CTAS = BY_SMEM < CAP ? BY_SMEM : CAP;
+};
+
+template <int N>
+__global__ void __launch_bounds__(RowPairCfg<N>::TP, RowPairCfg<N>::MIN_CTAS) row_pair_kernel(const PassArgs a)
+{
+    using C = RowPairCfg<N>;
+    constexpr int E = C::E, TP = C::TP;
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *tile = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    float2 *rows = reinterpret_cast<float2 *>(tile);                  // row A [0, N), row B [N, 2N)
+    float4 *stw = tile + C::SLOTS;
+    const Tables &T = a.T;
+    const bool inb = check_index((long long)blockIdx.x * 2 + 1, a.ny, T.sc) &&
+                     check_index((long long)((unsigned char *)(stw + C::TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
+    const int y0 = inb ? blockIdx.x * 2 : 0;
+    float2 *src = a.psi + (size_t)y0 * N;
+
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, C::ROW_BYTES + C::TW_BYTES);
+        if constexpr (!C::TW_L1) bulk_load_1d(stw, T.twx, C::TW_BYTES, &bar);
+        bulk_load_1d(rows, src, C::ROW_BYTES, &bar);
+    }
+    // the rows and the twiddles arrived in time; otherwise the copies are
+    // given time to land and the CTA stores nothing
+    if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins))) {
+        if (threadIdx.x == 0) {
+            latch_status(T.sc, GPE_ETIMEOUT);
+            mbar_drain(&bar, 0);
+        }
+        return;
+    }
+
+    const int j = threadIdx.x;
+    const float cs = a.use_c ? (float)T.sc->c : 1.f;
+    float2 X[E], Y[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const float2 p = rows[j + r * TP], q = rows[N + j + r * TP];
+        X[r] = make_float2(p.x * cs, q.x * cs);
+        Y[r] = make_float2(p.y * cs, q.y * cs);
+    }
+    __syncthreads();                                // dense reads done before the exchange writes
+
+    const PotCoefs pa = row_coefs(a, __ldg(&T.ytab[y0])), pb = row_coefs(a, __ldg(&T.ytab[y0 + 1]));
+    const float *Va = a.V ? a.V + (size_t)y0 * N : nullptr;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int xi = j + r * TP;
+        float2 V = pot_at2(pa, pb, __ldg(&T.xtab[xi]));
+        if (Va) V = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V);
+        phase_mul2(X[r], Y[r], V, a.g, a.ph.h, a.imag);
+    }
+    const float4 *tw = C::TW_L1 ? T.twx : stw;
+    fft_pair<N, E, false>(X, Y, tile, j, tw);
+    kinetic_pair<E, TP>(X, Y, T.kinx, j, a.sx, a.imag);
+    fft_pair<N, E, true>(X, Y, tile, j, tw);
+
+    // every exchange read finished at the last stage's barrier
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        rows[j + r * TP] = make_float2(X[r].x, Y[r].x);
+        rows[N + j + r * TP] = make_float2(X[r].y, Y[r].y);
+    }
+    fence_proxy_async();                            // generic-proxy writes visible to the bulk store
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (inb) {
+            bulk_store_1d(src, rows, C::ROW_BYTES);
+            bulk_commit();
+        }
+        bulk_wait_read_all();                       // the rows are read before the CTA exits
+    }
+}
+
+template <int N> static cudaError_t row_pair_launch(const PassArgs &a, cudaStream_t s)
+{
+    using C = RowPairCfg<N>;
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_opt_in(row_pair_kernel<N>, (int)C::SMEM, attr);
+    if (e != cudaSuccess) return e;
+    row_pair_kernel<N><<<a.ny / 2, C::TP, C::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Rows of 2048..8192 points (the grid has at least 8 rows, an even number).
+bool row_pair_ok(int nx, int ny) { return (nx == 2048 || nx == 4096 || nx == 8192) && ny >= 2; }
+
+cudaError_t launch_row_pair(const PassArgs &a, cudaStream_t s)
+{
+    if (!row_pair_ok(a.nx, a.ny)) return cudaErrorInvalidValue;
+    switch (a.nx) {
+    case 2048: return row_pair_launch<2048>(a, s);
+    case 4096: return row_pair_launch<4096>(a, s);
+    case 8192: return row_pair_launch<8192>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------ column launchers
 template <int N, int MODE>
 static cudaError_t col_pair_launch(const PassArgs &a, const CUtensorMap &map, cudaStream_t s)
 {

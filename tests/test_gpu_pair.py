@@ -114,8 +114,11 @@ def test_pair_variant_bits():
     v = s.variants
     s.variants = v | abi.GPE_VARIANT_PAIR_COLS
     assert s.variants == v | 32
+    s.variants = v | abi.GPE_VARIANT_PAIR_COLS | abi.GPE_VARIANT_PAIR_ROWS
+    assert s.variants == v | 32 | 64
+    s.variants = v | abi.GPE_VARIANT_PAIR_COLS
     with pytest.raises(Exception):
-        s.variants = 64                       # unknown bit
+        s.variants = 128                      # unknown bit
     with pytest.raises(Exception):
         s.variants = 3 << 3                   # row-tile value 3
     assert s.variants == v | 32
@@ -208,3 +211,99 @@ def test_pair_and_one_pencil_reducing_columns_agree(imag, cavity):
     assert rel_l2(outs[1], outs[0]) < 1e-6
     for k in ("norm", "energy") + (("alpha_re", "O", "B") if cavity else ()):
         assert abs(obs[1][k] - obs[0][k]) < 1e-6 * abs(obs[0][k]), k
+
+
+# ------------------------------------------------------------------ row pairs
+def sim_rows(p, pair):
+    from paper_2404_14401_b300 import gpe as abi
+    s = sim_for(p, p["ny"] >= 2048)
+    s.variants = (s.variants & ~abi.GPE_VARIANT_PAIR_ROWS) | (abi.GPE_VARIANT_PAIR_ROWS if pair else 0)
+    return s
+
+
+@pytest.mark.parametrize("nx,ny", [(2048, 8), (4096, 16), (8192, 8), (2048, 64)])
+def test_pair_rows_real_time_match_oracle(nx, ny):
+    w = gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=310 + ny)
+    s = sim_rows(p, True)
+    assert s.variants & 64
+    s.set_psi(c64(psi0))
+    s.step(40, 5e-4)
+    got, obs = s.get_psi(), s.observables()
+    assert s.sync() == 0
+    ref, _ = oracle.evolve(p, c64(psi0).astype(np.complex128), 40, 5e-4, False)
+    ro = oracle.observables(p, ref, t=s.t)
+    assert rel_l2(got, ref) < state_tol(40)
+    assert abs(obs["norm"] - ro["norm"]) < 1e-6
+    for k in ("energy", "mu"):
+        assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+
+
+def check_rows_oracle(p, psi0, n, dt, imag, cavity=False):
+    s = sim_rows(p, True)
+    s.set_psi(c64(psi0))
+    s.step(n, dt, imag)
+    got, obs = s.get_psi(), s.observables()
+    assert s.sync() == 0
+    ref, _ = oracle.evolve(p, c64(psi0).astype(np.complex128), n, dt, imag)
+    ro = oracle.observables(p, ref, t=s.t)
+    assert rel_l2(got, ref) < state_tol(n)
+    assert abs(obs["norm"] - (1.0 if imag else ro["norm"])) < 1e-6
+    for k in ("energy", "mu"):
+        assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+    if cavity:
+        a_gpu, a_ref = complex(obs["alpha_re"], obs["alpha_im"]), complex(ro["alpha_re"], ro["alpha_im"])
+        assert abs(a_ref) > 1e-3
+        assert abs(a_gpu - a_ref) < 1e-5 * abs(a_ref)
+
+
+@pytest.mark.parametrize("nx", [2048, 4096])
+def test_pair_rows_imaginary_time_match_oracle(nx):
+    """Imaginary time: the row pass scales by 1/sqrt(norm) of the previous
+    column pass before its phase."""
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0)
+    p = dict(w["params"], nx=nx, ny=16, Lx=box(nx), Ly=10.0)
+    check_rows_oracle(p, gi.gaussian_state(nx, 16, p["Lx"], 10.0, 1.5, 1e-3, seed=320), 40, 2e-3, True)
+
+
+@pytest.mark.parametrize("nx", [2048, 4096])
+def test_pair_rows_cavity_real_time_match_oracle(nx):
+    """The V_c and V_i terms of the row phase differ between the two rows of
+    a pair through cos(kc y)."""
+    w = gi.cavity_ramp(n=64, L=16.0, steps=40, dt=2e-4)
+    p = dict(w["params"], nx=nx, ny=16, Lx=box(nx), Ly=16.0, ctrl_v=np.array([1.0, 4.0]))
+    psi0 = gi.gaussian_state(nx, 16, p["Lx"], 16.0, 1.5, 1e-2, seed=330, checker=0.3, kc=p["kc"])
+    check_rows_oracle(p, psi0, 40, 2e-4, False, cavity=True)
+
+
+def test_pair_rows_lattice_control_and_potential_array():
+    """Time-dependent lattice depth and a static potential array (the two
+    rows of a pair read different array rows)."""
+    nx, ny = 4096, 8
+    p = gi.potential_defaults()
+    t, v = gi.control_points(seed=340, n=200, T=0.2, lo=0.0, hi=8.0)
+    Varr = (0.5 * gi.normal(341, nx * ny).reshape(ny, nx)).astype(np.float32).astype(np.float64)
+    p.update(nx=nx, ny=ny, Lx=box(nx), Ly=10.0, m=1.0, g=500.0, wx=1.0, wy=1.0, lat_V0x=1.0, lat_V0y=1.0,
+             lat_kx=2 * np.pi, lat_ky=2 * np.pi, ctrl_target=1, ctrl_t=t, ctrl_v=v, Varr=Varr, V_scale=0.7)
+    check_rows_oracle(p, gi.gaussian_state(nx, ny, p["Lx"], 10.0, 1.5, 1e-3, seed=342), 60, 5e-4, False)
+
+
+@pytest.mark.parametrize("nx,ny,imag", [(2048, 2048, False), (4096, 64, False), (4096, 64, True)])
+def test_pair_rows_and_default_rows_agree(nx, ny, imag):
+    """The same 12 steps with the pair row pass and with the default row
+    pass of the length (grouped at 2048, streaming at 4096): equal to FP32
+    rounding, one row pass per step either way."""
+    w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
+    psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=350))
+    outs, launches = [], []
+    for pair in (False, True):
+        s = sim_rows(p, pair)
+        s.set_psi(psi0)
+        s.step(12, 2e-3 if imag else 5e-4, imag)
+        outs.append(s.get_psi())
+        launches.append(s.launches)
+        assert s.sync() == 0
+    assert rel_l2(outs[1], outs[0]) < 1e-6
+    assert launches[0] == launches[1]

@@ -70,9 +70,10 @@ def test_fft2_passes_match_oracle(nx, ny):
 # ------------------------------------------------------------------ split steps
 def run_both(p, psi0, n, dt, imag, t0=0.0, streaming=False):
     s = sim_for(p)
-    if streaming:                       # the streaming passes where they apply (not the default at 2048)
+    if streaming:                       # the streaming passes where they apply (the pair passes off)
         from paper_2404_14401_b300 import gpe as abi
-        s.variants = s.variants | abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS
+        pairs = abi.GPE_VARIANT_PAIR_ROWS | abi.GPE_VARIANT_PAIR_COLS
+        s.variants = (s.variants & ~pairs) | abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS
     s.set_psi(c64(psi0))
     s.t = t0
     s.step(n, dt, imag)
@@ -386,10 +387,12 @@ def test_streaming_and_one_shot_passes_agree_bitwise(nx, ny, monkeypatch):
         if env:
             monkeypatch.setenv("GPE_NO_STREAM_PASSES", env)
         s = sim_for(p)
+        pairs = abi.GPE_VARIANT_PAIR_ROWS | abi.GPE_VARIANT_PAIR_COLS      # one-pencil passes on both sides
         if not env:
-            s.variants = s.variants | abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS
+            s.variants = (s.variants & ~pairs) | abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS
         else:
             assert s.variants & (abi.GPE_VARIANT_STREAM_ROWS | abi.GPE_VARIANT_STREAM_COLS) == 0
+            s.variants = s.variants & ~pairs
         s.set_psi(psi0)
         s.step(10, w["dt"], False)
         outs.append(s.get_psi())
@@ -428,6 +431,7 @@ def test_default_row_variants_follow_the_row_length():
         assert bool(s.variants & abi.GPE_VARIANT_GROUP_ROWS) == (nx == 2048)
         assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
         assert (s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3 == (1 if nx in (512, 1024) else 0)
+        assert bool(s.variants & abi.GPE_VARIANT_PAIR_ROWS) == (nx == 4096)
         assert not s.variants & abi.GPE_VARIANT_PAIR_COLS                  # 16-point columns
     for ny in (512, 1024, 2048, 4096, 8192):            # pencil-pair column passes from 2048 points on
         s = sim_for(dict(w["params"], nx=64, ny=ny, Lx=box(64), Ly=box(ny)))
@@ -689,6 +693,10 @@ def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     if ny not in (512, 1024, 2048, 4096, 8192) or v & abi.GPE_VARIANT_STREAM_COLS:
         assert not v & abi.GPE_VARIANT_PAIR_COLS       # no pair form here, or the streaming pass won
     assert r["row_tile"] in (0, 1) and (r["row_tile"] == 0 or best == 0)
+    if nx not in (2048, 4096, 8192) or best != 0:
+        assert not v & abi.GPE_VARIANT_PAIR_ROWS       # no pair form here, or a persistent pass won
+    if v & abi.GPE_VARIANT_PAIR_ROWS:
+        assert r["row_tile"] == 0
     # stepping with the chosen variants still matches the oracle
     s.step(20, w["dt"], False)
     ref, _ = oracle.evolve(p, psi0.astype(np.complex128), 20, w["dt"], False)
