@@ -55,42 +55,58 @@ __device__ __forceinline__ float2 pot_at2(const PotCoefs &pa, const PotCoefs &pb
     return fma2(w, bc2(t.z), u);
 }
 
-// phase_mul on a packed pair of points: exp(-i theta) (real time, the 1 + d
-// form with the Taylor series of sin and cos of theta/2 for |theta| <= 1) or
-// exp(-theta) (imaginary time), theta = (V + g |psi|^2) h
-__device__ __forceinline__ void phase_mul2(float2 &x, float2 &y, float2 V, float g, float h, int imag)
+// phase_mul (exp(-i theta) in the 1 + d form with the Taylor series of sin
+// and cos of theta/2, or exp(-theta) in imaginary time; theta = (V + g
+// |psi|^2) h) on all E packed pairs of a thread: every theta first, then one
+// branch for the whole thread -- the packed Taylor path unless some |theta|
+// exceeds 1 -- so that the per-element code is one straight line (the rare
+// sincosf path sits in a block of its own instead of beside every element)
+template <int E>
+__device__ __forceinline__ void phase_all2(float2 (&X)[E], float2 (&Y)[E], float2 (&V)[E], float g, float h,
+                                           int imag)
 {
-    const float2 n = fma2(x, x, mul2(y, y));
-    const float2 th = mul2(fma2(bc2(g), n, V), bc2(h));
+    bool small = true;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const float2 n = fma2(X[r], X[r], mul2(Y[r], Y[r]));
+        V[r] = mul2(fma2(bc2(g), n, V[r]), bc2(h));           // V[r] now holds theta
+        small = small && fabsf(V[r].x) <= 1.f && fabsf(V[r].y) <= 1.f;
+    }
     if (imag) {
-        const float2 f = make_float2(expf(-th.x), expf(-th.y));
-        x = mul2(x, f);
-        y = mul2(y, f);
-        return;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 f = make_float2(expf(-V[r].x), expf(-V[r].y));
+            X[r] = mul2(X[r], f);
+            Y[r] = mul2(Y[r], f);
+        }
+    } else if (small) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 w = mul2(bc2(0.5f), V[r]);
+            const float2 v = mul2(w, w);
+            float2 ps = fma2(v, bc2(1.f / 362880.f), bc2(-1.f / 5040.f));
+            ps = fma2(v, ps, bc2(1.f / 120.f));
+            ps = fma2(v, ps, bc2(-1.f / 6.f));
+            const float2 s = fma2(mul2(w, v), ps, w);
+            float2 pc = fma2(v, bc2(1.f / 40320.f), bc2(-1.f / 720.f));
+            pc = fma2(v, pc, bc2(1.f / 24.f));
+            pc = fma2(v, pc, bc2(-0.5f));
+            const float2 c = fma2(v, pc, bc2(1.f));
+            const float2 m2s = mul2(bc2(-2.f), s);
+            const float2 dr = mul2(m2s, s), di = mul2(m2s, c);
+            const float2 nx = add2(X[r], fma2(X[r], dr, mul2(Y[r], make_float2(-di.x, -di.y))));
+            Y[r] = add2(Y[r], fma2(X[r], di, mul2(Y[r], dr)));
+            X[r] = nx;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 r0 = phase_rot(make_float2(X[r].x, Y[r].x), V[r].x);
+            const float2 r1 = phase_rot(make_float2(X[r].y, Y[r].y), V[r].y);
+            X[r] = make_float2(r0.x, r1.x);
+            Y[r] = make_float2(r0.y, r1.y);
+        }
     }
-    if (!(fabsf(th.x) <= 1.f && fabsf(th.y) <= 1.f)) {
-        // lane by lane, as phase_mul does for one point
-        const float2 r0 = phase_mul(make_float2(x.x, y.x), V.x, g, h, 0);
-        const float2 r1 = phase_mul(make_float2(x.y, y.y), V.y, g, h, 0);
-        x = make_float2(r0.x, r1.x);
-        y = make_float2(r0.y, r1.y);
-        return;
-    }
-    const float2 w = mul2(bc2(0.5f), th);
-    const float2 v = mul2(w, w);
-    float2 ps = fma2(v, bc2(1.f / 362880.f), bc2(-1.f / 5040.f));
-    ps = fma2(v, ps, bc2(1.f / 120.f));
-    ps = fma2(v, ps, bc2(-1.f / 6.f));
-    const float2 s = fma2(mul2(w, v), ps, w);
-    float2 pc = fma2(v, bc2(1.f / 40320.f), bc2(-1.f / 720.f));
-    pc = fma2(v, pc, bc2(1.f / 24.f));
-    pc = fma2(v, pc, bc2(-0.5f));
-    const float2 c = fma2(v, pc, bc2(1.f));
-    const float2 m2s = mul2(bc2(-2.f), s);
-    const float2 dr = mul2(m2s, s), di = mul2(m2s, c);
-    const float2 nx = add2(x, fma2(x, dr, mul2(y, make_float2(-di.x, -di.y))));
-    y = add2(y, fma2(x, di, mul2(y, dr)));
-    x = nx;
 }
 
 // T_y's kinetic factor on the pair: real time (p + p d) / N with the 1 + D
@@ -179,16 +195,17 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     if constexpr (MODE == COL_T_P) {
         // the closing half phase alone (each y-table entry read once for both columns)
         const PotCoefs pa = col_coefs(a, __ldg(&T.xtab[c0])), pb = col_coefs(a, __ldg(&T.xtab[c0 + 1]));
+        float2 V[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int yi = j + r * TP;
-            float2 V = pot_at2(pa, pb, __ldg(&T.ytab[yi]));
+            V[r] = pot_at2(pa, pb, __ldg(&T.ytab[yi]));
             if (a.V) {
                 const float2 va = make_float2(__ldg(&a.V[(size_t)yi * a.nx + c0]), __ldg(&a.V[(size_t)yi * a.nx + c0 + 1]));
-                V = fma2(bc2(a.V_scale), va, V);
+                V[r] = fma2(bc2(a.V_scale), va, V[r]);
             }
-            phase_mul2(X[r], Y[r], V, a.g, a.ph.h, a.imag);
         }
+        phase_all2<E>(X, Y, V, a.g, a.ph.h, a.imag);
     }
     if constexpr (REDUCE) {
         // per column: n0 = sum |psi|^2, n1 = sum cos(kc y) |psi|^2 (after the
@@ -200,21 +217,30 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
             pb = col_coefs(a, xb);
         }
         float2 n0 = make_float2(0.f, 0.f), n1 = n0;
+        float cz[E];                                // cos(kc y) of each element
+        if constexpr (MODE == COL_T_PR) {
+            float2 V[E];
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int yi = j + r * TP;
-            const float4 yt = __ldg(&T.ytab[yi]);
-            if constexpr (MODE == COL_T_PR) {
-                float2 V = pot_at2(pa, pb, yt);
+            for (int r = 0; r < E; ++r) {
+                const int yi = j + r * TP;
+                const float4 yt = __ldg(&T.ytab[yi]);
+                cz[r] = yt.z;
+                V[r] = pot_at2(pa, pb, yt);
                 if (a.V) {
                     const float2 va = make_float2(__ldg(&a.V[(size_t)yi * a.nx + c0]), __ldg(&a.V[(size_t)yi * a.nx + c0 + 1]));
-                    V = fma2(bc2(a.V_scale), va, V);
+                    V[r] = fma2(bc2(a.V_scale), va, V[r]);
                 }
-                phase_mul2(X[r], Y[r], V, a.g, a.ph.h, a.imag);
             }
+            phase_all2<E>(X, Y, V, a.g, a.ph.h, a.imag);
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; ++r) cz[r] = __ldg(&T.ytab[j + r * TP]).z;
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
             const float2 n = fma2(X[r], X[r], mul2(Y[r], Y[r]));
             n0 = add2(n0, n);
-            n1 = fma2(bc2(yt.z), n, n1);
+            n1 = fma2(bc2(cz[r]), n, n1);
         }
         q[0] = n0.x + n0.y;
         q[1] = xa.z * n1.x + xb.z * n1.y;
@@ -308,13 +334,14 @@ __global__ void __launch_bounds__(RowPairCfg<N>::TP, RowPairCfg<N>::MIN_CTAS) ro
 
     const PotCoefs pa = row_coefs(a, __ldg(&T.ytab[y0])), pb = row_coefs(a, __ldg(&T.ytab[y0 + 1]));
     const float *Va = a.V ? a.V + (size_t)y0 * N : nullptr;
+    float2 V[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int xi = j + r * TP;
-        float2 V = pot_at2(pa, pb, __ldg(&T.xtab[xi]));
-        if (Va) V = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V);
-        phase_mul2(X[r], Y[r], V, a.g, a.ph.h, a.imag);
+        V[r] = pot_at2(pa, pb, __ldg(&T.xtab[xi]));
+        if (Va) V[r] = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V[r]);
     }
+    phase_all2<E>(X, Y, V, a.g, a.ph.h, a.imag);
     const float4 *tw = C::TW_L1 ? T.twx : stw;
     fft_pair<N, E, false>(X, Y, tile, j, tw);
     kinetic_pair<E, TP>(X, Y, T.kinx, j, a.sx, a.imag);
