@@ -415,7 +415,9 @@ def test_grouped_and_one_shot_row_passes_agree_bitwise(nx, ny, imag):
     outs = []
     for grouped in (True, False):
         s = sim_for(p)
-        base = s.variants & ~abi.GPE_VARIANT_GROUP_ROWS            # the column variant stays as it is
+        # the column variant stays as it is; the pair row pass (which takes
+        # precedence where it is on) is off on both sides
+        base = s.variants & ~(abi.GPE_VARIANT_GROUP_ROWS | abi.GPE_VARIANT_PAIR_ROWS)
         s.variants = base | (abi.GPE_VARIANT_GROUP_ROWS if grouped else 0)
         s.set_psi(psi0)
         s.step(10, 2e-3 if imag else w["dt"], imag)
@@ -431,7 +433,7 @@ def test_default_row_variants_follow_the_row_length():
         assert bool(s.variants & abi.GPE_VARIANT_GROUP_ROWS) == (nx == 2048)
         assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
         assert (s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3 == (1 if nx in (512, 1024) else 0)
-        assert bool(s.variants & abi.GPE_VARIANT_PAIR_ROWS) == (nx == 4096)
+        assert bool(s.variants & abi.GPE_VARIANT_PAIR_ROWS) == (nx >= 2048)
         assert not s.variants & abi.GPE_VARIANT_PAIR_COLS                  # 16-point columns
     for ny in (512, 1024, 2048, 4096, 8192):            # pencil-pair column passes from 2048 points on
         s = sim_for(dict(w["params"], nx=64, ny=ny, Lx=box(64), Ly=box(ny)))
