@@ -157,8 +157,8 @@ def kernel_source_hash():
 def row_kernel_name(n):
     """Kernel of the interior real-time row pass for an n x n grid with a
     context's default variants (the dispatch in gpe_api.cu: pencil-pair pass
-    for rows of 2048 points and more, one-shot otherwise)."""
-    if n >= 2048:
+    for rows of 512 points and more, one-shot otherwise)."""
+    if n >= 512:
         return f"row_pair_kernel<{n}>"
     return f"row_kernel<{n},ROW_PT>"
 

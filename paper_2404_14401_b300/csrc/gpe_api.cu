@@ -437,11 +437,12 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // for the streaming pass; 8192^2: 888 against 943 us); at 512 and 1024
     // the one-pencil pass was as fast or faster
     c->pair_cols = (ny >= 2048 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
-    // the pencil-pair row pass by default for rows of 2048 points and more
-    // (each pass alone: 34.4 against 43.9 us for the grouped pass at 2048^2,
-    // 133 against 181 us for the streaming pass at 4096^2, 918 against 940
-    // us for the one-shot pass at 8192^2)
-    c->pair_rows = (nx >= 2048 && !getenv("GPE_NO_PAIR_ROWS")) ? 1 : 0;
+    // the pencil-pair row pass by default for rows of 512 points and more
+    // (each pass alone, eight grids: 11.8 against 14.6 us at 512^2, 14.6
+    // against 18.4 us at 1024^2, 34.4 against 43.9 us for the grouped pass
+    // at 2048^2, 133 against 181 us for the streaming pass at 4096^2, 918
+    // against 940 us for the one-shot pass at 8192^2)
+    c->pair_rows = (nx >= 512 && !getenv("GPE_NO_PAIR_ROWS")) ? 1 : 0;
     c->launches = 0;
     {
         static std::atomic<unsigned long long> next_uid{1};

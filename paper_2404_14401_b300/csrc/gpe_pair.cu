@@ -374,13 +374,15 @@ template <int N> static cudaError_t row_pair_launch(const PassArgs &a, cudaStrea
     return cudaGetLastError();
 }
 
-// Rows of 2048..8192 points (the grid has at least 8 rows, an even number).
-bool row_pair_ok(int nx, int ny) { return (nx == 2048 || nx == 4096 || nx == 8192) && ny >= 2; }
+// Rows of 512..8192 points (the grid has at least 8 rows, an even number).
+bool row_pair_ok(int nx, int ny) { return nx >= 512 && nx <= 8192 && (nx & (nx - 1)) == 0 && ny >= 2; }
 
 cudaError_t launch_row_pair(const PassArgs &a, cudaStream_t s)
 {
     if (!row_pair_ok(a.nx, a.ny)) return cudaErrorInvalidValue;
     switch (a.nx) {
+    case 512: return row_pair_launch<512>(a, s);
+    case 1024: return row_pair_launch<1024>(a, s);
     case 2048: return row_pair_launch<2048>(a, s);
     case 4096: return row_pair_launch<4096>(a, s);
     case 8192: return row_pair_launch<8192>(a, s);

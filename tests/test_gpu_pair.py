@@ -221,7 +221,7 @@ def sim_rows(p, pair):
     return s
 
 
-@pytest.mark.parametrize("nx,ny", [(2048, 8), (4096, 16), (8192, 8), (2048, 64)])
+@pytest.mark.parametrize("nx,ny", [(512, 16), (1024, 8), (2048, 8), (4096, 16), (8192, 8), (2048, 64), (512, 512)])
 def test_pair_rows_real_time_match_oracle(nx, ny):
     w = gi.lattice_real_time(n=64, L=16.0)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
@@ -258,7 +258,7 @@ def check_rows_oracle(p, psi0, n, dt, imag, cavity=False):
         assert abs(a_gpu - a_ref) < 1e-5 * abs(a_ref)
 
 
-@pytest.mark.parametrize("nx", [2048, 4096])
+@pytest.mark.parametrize("nx", [512, 1024, 2048, 4096])
 def test_pair_rows_imaginary_time_match_oracle(nx):
     """Imaginary time: the row pass scales by 1/sqrt(norm) of the previous
     column pass before its phase."""
@@ -267,7 +267,7 @@ def test_pair_rows_imaginary_time_match_oracle(nx):
     check_rows_oracle(p, gi.gaussian_state(nx, 16, p["Lx"], 10.0, 1.5, 1e-3, seed=320), 40, 2e-3, True)
 
 
-@pytest.mark.parametrize("nx", [2048, 4096])
+@pytest.mark.parametrize("nx", [512, 1024, 2048, 4096])
 def test_pair_rows_cavity_real_time_match_oracle(nx):
     """The V_c and V_i terms of the row phase differ between the two rows of
     a pair through cos(kc y)."""
@@ -289,11 +289,12 @@ def test_pair_rows_lattice_control_and_potential_array():
     check_rows_oracle(p, gi.gaussian_state(nx, ny, p["Lx"], 10.0, 1.5, 1e-3, seed=342), 60, 5e-4, False)
 
 
-@pytest.mark.parametrize("nx,ny,imag", [(2048, 2048, False), (4096, 64, False), (4096, 64, True)])
+@pytest.mark.parametrize("nx,ny,imag", [(512, 64, True), (1024, 1024, False), (2048, 2048, False), (4096, 64, False),
+                                        (4096, 64, True)])
 def test_pair_rows_and_default_rows_agree(nx, ny, imag):
     """The same 12 steps with the pair row pass and with the default row
-    pass of the length (grouped at 2048, streaming at 4096): equal to FP32
-    rounding, one row pass per step either way."""
+    pass of the length (one-shot at 512 and 1024, grouped at 2048, streaming
+    at 4096): equal to FP32 rounding, one row pass per step either way."""
     w = gi.harmonic_trap(n=64, L=10.0, g=100.0) if imag else gi.lattice_real_time(n=64, L=16.0)
     p = dict(w["params"], nx=nx, ny=ny, Lx=box(nx), Ly=box(ny))
     psi0 = c64(gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=350))

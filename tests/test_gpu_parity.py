@@ -433,7 +433,7 @@ def test_default_row_variants_follow_the_row_length():
         assert bool(s.variants & abi.GPE_VARIANT_GROUP_ROWS) == (nx == 2048)
         assert bool(s.variants & abi.GPE_VARIANT_STREAM_ROWS)      # applies where row_stream_ok holds
         assert (s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3 == (1 if nx in (512, 1024) else 0)
-        assert bool(s.variants & abi.GPE_VARIANT_PAIR_ROWS) == (nx >= 2048)
+        assert bool(s.variants & abi.GPE_VARIANT_PAIR_ROWS) == (nx >= 512)
         assert not s.variants & abi.GPE_VARIANT_PAIR_COLS                  # 16-point columns
     for ny in (512, 1024, 2048, 4096, 8192):            # pencil-pair column passes from 2048 points on
         s = sim_for(dict(w["params"], nx=64, ny=ny, Lx=box(64), Ly=box(ny)))
@@ -695,7 +695,7 @@ def test_autotuner_picks_an_applicable_fastest_variant_and_keeps_psi(nx, ny):
     if ny not in (512, 1024, 2048, 4096, 8192) or v & abi.GPE_VARIANT_STREAM_COLS:
         assert not v & abi.GPE_VARIANT_PAIR_COLS       # no pair form here, or the streaming pass won
     assert r["row_tile"] in (0, 1) and (r["row_tile"] == 0 or best == 0)
-    if nx not in (2048, 4096, 8192) or best != 0:
+    if nx not in (512, 1024, 2048, 4096, 8192) or best != 0:
         assert not v & abi.GPE_VARIANT_PAIR_ROWS       # no pair form here, or a persistent pass won
     if v & abi.GPE_VARIANT_PAIR_ROWS:
         assert r["row_tile"] == 0
