@@ -165,9 +165,9 @@ def row_kernel_name(n):
 
 def col_kernel_name(n):
     """Kernel of the interior real-time column pass for an n x n grid with a
-    context's default variants (pencil-pair pass for columns of 2048 points
+    context's default variants (pencil-pair pass for columns of 1024 points
     and more, one-shot one-pencil pass otherwise)."""
-    if n >= 2048:
+    if n >= 1024:
         return f"col_pair_kernel<{n},COL_T>"
     return f"col_kernel<{n},COL_T>"
 

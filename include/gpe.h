@@ -302,13 +302,14 @@ gpe_status gpe_momentum_populations(gpe_ctx *ctx, int axis, double k0, int nmax,
  * tables in shared memory, TMA double buffering), rows and columns of 4096
  * points a streaming persistent variant; every grid has the one-shot
  * variant (a CTA per group of rows or per TMA tile of columns), and the
- * column passes of 512..8192-point columns a pencil-pair form (bit 5).  A
- * context starts with the streaming row pass on where it applies, the
- * grouped row pass on for 2048-point rows only, the half row tile (below)
- * for 512- and 1024-point rows, and the pencil-pair row and column passes
- * for rows and columns of 2048 points and more (the streaming column pass
- * off): with those the passes of other grids overlapped best under
- * gpe_step_many.  The bits select them: */
+ * row and column passes of 512..8192 points a pencil-pair form (bits 5 and
+ * 6).  A context starts with the streaming row pass on where it applies,
+ * the grouped row pass on for 2048-point rows only, the half row tile
+ * (below) for 512- and 1024-point rows, the pencil-pair row pass for rows
+ * of 512 points and more and the pencil-pair column pass for columns of
+ * 1024 points and more (the streaming column pass off): with those the
+ * passes of other grids overlapped best under gpe_step_many.  The bits
+ * select them: */
 enum { GPE_VARIANT_GROUP_ROWS = 1, GPE_VARIANT_STREAM_ROWS = 2, GPE_VARIANT_STREAM_COLS = 4 };
 /* Bits 3-4 (value << GPE_VARIANT_ROW_TILE_SHIFT, value 0..2): on rows of
  * 256 points and more the one-shot row passes of the context's steps,
@@ -320,11 +321,11 @@ enum { GPE_VARIANT_ROW_TILE_SHIFT = 3 };
  * 512..8192-point columns as pencil pairs: both columns of a 2-column tile
  * in one packed f32x2 transform, each table entry read once for both (equal
  * to the one-pencil passes to FP32 rounding).  On by default for columns
- * of 2048 points and more, where it measured faster. */
+ * of 1024 points and more, where it measured faster. */
 enum { GPE_VARIANT_PAIR_COLS = 32 };
-/* Bit 6: the row pass (potential phase + T_x) of 2048..8192-point rows as
+/* Bit 6: the row pass (potential phase + T_x) of 512..8192-point rows as
  * pencil pairs of consecutive rows, one CTA per pair (equal to the
- * one-pencil passes to FP32 rounding).  On by default for rows of 2048
+ * one-pencil passes to FP32 rounding).  On by default for rows of 512
  * points and more, where it measured faster; it takes precedence over bits
  * 0 and 1. */
 enum { GPE_VARIANT_PAIR_ROWS = 64 };

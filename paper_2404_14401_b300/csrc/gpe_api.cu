@@ -431,12 +431,15 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // 512^2 at 56.0 against 53.8; at 2048 the half tile was slower (65.7
     // against 71.7) and at 256 the same
     c->row_tile_shift = (nx == 512 || nx == 1024) ? 1 : 0;
-    // the pencil-pair column passes by default for columns of 2048 points and
-    // more (8 x 2048^2 under gpe_step_many: 69.7 against 67.6 G pt*steps/s,
-    // the T_y pass alone 33.7 against 36.0 us; 4096^2: 126 against 183 us
-    // for the streaming pass; 8192^2: 888 against 943 us); at 512 and 1024
-    // the one-pencil pass was as fast or faster
-    c->pair_cols = (ny >= 2048 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
+    // the pencil-pair column passes by default for columns of 1024 points and
+    // more (8 x 1024^2 under gpe_step_many: 100.1 against 92.2 G pt*steps/s
+    // for the one-pencil pass, although alone each pass timed within 2%; 8 x
+    // 2048^2: 69.7 against 67.6, the T_y pass alone 33.7 against 36.0 us;
+    // 4096^2: 126 against 183 us for the streaming pass; 8192^2: 888 against
+    // 943 us).  At 512 the one-pencil pass stays: one 512^2 grid with the
+    // cavity (a reducing column pass every step) ran 24.6 us per step with it
+    // and 27.6 with the pair pass.
+    c->pair_cols = (ny >= 1024 && !getenv("GPE_NO_PAIR_COLS")) ? 1 : 0;
     // the pencil-pair row pass by default for rows of 512 points and more
     // (each pass alone, eight grids: 11.8 against 14.6 us at 512^2, 14.6
     // against 18.4 us at 1024^2, 34.4 against 43.9 us for the grouped pass

@@ -8,9 +8,9 @@
 // transform, the kinetic factor and the phase is one f32x2 instruction for
 // the two columns, and each twiddle, kinetic-factor and y-table entry is
 // loaded once for both.  Against the one-pencil pass (gpe_kernels.cu) that
-// halves the twiddle reads from shared memory and the table reads through
-// L1, and removes the stride-2 dense tile accesses; the CTA has half the
-// threads (N/16 for a 2-column tile), each with twice the registers.
+// halves the twiddle and table reads, and removes the stride-2 dense tile
+// accesses; the CTA has half the threads (N/16 for a 2-column tile), each
+// with twice the registers.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,24 +25,28 @@
 
 namespace gpe {
 
-template <int N> struct ColPairCfg {
-    static constexpr int E = 16, TP = N / E;       // threads per 2-column tile
-    static constexpr int BR = N < 256 ? N : 256;   // rows per TMA box (the context's tensor map)
-    static constexpr int SLOTS = pad8_len(N);      // 16-byte exchange slots, overlaying the dense tile
-    // twiddles staged in shared memory up to 2048-point columns; the 4096-
-    // and 8192-point tables (65 and 131 KB) are read through L1 instead, so
-    // that two CTAs (one at 8192) fit on an SM
-    static constexpr bool TW_L1 = N >= 4096;
-    static constexpr int TWN = TW_L1 ? 0 : fft_tw_count(N);
-    static constexpr uint32_t TW_BYTES = (uint32_t)TWN * 16u;
-    static constexpr size_t SMEM = (size_t)SLOTS * 16 + TW_BYTES + 128;
+// Shared memory holds the exchange slots alone: the twiddle table is read
+// through L1 at every length.  Staged per CTA (32.6 KB at 2048 points) it
+// held an SM to 3 CTAs of 4 warps; from L1 the registers set the limit, 4
+// CTAs at 2048 points.  Each pass alone ran a little slower (2048: row 34.0
+// -> 34.6 us, column 33.0 -> 34.7 us), but the lockstep step of 8 grids,
+// whose passes share the SMs, ran 95.5 -> 98.1 G pt*steps/s (1024^2: 89.4 ->
+// 93.7).
+template <int N> struct PairOccupancy {
+    static constexpr int E = 16, TP = N / E;       // threads per pencil pair
+    static constexpr int SLOTS = pad8_len(N);      // 16-byte exchange slots, overlaying the dense pair
+    static constexpr size_t SMEM = (size_t)SLOTS * 16 + 128;
     // CTAs per SM the registers are sized for: as many as the shared memory
-    // holds (3 at 2048), but no fewer than 128 registers per thread (2 at
-    // 4096), at most 16
+    // holds, but no fewer than 128 registers per thread (4 CTAs at 2048
+    // points, 2 at 4096, 1 at 8192), at most 16
     static constexpr int BY_SMEM = (int)((224u * 1024u) / (SMEM + 1024));
     static constexpr int BY_REGS = 65536 / (TP * 128);
     static constexpr int CAP = BY_REGS < 16 ? BY_REGS : 16;
     static constexpr int MIN_CTAS = BY_SMEM < CAP ? BY_SMEM : CAP;
+};
+
+template <int N> struct ColPairCfg : PairOccupancy<N> {
+    static constexpr int BR = N < 256 ? N : 256;   // rows per TMA box (the context's tensor map)
 };
 
 // V at the same y of two columns (coefficients pa, pb; y-table entry t), in
@@ -173,20 +177,18 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
 
     const uint32_t s0 = smem_u32(smraw);
     float4 *tile = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));   // [N] {A, B} rows
-    float4 *stw = tile + C::SLOTS;
     const Tables &T = a.T;
     const bool inb = check_index((long long)blockIdx.x * 2 + 1, a.nx, T.sc) &&
-                     check_index((long long)((unsigned char *)(stw + C::TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
+                     check_index((long long)((unsigned char *)(tile + C::SLOTS) - smraw) - 1, dyn_smem_bytes(), T.sc);
     const int c0 = inb ? blockIdx.x * 2 : 0;
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar, (uint32_t)N * 16u + C::TW_BYTES);
-        if constexpr (!C::TW_L1) bulk_load_1d(stw, T.twy, C::TW_BYTES, &bar);
+        mbar_expect_tx(&bar, (uint32_t)N * 16u);
         for (int r0 = 0; r0 < N; r0 += C::BR) tma_load_2d(tile + r0, &map, &bar, 2 * c0, r0);
     }
-    // the tile and the twiddles arrived in time.  Otherwise the copies are
+    // the tile arrived in time.  Otherwise the copies are
     // given time to land, the CTA stores nothing and adds zero partial sums,
     // so that every reduction still counts all of its CTAs.
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins));
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
     }
     __syncthreads();                                // dense reads done before the exchange writes
 
-    transform_pair<N, E, TP>(X, Y, tile, j, C::TW_L1 ? T.twy : stw, T.kiny, a.sy, a.imag);
+    transform_pair<N, E, TP>(X, Y, tile, j, T.twy, T.kiny, a.sy, a.imag);
 
     float q[3] = {0.f, 0.f, 0.f};
     if constexpr (MODE == COL_T_P) {
@@ -290,19 +292,9 @@ __global__ void __launch_bounds__(ColPairCfg<N>::TP, ColPairCfg<N>::MIN_CTAS)
 // consecutive rows as one pencil pair: one CTA of N/16 threads per row pair,
 // the two rows (contiguous in psi) brought in with one bulk copy and written
 // back with one; the coordinate table and kinetic factors of each x are read
-// once for both rows.  Twiddles as in the column pass of the same length.
-template <int N> struct RowPairCfg {
-    static constexpr int E = 16, TP = N / E;
-    static constexpr int SLOTS = pad8_len(N);      // 16-byte exchange slots, overlaying the two dense rows
-    static constexpr bool TW_L1 = N >= 4096;
-    static constexpr int TWN = TW_L1 ? 0 : fft_tw_count(N);
-    static constexpr uint32_t TW_BYTES = (uint32_t)TWN * 16u;
+// once for both rows.  Twiddles through L1 as in the column pass.
+template <int N> struct RowPairCfg : PairOccupancy<N> {
     static constexpr uint32_t ROW_BYTES = 2u * N * 8u;
-    static constexpr size_t SMEM = (size_t)SLOTS * 16 + TW_BYTES + 128;
-    static constexpr int BY_SMEM = (int)((224u * 1024u) / (SMEM + 1024));
-    static constexpr int BY_REGS = 65536 / (TP * 128);
-    static constexpr int CAP = BY_REGS < 16 ? BY_REGS : 16;
-    static constexpr int MIN_CTAS = BY_SMEM < CAP ? BY_SMEM : CAP;
 };
 
 template <int N>
@@ -316,21 +308,19 @@ __global__ void __launch_bounds__(RowPairCfg<N>::TP, RowPairCfg<N>::MIN_CTAS) ro
     const uint32_t s0 = smem_u32(smraw);
     float4 *tile = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
     float2 *rows = reinterpret_cast<float2 *>(tile);                  // row A [0, N), row B [N, 2N)
-    float4 *stw = tile + C::SLOTS;
     const Tables &T = a.T;
     const bool inb = check_index((long long)blockIdx.x * 2 + 1, a.ny, T.sc) &&
-                     check_index((long long)((unsigned char *)(stw + C::TWN) - smraw) - 1, dyn_smem_bytes(), T.sc);
+                     check_index((long long)((unsigned char *)(tile + C::SLOTS) - smraw) - 1, dyn_smem_bytes(), T.sc);
     const int y0 = inb ? blockIdx.x * 2 : 0;
     float2 *src = a.psi + (size_t)y0 * N;
 
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar, C::ROW_BYTES + C::TW_BYTES);
-        if constexpr (!C::TW_L1) bulk_load_1d(stw, T.twx, C::TW_BYTES, &bar);
+        mbar_expect_tx(&bar, C::ROW_BYTES);
         bulk_load_1d(rows, src, C::ROW_BYTES, &bar);
     }
-    // the rows and the twiddles arrived in time; otherwise the copies are
+    // the rows arrived in time; otherwise the copy is
     // given time to land and the CTA stores nothing
     if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, a.spins))) {
         if (threadIdx.x == 0) {
@@ -361,7 +351,7 @@ __global__ void __launch_bounds__(RowPairCfg<N>::TP, RowPairCfg<N>::MIN_CTAS) ro
         if (Va) V[r] = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V[r]);
     }
     phase_all2<E>(X, Y, V, a.g, a.ph.h, a.imag);
-    transform_pair<N, E, TP>(X, Y, tile, j, C::TW_L1 ? T.twx : stw, T.kinx, a.sx, a.imag);
+    transform_pair<N, E, TP>(X, Y, tile, j, T.twx, T.kinx, a.sx, a.imag);
 
     // every exchange read finished at the last stage's barrier
 #pragma unroll

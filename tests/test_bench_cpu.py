@@ -43,7 +43,7 @@ def test_reference_arm_prints_nothing_on_other_ranks():
 @pytest.mark.parametrize("n,row,col", [
     (256, "row_kernel<256,ROW_PT>", "col_kernel<256,COL_T>"),
     (512, "row_pair_kernel<512>", "col_kernel<512,COL_T>"),
-    (1024, "row_pair_kernel<1024>", "col_kernel<1024,COL_T>"),
+    (1024, "row_pair_kernel<1024>", "col_pair_kernel<1024,COL_T>"),
     (2048, "row_pair_kernel<2048>", "col_pair_kernel<2048,COL_T>"),
     (4096, "row_pair_kernel<4096>", "col_pair_kernel<4096,COL_T>"),
     (8192, "row_pair_kernel<8192>", "col_pair_kernel<8192,COL_T>")])

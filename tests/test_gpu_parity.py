@@ -435,9 +435,9 @@ def test_default_row_variants_follow_the_row_length():
         assert (s.variants >> abi.GPE_VARIANT_ROW_TILE_SHIFT) & 3 == (1 if nx in (512, 1024) else 0)
         assert bool(s.variants & abi.GPE_VARIANT_PAIR_ROWS) == (nx >= 512)
         assert not s.variants & abi.GPE_VARIANT_PAIR_COLS                  # 16-point columns
-    for ny in (512, 1024, 2048, 4096, 8192):            # pencil-pair column passes from 2048 points on
+    for ny in (512, 1024, 2048, 4096, 8192):            # pencil-pair column passes from 1024 points on
         s = sim_for(dict(w["params"], nx=64, ny=ny, Lx=box(64), Ly=box(ny)))
-        assert bool(s.variants & abi.GPE_VARIANT_PAIR_COLS) == (ny >= 2048)
+        assert bool(s.variants & abi.GPE_VARIANT_PAIR_COLS) == (ny >= 1024)
         assert not s.variants & abi.GPE_VARIANT_STREAM_COLS
 
 
