@@ -148,7 +148,8 @@ def measured_hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gpe_kernels.cu", "gpe_pair.cu", "gpe_fft.cuh", "gpe_fft2.cuh", "gpe_device.cuh", "gpe_internal.h"):
+    for f in ("gpe_kernels.cu", "gpe_pair.cu", "gpe_pair.cuh", "gpe_fft.cuh", "gpe_fft2.cuh", "gpe_device.cuh",
+              "gpe_internal.h"):
         with open(os.path.join(ROOT, "paper_2404_14401_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -409,6 +410,7 @@ def grids_leg(dev):
     # trajectory, eta ramped 0 -> 3 over 20,000 real-time steps of 2e-4, the
     # whole ramp timed (one gpe_step call: two passes per step, launched per
     # step because eta(t) changes the passes' arguments every step)
+    from paper_2404_14401_b300 import gpe as abi
     w = gi.cavity_ramp()
     p, dt, nramp = w["params"], w["dt"], 20000
     s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
@@ -425,6 +427,25 @@ def grids_leg(dev):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     obs = s.observables()
+    # the same call as one cooperative launch of all 20,000 steps
+    # (GPE_VARIANT_COOP: the passes in one persistent kernel, eta(t) and
+    # alpha evaluated on the device)
+    s.variants = s.variants | abi.GPE_VARIANT_COOP
+    s.set_psi(w["psi0"]().astype(np.complex64))
+    s.t = 0.0
+    s.step(10, dt)
+    s.set_psi(w["psi0"]().astype(np.complex64))
+    s.t = 0.0
+    torch.cuda.synchronize()
+    l0 = s.launches
+    e0.record()
+    s.step(nramp, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    qms = e0.elapsed_time(e1)
+    qlaunches = s.launches - l0
+    qobs = s.observables()
+    s.variants = s.variants & ~abi.GPE_VARIANT_COOP
     # the same ramp as a persistent batch of one: one launch per 2000 steps
     # (eta(t) evaluated on the device)
     from paper_2404_14401_b300 import Batch
@@ -444,6 +465,10 @@ def grids_leg(dev):
     pobs = s.observables()
     one.close()
     cav = {"grid": [512, 512], "trajectories": 1, "steps": nramp, "value": 512 * 512 * nramp / (ms * 1e-3),
+           "path": "per-pass launches (the default)",
+           "cooperative": {"value": 512 * 512 * nramp / (qms * 1e-3), "ms_per_step": qms / nramp,
+                           "gpu_launches": qlaunches, "norm_after": qobs["norm"],
+                           "alpha_abs_after": abs(complex(qobs["alpha_re"], qobs["alpha_im"]))},
            "persistent_batch": {"value": 512 * 512 * nramp / (pms * 1e-3), "ms_per_step": pms / nramp,
                                 "gpu_launches": nramp // 2000, "norm_after": pobs["norm"],
                                 "alpha_abs_after": abs(complex(pobs["alpha_re"], pobs["alpha_im"]))},
@@ -463,22 +488,17 @@ def single_leg(dev, steps=400):
     by gpe_step on one context: the per-grid rate that the batched headline
     does not show.  The 8 MB / 32 MB state fits in L2, so between the timed
     runs a 256 MB buffer is written to flush it; each run's device time is
-    taken with CUDA events and the median of 5 runs is reported."""
+    taken with CUDA events and the median of 5 runs is reported.  At 1024^2
+    the cooperative kernel (one launch per call, GPE_VARIANT_COOP) is timed
+    beside the default per-pass path."""
     import numpy as np
     import torch
 
-    import gpe_inputs as gi
     from paper_2404_14401_b300 import Simulation
+    from paper_2404_14401_b300 import gpe as abi
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    out = []
-    for n in (1024, 2048):
-        w = workload(n)
-        p, dt = w["params"], w["dt"]
-        s = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
-        s.set_potential(p)
-        s.set_psi(w["psi0"]().astype(np.complex64))
-        s.step(2000, 1e-3, imag=True)
-        s.t = 0.0
+
+    def timed(s, n, dt):
         s.step(steps, dt)                               # builds and keeps this call's graph; warm-up
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -490,10 +510,29 @@ def single_leg(dev, steps=400):
             e1.record()
             torch.cuda.synchronize()
             rates.append(n * n * steps / (e0.elapsed_time(e1) * 1e-3))
+        return rates
+
+    out = []
+    for n in (1024, 2048):
+        w = workload(n)
+        p, dt = w["params"], w["dt"]
+        s = Simulation(n, n, p["Lx"], p["Ly"], p["m"], p["g"], device=dev)
+        s.set_potential(p)
+        s.set_psi(w["psi0"]().astype(np.complex64))
+        s.step(2000, 1e-3, imag=True)
+        s.t = 0.0
+        rates = timed(s, n, dt)
         med = statistics.median(rates)
-        out.append({"grid": [n, n], "trajectories": 1, "steps_per_run": steps, "value": med, "unit": UNIT,
-                    "ms_per_step": n * n / med * 1e3, "runs": rates, "status": s.sync(),
-                    "l2": "state fits in L2; a 256 MB write flushes it before each run"})
+        case = {"grid": [n, n], "trajectories": 1, "steps_per_run": steps, "value": med, "unit": UNIT,
+                "ms_per_step": n * n / med * 1e3, "runs": rates, "path": "per-pass launches, graph replay",
+                "l2": "state fits in L2; a 256 MB write flushes it before each run"}
+        if n == 1024:
+            s.variants = s.variants | abi.GPE_VARIANT_COOP
+            q = statistics.median(timed(s, n, dt))
+            case["cooperative"] = {"value": q, "ms_per_step": n * n / q * 1e3}
+            s.variants = s.variants & ~abi.GPE_VARIANT_COOP
+        case["status"] = s.sync()
+        out.append(case)
         del s
     del flush
     torch.cuda.empty_cache()

@@ -329,6 +329,24 @@ enum { GPE_VARIANT_PAIR_COLS = 32 };
  * points and more, where it measured faster; it takes precedence over bits
  * 0 and 1. */
 enum { GPE_VARIANT_PAIR_ROWS = 64 };
+/* Bit 7: gpe_step (or gpe_step_many of one context) on a grid of 512 or
+ * 1024 points per axis runs all n steps as ONE cooperative launch of a
+ * persistent kernel, one CTA per SM: the same passes (pencil-pair row and
+ * column transforms, the pointwise prologue and epilogue passes) separated
+ * by a grid barrier, the phase and reduction arguments evaluated on the
+ * device, psi kept in L2 between passes.  Equal to the per-pass path to
+ * FP32 rounding.  Off by default: on a B300 it measured slower than the
+ * per-pass path (512^2 real time 19.6 against 13.2 us per step, the 512^2
+ * cavity ramp 28.4 against 24.6 us); it takes one host launch per call
+ * instead of two or three per step.  It does not apply while the context
+ * profiles its passes (gpe_profile), when it has more than 256 control
+ * points, for more than 2^22 steps in one call, or while its stream is being
+ * captured; a device that refuses the cooperative launch makes the context
+ * fall back to the per-pass path (gpe_last_error says so).  The barrier's
+ * waits are bounded by the wait limit (gpe_set_wait_limit): one that runs
+ * out latches GPE_ETIMEOUT and ends the launch.  gpe_tune leaves this bit
+ * as it was. */
+enum { GPE_VARIANT_COOP = 128 };
 int gpe_get_pass_variants(const gpe_ctx *ctx);                /* -1 for a null context */
 /* GPE_EINVAL for bits other than those above or a row-tile value above 2 */
 gpe_status gpe_set_pass_variants(gpe_ctx *ctx, int variants);

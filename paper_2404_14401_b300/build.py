@@ -13,8 +13,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = [os.path.join(HERE, "csrc", f) for f in ("gpe_api.cu", "gpe_kernels.cu", "gpe_batch.cu", "gpe_static.cu",
-                                                       "gpe_pair.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("gpe_fft.cuh", "gpe_fft2.cuh", "gpe_device.cuh", "gpe_internal.h")] + [
+                                                       "gpe_pair.cu", "gpe_coop.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("gpe_fft.cuh", "gpe_fft2.cuh", "gpe_device.cuh", "gpe_internal.h",
+                                                       "gpe_pair.cuh", "gpe_ctrl.cuh")] + [
     os.path.join(os.path.dirname(HERE), "include", "gpe.h")]
 LIB = os.path.join(HERE, "libgpe.so")
 DEBUG_LIB = os.path.join(HERE, "libgpe_debug.so")  # -DGPE_DEBUG_BOUNDS=1: index checks that latch GPE_EBOUNDS

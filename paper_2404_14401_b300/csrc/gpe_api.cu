@@ -29,6 +29,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -61,6 +62,7 @@ struct gpe_ctx {
     int group_rows;          // use the grouped persistent row pass where it applies
     int pair_cols;           // use the pencil-pair column pass (T_y) where it applies
     int pair_rows;           // use the pencil-pair row pass where it applies
+    int coop;                // gpe_step on this context alone: the cooperative kernel where it applies
     int row_tile_shift;      // one-shot row pass: 2^-shift of the default rows per CTA (0..2)
     long long launches;
     unsigned long long uid;          // unique over the process (never reused, unlike the pointer)
@@ -446,6 +448,14 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // at 2048^2, 133 against 181 us for the streaming pass at 4096^2, 918
     // against 940 us for the one-shot pass at 8192^2)
     c->pair_rows = (nx >= 512 && !getenv("GPE_NO_PAIR_ROWS")) ? 1 : 0;
+    // the cooperative kernel off by default: on B300 it measured slower than
+    // the per-pass path on every grid it is built for (512^2 real time 19.6
+    // against 13.2 us per step, the 512^2 cavity ramp 28.4 against 24.6,
+    // 1024^2 24.7 against 21.4): each pass waits for the transform of one
+    // pencil pair by one warp (about 7.5 us at 512 points), as the per-pass
+    // kernels do, and a grid barrier costs about 1.2 us, more than the
+    // launch gaps that graph replay leaves between per-pass kernels
+    c->coop = 0;
     c->launches = 0;
     {
         static std::atomic<unsigned long long> next_uid{1};
@@ -595,6 +605,94 @@ gpe_status step_epilogue(gpe_ctx *c, int n, double dt, gpe_mode mode)
         TRY(run_row(c, ROW_SCALE, none, red_at(c, tn), 1, 0));
     }
     c->t = tn;
+    return GPE_OK;
+}
+
+// The cooperative kernel runs gpe_step on one context whose grid it is built
+// for when the context's bit is set (off by default), unless the context
+// profiles its passes (per-pass events), has more control points than the
+// launch arguments carry, or its stream is being captured into a graph.
+bool coop_applies(gpe_ctx *c, int n)
+{
+    // at most 3 barriers per step: the 32-bit arrival count of one launch
+    // stays below 2^32 for n <= 2^22 on any GPU of up to 256 SMs
+    if (!c->coop || c->prof || !coop_ok(c->nx, c->ny) || c->ctrl_t.size() > (size_t)COOP_MAX_CTRL || n > (1 << 22))
+        return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// All n steps of one context in one cooperative launch: the program of
+// step_prologue / step_part / step_epilogue with the phase and reduction
+// arguments evaluated on the device (the kinetic tables for (dt, mode) are
+// made here first, as step_prologue makes them).  If the device refuses the
+// cooperative launch (nothing of it ran), *ran is false and the context
+// keeps to the per-pass path from then on.
+gpe_status step_coop(gpe_ctx *c, int n, double dt, gpe_mode mode, bool *ran)
+{
+    *ran = false;
+    const int imag = mode == GPE_IMAG;
+    if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
+        TRY(timed_launch(c, 2, [&] {
+            return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
+        }, "kinetic tables"));
+        c->kin_valid = true;
+        c->kin_dt = dt;
+        c->kin_mode = (int)mode;
+    }
+    static_assert(sizeof(CoopArgs) < 32000, "launch arguments");
+    std::unique_ptr<CoopArgs> a(new CoopArgs());
+    memset(a.get(), 0, sizeof(CoopArgs));
+    const gpe_potential &p = c->pot;
+    a->psi = c->psi;
+    a->T = c->T;
+    a->V = p.V;
+    a->V_scale = (float)p.V_scale;
+    a->g = (float)c->g;
+    a->sx = (float)(1.0 / c->nx);
+    a->sy = (float)(1.0 / c->ny);
+    a->nx = c->nx;
+    a->ny = c->ny;
+    a->n = n;
+    a->imag = imag;
+    a->spins = c->spins;
+    a->dt = dt;
+    a->t0 = c->t;
+    a->lat_V0x = p.lat_V0x;
+    a->lat_V0y = p.lat_V0y;
+    a->eta = p.eta;
+    a->U0 = p.U0;
+    a->dc = p.dc;
+    a->kappa = p.kappa;
+    a->N = p.N;
+    a->dxdy = (c->Lx / c->nx) * (c->Ly / c->ny);
+    a->probe_omega = p.probe_omega;
+    a->probe_delta = p.probe_delta;
+    a->probe_phi = p.probe_phi;
+    a->cavity = p.cavity;
+    a->pump_lattice = p.pump_lattice;
+    a->ctrl_target = p.ctrl_target;
+    a->nctrl = (int)c->ctrl_t.size();
+    for (int i = 0; i < a->nctrl; ++i) {
+        a->ctrl_t[i] = c->ctrl_t[i];
+        a->ctrl_v[i] = c->ctrl_v[i];
+    }
+    // the barrier's counter, generation and abort flag start at zero
+    TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
+    const cudaError_t e = launch_coop(*a, c->stream);
+    if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
+        cudaGetLastError();
+        c->coop = 0;
+        return fail(c, GPE_OK, "cooperative launch refused (%s): the per-pass path from now on", cudaGetErrorString(e));
+    }
+    TRY(cuda_check(c, e, "cooperative step kernel"));
+    c->launches++;
+    *ran = true;
+    c->t = c->t + n * dt;
     return GPE_OK;
 }
 
@@ -959,6 +1057,11 @@ gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_
             if (ctxs[j] == ctxs[i]) return fail(ctxs[i], GPE_EINVAL, "gpe_step_many: repeated context");
     }
     if (n == 0) return GPE_OK;
+    if (count == 1 && coop_applies(ctxs[0], n)) {
+        bool ran = false;
+        TRY(step_coop(ctxs[0], n, dt, mode, &ran));
+        if (ran) return GPE_OK;
+    }
     // Contexts are spread over the library's lanes: each context's work is
     // ordered after what its own stream held (fork) and its stream waits for
     // that work (join), so the caller sees the usual per-stream ordering
@@ -1224,13 +1327,15 @@ int gpe_get_pass_variants(const gpe_ctx *c)
     if (!c) return -1;
     return (c->group_rows ? GPE_VARIANT_GROUP_ROWS : 0) | (c->stream_passes ? GPE_VARIANT_STREAM_ROWS : 0) |
            (c->stream_cols ? GPE_VARIANT_STREAM_COLS : 0) | (c->row_tile_shift << GPE_VARIANT_ROW_TILE_SHIFT) |
-           (c->pair_cols ? GPE_VARIANT_PAIR_COLS : 0) | (c->pair_rows ? GPE_VARIANT_PAIR_ROWS : 0);
+           (c->pair_cols ? GPE_VARIANT_PAIR_COLS : 0) | (c->pair_rows ? GPE_VARIANT_PAIR_ROWS : 0) |
+           (c->coop ? GPE_VARIANT_COOP : 0);
 }
 
 gpe_status gpe_set_pass_variants(gpe_ctx *c, int v)
 {
     const int known = GPE_VARIANT_GROUP_ROWS | GPE_VARIANT_STREAM_ROWS | GPE_VARIANT_STREAM_COLS |
-                      (3 << GPE_VARIANT_ROW_TILE_SHIFT) | GPE_VARIANT_PAIR_COLS | GPE_VARIANT_PAIR_ROWS;
+                      (3 << GPE_VARIANT_ROW_TILE_SHIFT) | GPE_VARIANT_PAIR_COLS | GPE_VARIANT_PAIR_ROWS |
+                      GPE_VARIANT_COOP;
     if (!c || v < 0 || (v & ~known) || ((v >> GPE_VARIANT_ROW_TILE_SHIFT) & 3) > 2) return GPE_EINVAL;
     c->group_rows = (v & GPE_VARIANT_GROUP_ROWS) != 0;
     c->pair_cols = (v & GPE_VARIANT_PAIR_COLS) != 0;
@@ -1238,6 +1343,7 @@ gpe_status gpe_set_pass_variants(gpe_ctx *c, int v)
     c->stream_passes = (v & GPE_VARIANT_STREAM_ROWS) != 0;
     c->stream_cols = (v & GPE_VARIANT_STREAM_COLS) != 0;
     c->row_tile_shift = (v >> GPE_VARIANT_ROW_TILE_SHIFT) & 3;
+    c->coop = (v & GPE_VARIANT_COOP) != 0;
     c->version++;
     return GPE_OK;
 }
@@ -1326,6 +1432,7 @@ gpe_status gpe_tune(gpe_ctx *c, double dt, gpe_mode mode, void *scratch_dev, siz
     if (pair) t[3] = t_pair;
     if (t[4] == t[4] && t[4] < t[3]) v |= GPE_VARIANT_STREAM_COLS;
     else if (pair) v |= GPE_VARIANT_PAIR_COLS;
+    v |= c->coop ? GPE_VARIANT_COOP : 0;                 // not a per-pass choice: left as it was
     TRY(gpe_set_pass_variants(c, v));
     *variants_out = v;
     if (times_out)

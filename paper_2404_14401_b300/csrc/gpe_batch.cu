@@ -35,6 +35,7 @@
 #include <atomic>
 
 #include "../../include/gpe.h"
+#include "gpe_ctrl.cuh"
 #include "gpe_device.cuh"
 #include "gpe_fft.cuh"
 #include "gpe_internal.h"
@@ -54,74 +55,6 @@ int batch_supported(int nx, int ny, int bt)
     // a row tile holds whole rows; a column tile at least 2 whole columns (a
     // TMA box row of 16 bytes) and at most the grid's width
     return ok(nx) && ok(ny) && rpi >= 1 && rpi <= ny && cpi >= 2 && cpi <= nx;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// ------------------------------------------------------------------ per-pass arguments
-// The piecewise-linear control v(t), the phase and the reduction arguments of
-// a pass at time t, computed as the host scheduler computes them (the same
-// double operations, without contraction into fused multiply-adds).
-__device__ double ctrl_value(const BatchCtx &c, double t)
-{
-    const int n = c.nctrl;
-    if (n == 0) return 1.0;
-    const double *T = c.ctrl_t, *V = c.ctrl_v;
-    if (t <= T[0]) return V[0];
-    if (t >= T[n - 1]) return V[n - 1];
-    int lo = 0, hi = n - 1;                        // T[lo] < t < T[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) / 2;
-        if (T[mid] < t) lo = mid; else hi = mid;
-    }
-    const double f = __ddiv_rn(__dsub_rn(t, T[lo]), __dsub_rn(T[hi], T[lo]));
-    return __dadd_rn(V[lo], __dmul_rn(f, __dsub_rn(V[hi], V[lo])));
-}
-
-__device__ double eta_dev(const BatchCtx &c, double t)
-{
-    return c.ctrl_target == GPE_CTRL_ETA ? ctrl_value(c, t) : c.eta;
-}
-
-__device__ PhaseArgs phase_dev(const BatchCtx &c, double t, double h)
-{
-    const double ls = c.ctrl_target == GPE_CTRL_LATTICE ? ctrl_value(c, t) : 1.0;
-    const double eta = eta_dev(c, t);
-    PhaseArgs a;
-    a.h = (float)h;
-    a.a_latx = (float)__dmul_rn(c.lat_V0x, ls);
-    a.a_laty = (float)__dmul_rn(c.lat_V0y, ls);
-    a.a_pump = (c.cavity && c.pump_lattice && c.U0 != 0.0) ? (float)__ddiv_rn(__dmul_rn(eta, eta), c.U0) : 0.f;
-    a.U0 = c.cavity ? (float)c.U0 : 0.f;
-    a.two_eta = c.cavity ? (float)__dmul_rn(2.0, eta) : 0.f;
-    a.use_alpha = c.cavity ? 1 : 0;
-    return a;
-}
-
-__device__ RedArgs red_dev(const BatchCtx &c, double t)
-{
-    RedArgs r;
-    r.eta = eta_dev(c, t);
-    r.U0 = c.U0;
-    r.dc = c.dc;
-    r.kappa = c.kappa;
-    r.N = c.N;
-    r.dxdy = c.dxdy;
-    r.cavity = c.cavity;
-    r.probe_omega = c.probe_omega;
-    r.probe_delta = c.probe_delta;
-    r.probe_phi = c.probe_phi;
-    r.t = t;
-    return r;
 }
 
 // ------------------------------------------------------------------ the queue

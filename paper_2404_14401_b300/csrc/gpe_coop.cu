@@ -1,0 +1,474 @@
+// gpe_coop.cu -- cooperative persistent kernel (sm_103a): every split step of
+// one gpe_step call (Sec. 3.1, Eqs. 3-4; imaginary time Sec. 3.3; cavity
+// Sec. 5.3, Eqs. 10-15) on one grid that fits on chip, in one launch.
+//
+// The per-pass path launches two or three kernels per step; on a 512^2 grid
+// each of them is a few hundred small CTAs whose time is mostly launch,
+// ramp-up and the latency of one FFT chain.  Here one CTA per SM stays
+// resident for all n steps and runs the host scheduler's pass program itself:
+// a row pass (potential phase, T_x) on pairs of rows, a column pass (T_y
+// [+ closing phase] [+ reductions]) on pairs of columns, and the pointwise
+// prologue / epilogue passes, each pass separated from the next by a grid
+// barrier.  psi stays in L2 between passes (2 MB at 512^2): loads and stores
+// go through L2 (ld.global.cg / st.global.cg), never the non-coherent L1.
+//
+// A group of N/16 threads owns one pencil pair at a time and transforms it
+// with the pair code of the pair passes (gpe_pair.cuh): the two rows (or
+// columns) in packed f32x2 registers, exchanges through the group's own
+// shared-memory slots, synchronised with a named barrier of the group.
+// Reducing passes: each CTA sums its threads' partials in FP64 (fixed tree),
+// stores them, and after the grid barrier every CTA sums all CTAs' partials in
+// the same fixed order and finalises the norm, 1/sqrt(norm) and alpha (Eqs.
+// 14-15) itself, so no second barrier is needed to share them; CTA 0 also
+// writes them to the context's scalars.  Row-pass and column-pass partials use
+// separate arrays, so a reduction's partials are never overwritten before
+// every CTA has read them.
+//
+// The grid barrier: thread 0 of each CTA adds its arrival to a counter that
+// only grows and polls it until every CTA has arrived, with a bounded number
+// of polls.  A wait that runs out latches GPE_ETIMEOUT and raises an abort
+// flag that ends every CTA at its next barrier.  The cooperative launch
+// guarantees that all CTAs are resident, so every wait ends.
+//
+// Measured on a B300 (512^2 lattice, real time): 19.5 us per step, of which
+// about 2.4 us are the two grid barriers and about 15 us the two passes, each
+// the time one warp takes to transform its pencil pair.  The per-pass path
+// takes 13.2 us per step with the same per-pair latency, since graph replay
+// leaves almost no gap between its kernels; so the kernel is a choice for
+// callers that need one launch per call (a busy host, time-dependent
+// controls), not the default.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/gpe.h"
+#include "gpe_ctrl.cuh"
+#include "gpe_device.cuh"
+#include "gpe_fft2.cuh"
+#include "gpe_internal.h"
+#include "gpe_pair.cuh"
+
+namespace gpe {
+
+constexpr int kCT = 256;                                   // threads per CTA
+// exchange slots of the CTA's groups: (256 / TP) groups of pad8_len(N)
+// 16-byte slots, 73,728 bytes whatever the length N = 16 TP
+constexpr size_t kCoopSlotBytes = (size_t)kCT * 16 * 18;
+constexpr size_t kCoopSmem = kCoopSlotBytes + 128;
+
+// The tables and the potential array, read by the passes through a copy in
+// shared memory: a pointer loaded from shared memory after a barrier is new
+// to the compiler at every pass, so it cannot hoist the passes' table loads
+// out of the step loop (which it did from the launch arguments, keeping the
+// kinetic factors and coordinates of every pass live across the whole loop
+// and spilling them).
+struct CoopPtrs {
+    Tables T;
+    const float *V;
+};
+
+template <int N> struct CoopAxis {
+    static constexpr int E = 16, TP = N / E, GPB = kCT / TP, SLOTS = pad8_len(N);
+    static_assert((size_t)GPB * SLOTS * 16 == kCoopSlotBytes, "group slots");
+    static_assert(TP % 32 == 0 && GPB <= 15, "groups of whole warps, one named barrier each");
+};
+
+// ------------------------------------------------------------------ grid barrier
+// Every thread of every CTA calls it, the same number of times (k counts this
+// CTA's barriers in shared memory).  Writes made before it (by any thread of
+// any CTA) are visible, through L2, to reads after it.  The arrival counter
+// only grows: barrier k is complete when it reaches k * gridDim.x, so there
+// is no reset and no second word to release.  Returns false once a wait has
+// run out anywhere (the launch is being abandoned).
+__device__ bool coop_sync(const CoopArgs &a, int *s_ok, unsigned int *k)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DevScalars *sc = a.T.sc;
+        const unsigned int target = (++*k) * gridDim.x;
+        __threadfence();                           // this CTA's writes before the arrival
+        int ok = 1;
+        if (atomicAdd(&sc->bar_count, 1u) + 1u < target) {
+            const int limit = a.spins < (1 << 22) ? a.spins : (1 << 22);
+            int polls = 0;
+            unsigned int ns = 32;
+            while (ld_acquire(&sc->bar_count) < target) {
+                if (polls++ >= limit || ld_acquire(&sc->bar_abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (polls > 64) {                  // back off once the wait is long
+                    __nanosleep(ns);
+                    if (ns < 256) ns *= 2;
+                }
+            }
+        }
+        if (!ok) {
+            latch_status(sc, GPE_ETIMEOUT);
+            atomicExch(&sc->bar_abort, 1u);
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Finish a reducing pass: the CTA's FP64 partials (norm, O and B sums) into
+// part[blockIdx.x], the grid barrier, then every CTA sums all partials in
+// block order and finalises norm, c and alpha into its own copy `loc`; CTA 0
+// also writes them to the context's scalars.
+__device__ bool coop_reduce(const CoopArgs &a, const float (&q)[3], const RedArgs &rd, double *part, DevScalars *loc,
+                            double *red, int *s_ok, unsigned int *k)
+{
+    block_sum<3>(q, part + (size_t)blockIdx.x * NQ, red);
+    if (!coop_sync(a, s_ok, k)) return false;
+    double S[3];
+    sum_partials<3>(part, (int)gridDim.x, S, red);
+    if (threadIdx.x == 0) {
+        finalize_fields(S, rd, loc);
+        if (blockIdx.x == 0) {
+            DevScalars *sc = a.T.sc;
+            sc->norm = loc->norm;
+            sc->O = loc->O;
+            sc->B = loc->B;
+            sc->c = loc->c;
+            sc->alpha_re = loc->alpha_re;
+            sc->alpha_im = loc->alpha_im;
+            if (loc->status) latch_status(sc, loc->status);
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------------------ passes
+// The pass functions are not inlined into the kernel: compiled as one
+// function, the kernel's five transforming passes kept enough values live
+// across the step loop to spill 1-3 KB at 128 and 255 registers per thread;
+// out of line each pass gets its own allocation and spills at most 20 bytes.
+//
+// Units (pencil pairs) are dealt to groups CTA-first: unit u goes to CTA
+// u mod gridDim.x, so a pass narrower than the grid's groups spreads over
+// every SM.  Every group runs the same number of rounds (a group without a
+// unit in a round transforms zeros and stores nothing), so the named
+// barriers inside the transform see all of their threads.
+// The thread's and the CTA's index are read with volatile moves at every
+// pass, so that the index and address arithmetic derived from them (the
+// exchange-slot offsets of every stage, the elements' offsets) is pass-local
+// for the compiler rather than hoisted out of the step loop and kept live
+// across all passes.
+__device__ __forceinline__ int tid_fresh()
+{
+    int t;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+    return t;
+}
+__device__ __forceinline__ int cta_fresh()
+{
+    int b;
+    asm volatile("mov.u32 %0, %%ctaid.x;" : "=r"(b));
+    return b;
+}
+
+template <int N> struct CoopUnits {
+    int g, j, gg, G, rounds;
+    __device__ CoopUnits(int units)
+    {
+        using A = CoopAxis<N>;
+        const int t = tid_fresh();
+        g = t / A::TP;
+        j = t % A::TP;
+        gg = cta_fresh() + gridDim.x * g;
+        G = gridDim.x * A::GPB;
+        rounds = (units + G - 1) / G;
+    }
+};
+
+// Row pass ROW_PT on the row pairs (2u, 2u + 1): [scale c] potential phase,
+// T_x, as row_pair_kernel computes it.
+template <int N>
+__device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, int use_c,
+                             const DevScalars &loc, float4 *slots)
+{
+    const Tables &T = P.T;
+    using A = CoopAxis<N>;
+    constexpr int E = A::E, TP = A::TP;
+    const int units = a.ny / 2;
+    const CoopUnits<N> U(units);
+    float4 *sb = slots + U.g * A::SLOTS;
+    const GroupSync gs{1 + U.g, TP};
+    const float cs = use_c ? (float)loc.c : 1.f;
+    float acx2, acxcy;
+    alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
+    for (int it = 0; it < U.rounds; ++it) {
+        const int u = U.gg + it * U.G;
+        const bool act = u < units && check_index((long long)2 * u + 1, a.ny, T.sc);
+        const int y0 = act ? 2 * u : 0;
+        float2 *ra = a.psi + (size_t)y0 * N, *rb = ra + N;
+        float2 X[E], Y[E], V[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = U.j + r * TP;
+            const float2 p = act ? __ldcg(ra + xi) : make_float2(0.f, 0.f);
+            const float2 q = act ? __ldcg(rb + xi) : make_float2(0.f, 0.f);
+            X[r] = make_float2(p.x * cs, q.x * cs);
+            Y[r] = make_float2(p.y * cs, q.y * cs);
+        }
+        const PotCoefs pa = row_coefs_from(ph, acx2, acxcy, __ldg(&T.ytab[y0]));
+        const PotCoefs pb = row_coefs_from(ph, acx2, acxcy, __ldg(&T.ytab[y0 + 1]));
+        const float *Va = P.V ? P.V + (size_t)y0 * N : nullptr;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = U.j + r * TP;
+            V[r] = pot_at2(pa, pb, __ldg(&T.xtab[xi]));
+            if (Va) V[r] = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V[r]);
+        }
+        phase_all2<E>(X, Y, V, a.g, ph.h, a.imag);
+        transform_pair<N, E, TP>(X, Y, sb, U.j, T.twx, T.kinx, a.sx, a.imag, gs);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int xi = U.j + r * TP;
+                __stcg(ra + xi, make_float2(X[r].x, Y[r].x));
+                __stcg(rb + xi, make_float2(X[r].y, Y[r].y));
+            }
+        }
+    }
+}
+
+// Column pass on the column pairs (2u, 2u + 1) of columns of N points in a
+// grid NX wide, as col_pair_kernel computes it: T_y, then (COL_T_P,
+// COL_T_PR) the closing half phase, then (COL_T_R, COL_T_PR) the norm and
+// overlap sums added to q.  With the width a constant, a thread's 16 strided
+// elements are immediate offsets from one address.
+template <int N, int NX, int MODE>
+__device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, const DevScalars &loc,
+                          float4 *slots, float (&q)[3])
+{
+    const Tables &T = P.T;
+    using A = CoopAxis<N>;
+    constexpr int E = A::E, TP = A::TP;
+    constexpr bool PHASE = (MODE == COL_T_P || MODE == COL_T_PR);
+    constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
+    constexpr int units = NX / 2, w4 = NX / 2;                 // float4 per grid row
+    const CoopUnits<N> U(units);
+    float4 *sb = slots + U.g * A::SLOTS;
+    const GroupSync gs{1 + U.g, TP};
+    float acx2, acxcy;
+    alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
+    for (int it = 0; it < U.rounds; ++it) {
+        const int u = U.gg + it * U.G;
+        const bool act = u < units && check_index((long long)2 * u + 1, NX, T.sc);
+        const int x0 = act ? 2 * u : 0;
+        // {re, im} of columns x0, x0 + 1 at row j + r TP: cb[r TP w4]
+        float4 *cb = reinterpret_cast<float4 *>(a.psi + x0) + (size_t)U.j * w4;
+        float2 X[E], Y[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float4 t = act ? __ldcg(cb + r * TP * w4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            X[r] = make_float2(t.x, t.z);
+            Y[r] = make_float2(t.y, t.w);
+        }
+        transform_pair<N, E, TP>(X, Y, sb, U.j, T.twy, T.kiny, a.sy, a.imag, gs);
+        const float4 xa = __ldg(&T.xtab[x0]), xb = __ldg(&T.xtab[x0 + 1]);
+        if constexpr (PHASE) {
+            const PotCoefs pa = col_coefs_from(ph, acx2, acxcy, xa), pb = col_coefs_from(ph, acx2, acxcy, xb);
+            float2 V[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int y = U.j + r * TP;
+                V[r] = pot_at2(pa, pb, __ldg(&T.ytab[y]));
+                if (P.V) {
+                    const float2 va = make_float2(__ldg(&P.V[(size_t)y * NX + x0]), __ldg(&P.V[(size_t)y * NX + x0 + 1]));
+                    V[r] = fma2(bc2(a.V_scale), va, V[r]);
+                }
+            }
+            phase_all2<E>(X, Y, V, a.g, ph.h, a.imag);
+        }
+        if constexpr (REDUCE) {
+            float2 n0 = make_float2(0.f, 0.f), n1 = n0;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float2 nn = fma2(X[r], X[r], mul2(Y[r], Y[r]));
+                n0 = add2(n0, nn);
+                n1 = fma2(bc2(__ldg(&T.ytab[U.j + r * TP]).z), nn, n1);
+            }
+            if (act) {
+                q[0] += n0.x + n0.y;
+                q[1] += xa.z * n1.x + xb.z * n1.y;
+                q[2] += xa.z * xa.z * n0.x + xb.z * xb.z * n0.y;
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) __stcg(cb + r * TP * w4, make_float4(X[r].x, Y[r].x, X[r].y, Y[r].y));
+        }
+    }
+}
+
+// Pointwise row passes over the whole grid (grid-stride): ROW_PHASE (the
+// closing half phase), ROW_PHASE_R (the same, then the sums), ROW_REDUCE_R
+// (the sums only, nothing stored), ROW_SCALE (multiply by c).  Point
+// arithmetic as in row_kernel.
+template <int NX, int MODE>
+__device__ __noinline__ void coop_points(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, const DevScalars &loc,
+                            float (&q)[3])
+{
+    const Tables &T = P.T;
+    constexpr bool PHASE = (MODE == ROW_PHASE || MODE == ROW_PHASE_R);
+    constexpr bool REDUCE = (MODE == ROW_PHASE_R || MODE == ROW_REDUCE_R);
+    const int total = NX * a.ny;
+    float acx2, acxcy;
+    alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
+    const float cs = (float)loc.c;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int x = idx & (NX - 1), y = idx / NX;
+        float2 v = __ldcg(a.psi + idx);
+        const float4 xt = __ldg(&T.xtab[x]);
+        if constexpr (MODE == ROW_SCALE) v = make_float2(v.x * cs, v.y * cs);
+        if constexpr (PHASE) {
+            const PotCoefs pc = row_coefs_from(ph, acx2, acxcy, __ldg(&T.ytab[y]));
+            float V = pot_at(pc, xt);
+            if (P.V) V += a.V_scale * __ldg(&P.V[idx]);
+            v = phase_mul(v, V, a.g, ph.h, a.imag);
+        }
+        if constexpr (REDUCE) {
+            const float n = v.x * v.x + v.y * v.y, cy = __ldg(&T.ytab[y]).z;
+            q[0] += n;
+            q[1] += xt.z * cy * n;
+            q[2] += xt.z * xt.z * n;
+        }
+        if constexpr (MODE != ROW_REDUCE_R) __stcg(a.psi + idx, v);
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+// The program of step_prologue (alpha of the initial density), n x step_part
+// and step_epilogue, with the same pass times, phase lengths and modes.
+template <int NX, int NY>
+__global__ void __launch_bounds__(kCT, 1) coop_kernel(const __grid_constant__ CoopArgs a)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32 * NQ];
+    __shared__ DevScalars loc;                     // c and alpha of the last reduction, the same in every CTA
+    __shared__ PhaseArgs s_ph;
+    __shared__ RedArgs s_rd;
+    __shared__ CoopPtrs s_P;
+    __shared__ int s_ok;
+    __shared__ unsigned int s_k;                   // grid barriers this CTA has passed
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *slots = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    if (threadIdx.x == 0) {
+        memset(&loc, 0, sizeof(loc));
+        loc.c = __ldcg(&a.T.sc->c);
+        loc.alpha_re = __ldcg(&a.T.sc->alpha_re);
+        loc.alpha_im = __ldcg(&a.T.sc->alpha_im);
+        memset(&s_ph, 0, sizeof(s_ph));
+        s_k = 0;
+        s_P.T = a.T;
+        s_P.V = a.V;
+        s_ok = check_index((long long)((unsigned char *)slots + kCoopSlotBytes - smraw) - 1, dyn_smem_bytes(),
+                           a.T.sc);
+        if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
+    }
+    __syncthreads();
+    if (!s_ok) return;                             // the others stop at their first barrier
+
+    const double t0 = a.t0, dt = a.dt, hh = __dmul_rn(0.5, dt);
+    const int n = a.n, imag = a.imag, cav = a.cavity;
+    float q[3];
+    bool ok = true;
+    if (cav) {                                     // alpha of the initial density (Eq. 14)
+        if (threadIdx.x == 0) s_rd = red_dev(a, t0);
+        __syncthreads();
+        q[0] = q[1] = q[2] = 0.f;
+        coop_points<NX, ROW_REDUCE_R>(a, s_P, s_ph, loc, q);
+        ok = coop_reduce(a, q, s_rd, a.T.part_row, &loc, red, &s_ok, &s_k);
+    }
+    for (int s = 0; ok && s < n; ++s) {
+        const double ts = __dadd_rn(t0, __dmul_rn((double)s, dt));
+        const double te = __dadd_rn(t0, __dmul_rn((double)(s + 1), dt));
+        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, (imag || s == 0) ? hh : dt);
+        __syncthreads();
+        coop_rows_pt<NX>(a, s_P, s_ph, imag && s > 0, loc, slots);
+        if (!coop_sync(a, &s_ok, &s_k)) {
+            ok = false;
+            break;
+        }
+        q[0] = q[1] = q[2] = 0.f;
+        if (!imag && !cav) {
+            if (s == n - 1) {
+                if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
+                __syncthreads();
+                coop_cols<NY, NX, COL_T_P>(a, s_P, s_ph, loc, slots, q);
+            } else {
+                coop_cols<NY, NX, COL_T>(a, s_P, s_ph, loc, slots, q);
+                ok = coop_sync(a, &s_ok, &s_k);
+            }
+        } else if (!imag) {
+            if (threadIdx.x == 0) s_rd = red_dev(a, te);
+            __syncthreads();
+            coop_cols<NY, NX, COL_T_R>(a, s_P, s_ph, loc, slots, q);
+            ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
+        } else if (!cav) {
+            if (threadIdx.x == 0) {
+                s_ph = phase_dev(a, te, hh);
+                s_rd = red_dev(a, te);
+            }
+            __syncthreads();
+            coop_cols<NY, NX, COL_T_PR>(a, s_P, s_ph, loc, slots, q);
+            ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
+        } else {                                   // imaginary time with a cavity: a third, pointwise pass
+            if (threadIdx.x == 0) s_rd = red_dev(a, te);
+            __syncthreads();
+            coop_cols<NY, NX, COL_T_R>(a, s_P, s_ph, loc, slots, q);
+            ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
+            if (!ok) break;
+            if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
+            __syncthreads();
+            q[0] = q[1] = q[2] = 0.f;
+            coop_points<NX, ROW_PHASE_R>(a, s_P, s_ph, loc, q);
+            ok = coop_reduce(a, q, s_rd, a.T.part_row, &loc, red, &s_ok, &s_k);
+        }
+    }
+    if (!ok) return;
+    const double tn = __dadd_rn(t0, __dmul_rn((double)n, dt));
+    if (!imag && cav) {                            // the closing half phase with alpha of the final density
+        if (threadIdx.x == 0) s_ph = phase_dev(a, tn, hh);
+        __syncthreads();
+        coop_points<NX, ROW_PHASE>(a, s_P, s_ph, loc, q);
+    } else if (imag) {                             // the pending normalisation
+        coop_points<NX, ROW_SCALE>(a, s_P, s_ph, loc, q);
+    }
+}
+
+// ------------------------------------------------------------------ launch
+bool coop_ok(int nx, int ny) { return (nx == 512 || nx == 1024) && (ny == 512 || ny == 1024); }
+
+template <int NX, int NY> static cudaError_t coop_launch(const CoopArgs &a, cudaStream_t s)
+{
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_opt_in(coop_kernel<NX, NY>, (int)kCoopSmem, attr);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coop_kernel<NX, NY>, kCT, kCoopSmem);
+    if (r != cudaSuccess) return r;
+    if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = sm_count();                   // one CTA per SM, all resident
+    if (grid < 1) return cudaErrorInvalidValue;
+    void *args[] = {const_cast<CoopArgs *>(&a)};
+    return cudaLaunchCooperativeKernel((const void *)coop_kernel<NX, NY>, dim3(grid), dim3(kCT), args, kCoopSmem, s);
+}
+
+cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s)
+{
+    if (!coop_ok(a.nx, a.ny) || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL) return cudaErrorInvalidValue;
+    if (a.nx == 512) return a.ny == 512 ? coop_launch<512, 512>(a, s) : coop_launch<512, 1024>(a, s);
+    return a.ny == 512 ? coop_launch<1024, 512>(a, s) : coop_launch<1024, 1024>(a, s);
+}
+
+}  // namespace gpe

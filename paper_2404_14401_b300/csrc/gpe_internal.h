@@ -22,6 +22,9 @@ struct DevScalars {
     unsigned int ticket[2];        // last-CTA counters (row / column kernels)
     int status;                    // first device error (gpe_status), 0 = none
     int pad;
+    // grid barrier of the cooperative kernel (gpe_coop.cu): arrivals so far
+    // in the launch and the abort flag, zeroed before each launch
+    unsigned int bar_count, bar_abort;
 };
 
 // Device pointers into the caller's workspace.
@@ -141,6 +144,30 @@ int batch_resident_ctas(int bt);          // CTAs of a batch-kernel variant that
 int batch_supported(int nx, int ny, int bt);   // 1 if a context of this size can join a batch of bt-thread tiles
 int batch_rows_per_item(int n, int bt);   // rows (of n points) in a row tile; columns of length n in a column tile
 long long batch_queue_length(int n, int imag, int cavity, int row_items, int col_items);
+
+// ---- Cooperative single-grid kernel (gpe_coop.cu): all n steps of one
+// context whose grid fits on chip in one cooperative launch, one CTA per SM;
+// the passes of the host scheduler's program (step_prologue / step_part /
+// step_epilogue, minus the kinetic tables) separated by a grid barrier with
+// bounded waits, the FP64 reductions finished by every CTA from the per-CTA
+// partials in the same fixed order.
+constexpr int COOP_MAX_CTRL = 256; // control points carried in the launch arguments
+struct CoopArgs {
+    float2 *psi;
+    Tables T;
+    const float *V;
+    float V_scale, g, sx, sy;
+    int nx, ny;
+    int n, imag, spins;
+    double dt, t0;
+    // potential parameters for the per-pass phase and reduction arguments,
+    // evaluated on the device as the host scheduler does (phase_at, red_at)
+    double lat_V0x, lat_V0y, eta, U0, dc, kappa, N, dxdy, probe_omega, probe_delta, probe_phi;
+    int cavity, pump_lattice, ctrl_target, nctrl;
+    double ctrl_t[COOP_MAX_CTRL], ctrl_v[COOP_MAX_CTRL];
+};
+bool coop_ok(int nx, int ny);              // grid sizes the cooperative kernel is built for
+cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s);
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
 // tile_shift: the one-shot row pass takes 2^-tile_shift of its default rows

@@ -248,7 +248,8 @@ def gpe_momentum_populations(ctx, axis: int, k0: float, nmax: int, scratch_ptr: 
 GPE_VARIANT_GROUP_ROWS, GPE_VARIANT_STREAM_ROWS, GPE_VARIANT_STREAM_COLS = 1, 2, 4
 GPE_VARIANT_ROW_TILE_SHIFT = 3          # bits 3-4: one-shot row pass at 2^-value of its default rows per CTA
 GPE_VARIANT_PAIR_COLS = 32              # column passes as pencil pairs (512..8192-point columns)
-GPE_VARIANT_PAIR_ROWS = 64              # row pass (phase + T_x) on pairs of rows (2048..8192 points)
+GPE_VARIANT_PAIR_ROWS = 64              # row pass (phase + T_x) on pairs of rows (512..8192 points)
+GPE_VARIANT_COOP = 128                  # gpe_step of one 512/1024-point grid: one cooperative persistent launch
 
 
 def gpe_get_pass_variants(ctx) -> int:

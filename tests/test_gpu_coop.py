@@ -1,0 +1,215 @@
+"""Cooperative persistent step kernel (GPE_VARIANT_COOP): every split step of
+one gpe_step call on a grid of 512 or 1024 points per axis in ONE cooperative
+launch, the passes separated by a grid barrier (Sec. 3.1 steps, Sec. 3.3
+renormalisation, Sec. 5.3 cavity field, Eqs. 14-15).
+
+Against the FP64 oracle in every program the kernel runs (real time with and
+without the cavity, imaginary time with and without it, a time-dependent
+control with a potential array, rectangular grids), against the per-pass
+path of the same context (equal to FP32 rounding), and for its launch count,
+its defaults, its fall-backs and a barrier wait that runs out.  Tolerances as
+in test_gpu_parity.
+"""
+import numpy as np
+import pytest
+
+import gpe_inputs as gi
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def state_tol(n):
+    return max(1e-5, 1e-4 * n / 1000)
+
+
+def c64(a):
+    return np.asarray(a, dtype=np.complex64)
+
+
+def sim_for(p, coop=True):
+    from paper_2404_14401_b300 import Simulation
+    from paper_2404_14401_b300 import gpe as abi
+    s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+    s.set_potential(p)
+    v = s.variants & ~abi.GPE_VARIANT_COOP
+    s.variants = v | (abi.GPE_VARIANT_COOP if coop else 0)
+    return s
+
+
+def lattice(nx, ny):
+    w = gi.lattice_real_time(n=64, L=16.0)
+    return dict(w["params"], nx=nx, ny=ny, Lx=0.02 * nx, Ly=0.02 * ny)
+
+
+def check_oracle(p, psi0, n, dt, imag, t0=0.0, cavity=False):
+    s = sim_for(p)
+    s.set_psi(c64(psi0))
+    s.t = t0
+    launches = s.launches
+    s.step(n, dt, imag)
+    assert s.launches - launches <= 2                 # the kinetic tables, then the one cooperative launch
+    got, obs = s.get_psi(), s.observables()
+    assert s.sync() == 0
+    assert abs(s.t - (t0 + n * dt)) < 1e-12
+    ref, _ = oracle.evolve(p, c64(psi0).astype(np.complex128), n, dt, imag, t0=t0)
+    ro = oracle.observables(p, ref, t=s.t)
+    assert rel_l2(got, ref) < state_tol(n)
+    assert abs(obs["norm"] - (1.0 if imag else ro["norm"])) < 1e-6
+    for k in ("energy", "mu"):
+        assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+    if cavity:
+        a_gpu, a_ref = complex(obs["alpha_re"], obs["alpha_im"]), complex(ro["alpha_re"], ro["alpha_im"])
+        assert abs(a_ref) > 1e-3
+        assert abs(a_gpu - a_ref) < 1e-5 * abs(a_ref)
+        for k in ("O", "B"):
+            assert abs(obs[k] - ro[k]) < 1e-5 * abs(ro[k]), k
+    return s
+
+
+@pytest.mark.parametrize("nx,ny,n", [(512, 512, 100), (1024, 512, 60), (512, 1024, 60), (1024, 1024, 40)])
+def test_coop_real_time_matches_oracle(nx, ny, n):
+    """Real time without cavity: row passes on row pairs, column passes on
+    column pairs, the closing half phase in the last column pass."""
+    p = lattice(nx, ny)
+    check_oracle(p, gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=400 + nx + ny), n, 5e-4, False)
+
+
+def test_coop_cavity_ramp_matches_oracle():
+    """The 512^2 cavity ramp at step 18,000 (eta = 2.7, a checkerboard
+    density, |alpha| > 0.01): alpha of the initial density in the kernel's
+    prologue, the overlaps reduced in every column pass and finished by every
+    CTA, the closing half phase with the final alpha in its epilogue."""
+    w = gi.cavity_ramp()
+    p, dt = w["params"], w["dt"]
+    psi0 = gi.gaussian_state(512, 512, 40.0, 40.0, 1.5, 1e-3, seed=2, checker=0.3, kc=p["kc"])
+    check_oracle(p, psi0, 200, dt, False, t0=18000 * dt, cavity=True)
+
+
+def test_coop_imaginary_time_matches_oracle():
+    """Imaginary time: the closing half phase and the norm in the column
+    pass, 1/sqrt(norm) applied by the next row pass and by the epilogue."""
+    w = gi.harmonic_trap(n=512, L=20.0, g=100.0)
+    p = w["params"]
+    check_oracle(p, w["psi0"](), 200, 1e-3, True)
+
+
+@pytest.mark.parametrize("nx,ny", [(512, 512), (1024, 512)])
+def test_coop_imaginary_time_cavity_matches_oracle(nx, ny):
+    """Imaginary time with the cavity: three passes per step, the third a
+    pointwise closing phase with alpha of the new density that reduces again
+    (its partial sums in the row array, while the column reduction's are
+    still being read)."""
+    ws = gi.phase_diagram_sweep()
+    w = max((v for v in ws if v["params"]["nx"] == 512), key=lambda v: v["params"]["eta"])
+    p = dict(w["params"], nx=nx, ny=ny, Lx=20.0 * nx / 512, Ly=20.0 * ny / 512)
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=410, checker=0.1, kc=p["kc"])
+    check_oracle(p, psi0, 50, 1e-3, True, cavity=True)
+
+
+def test_coop_lattice_control_and_potential_array():
+    """A 200-point lattice-depth control evaluated on the device at every
+    pass, and a static potential array (the two rows, and the two columns, of
+    a pair read different entries)."""
+    nx, ny = 512, 1024
+    p = gi.potential_defaults()
+    t, v = gi.control_points(seed=420, n=200, T=0.03, lo=0.0, hi=8.0)
+    Varr = (0.5 * gi.normal(421, nx * ny).reshape(ny, nx)).astype(np.float32).astype(np.float64)
+    p.update(nx=nx, ny=ny, Lx=10.24, Ly=20.48, m=1.0, g=500.0, wx=1.0, wy=1.0, lat_V0x=1.0, lat_V0y=1.0,
+             lat_kx=2 * np.pi, lat_ky=2 * np.pi, ctrl_target=1, ctrl_t=t, ctrl_v=v, Varr=Varr, V_scale=0.7)
+    check_oracle(p, gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.5, 1e-3, seed=422), 60, 5e-4, False)
+
+
+@pytest.mark.parametrize("mode", ["real cavity", "imaginary"])
+def test_coop_agrees_with_per_pass_path(mode):
+    """The same 20 steps through the cooperative kernel and through the
+    per-pass path: equal to FP32 rounding (the reductions sum in another
+    order, the 512-point column pass differs in form)."""
+    if mode == "real cavity":
+        w = gi.cavity_ramp()
+        p, dt, imag = w["params"], w["dt"], False
+        psi0 = gi.gaussian_state(512, 512, 40.0, 40.0, 1.5, 1e-3, seed=430, checker=0.3, kc=p["kc"])
+    else:
+        w = gi.harmonic_trap(n=512, L=20.0, g=100.0)
+        p, dt, imag = w["params"], 1e-3, True
+        psi0 = w["psi0"]()
+    outs, obs, calls = [], [], []
+    for coop in (True, False):
+        s = sim_for(p, coop)
+        s.set_psi(c64(psi0))
+        s.t = 18000 * dt if mode == "real cavity" else 0.0
+        l0 = s.launches
+        s.step(20, dt, imag)
+        calls.append(s.launches - l0)
+        outs.append(s.get_psi())
+        obs.append(s.observables())
+        assert s.sync() == 0
+    assert calls[0] <= 2 < calls[1]
+    assert rel_l2(outs[0], outs[1]) < 1e-6
+    for k in ("norm", "energy") + (("alpha_re", "O", "B") if mode == "real cavity" else ()):
+        assert abs(obs[0][k] - obs[1][k]) < 1e-6 * abs(obs[1][k]), k
+
+
+def test_coop_wait_limit_runs_out_and_context_recovers():
+    """With a wait limit of 0 the first CTA that has to wait at the grid
+    barrier gives up at once: GPE_ETIMEOUT is latched, the abort flag ends
+    every CTA at its next barrier, and the launch returns.  After gpe_sync
+    and a normal limit the next call starts from clean barrier words and
+    matches the oracle from the state psi then holds."""
+    from paper_2404_14401_b300 import gpe as abi
+    p = lattice(512, 512)
+    s = sim_for(p)
+    s.set_psi(c64(gi.gaussian_state(512, 512, p["Lx"], p["Ly"], 1.5, 1e-3, seed=440)))
+    abi.gpe_set_wait_limit(s.ctx, 0)
+    s.step(5, 5e-4)
+    assert s.sync() == abi.GPE_ETIMEOUT
+    assert s.sync() == abi.GPE_OK
+    abi.gpe_set_wait_limit(s.ctx, 1 << 24)
+    cur, t0 = s.get_psi(), s.t
+    assert np.all(np.isfinite(cur))
+    s.step(30, 5e-4)
+    assert s.sync() == abi.GPE_OK
+    ref, _ = oracle.evolve(p, cur.astype(np.complex128), 30, 5e-4, False, t0=t0)
+    assert rel_l2(s.get_psi(), ref) < state_tol(30)
+
+
+def test_coop_defaults_and_fallbacks():
+    """Off by default; set, the bit sticks and gpe_tune keeps it; a
+    profiling context and a batch of two contexts take the per-pass path;
+    on a grid it is not built for the bit changes nothing."""
+    from paper_2404_14401_b300 import Simulation
+    from paper_2404_14401_b300 import gpe as abi
+    for nx, ny in ((512, 512), (1024, 1024), (512, 1024), (256, 256), (2048, 2048), (256, 512)):
+        p = lattice(nx, ny)
+        s = Simulation(nx, ny, p["Lx"], p["Ly"], p["m"], p["g"])
+        assert not s.variants & abi.GPE_VARIANT_COOP, (nx, ny)
+    p = lattice(256, 256)
+    s = sim_for(p)
+    s.set_psi(c64(gi.gaussian_state(256, 256, p["Lx"], p["Ly"], 1.5, 1e-3, seed=449)))
+    s.step(2, 5e-4)
+    l0 = s.launches
+    s.step(4, 5e-4)
+    assert s.launches - l0 > 1 and s.sync() == 0
+    p = lattice(512, 512)
+    s = sim_for(p)
+    s.set_psi(c64(gi.gaussian_state(512, 512, p["Lx"], p["Ly"], 1.5, 1e-3, seed=450)))
+    s.tune(5e-4)
+    assert s.variants & abi.GPE_VARIANT_COOP
+    s.step(2, 5e-4)
+    l0 = s.launches
+    s.profile(True)
+    s.step(4, 5e-4)
+    s.profile_read()
+    s.profile(False)
+    assert s.launches - l0 == 8                        # per-pass launches, two per step
+    l0 = s.launches
+    s2 = sim_for(p)
+    s2.set_psi(c64(gi.gaussian_state(512, 512, p["Lx"], p["Ly"], 1.5, 1e-3, seed=451)))
+    Simulation.step_many([s, s2], 4, 5e-4)
+    assert s.launches - l0 > 1
+    assert s.sync() == 0 and s2.sync() == 0

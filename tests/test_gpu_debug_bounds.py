@@ -7,8 +7,9 @@ loads that library (GPE_LIBRARY=debug) and runs cases through every pass
 kernel family -- the one-shot row and column passes on short pencils (the
 32 x 256 and 64 x 64 grids among them), the grouped, streaming, adjoint and
 readout passes, the pencil-pair column passes (2048-point columns by
-default, 512 by choice) and the persistent batch -- each checked against
-the FP64 oracle and for a clean device status.
+default, 512 by choice), the persistent batch and the cooperative step
+kernel -- each checked against the FP64 oracle and for a clean device
+status.
 """
 import os
 import subprocess
@@ -79,6 +80,17 @@ for nx, ny in ((256, 256), (64, 1024)):
     sims.append(q)
 Batch(sims).step(10, 5e-4)
 assert all(q.sync() == 0 for q in sims)
+# the cooperative step kernel: real time with the cavity on a rectangular grid
+p = dict(w["params"], nx=1024, ny=512, Lx=20.48, Ly=10.24, **cav)
+x = gi.gaussian_state(1024, 512, 20.48, 10.24, 1.2, 1e-2, seed=7, checker=0.2, kc=2 * np.pi).astype(np.complex64)
+s = sim(p)
+s.variants = s.variants | abi.GPE_VARIANT_COOP
+s.set_psi(x)
+l0 = s.launches
+s.step(20, 5e-4)
+assert s.launches - l0 <= 2 and s.sync() == 0
+ref, _ = oracle.evolve(p, x.astype(np.complex128), 20, 5e-4, False)
+assert rel(s.get_psi(), ref) < 1e-5, rel(s.get_psi(), ref)
 print("debug bounds build: all cases clean")
 '''
 

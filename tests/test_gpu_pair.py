@@ -118,7 +118,7 @@ def test_pair_variant_bits():
     assert s.variants == v | 32 | 64
     s.variants = v | abi.GPE_VARIANT_PAIR_COLS
     with pytest.raises(Exception):
-        s.variants = 128                      # unknown bit
+        s.variants = 256                      # unknown bit
     with pytest.raises(Exception):
         s.variants = 3 << 3                   # row-tile value 3
     assert s.variants == v | 32
