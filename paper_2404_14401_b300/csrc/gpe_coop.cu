@@ -152,9 +152,9 @@ __device__ bool coop_reduce(const CoopArgs &a, const float (&q)[3], const RedArg
 //
 // Units (pencil pairs) are dealt to groups CTA-first: unit u goes to CTA
 // u mod gridDim.x, so a pass narrower than the grid's groups spreads over
-// every SM.  Every group runs the same number of rounds (a group without a
-// unit in a round transforms zeros and stores nothing), so the named
-// barriers inside the transform see all of their threads.
+// every SM.  All threads of a group share its units, and the named barrier
+// inside the transform is the group's own, so a group without a unit skips
+// the pass and waits at the CTA barrier that ends it.
 // The thread's and the CTA's index are read with volatile moves at every
 // pass, so that the index and address arithmetic derived from them (the
 // exchange-slot offsets of every stage, the elements' offsets) is pass-local
@@ -174,8 +174,8 @@ __device__ __forceinline__ int cta_fresh()
 }
 
 template <int N> struct CoopUnits {
-    int g, j, gg, G, rounds;
-    __device__ CoopUnits(int units)
+    int g, j, gg, G;
+    __device__ CoopUnits()
     {
         using A = CoopAxis<N>;
         const int t = tid_fresh();
@@ -183,7 +183,6 @@ template <int N> struct CoopUnits {
         j = t % A::TP;
         gg = cta_fresh() + gridDim.x * g;
         G = gridDim.x * A::GPB;
-        rounds = (units + G - 1) / G;
     }
 };
 
@@ -197,15 +196,14 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
     using A = CoopAxis<N>;
     constexpr int E = A::E, TP = A::TP;
     const int units = a.ny / 2;
-    const CoopUnits<N> U(units);
+    const CoopUnits<N> U;
     float4 *sb = slots + U.g * A::SLOTS;
     const GroupSync gs{1 + U.g, TP};
     const float cs = use_c ? (float)loc.c : 1.f;
     float acx2, acxcy;
     alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
-    for (int it = 0; it < U.rounds; ++it) {
-        const int u = U.gg + it * U.G;
-        const bool act = u < units && check_index((long long)2 * u + 1, a.ny, T.sc);
+    for (int u = U.gg; u < units; u += U.G) {
+        const bool act = check_index((long long)2 * u + 1, a.ny, T.sc);
         const int y0 = act ? 2 * u : 0;
         float2 *ra = a.psi + (size_t)y0 * N, *rb = ra + N;
         float2 X[E], Y[E], V[E];
@@ -254,14 +252,13 @@ __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, con
     constexpr bool PHASE = (MODE == COL_T_P || MODE == COL_T_PR);
     constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
     constexpr int units = NX / 2, w4 = NX / 2;                 // float4 per grid row
-    const CoopUnits<N> U(units);
+    const CoopUnits<N> U;
     float4 *sb = slots + U.g * A::SLOTS;
     const GroupSync gs{1 + U.g, TP};
     float acx2, acxcy;
     alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
-    for (int it = 0; it < U.rounds; ++it) {
-        const int u = U.gg + it * U.G;
-        const bool act = u < units && check_index((long long)2 * u + 1, NX, T.sc);
+    for (int u = U.gg; u < units; u += U.G) {
+        const bool act = check_index((long long)2 * u + 1, NX, T.sc);
         const int x0 = act ? 2 * u : 0;
         // {re, im} of columns x0, x0 + 1 at row j + r TP: cb[r TP w4]
         float4 *cb = reinterpret_cast<float4 *>(a.psi + x0) + (size_t)U.j * w4;
