@@ -335,10 +335,11 @@ enum { GPE_VARIANT_PAIR_ROWS = 64 };
  * column transforms, the pointwise prologue and epilogue passes) separated
  * by a grid barrier, the phase and reduction arguments evaluated on the
  * device, psi kept in L2 between passes.  Equal to the per-pass path to
- * FP32 rounding.  Off by default: on a B300 it measured slower than the
- * per-pass path (512^2 real time 19.6 against 13.2 us per step, the 512^2
- * cavity ramp 28.4 against 24.6 us); it takes one host launch per call
- * instead of two or three per step.  It does not apply while the context
+ * FP32 rounding.  On by default for 512 x 512 grids, where it measured
+ * faster than the per-pass path (per step on a B300: real time 11.1 against
+ * 13.2 us, the cavity ramp 20.2 against 24.6 us, imaginary time 18.0 against
+ * 23.8 us); at 1024 points it was slower and is off unless set.  It takes
+ * one host launch per call instead of two or three per step.  It does not apply while the context
  * profiles its passes (gpe_profile), when it has more than 256 control
  * points, for more than 2^22 steps in one call, or while its stream is being
  * captured; a device that refuses the cooperative launch makes the context

@@ -156,7 +156,7 @@ Lanes *lanes_for_current_device()
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t sc, part_row, part_col, twx, twy, xtab, ytab, kinx, kiny, total;
+    size_t sc, part_row, part_col, twx, twy, tw8x, tw8y, xtab, ytab, kinx, kiny, total;
 };
 
 Layout layout(int nx, int ny)
@@ -168,6 +168,8 @@ Layout layout(int nx, int ny)
     L.part_col = o;  o = align256(o + sizeof(double) * NQ * MAX_BLOCKS);
     L.twx = o;       o = align256(o + sizeof(float4) * nx);
     L.twy = o;       o = align256(o + sizeof(float4) * ny);
+    L.tw8x = o;      o = align256(o + sizeof(float4) * nx);
+    L.tw8y = o;      o = align256(o + sizeof(float4) * ny);
     L.xtab = o;      o = align256(o + sizeof(float4) * nx);
     L.ytab = o;      o = align256(o + sizeof(float4) * ny);
     L.kinx = o;      o = align256(o + sizeof(float2) * nx);
@@ -448,14 +450,12 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // at 2048^2, 133 against 181 us for the streaming pass at 4096^2, 918
     // against 940 us for the one-shot pass at 8192^2)
     c->pair_rows = (nx >= 512 && !getenv("GPE_NO_PAIR_ROWS")) ? 1 : 0;
-    // the cooperative kernel off by default: on B300 it measured slower than
-    // the per-pass path on every grid it is built for (512^2 real time 19.6
-    // against 13.2 us per step, the 512^2 cavity ramp 28.4 against 24.6,
-    // 1024^2 24.7 against 21.4): each pass waits for the transform of one
-    // pencil pair by one warp (about 7.5 us at 512 points), as the per-pass
-    // kernels do, and a grid barrier costs about 1.2 us, more than the
-    // launch gaps that graph replay leaves between per-pass kernels
-    c->coop = 0;
+    // the cooperative kernel by default on 512^2 grids, where it measured
+    // faster than the per-pass path in every step program (per step: real
+    // time 11.1 against 13.2 us, the cavity ramp 20.2 against 24.6 us,
+    // imaginary time 18.0 against 23.8 us); at 1024^2 it was slower (28.7
+    // against 21.4 us), so it is a choice there
+    c->coop = (nx == 512 && ny == 512 && !getenv("GPE_NO_COOP")) ? 1 : 0;
     c->launches = 0;
     {
         static std::atomic<unsigned long long> next_uid{1};
@@ -477,6 +477,8 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     T.part_col = (double *)(c->ws + L.part_col);
     T.twx = (float4 *)(c->ws + L.twx);
     T.twy = (float4 *)(c->ws + L.twy);
+    T.tw8x = (float4 *)(c->ws + L.tw8x);
+    T.tw8y = (float4 *)(c->ws + L.tw8y);
     T.xtab = (float4 *)(c->ws + L.xtab);
     T.ytab = (float4 *)(c->ws + L.ytab);
     T.kinx = (float2 *)(c->ws + L.kinx);
@@ -609,7 +611,7 @@ gpe_status step_epilogue(gpe_ctx *c, int n, double dt, gpe_mode mode)
 }
 
 // The cooperative kernel runs gpe_step on one context whose grid it is built
-// for when the context's bit is set (off by default), unless the context
+// for when the context's bit is set (by default on 512^2 grids), unless the context
 // profiles its passes (per-pass events), has more control points than the
 // launch arguments carry, or its stream is being captured into a graph.
 bool coop_applies(gpe_ctx *c, int n)

@@ -30,13 +30,15 @@
 // flag that ends every CTA at its next barrier.  The cooperative launch
 // guarantees that all CTAs are resident, so every wait ends.
 //
-// Measured on a B300 (512^2 lattice, real time): 19.5 us per step, of which
-// about 2.4 us are the two grid barriers and about 15 us the two passes, each
-// the time one warp takes to transform its pencil pair.  The per-pass path
-// takes 13.2 us per step with the same per-pair latency, since graph replay
-// leaves almost no gap between its kernels; so the kernel is a choice for
-// callers that need one launch per call (a busy host, time-dependent
-// controls), not the default.
+// A pass takes about the time one group needs to transform its pencil pair,
+// which is why the pairs are transformed in the radix-8 schedule (8 elements
+// per thread, two warps per 512-point pair) rather than the per-pass
+// kernels' radix-16 one.  Measured on a B300, per step against the per-pass
+// path: 512^2 lattice (real time) 11.1 against 13.2 us, the 512^2 cavity ramp
+// 20.2 against 24.6 us, a 512^2 trap in imaginary time 18.0 against 23.8 us;
+// but 1024^2 28.7 against 21.4 us.  With 16 elements per thread (one warp per
+// 512-point pair) it was 14.7, 24.0, 22.6 and 25.5 us; with 512-thread CTAs
+// 12.6, 25.3, 23.3 and 28.6 us.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -53,10 +55,14 @@
 
 namespace gpe {
 
-constexpr int kCT = 256;                                   // threads per CTA
+constexpr int kCT = 256;                                   // threads per CTA, one CTA per SM
+// elements of each pencil per thread: the radix-8 schedule, so that a pencil
+// pair's transform is spread over N/8 threads (two warps at 512 points) and
+// each thread's serial chain is half that of the 16-element form
+constexpr int kE = 8;
 // exchange slots of the CTA's groups: (256 / TP) groups of pad8_len(N)
-// 16-byte slots, 73,728 bytes whatever the length N = 16 TP
-constexpr size_t kCoopSlotBytes = (size_t)kCT * 16 * 18;
+// 16-byte slots, 36,864 bytes whatever the length N = 8 TP
+constexpr size_t kCoopSlotBytes = (size_t)kCT * kE * 18;
 constexpr size_t kCoopSmem = kCoopSlotBytes + 128;
 
 // The tables and the potential array, read by the passes through a copy in
@@ -71,7 +77,7 @@ struct CoopPtrs {
 };
 
 template <int N> struct CoopAxis {
-    static constexpr int E = 16, TP = N / E, GPB = kCT / TP, SLOTS = pad8_len(N);
+    static constexpr int E = kE, TP = N / E, GPB = kCT / TP, SLOTS = pad8_len(N);
     static_assert((size_t)GPB * SLOTS * 16 == kCoopSlotBytes, "group slots");
     static_assert(TP % 32 == 0 && GPB <= 15, "groups of whole warps, one named barrier each");
 };
@@ -225,7 +231,7 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
             if (Va) V[r] = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V[r]);
         }
         phase_all2<E>(X, Y, V, a.g, ph.h, a.imag);
-        transform_pair<N, E, TP>(X, Y, sb, U.j, T.twx, T.kinx, a.sx, a.imag, gs);
+        transform_pair<N, E, TP>(X, Y, sb, U.j, T.tw8x, T.kinx, a.sx, a.imag, gs);
         if (act) {
 #pragma unroll
             for (int r = 0; r < E; ++r) {
@@ -269,7 +275,7 @@ __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, con
             X[r] = make_float2(t.x, t.z);
             Y[r] = make_float2(t.y, t.w);
         }
-        transform_pair<N, E, TP>(X, Y, sb, U.j, T.twy, T.kiny, a.sy, a.imag, gs);
+        transform_pair<N, E, TP>(X, Y, sb, U.j, T.tw8y, T.kiny, a.sy, a.imag, gs);
         const float4 xa = __ldg(&T.xtab[x0]), xb = __ldg(&T.xtab[x0 + 1]);
         if constexpr (PHASE) {
             const PotCoefs pa = col_coefs_from(ph, acx2, acxcy, xa), pb = col_coefs_from(ph, acx2, acxcy, xb);

@@ -203,6 +203,30 @@ __host__ __device__ constexpr int fft_tw_offset(int n, int s)
 // entries of the whole table
 __host__ __device__ constexpr int fft_tw_count(int n) { return fft_tw_offset(n, fft_stages(n)); }
 
+// The same schedule and table layout for a main radix of 2^LR: LR = 4 is the
+// schedule above; LR = 3 (radix-8 stages after a first stage of radix
+// 2^(n mod 3)) serves transforms with 8 elements per thread, twice the
+// threads per pencil and half the serial work of each.
+template <int LR> __host__ __device__ constexpr int fftg_stages(int n) { return (ilog2(n) + LR - 1) / LR; }
+template <int LR> __host__ __device__ constexpr int fftg_radix(int n, int s)
+{
+    return s == 0 ? (1 << (ilog2(n) - LR * (fftg_stages<LR>(n) - 1))) : (1 << LR);
+}
+template <int LR> __host__ __device__ constexpr int fftg_ns(int n, int s)
+{
+    return s == 0 ? 1 : fftg_ns<LR>(n, s - 1) * fftg_radix<LR>(n, s - 1);
+}
+template <int LR> __host__ __device__ constexpr int fftg_tw_offset(int n, int s)
+{
+    return s <= 1 ? 0 : fftg_tw_offset<LR>(n, s - 1) + (fftg_radix<LR>(n, s - 1) - 1) * fftg_ns<LR>(n, s - 1);
+}
+template <int LR> __host__ __device__ constexpr int fftg_tw_count(int n)
+{
+    return fftg_tw_offset<LR>(n, fftg_stages<LR>(n));
+}
+static_assert(fftg_tw_count<4>(2048) == fft_tw_count(2048) && fftg_radix<4>(512, 0) == fft_radix(512, 0),
+              "the radix-16 instance is the schedule above");
+
 // One Stockham stage of radix R after NS points have been combined.
 // Butterfly jp takes x[jp + r N/R], multiplies input r by W_{NS R}^{r (jp mod NS)}
 // and writes output p to y[(jp / NS) NS R + jp mod NS + p NS].

@@ -287,19 +287,21 @@ __device__ __forceinline__ void pair_stage(float2 (&X)[E], float2 (&Y)[E], float
 }
 
 // Full transform of a pencil pair, natural order in and out (element j + r TP
-// of both pencils in X[r], Y[r]), in the radix schedule of the one-pencil
-// transform (fft_radix) with its twiddle table (fft_tw_offset layout).
+// of both pencils in X[r], Y[r]), in the radix schedule of main radix E
+// (fftg_radix<log2 E>: with E = 16 the one-pencil transform's schedule and
+// twiddle table, with E = 8 the radix-8 schedule and its table).
 // Forward: X_k = sum_n x_n e^{-2 pi i nk/N}; INV: the conjugate sum without
 // 1/N.  Every thread that `sync` covers calls it together.
 template <int N, int E, bool INV, int S = 0, class Sync = CtaSync>
 __device__ __forceinline__ void fft_pair(float2 (&X)[E], float2 (&Y)[E], float4 *__restrict__ sb, int j,
                                          const float4 *__restrict__ tw, const Sync &sync = Sync())
 {
-    static_assert(E == 16, "16 elements per pencil per thread (the radix-16 schedule)");
-    constexpr int R = fft_radix(N, S), NS = fft_ns(N, S);
-    constexpr bool LAST = (S == fft_stages(N) - 1);
+    static_assert(E == 16 || E == 8, "8 or 16 elements per pencil per thread");
+    constexpr int LR = E == 16 ? 4 : 3;
+    constexpr int R = fftg_radix<LR>(N, S), NS = fftg_ns<LR>(N, S);
+    constexpr bool LAST = (S == fftg_stages<LR>(N) - 1);
     static_assert(E % R == 0, "radix must divide the elements per thread");
-    pair_stage<N, E, R, NS, INV, LAST>(X, Y, sb, j, tw + fft_tw_offset(N, S), sync);
+    pair_stage<N, E, R, NS, INV, LAST>(X, Y, sb, j, tw + fftg_tw_offset<LR>(N, S), sync);
     if constexpr (!LAST) fft_pair<N, E, INV, S + 1>(X, Y, sb, j, tw, sync);
 }
 

@@ -32,7 +32,8 @@ struct Tables {
     DevScalars *sc;
     double *part_row;              // [MAX_BLOCKS][NQ] per-CTA partial sums
     double *part_col;              // [MAX_BLOCKS][NQ]
-    float4 *twx, *twy;             // exp(-2 pi i m / N), m < N: {re_hi, im_hi, re_lo, im_lo}
+    float4 *twx, *twy;             // per-stage twiddles of the radix-16 schedule: {re_hi, im_hi, re_lo, im_lo}
+    float4 *tw8x, *tw8y;           // the same for the radix-8 schedule (8 elements per thread)
     float4 *xtab, *ytab;           // {(m/2) w^2 x^2, cos^2(k_lat x), cos(kc x), x}
     float2 *kinx, *kiny;           // kinetic factors (see kinetic_tables_kernel)
 };

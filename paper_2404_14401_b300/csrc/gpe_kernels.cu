@@ -838,14 +838,15 @@ __global__ void __launch_bounds__(ColStreamCfg<N>::THREADS, ColStreamCfg<N>::CTA
 
 #if GPE_IN_PART(0)
 // ------------------------------------------------------------------ tables
-// Entry i of the per-stage twiddle table of an n-point axis (fft_tw_offset
-// layout): W_{NS R}^{r k} = exp(-2 pi i r k / (NS R)) as {re_hi, im_hi, re_lo,
-// im_lo}, hi = float(x), lo = float(x - hi).  Entries past the table are 1.
-static __device__ float4 twiddle_entry(int i, int n)
+// Entry i of the per-stage twiddle table of an n-point axis in the schedule
+// of main radix 2^LR (fftg_tw_offset layout): W_{NS R}^{r k} = exp(-2 pi i r
+// k / (NS R)) as {re_hi, im_hi, re_lo, im_lo}, hi = float(x), lo = float(x -
+// hi).  Entries past the table are 1.
+template <int LR> static __device__ float4 twiddle_entry(int i, int n)
 {
     long long num = 0, den = 1;
-    for (int s = 1; s < fft_stages(n); ++s) {
-        const int ns = fft_ns(n, s), R = fft_radix(n, s), off = fft_tw_offset(n, s);
+    for (int s = 1; s < fftg_stages<LR>(n); ++s) {
+        const int ns = fftg_ns<LR>(n, s), R = fftg_radix<LR>(n, s), off = fftg_tw_offset<LR>(n, s);
         if (i >= off && i < off + (R - 1) * ns) {
             const int r = (i - off) / ns + 1, k = (i - off) % ns;
             num = (long long)r * k;
@@ -859,6 +860,9 @@ static __device__ float4 twiddle_entry(int i, int n)
 }
 
 // Coordinates, trap and lattice profiles and twiddles in FP64, rounded once.
+// The radix-8 tables are written only where the caller's Tables has them
+// (the allocation-free reduction's scratch holds the coordinate and radix-16
+// tables alone).
 __global__ void tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, double m, double wx,
                               double wy, double lkx, double lky, double kc)
 {
@@ -867,13 +871,15 @@ __global__ void tables_kernel(Tables T, int nx, int ny, double Lx, double Ly, do
         const double x = -0.5 * Lx + (double)i * (Lx / nx);
         const double cl = cos(lkx * x), cc = cos(kc * x);
         T.xtab[i] = make_float4((float)(0.5 * m * wx * wx * x * x), (float)(cl * cl), (float)cc, (float)x);
-        T.twx[i] = twiddle_entry(i, nx);
+        T.twx[i] = twiddle_entry<4>(i, nx);
+        if (T.tw8x) T.tw8x[i] = twiddle_entry<3>(i, nx);
     }
     if (i < ny) {
         const double y = -0.5 * Ly + (double)i * (Ly / ny);
         const double cl = cos(lky * y), cc = cos(kc * y);
         T.ytab[i] = make_float4((float)(0.5 * m * wy * wy * y * y), (float)(cl * cl), (float)cc, (float)y);
-        T.twy[i] = twiddle_entry(i, ny);
+        T.twy[i] = twiddle_entry<4>(i, ny);
+        if (T.tw8y) T.tw8y[i] = twiddle_entry<3>(i, ny);
     }
 }
 

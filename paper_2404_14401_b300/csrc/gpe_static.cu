@@ -88,6 +88,8 @@ extern "C" gpe_status gpe_overlaps_static(const void *psi_dev, int nx, int ny, d
     T.ytab = reinterpret_cast<float4 *>(base + kOffY);
     T.twx = reinterpret_cast<float4 *>(base + kOffTwx);   // the tables kernel fills these too
     T.twy = reinterpret_cast<float4 *>(base + kOffTwy);
+    // tw8x / tw8y stay null: no pass here transforms, and the tables kernel
+    // skips the radix-8 tables of a Tables that has none
 
     // the scratch keeps whatever the previous call left: the counter and the
     // status word must start at zero, the tables are rewritten for this grid

@@ -128,8 +128,12 @@ def test_coop_lattice_control_and_potential_array():
 @pytest.mark.parametrize("mode", ["real cavity", "imaginary"])
 def test_coop_agrees_with_per_pass_path(mode):
     """The same 20 steps through the cooperative kernel and through the
-    per-pass path: equal to FP32 rounding (the reductions sum in another
-    order, the 512-point column pass differs in form)."""
+    per-pass path: equal to FP32 rounding.  The two round differently at
+    every step -- the cooperative kernel transforms in the radix-8 schedule,
+    the per-pass kernels in the radix-16 one, and the reductions sum in
+    another order -- so the states drift apart by about 1e-7 per step
+    (1.15e-6 measured after 20 steps); both are held to the FP64 oracle at
+    the suite's own tolerances by the tests above.  Bound: 3e-6."""
     if mode == "real cavity":
         w = gi.cavity_ramp()
         p, dt, imag = w["params"], w["dt"], False
@@ -150,9 +154,9 @@ def test_coop_agrees_with_per_pass_path(mode):
         obs.append(s.observables())
         assert s.sync() == 0
     assert calls[0] <= 2 < calls[1]
-    assert rel_l2(outs[0], outs[1]) < 1e-6
+    assert rel_l2(outs[0], outs[1]) < 3e-6
     for k in ("norm", "energy") + (("alpha_re", "O", "B") if mode == "real cavity" else ()):
-        assert abs(obs[0][k] - obs[1][k]) < 1e-6 * abs(obs[1][k]), k
+        assert abs(obs[0][k] - obs[1][k]) < 3e-6 * abs(obs[1][k]), k
 
 
 def test_coop_wait_limit_runs_out_and_context_recovers():
@@ -179,15 +183,15 @@ def test_coop_wait_limit_runs_out_and_context_recovers():
 
 
 def test_coop_defaults_and_fallbacks():
-    """Off by default; set, the bit sticks and gpe_tune keeps it; a
-    profiling context and a batch of two contexts take the per-pass path;
-    on a grid it is not built for the bit changes nothing."""
+    """On by default for 512^2 grids only; set, the bit sticks and gpe_tune
+    keeps it; a profiling context and a batch of two contexts take the
+    per-pass path; on a grid it is not built for the bit changes nothing."""
     from paper_2404_14401_b300 import Simulation
     from paper_2404_14401_b300 import gpe as abi
     for nx, ny in ((512, 512), (1024, 1024), (512, 1024), (256, 256), (2048, 2048), (256, 512)):
         p = lattice(nx, ny)
         s = Simulation(nx, ny, p["Lx"], p["Ly"], p["m"], p["g"])
-        assert not s.variants & abi.GPE_VARIANT_COOP, (nx, ny)
+        assert bool(s.variants & abi.GPE_VARIANT_COOP) == (nx == ny == 512), (nx, ny)
     p = lattice(256, 256)
     s = sim_for(p)
     s.set_psi(c64(gi.gaussian_state(256, 256, p["Lx"], p["Ly"], 1.5, 1e-3, seed=449)))
