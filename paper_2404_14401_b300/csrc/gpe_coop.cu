@@ -34,11 +34,12 @@
 // which is why the pairs are transformed in the radix-8 schedule (8 elements
 // per thread, two warps per 512-point pair) rather than the per-pass
 // kernels' radix-16 one.  Measured on a B300, per step against the per-pass
-// path: 512^2 lattice (real time) 11.1 against 13.2 us, the 512^2 cavity ramp
-// 20.2 against 24.6 us, a 512^2 trap in imaginary time 18.0 against 23.8 us;
-// but 1024^2 28.7 against 21.4 us.  With 16 elements per thread (one warp per
-// 512-point pair) it was 14.7, 24.0, 22.6 and 25.5 us; with 512-thread CTAs
-// 12.6, 25.3, 23.3 and 28.6 us.
+// path: 512^2 lattice (real time) 10.7 against 13.2 us, the 512^2 cavity ramp
+// 18.9 against 24.6 us, a 512^2 trap in imaginary time 16.9 against 24.1 us;
+// but 1024^2 28.7 against 21.4 us.  With 256-thread CTAs at 512^2 it was
+// 11.1, 20.2 and 18.0 us; with 16 elements per thread (one warp per
+// 512-point pair) 14.7, 24.0 and 22.6 us; with 512-thread CTAs 12.6, 25.3
+// and 23.3 us.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -55,15 +56,20 @@
 
 namespace gpe {
 
-constexpr int kCT = 256;                                   // threads per CTA, one CTA per SM
 // elements of each pencil per thread: the radix-8 schedule, so that a pencil
 // pair's transform is spread over N/8 threads (two warps at 512 points) and
 // each thread's serial chain is half that of the 16-element form
 constexpr int kE = 8;
-// exchange slots of the CTA's groups: (256 / TP) groups of pad8_len(N)
-// 16-byte slots, 36,864 bytes whatever the length N = 8 TP
-constexpr size_t kCoopSlotBytes = (size_t)kCT * kE * 18;
-constexpr size_t kCoopSmem = kCoopSlotBytes + 128;
+// One CTA per SM of two groups of the longer axis: 128 threads on a 512^2
+// grid, 256 on grids with a 1024-point axis (a 512^2 pass keeps only one or
+// two groups per SM busy, and fewer idle warps make every CTA barrier and
+// reduction shorter); the exchange slots of its groups, (CT / TP) groups of
+// pad8_len(N) 16-byte slots, are CT * 8 * 18 bytes whatever the length.
+template <int NX, int NY> struct CoopCfg {
+    static constexpr int CT = 2 * ((NX > NY ? NX : NY) / kE);
+    static constexpr size_t SLOT_BYTES = (size_t)CT * kE * 18;
+    static constexpr size_t SMEM = SLOT_BYTES + 128;
+};
 
 // The tables and the potential array, read by the passes through a copy in
 // shared memory: a pointer loaded from shared memory after a barrier is new
@@ -76,9 +82,9 @@ struct CoopPtrs {
     const float *V;
 };
 
-template <int N> struct CoopAxis {
-    static constexpr int E = kE, TP = N / E, GPB = kCT / TP, SLOTS = pad8_len(N);
-    static_assert((size_t)GPB * SLOTS * 16 == kCoopSlotBytes, "group slots");
+template <int N, int CT> struct CoopAxis {
+    static constexpr int E = kE, TP = N / E, GPB = CT / TP, SLOTS = pad8_len(N);
+    static_assert((size_t)GPB * SLOTS * 16 == (size_t)CT * kE * 18, "group slots");
     static_assert(TP % 32 == 0 && GPB <= 15, "groups of whole warps, one named barrier each");
 };
 
@@ -179,11 +185,11 @@ __device__ __forceinline__ int cta_fresh()
     return b;
 }
 
-template <int N> struct CoopUnits {
+template <int N, int CT> struct CoopUnits {
     int g, j, gg, G;
     __device__ CoopUnits()
     {
-        using A = CoopAxis<N>;
+        using A = CoopAxis<N, CT>;
         const int t = tid_fresh();
         g = t / A::TP;
         j = t % A::TP;
@@ -194,15 +200,15 @@ template <int N> struct CoopUnits {
 
 // Row pass ROW_PT on the row pairs (2u, 2u + 1): [scale c] potential phase,
 // T_x, as row_pair_kernel computes it.
-template <int N>
+template <int N, int CT>
 __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, int use_c,
                              const DevScalars &loc, float4 *slots)
 {
     const Tables &T = P.T;
-    using A = CoopAxis<N>;
+    using A = CoopAxis<N, CT>;
     constexpr int E = A::E, TP = A::TP;
     const int units = a.ny / 2;
-    const CoopUnits<N> U;
+    const CoopUnits<N, CT> U;
     float4 *sb = slots + U.g * A::SLOTS;
     const GroupSync gs{1 + U.g, TP};
     const float cs = use_c ? (float)loc.c : 1.f;
@@ -248,17 +254,17 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
 // COL_T_PR) the closing half phase, then (COL_T_R, COL_T_PR) the norm and
 // overlap sums added to q.  With the width a constant, a thread's 16 strided
 // elements are immediate offsets from one address.
-template <int N, int NX, int MODE>
+template <int N, int NX, int MODE, int CT>
 __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, const DevScalars &loc,
                           float4 *slots, float (&q)[3])
 {
     const Tables &T = P.T;
-    using A = CoopAxis<N>;
+    using A = CoopAxis<N, CT>;
     constexpr int E = A::E, TP = A::TP;
     constexpr bool PHASE = (MODE == COL_T_P || MODE == COL_T_PR);
     constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
     constexpr int units = NX / 2, w4 = NX / 2;                 // float4 per grid row
-    const CoopUnits<N> U;
+    const CoopUnits<N, CT> U;
     float4 *sb = slots + U.g * A::SLOTS;
     const GroupSync gs{1 + U.g, TP};
     float acx2, acxcy;
@@ -352,7 +358,7 @@ __device__ __noinline__ void coop_points(const CoopArgs &a, const CoopPtrs &P, c
 // The program of step_prologue (alpha of the initial density), n x step_part
 // and step_epilogue, with the same pass times, phase lengths and modes.
 template <int NX, int NY>
-__global__ void __launch_bounds__(kCT, 1) coop_kernel(const __grid_constant__ CoopArgs a)
+__global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, 1) coop_kernel(const __grid_constant__ CoopArgs a)
 {
     extern __shared__ unsigned char smraw[];
     __shared__ double red[32 * NQ];
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(kCT, 1) coop_kernel(const __grid_constant__ Co
         s_k = 0;
         s_P.T = a.T;
         s_P.V = a.V;
-        s_ok = check_index((long long)((unsigned char *)slots + kCoopSlotBytes - smraw) - 1, dyn_smem_bytes(),
+        s_ok = check_index((long long)((unsigned char *)slots + CoopCfg<NX, NY>::SLOT_BYTES - smraw) - 1, dyn_smem_bytes(),
                            a.T.sc);
         if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
     }
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(kCT, 1) coop_kernel(const __grid_constant__ Co
         const double te = __dadd_rn(t0, __dmul_rn((double)(s + 1), dt));
         if (threadIdx.x == 0) s_ph = phase_dev(a, ts, (imag || s == 0) ? hh : dt);
         __syncthreads();
-        coop_rows_pt<NX>(a, s_P, s_ph, imag && s > 0, loc, slots);
+        coop_rows_pt<NX, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, imag && s > 0, loc, slots);
         if (!coop_sync(a, &s_ok, &s_k)) {
             ok = false;
             break;
@@ -407,15 +413,15 @@ __global__ void __launch_bounds__(kCT, 1) coop_kernel(const __grid_constant__ Co
             if (s == n - 1) {
                 if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
                 __syncthreads();
-                coop_cols<NY, NX, COL_T_P>(a, s_P, s_ph, loc, slots, q);
+                coop_cols<NY, NX, COL_T_P, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
             } else {
-                coop_cols<NY, NX, COL_T>(a, s_P, s_ph, loc, slots, q);
+                coop_cols<NY, NX, COL_T, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
                 ok = coop_sync(a, &s_ok, &s_k);
             }
         } else if (!imag) {
             if (threadIdx.x == 0) s_rd = red_dev(a, te);
             __syncthreads();
-            coop_cols<NY, NX, COL_T_R>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
         } else if (!cav) {
             if (threadIdx.x == 0) {
@@ -423,12 +429,12 @@ __global__ void __launch_bounds__(kCT, 1) coop_kernel(const __grid_constant__ Co
                 s_rd = red_dev(a, te);
             }
             __syncthreads();
-            coop_cols<NY, NX, COL_T_PR>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_PR, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
         } else {                                   // imaginary time with a cavity: a third, pointwise pass
             if (threadIdx.x == 0) s_rd = red_dev(a, te);
             __syncthreads();
-            coop_cols<NY, NX, COL_T_R>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
             if (!ok) break;
             if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
@@ -454,17 +460,18 @@ bool coop_ok(int nx, int ny) { return (nx == 512 || nx == 1024) && (ny == 512 ||
 
 template <int NX, int NY> static cudaError_t coop_launch(const CoopArgs &a, cudaStream_t s)
 {
+    using C = CoopCfg<NX, NY>;
     static std::atomic<unsigned long long> attr{0};
-    const cudaError_t e = smem_opt_in(coop_kernel<NX, NY>, (int)kCoopSmem, attr);
+    const cudaError_t e = smem_opt_in(coop_kernel<NX, NY>, (int)C::SMEM, attr);
     if (e != cudaSuccess) return e;
     int per = 0;
-    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coop_kernel<NX, NY>, kCT, kCoopSmem);
+    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coop_kernel<NX, NY>, C::CT, C::SMEM);
     if (r != cudaSuccess) return r;
     if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
     const int grid = sm_count();                   // one CTA per SM, all resident
     if (grid < 1) return cudaErrorInvalidValue;
     void *args[] = {const_cast<CoopArgs *>(&a)};
-    return cudaLaunchCooperativeKernel((const void *)coop_kernel<NX, NY>, dim3(grid), dim3(kCT), args, kCoopSmem, s);
+    return cudaLaunchCooperativeKernel((const void *)coop_kernel<NX, NY>, dim3(grid), dim3(C::CT), args, C::SMEM, s);
 }
 
 cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s)
