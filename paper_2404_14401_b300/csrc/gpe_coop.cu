@@ -36,7 +36,7 @@
 // kernels' radix-16 one.  Measured on a B300, per step against the per-pass
 // path: 512^2 lattice (real time) 10.7 against 13.2 us, the 512^2 cavity ramp
 // 18.9 against 24.6 us, a 512^2 trap in imaginary time 16.9 against 24.1 us;
-// but 1024^2 28.7 against 21.4 us.  With 256-thread CTAs at 512^2 it was
+// but 1024^2 26.6 against 21.4 us.  With 256-thread CTAs at 512^2 it was
 // 11.1, 20.2 and 18.0 us; with 16 elements per thread (one warp per
 // 512-point pair) 14.7, 24.0 and 22.6 us; with 512-thread CTAs 12.6, 25.3
 // and 23.3 us.
@@ -60,13 +60,16 @@ namespace gpe {
 // pair's transform is spread over N/8 threads (two warps at 512 points) and
 // each thread's serial chain is half that of the 16-element form
 constexpr int kE = 8;
-// One CTA per SM of two groups of the longer axis: 128 threads on a 512^2
-// grid, 256 on grids with a 1024-point axis (a 512^2 pass keeps only one or
-// two groups per SM busy, and fewer idle warps make every CTA barrier and
-// reduction shorter); the exchange slots of its groups, (CT / TP) groups of
-// pad8_len(N) 16-byte slots, are CT * 8 * 18 bytes whatever the length.
+// CTAs of two groups of the longer axis: 128 threads on a 512^2 grid, one per
+// SM (a 512^2 pass keeps one or two groups per SM busy, and fewer idle warps
+// make every CTA barrier and reduction shorter); 256 threads on grids with a
+// 1024-point axis, two per SM, so that each group has one pencil pair per
+// pass (1024^2: 26.6 us per step against 28.7 with one CTA per SM).  The
+// exchange slots of a CTA's groups, (CT / TP) groups of pad8_len(N) 16-byte
+// slots, are CT * 8 * 18 bytes whatever the length.
 template <int NX, int NY> struct CoopCfg {
     static constexpr int CT = 2 * ((NX > NY ? NX : NY) / kE);
+    static constexpr int CPS = CT > 128 ? 2 : 1;           // CTAs per SM
     static constexpr size_t SLOT_BYTES = (size_t)CT * kE * 18;
     static constexpr size_t SMEM = SLOT_BYTES + 128;
 };
@@ -358,7 +361,7 @@ __device__ __noinline__ void coop_points(const CoopArgs &a, const CoopPtrs &P, c
 // The program of step_prologue (alpha of the initial density), n x step_part
 // and step_epilogue, with the same pass times, phase lengths and modes.
 template <int NX, int NY>
-__global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, 1) coop_kernel(const __grid_constant__ CoopArgs a)
+__global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coop_kernel(const __grid_constant__ CoopArgs a)
 {
     extern __shared__ unsigned char smraw[];
     __shared__ double red[32 * NQ];
@@ -467,8 +470,8 @@ template <int NX, int NY> static cudaError_t coop_launch(const CoopArgs &a, cuda
     int per = 0;
     const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coop_kernel<NX, NY>, C::CT, C::SMEM);
     if (r != cudaSuccess) return r;
-    if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
-    const int grid = sm_count();                   // one CTA per SM, all resident
+    if (per < C::CPS) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = C::CPS * sm_count();          // all resident
     if (grid < 1) return cudaErrorInvalidValue;
     void *args[] = {const_cast<CoopArgs *>(&a)};
     return cudaLaunchCooperativeKernel((const void *)coop_kernel<NX, NY>, dim3(grid), dim3(C::CT), args, C::SMEM, s);
