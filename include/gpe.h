@@ -128,10 +128,11 @@ gpe_status gpe_set_potential(gpe_ctx *ctx, const gpe_potential *p);
 
 /* Enqueue n >= 0 split steps of length dt > 0 (Sec. 3.1; GPE_IMAG: Sec. 3.3),
  * advancing the context's time by n dt.  psi is in real space before and
- * after.  Asynchronous.  The same as gpe_step_many over this one context
- * (so small grids with nothing time-dependent replay their interior steps
- * from a CUDA graph on a library lane, ordered with the context's stream).
- * Errors: GPE_EINVAL, GPE_ECUDA. */
+ * after.  Asynchronous.  The same as gpe_step_many over this one context:
+ * on a 512 x 512 grid (GPE_VARIANT_COOP, below) all n steps are one
+ * cooperative launch; otherwise small grids with nothing time-dependent
+ * replay their interior steps from a CUDA graph on a library lane, ordered
+ * with the context's stream.  Errors: GPE_EINVAL, GPE_ECUDA. */
 gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
 
 /* Enqueue n steps on each of `count` contexts in lockstep: step s of every
