@@ -4,15 +4,15 @@
 //
 // The per-pass path launches two or three kernels per step; on a 512^2 grid
 // each of them is a few hundred small CTAs whose time is mostly launch,
-// ramp-up and the latency of one FFT chain.  Here one CTA per SM stays
-// resident for all n steps and runs the host scheduler's pass program itself:
+// ramp-up and the latency of one FFT chain.  Here one or two CTAs per SM stay
+// resident for all n steps and run the host scheduler's pass program itself:
 // a row pass (potential phase, T_x) on pairs of rows, a column pass (T_y
 // [+ closing phase] [+ reductions]) on pairs of columns, and the pointwise
 // prologue / epilogue passes, each pass separated from the next by a grid
 // barrier.  psi stays in L2 between passes (2 MB at 512^2): loads and stores
 // go through L2 (ld.global.cg / st.global.cg), never the non-coherent L1.
 //
-// A group of N/16 threads owns one pencil pair at a time and transforms it
+// A group of N/8 threads owns one pencil pair at a time and transforms it
 // with the pair code of the pair passes (gpe_pair.cuh): the two rows (or
 // columns) in packed f32x2 registers, exchanges through the group's own
 // shared-memory slots, synchronised with a named barrier of the group.
