@@ -453,8 +453,9 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     // the cooperative kernel by default on 512^2 grids, where it measured
     // faster than the per-pass path in every step program (per step: real
     // time 10.7 against 13.2 us, the cavity ramp 18.9 against 24.6 us,
-    // imaginary time 16.9 against 24.1 us); at 1024^2 it was slower (26.6
-    // against 21.4 us), so it is a choice there
+    // imaginary time 16.9 against 24.1 us); at 1024^2 it was slower in real
+    // time (24.1 against 21.1 us) and within 4% otherwise, so it is a choice
+    // there
     c->coop = (nx == 512 && ny == 512 && !getenv("GPE_NO_COOP")) ? 1 : 0;
     c->launches = 0;
     {

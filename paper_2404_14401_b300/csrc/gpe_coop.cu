@@ -31,15 +31,17 @@
 // guarantees that all CTAs are resident, so every wait ends.
 //
 // A pass takes about the time one group needs to transform its pencil pair,
-// which is why the pairs are transformed in the radix-8 schedule (8 elements
-// per thread, two warps per 512-point pair) rather than the per-pass
-// kernels' radix-16 one.  Measured on a B300, per step against the per-pass
-// path: 512^2 lattice (real time) 10.7 against 13.2 us, the 512^2 cavity ramp
-// 18.9 against 24.6 us, a 512^2 trap in imaginary time 16.9 against 24.1 us;
-// but 1024^2 26.6 against 21.4 us.  With 256-thread CTAs at 512^2 it was
-// 11.1, 20.2 and 18.0 us; with 16 elements per thread (one warp per
-// 512-point pair) 14.7, 24.0 and 22.6 us; with 512-thread CTAs 12.6, 25.3
-// and 23.3 us.
+// which is why 512-point pairs are transformed in the radix-8 schedule (8
+// elements per thread, two warps per pair) rather than the per-pass kernels'
+// radix-16 one.  Measured on a B300, per step against the per-pass path:
+// 512^2 lattice (real time) 10.7 against 13.2 us, the 512^2 cavity ramp 18.9
+// against 24.6 us, a 512^2 trap in imaginary time 16.9 against 24.1 us.  At
+// 1024^2: real time 24.1 against 21.1 us, imaginary time 31.9 against 33.2
+// us, the cavity 34.0 against 35.3 us.  At 512^2 with 256-thread CTAs it was
+// 11.1, 20.2 and 18.0 us; with 16 elements per thread (one warp per pair)
+// 14.7, 24.0 and 22.6 us; with 512-thread CTAs 12.6, 25.3 and 23.3 us.  At
+// 1024^2 with the radix-8 schedule, real time took 26.6 us (two CTAs per SM)
+// and 28.7 us (one).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -56,21 +58,22 @@
 
 namespace gpe {
 
-// elements of each pencil per thread: the radix-8 schedule, so that a pencil
-// pair's transform is spread over N/8 threads (two warps at 512 points) and
-// each thread's serial chain is half that of the 16-element form
-constexpr int kE = 8;
-// CTAs of two groups of the longer axis: 128 threads on a 512^2 grid, one per
-// SM (a 512^2 pass keeps one or two groups per SM busy, and fewer idle warps
-// make every CTA barrier and reduction shorter); 256 threads on grids with a
-// 1024-point axis, two per SM, so that each group has one pencil pair per
-// pass (1024^2: 26.6 us per step against 28.7 with one CTA per SM).  The
-// exchange slots of a CTA's groups, (CT / TP) groups of pad8_len(N) 16-byte
-// slots, are CT * 8 * 18 bytes whatever the length.
+// Elements of each pencil per thread, and CTA shape, by the longer axis.
+// 512 points: the radix-8 schedule (8 elements, a pencil pair over two
+// warps), CTAs of two such groups (128 threads), one per SM -- a 512^2 pass
+// keeps one or two groups per SM busy, and fewer idle warps make every CTA
+// barrier and reduction shorter.  1024 points: the radix-16 schedule (16
+// elements, two warps per pair; the radix-8 one needs a fourth stage and a
+// third exchange there, 208 against about 170 instructions per point-step),
+// two groups per CTA, two CTAs per SM so that each group has one pair per
+// pass.  The exchange slots of a CTA's groups, (CT / TP) groups of
+// pad8_len(N) 16-byte slots, are CT * E * 18 bytes whatever the length.
 template <int NX, int NY> struct CoopCfg {
-    static constexpr int CT = 2 * ((NX > NY ? NX : NY) / kE);
-    static constexpr int CPS = CT > 128 ? 2 : 1;           // CTAs per SM
-    static constexpr size_t SLOT_BYTES = (size_t)CT * kE * 18;
+    static constexpr int NMAX = NX > NY ? NX : NY;
+    static constexpr int E = NMAX >= 1024 ? 16 : 8;
+    static constexpr int CT = 2 * (NMAX / E);
+    static constexpr int CPS = NMAX >= 1024 ? 2 : 1;       // CTAs per SM
+    static constexpr size_t SLOT_BYTES = (size_t)CT * E * 18;
     static constexpr size_t SMEM = SLOT_BYTES + 128;
 };
 
@@ -85,9 +88,9 @@ struct CoopPtrs {
     const float *V;
 };
 
-template <int N, int CT> struct CoopAxis {
-    static constexpr int E = kE, TP = N / E, GPB = CT / TP, SLOTS = pad8_len(N);
-    static_assert((size_t)GPB * SLOTS * 16 == (size_t)CT * kE * 18, "group slots");
+template <int N, int CT, int E_> struct CoopAxis {
+    static constexpr int E = E_, TP = N / E, GPB = CT / TP, SLOTS = pad8_len(N);
+    static_assert((size_t)GPB * SLOTS * 16 == (size_t)CT * E * 18, "group slots");
     static_assert(TP % 32 == 0 && GPB <= 15, "groups of whole warps, one named barrier each");
 };
 
@@ -188,11 +191,11 @@ __device__ __forceinline__ int cta_fresh()
     return b;
 }
 
-template <int N, int CT> struct CoopUnits {
+template <int N, int CT, int E> struct CoopUnits {
     int g, j, gg, G;
     __device__ CoopUnits()
     {
-        using A = CoopAxis<N, CT>;
+        using A = CoopAxis<N, CT, E>;
         const int t = tid_fresh();
         g = t / A::TP;
         j = t % A::TP;
@@ -203,15 +206,15 @@ template <int N, int CT> struct CoopUnits {
 
 // Row pass ROW_PT on the row pairs (2u, 2u + 1): [scale c] potential phase,
 // T_x, as row_pair_kernel computes it.
-template <int N, int CT>
+template <int N, int CT, int EE>
 __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, int use_c,
                              const DevScalars &loc, float4 *slots)
 {
     const Tables &T = P.T;
-    using A = CoopAxis<N, CT>;
+    using A = CoopAxis<N, CT, EE>;
     constexpr int E = A::E, TP = A::TP;
     const int units = a.ny / 2;
-    const CoopUnits<N, CT> U;
+    const CoopUnits<N, CT, EE> U;
     float4 *sb = slots + U.g * A::SLOTS;
     const GroupSync gs{1 + U.g, TP};
     const float cs = use_c ? (float)loc.c : 1.f;
@@ -240,7 +243,7 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
             if (Va) V[r] = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V[r]);
         }
         phase_all2<E>(X, Y, V, a.g, ph.h, a.imag);
-        transform_pair<N, E, TP>(X, Y, sb, U.j, T.tw8x, T.kinx, a.sx, a.imag, gs);
+        transform_pair<N, E, TP>(X, Y, sb, U.j, E == 8 ? T.tw8x : T.twx, T.kinx, a.sx, a.imag, gs);
         if (act) {
 #pragma unroll
             for (int r = 0; r < E; ++r) {
@@ -257,17 +260,17 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
 // COL_T_PR) the closing half phase, then (COL_T_R, COL_T_PR) the norm and
 // overlap sums added to q.  With the width a constant, a thread's 16 strided
 // elements are immediate offsets from one address.
-template <int N, int NX, int MODE, int CT>
+template <int N, int NX, int MODE, int CT, int EE>
 __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, const DevScalars &loc,
                           float4 *slots, float (&q)[3])
 {
     const Tables &T = P.T;
-    using A = CoopAxis<N, CT>;
+    using A = CoopAxis<N, CT, EE>;
     constexpr int E = A::E, TP = A::TP;
     constexpr bool PHASE = (MODE == COL_T_P || MODE == COL_T_PR);
     constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
     constexpr int units = NX / 2, w4 = NX / 2;                 // float4 per grid row
-    const CoopUnits<N, CT> U;
+    const CoopUnits<N, CT, EE> U;
     float4 *sb = slots + U.g * A::SLOTS;
     const GroupSync gs{1 + U.g, TP};
     float acx2, acxcy;
@@ -284,7 +287,7 @@ __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, con
             X[r] = make_float2(t.x, t.z);
             Y[r] = make_float2(t.y, t.w);
         }
-        transform_pair<N, E, TP>(X, Y, sb, U.j, T.tw8y, T.kiny, a.sy, a.imag, gs);
+        transform_pair<N, E, TP>(X, Y, sb, U.j, E == 8 ? T.tw8y : T.twy, T.kiny, a.sy, a.imag, gs);
         const float4 xa = __ldg(&T.xtab[x0]), xb = __ldg(&T.xtab[x0 + 1]);
         if constexpr (PHASE) {
             const PotCoefs pa = col_coefs_from(ph, acx2, acxcy, xa), pb = col_coefs_from(ph, acx2, acxcy, xb);
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
         const double te = __dadd_rn(t0, __dmul_rn((double)(s + 1), dt));
         if (threadIdx.x == 0) s_ph = phase_dev(a, ts, (imag || s == 0) ? hh : dt);
         __syncthreads();
-        coop_rows_pt<NX, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, imag && s > 0, loc, slots);
+        coop_rows_pt<NX, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, imag && s > 0, loc, slots);
         if (!coop_sync(a, &s_ok, &s_k)) {
             ok = false;
             break;
@@ -416,15 +419,15 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
             if (s == n - 1) {
                 if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
                 __syncthreads();
-                coop_cols<NY, NX, COL_T_P, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
+                coop_cols<NY, NX, COL_T_P, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
             } else {
-                coop_cols<NY, NX, COL_T, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
+                coop_cols<NY, NX, COL_T, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
                 ok = coop_sync(a, &s_ok, &s_k);
             }
         } else if (!imag) {
             if (threadIdx.x == 0) s_rd = red_dev(a, te);
             __syncthreads();
-            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
         } else if (!cav) {
             if (threadIdx.x == 0) {
@@ -432,12 +435,12 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
                 s_rd = red_dev(a, te);
             }
             __syncthreads();
-            coop_cols<NY, NX, COL_T_PR, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_PR, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
         } else {                                   // imaginary time with a cavity: a third, pointwise pass
             if (threadIdx.x == 0) s_rd = red_dev(a, te);
             __syncthreads();
-            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
             if (!ok) break;
             if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
