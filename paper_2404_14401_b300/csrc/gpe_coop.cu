@@ -134,19 +134,74 @@ __device__ bool coop_sync(const CoopArgs &a, int *s_ok, unsigned int *k)
     return *s_ok != 0;
 }
 
+// Norm, overlaps, 1/sqrt(norm) and the cavity field from the sums (Sec. 3.3
+// normalisation, Eqs. 14-15), in FP64 on one thread: the quantities and the
+// status latching of finalize_fields, with one reciprocal per denominator
+// instead of a division per quantity (every CTA runs this between two passes
+// while its other threads wait).
+__device__ void coop_finalize(const double *S, const RedArgs &r, DevScalars *sc)
+{
+    const double inv0 = 1.0 / S[0];
+    const double norm = S[0] * r.dxdy, O = S[1] * inv0, B = S[2] * inv0;
+    sc->norm = norm;
+    sc->O = O;
+    sc->B = B;
+    sc->c = rsqrt(norm);
+    if (!isfinite(norm) || !(norm > 0.0) || !isfinite(O) || !isfinite(B)) {
+        latch_status(sc, GPE_ENONFINITE);
+        return;
+    }
+    if (r.cavity) {
+        const double dr = r.dc - r.U0 * B, di = r.kappa;
+        const double den = dr * dr + di * di;
+        if (!(den > 1e-24)) {
+            latch_status(sc, GPE_EILLCOND);
+            sc->alpha_re = 0.0;
+            sc->alpha_im = 0.0;
+            return;
+        }
+        const double iden = 1.0 / den;
+        double ps = 0.0, pc = 0.0;               // probe Omega_c exp(i (Delta_p t + phi)) (Sec. 5.4)
+        if (r.probe_omega != 0.0) sincos(r.probe_delta * r.t + r.probe_phi, &ps, &pc);
+        const double fa = r.N * r.eta * O + r.probe_omega * pc, fb = r.probe_omega * ps;
+        sc->alpha_re = (fa * dr + fb * di) * iden;
+        sc->alpha_im = (fb * dr - fa * di) * iden;
+    } else {
+        sc->alpha_re = 0.0;
+        sc->alpha_im = 0.0;
+    }
+}
+
+// Sum of the first `count` rows of part[][NQ] (K of them), by warp 0 alone in
+// a fixed order (lane-strided, then a shuffle tree): the same in every CTA.
+// Valid in lane 0.
+__device__ void coop_sum_partials(const double *part, int count, double (&S)[3])
+{
+    const int lane = threadIdx.x & 31;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int b = lane; b < count; b += 32)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i] += __ldcg(&part[(size_t)b * NQ + i]);
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S[i] = acc[i];
+}
+
 // Finish a reducing pass: the CTA's FP64 partials (norm, O and B sums) into
-// part[blockIdx.x], the grid barrier, then every CTA sums all partials in
-// block order and finalises norm, c and alpha into its own copy `loc`; CTA 0
-// also writes them to the context's scalars.
+// part[blockIdx.x], the grid barrier, then warp 0 of every CTA sums all
+// partials in block order and thread 0 finalises norm, c and alpha into the
+// CTA's own copy `loc`; CTA 0 also writes them to the context's scalars.
 __device__ bool coop_reduce(const CoopArgs &a, const float (&q)[3], const RedArgs &rd, double *part, DevScalars *loc,
                             double *red, int *s_ok, unsigned int *k)
 {
     block_sum<3>(q, part + (size_t)blockIdx.x * NQ, red);
     if (!coop_sync(a, s_ok, k)) return false;
     double S[3];
-    sum_partials<3>(part, (int)gridDim.x, S, red);
+    if (threadIdx.x < 32) coop_sum_partials(part, (int)gridDim.x, S);
     if (threadIdx.x == 0) {
-        finalize_fields(S, rd, loc);
+        coop_finalize(S, rd, loc);
         if (blockIdx.x == 0) {
             DevScalars *sc = a.T.sc;
             sc->norm = loc->norm;
