@@ -337,9 +337,9 @@ enum { GPE_VARIANT_PAIR_ROWS = 64 };
  * by a grid barrier, the phase and reduction arguments evaluated on the
  * device, psi kept in L2 between passes.  Equal to the per-pass path to
  * FP32 rounding.  On by default for 512 x 512 grids, where it measured
- * faster than the per-pass path (per step on a B300: real time 10.7 against
- * 13.2 us, the cavity ramp 18.9 against 24.6 us, imaginary time 16.9 against
- * 24.1 us); at 1024 points it was slower and is off unless set.  It takes
+ * faster than the per-pass path (per step on a B300: real time 10.9 against
+ * 13.3 us, the cavity ramp 17.8 against 24.6 us, imaginary time 16.2 against
+ * 23.8 us); at 1024 points it was slower in real time and is off unless set.  It takes
  * one host launch per call instead of two or three per step.  It does not apply while the context
  * profiles its passes (gpe_profile), when it has more than 256 control
  * points, for more than 2^22 steps in one call, or while its stream is being

@@ -452,9 +452,9 @@ gpe_status gpe_create(int nx, int ny, double Lx, double Ly, double m, double g, 
     c->pair_rows = (nx >= 512 && !getenv("GPE_NO_PAIR_ROWS")) ? 1 : 0;
     // the cooperative kernel by default on 512^2 grids, where it measured
     // faster than the per-pass path in every step program (per step: real
-    // time 10.7 against 13.2 us, the cavity ramp 18.9 against 24.6 us,
-    // imaginary time 16.9 against 24.1 us); at 1024^2 it was slower in real
-    // time (24.1 against 21.1 us) and within 4% otherwise, so it is a choice
+    // time 10.9 against 13.3 us, the cavity ramp 17.8 against 24.6 us,
+    // imaginary time 16.2 against 23.8 us); at 1024^2 it was slower in real
+    // time (24.2 against 21.4 us) and within 6% otherwise, so it is a choice
     // there
     c->coop = (nx == 512 && ny == 512 && !getenv("GPE_NO_COOP")) ? 1 : 0;
     c->launches = 0;

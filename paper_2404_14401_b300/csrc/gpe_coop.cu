@@ -34,10 +34,10 @@
 // which is why 512-point pairs are transformed in the radix-8 schedule (8
 // elements per thread, two warps per pair) rather than the per-pass kernels'
 // radix-16 one.  Measured on a B300, per step against the per-pass path:
-// 512^2 lattice (real time) 10.7 against 13.2 us, the 512^2 cavity ramp 18.9
-// against 24.6 us, a 512^2 trap in imaginary time 16.9 against 24.1 us.  At
-// 1024^2: real time 24.1 against 21.1 us, imaginary time 31.9 against 33.2
-// us, the cavity 34.0 against 35.3 us.  At 512^2 with 256-thread CTAs it was
+// 512^2 lattice (real time) 10.9 against 13.3 us, the 512^2 cavity ramp 17.8
+// against 24.6 us, a 512^2 trap in imaginary time 16.2 against 23.8 us.  At
+// 1024^2: real time 24.2 against 21.4 us, imaginary time 31.6 against 33.6
+// us, the cavity 33.4 against 35.2 us.  At 512^2 with 256-thread CTAs it was
 // 11.1, 20.2 and 18.0 us; with 16 elements per thread (one warp per pair)
 // 14.7, 24.0 and 22.6 us; with 512-thread CTAs 12.6, 25.3 and 23.3 us.  At
 // 1024^2 with the radix-8 schedule, real time took 26.6 us (two CTAs per SM)
