@@ -158,7 +158,10 @@ gpe_status gpe_step(gpe_ctx *ctx, int n, double dt, gpe_mode mode);
  * host threads on one device take turns on the lanes.  Contexts must be on
  * the current device.  Same argument rules and errors as gpe_step; contexts
  * must be distinct.  Environment: GPE_SERIAL_MANY (no lanes: the contexts'
- * own streams, one pass at a time) and GPE_NO_GRAPH (no graph replay). */
+ * own streams, one pass at a time) and GPE_NO_GRAPH (no graph replay).
+ * Read when a context is created, GPE_NO_PAIR_ROWS, GPE_NO_PAIR_COLS,
+ * GPE_NO_GROUP_ROWS, GPE_NO_STREAM_PASSES and GPE_NO_COOP clear the
+ * corresponding default pass variants (below). */
 gpe_status gpe_step_many(gpe_ctx *const *ctxs, int count, int n, double dt, gpe_mode mode);
 
 /* ---- Persistent batch: n lockstep steps of many contexts in one launch ----
