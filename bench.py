@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-single", action="store_true", help="skip the single-trajectory 1024^2 / 2048^2 leg")
     ap.add_argument("--ncu-case", default="", metavar="NX[xNY]",
                     help="only run `--steps` real-time steps of the lattice workload on one NX x NY grid (psi built "
-                         "on the device, no relaxation) and exit: a small case for ncu captures of the passes")
+                         "on the device, no relaxation) and exit: a small case for ncu captures of the passes; "
+                         "`adjoint`: one checkpointed adjoint call of `--steps` steps of the adjoint-control "
+                         "workload (512^2)")
     ap.add_argument("--ncu-sweep", type=int, default=0, metavar="K",
                     help="only run `--steps` persistent-batch steps of the first K sweep instances of each size and "
                          "exit: a small case for ncu captures of the batch kernel")
@@ -544,8 +546,11 @@ def single_leg(dev, steps=400):
 def adjoint_leg(dev, with_oracle):
     """The adjoint-control workload (512^2, 4000 real-time steps, 200 lattice
     control points): one gpe_adjoint_lattice call (checkpointed forward and
-    reverse sweep) timed end to end, the adjoint passes timed with events,
-    and, beside it, the FP64 oracle adjoint on a bounded sample of steps."""
+    reverse sweep) timed end to end on the default path (at 512^2 the
+    cooperative kernels: three launches per segment of 64 steps), the same
+    call on the per-pass path beside it, the per-pass adjoint kernels timed
+    with events over the first 256 steps, and the FP64 oracle adjoint on a
+    bounded sample of steps."""
     import numpy as np
     import torch
 
@@ -560,14 +565,28 @@ def adjoint_leg(dev, with_oracle):
     sim.set_potential(p)
     sim.set_psi(psi0)
     tuned = sim.tune(dt)                                  # pass variants and row tile of this grid
-    sim.adjoint_lattice(phi, 64, dt)                      # warm-up (tables, modules)
-    sim.set_psi(psi0)
-    sim.t = 0.0
+    coop = bool(sim.variants & abi.GPE_VARIANT_COOP)
+
+    def run(k, reverse=False):
+        sim.set_psi(psi0)
+        sim.t = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, grad = sim.adjoint_lattice(phi, k, dt, reverse=reverse)
+        return J, grad, time.perf_counter() - t0
+
+    run(64)                                               # warm-up (tables, modules)
+    l0 = sim.launches
+    J, grad, wall = run(steps)
+    calls = sim.launches - l0
+    # the same call pass by pass (per-pass launches throughout)
+    sim.variants = sim.variants ^ abi.GPE_VARIANT_COOP
+    run(64)
+    Jo, go, wall_o = run(steps)
+    sim.variants = sim.variants ^ abi.GPE_VARIANT_COOP
+    # the per-pass adjoint kernels with events (profiling keeps to the per-pass path)
     sim.profile(True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    J, grad = sim.adjoint_lattice(phi, steps, dt)
-    wall = time.perf_counter() - t0
+    run(256)
     rms, rn = abi.gpe_profile_read_kind(sim.ctx, abi.GPE_PASS_ADJ_ROW)
     cms, cn = abi.gpe_profile_read_kind(sim.ctx, abi.GPE_PASS_ADJ_COL)
     sim.profile(False)
@@ -578,19 +597,22 @@ def adjoint_leg(dev, with_oracle):
                        "points, J = E(psi_T) + |<phi|psi_T>|^2",
            "value": n * n * steps / wall, "unit": "pt*steps/s (checkpointed forward + reverse sweep)",
            "wall_s": wall, "J": J, "grad_norm": float(np.linalg.norm(grad)), "pass_variants": tuned,
+           "path": ("cooperative kernels: the forward sweep, each segment's recomputation and its adjoint passes "
+                    "one launch each" if coop else "per-pass launches"), "launches": calls,
+           ("per_pass" if coop else "cooperative"): {
+               "value": n * n * steps / wall_o, "wall_s": wall_o,
+               "J_rel_diff": abs(Jo - J) / abs(J),
+               "grad_max_abs_diff_over_max": float(np.max(np.abs(np.asarray(go) - np.asarray(grad)))
+                                                   / np.max(np.abs(np.asarray(grad))))},
            "adjoint_row_pass_ms": rms / max(rn, 1), "adjoint_col_pass_ms": cms / max(cn, 1),
+           "pass_ms_note": "the per-pass ROW_ADJ / COL_ADJ kernels, events around each launch, first 256 steps",
            "roofline": {"bound": "hbm", "kernel": f"{'row' if dom == 'ROW_ADJ' else 'col'}_kernel<{n},{dom}>",
                         "achieved": alg / (dom_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": alg / (dom_ms * 1e-3) / 1e9 / peak, "traffic": None,
                         "alg_bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs",
                         "note": "the 2 MB state stays in L2 across passes"}}
     # the same call with the reverse sweep stepping backward in time (no checkpoints)
-    sim.set_psi(psi0)
-    sim.t = 0.0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    Jr, gr = sim.adjoint_lattice(phi, steps, dt, reverse=True)
-    rwall = time.perf_counter() - t0
+    Jr, gr, rwall = run(steps, reverse=True)
     g0, g1 = np.asarray(grad), np.asarray(gr)
     out["reverse_sweep"] = {
         "value": n * n * steps / rwall, "wall_s": rwall, "J_equal": Jr == J,
@@ -914,7 +936,16 @@ def ncu_case(args):
 
     import gpe_inputs as gi
     from paper_2404_14401_b300 import Batch, Simulation
-    if args.ncu_case:
+    if args.ncu_case == "adjoint":
+        # one checkpointed adjoint call of the adjoint-control workload (512^2)
+        w = gi.adjoint_control()
+        p = w["params"]
+        s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
+        s.set_potential(p)
+        s.set_psi(w["psi0"]().astype(np.complex64))
+        s.adjoint_lattice(torch.from_numpy(w["phi"]().astype(np.complex64)).cuda(), args.steps, w["dt"])
+        status = s.sync()
+    elif args.ncu_case:
         nx, ny = (int(v) for v in (args.ncu_case + "x" + args.ncu_case).split("x")[:2])
         w = gi.lattice_real_time(n=nx, L=40.0)
         p = dict(w["params"], nx=nx, ny=ny, Lx=0.02 * nx, Ly=0.02 * ny)

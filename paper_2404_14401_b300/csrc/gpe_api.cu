@@ -611,42 +611,11 @@ gpe_status step_epilogue(gpe_ctx *c, int n, double dt, gpe_mode mode)
     return GPE_OK;
 }
 
-// The cooperative kernel runs gpe_step on one context whose grid it is built
-// for when the context's bit is set (by default on 512^2 grids), unless the context
-// profiles its passes (per-pass events), has more control points than the
-// launch arguments carry, or its stream is being captured into a graph.
-bool coop_applies(gpe_ctx *c, int n)
+// The launch arguments of the cooperative kernels for this context: its
+// tables and potential parameters, its control points, n steps of dt in
+// `mode` from the context's time.
+std::unique_ptr<CoopArgs> coop_args(const gpe_ctx *c, int n, double dt, int imag)
 {
-    // at most 3 barriers per step: the 32-bit arrival count of one launch
-    // stays below 2^32 for n <= 2^22 on any GPU of up to 256 SMs
-    if (!c->coop || c->prof || !coop_ok(c->nx, c->ny) || c->ctrl_t.size() > (size_t)COOP_MAX_CTRL || n > (1 << 22))
-        return false;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
-        cudaGetLastError();
-        return false;
-    }
-    return true;
-}
-
-// All n steps of one context in one cooperative launch: the program of
-// step_prologue / step_part / step_epilogue with the phase and reduction
-// arguments evaluated on the device (the kinetic tables for (dt, mode) are
-// made here first, as step_prologue makes them).  If the device refuses the
-// cooperative launch (nothing of it ran), *ran is false and the context
-// keeps to the per-pass path from then on.
-gpe_status step_coop(gpe_ctx *c, int n, double dt, gpe_mode mode, bool *ran)
-{
-    *ran = false;
-    const int imag = mode == GPE_IMAG;
-    if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
-        TRY(timed_launch(c, 2, [&] {
-            return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
-        }, "kinetic tables"));
-        c->kin_valid = true;
-        c->kin_dt = dt;
-        c->kin_mode = (int)mode;
-    }
     static_assert(sizeof(CoopArgs) < 32000, "launch arguments");
     std::unique_ptr<CoopArgs> a(new CoopArgs());
     memset(a.get(), 0, sizeof(CoopArgs));
@@ -684,7 +653,47 @@ gpe_status step_coop(gpe_ctx *c, int n, double dt, gpe_mode mode, bool *ran)
         a->ctrl_t[i] = c->ctrl_t[i];
         a->ctrl_v[i] = c->ctrl_v[i];
     }
-    // the barrier's counter, generation and abort flag start at zero
+    return a;
+}
+
+// The cooperative kernel runs gpe_step on one context whose grid it is built
+// for when the context's bit is set (by default on 512^2 grids), unless the context
+// profiles its passes (per-pass events), has more control points than the
+// launch arguments carry, or its stream is being captured into a graph.
+bool coop_applies(gpe_ctx *c, int n)
+{
+    // at most 3 barriers per step: the 32-bit arrival count of one launch
+    // stays below 2^32 for n <= 2^22 on any GPU of up to 256 SMs
+    if (!c->coop || c->prof || !coop_ok(c->nx, c->ny) || c->ctrl_t.size() > (size_t)COOP_MAX_CTRL || n > (1 << 22))
+        return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// All n steps of one context in one cooperative launch: the program of
+// step_prologue / step_part / step_epilogue with the phase and reduction
+// arguments evaluated on the device (the kinetic tables for (dt, mode) are
+// made here first, as step_prologue makes them).  If the device refuses the
+// cooperative launch (nothing of it ran), *ran is false and the context
+// keeps to the per-pass path from then on.
+gpe_status step_coop(gpe_ctx *c, int n, double dt, gpe_mode mode, bool *ran)
+{
+    *ran = false;
+    const int imag = mode == GPE_IMAG;
+    if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
+        TRY(timed_launch(c, 2, [&] {
+            return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
+        }, "kinetic tables"));
+        c->kin_valid = true;
+        c->kin_dt = dt;
+        c->kin_mode = (int)mode;
+    }
+    std::unique_ptr<CoopArgs> a = coop_args(c, n, dt, imag);
+    // the barrier's counter and abort flag start at zero
     TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
     const cudaError_t e = launch_coop(*a, c->stream);
     if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
@@ -801,16 +810,84 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     CUtensorMap lam_map;
     TRY(encode_map(c, lam, &lam_map));
 
-    // forward, one V/2 - T - V/2 step per call, keeping a checkpoint every S
-    // steps (none when the reverse sweep steps backward instead)
+    // The cooperative kernels take the forward sweep, each segment's
+    // recomputation and its adjoint passes, one launch each, where they apply
+    // (a checkpointed run without a cavity on a grid they are built for).
+    // The forward sweep and the recomputation both run the unfused steps of
+    // launch_coop_states, so the recomputed states are the forward sweep's.
+    bool coop = !reverse && !c->pot.cavity && coop_applies(c, L.S);
+    std::unique_ptr<CoopArgs> ca;
+    if (coop) {
+        if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)GPE_REAL) {
+            TRY(timed_launch(c, 2, [&] {
+                return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, 0, c->stream);
+            }, "kinetic tables"));
+            c->kin_valid = true;
+            c->kin_dt = dt;
+            c->kin_mode = (int)GPE_REAL;
+        }
+        ca = coop_args(c, 0, dt, 0);
+        ca->t0 = t0;
+        ca->lam = lam;
+        ca->st = st;
+        ca->P = P;
+        ca->gout = gdev;
+        ca->L0x = (float)c->pot.lat_V0x;
+        ca->L0y = (float)c->pot.lat_V0y;
+    }
+    // steps s0 .. s1 - 1 in one cooperative launch: their states into st
+    // (adj = false) or their adjoint passes (adj = true).  *ran is false if
+    // the device refused the launch (nothing of it ran); the context keeps to
+    // the per-pass path from then on.
+    auto coop_run = [&](bool adj, int s0, int s1, bool *ran) -> gpe_status {
+        *ran = false;
+        ca->s0 = s0;
+        ca->s1 = s1;
+        TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
+        const cudaError_t e = adj ? launch_coop_adj(*ca, c->stream) : launch_coop_states(*ca, c->stream);
+        if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
+            cudaGetLastError();
+            c->coop = 0;
+            coop = false;
+            return fail(c, GPE_OK, "cooperative launch refused (%s): the per-pass path from now on",
+                        cudaGetErrorString(e));
+        }
+        TRY(cuda_check(c, e, adj ? "cooperative adjoint kernel" : "cooperative states kernel"));
+        c->launches++;
+        *ran = true;
+        return GPE_OK;
+    };
+
+    // forward, keeping a checkpoint every S steps (none when the reverse
+    // sweep steps backward instead): segment by segment through st, else one
+    // V/2 - T - V/2 step per call
     if (!reverse) TRY(copy_d2d(c, ck, c->psi));
-    for (int s = 0; s < n; ++s) {
+    float2 *psiT = ck + (size_t)L.K * P;
+    int sf = 0;                                    // forward steps done
+    for (int k = 0; k < L.K && coop; ++k) {
+        const int s0 = k * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
+        TRY(copy_d2d(c, st, ck + (size_t)k * P));
+        bool ran = false;
+        TRY(coop_run(false, s0, s1, &ran));
+        if (!ran) break;
+        TRY(copy_d2d(c, ck + (size_t)(k + 1) * P, st + (size_t)(s1 - s0) * P));
+        sf = s1;
+    }
+    if (sf > 0 && sf < n) {                        // refused after the first segment: on from the checkpoint
+        TRY(copy_d2d(c, c->psi, ck + (size_t)(sf / L.S) * P));
+        c->t = t0 + sf * dt;
+    }
+    for (int s = sf; s < n; ++s) {
         TRY(gpe_step(c, 1, dt, GPE_REAL));
         if (!reverse && (s + 1) % L.S == 0 && s + 1 < n)
             TRY(copy_d2d(c, ck + (size_t)((s + 1) / L.S) * P, c->psi));
     }
-    float2 *psiT = ck + (size_t)L.K * P;
-    TRY(copy_d2d(c, psiT, c->psi));
+    if (sf < n) {
+        TRY(copy_d2d(c, psiT, c->psi));
+    } else {                                       // the context at psi_T, as gpe_step leaves it
+        TRY(copy_d2d(c, c->psi, psiT));
+        c->t = tT;
+    }
 
     // J = E(psi_T) + |<phi|psi_T>|^2
     gpe_obs o;
@@ -895,14 +972,22 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     // its checkpoint, then the two adjoint passes of each step
     for (int k = L.K - 1; k >= 0 && !reverse; --k) {
         const int s0 = k * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
-        TRY(copy_d2d(c, c->psi, ck + (size_t)k * P));
-        c->t = t0 + s0 * dt;
-        TRY(copy_d2d(c, st, c->psi));
-        for (int i = 1; i <= s1 - s0; ++i) {
-            TRY(gpe_step(c, 1, dt, GPE_REAL));
-            TRY(copy_d2d(c, st + (size_t)i * P, c->psi));
+        bool rec = false, done = false;
+        if (coop) {
+            TRY(copy_d2d(c, st, ck + (size_t)k * P));
+            TRY(coop_run(false, s0, s1, &rec));
         }
-        for (int s = s1 - 1; s >= s0; --s) {
+        if (!rec) {
+            TRY(copy_d2d(c, c->psi, ck + (size_t)k * P));
+            c->t = t0 + s0 * dt;
+            TRY(copy_d2d(c, st, c->psi));
+            for (int i = 1; i <= s1 - s0; ++i) {
+                TRY(gpe_step(c, 1, dt, GPE_REAL));
+                TRY(copy_d2d(c, st + (size_t)i * P, c->psi));
+            }
+        }
+        if (coop) TRY(coop_run(true, s0, s1, &done));
+        for (int s = s1 - 1; s >= s0 && !done; --s) {
             TRY(adjoint_row(s, st + (size_t)(s + 1 - s0) * P));
             TRY(adjoint_col(s, st + (size_t)(s - s0) * P));
         }

@@ -260,10 +260,11 @@ template <int N, int CT, int E> struct CoopUnits {
 };
 
 // Row pass ROW_PT on the row pairs (2u, 2u + 1): [scale c] potential phase,
-// T_x, as row_pair_kernel computes it.
+// T_x, as row_pair_kernel computes it, from src into dst (the same buffer
+// when the step is in place).
 template <int N, int CT, int EE>
 __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, int use_c,
-                             const DevScalars &loc, float4 *slots)
+                             const DevScalars &loc, float4 *slots, const float2 *src, float2 *dst)
 {
     const Tables &T = P.T;
     using A = CoopAxis<N, CT, EE>;
@@ -278,13 +279,14 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
     for (int u = U.gg; u < units; u += U.G) {
         const bool act = check_index((long long)2 * u + 1, a.ny, T.sc);
         const int y0 = act ? 2 * u : 0;
-        float2 *ra = a.psi + (size_t)y0 * N, *rb = ra + N;
+        const float2 *ia = src + (size_t)y0 * N, *ib = ia + N;
+        float2 *ra = dst + (size_t)y0 * N, *rb = ra + N;
         float2 X[E], Y[E], V[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int xi = U.j + r * TP;
-            const float2 p = act ? __ldcg(ra + xi) : make_float2(0.f, 0.f);
-            const float2 q = act ? __ldcg(rb + xi) : make_float2(0.f, 0.f);
+            const float2 p = act ? __ldcg(ia + xi) : make_float2(0.f, 0.f);
+            const float2 q = act ? __ldcg(ib + xi) : make_float2(0.f, 0.f);
             X[r] = make_float2(p.x * cs, q.x * cs);
             Y[r] = make_float2(p.y * cs, q.y * cs);
         }
@@ -313,11 +315,11 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
 // Column pass on the column pairs (2u, 2u + 1) of columns of N points in a
 // grid NX wide, as col_pair_kernel computes it: T_y, then (COL_T_P,
 // COL_T_PR) the closing half phase, then (COL_T_R, COL_T_PR) the norm and
-// overlap sums added to q.  With the width a constant, a thread's 16 strided
-// elements are immediate offsets from one address.
+// overlap sums added to q, in place on psi.  With the width a constant, a
+// thread's strided elements are immediate offsets from one address.
 template <int N, int NX, int MODE, int CT, int EE>
 __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, const DevScalars &loc,
-                          float4 *slots, float (&q)[3])
+                          float4 *slots, float (&q)[3], float2 *psi)
 {
     const Tables &T = P.T;
     using A = CoopAxis<N, CT, EE>;
@@ -334,7 +336,7 @@ __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, con
         const bool act = check_index((long long)2 * u + 1, NX, T.sc);
         const int x0 = act ? 2 * u : 0;
         // {re, im} of columns x0, x0 + 1 at row j + r TP: cb[r TP w4]
-        float4 *cb = reinterpret_cast<float4 *>(a.psi + x0) + (size_t)U.j * w4;
+        float4 *cb = reinterpret_cast<float4 *>(psi + x0) + (size_t)U.j * w4;
         float2 X[E], Y[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -464,7 +466,8 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
         const double te = __dadd_rn(t0, __dmul_rn((double)(s + 1), dt));
         if (threadIdx.x == 0) s_ph = phase_dev(a, ts, (imag || s == 0) ? hh : dt);
         __syncthreads();
-        coop_rows_pt<NX, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, imag && s > 0, loc, slots);
+        coop_rows_pt<NX, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, imag && s > 0, loc, slots, a.psi,
+                                                                   a.psi);
         if (!coop_sync(a, &s_ok, &s_k)) {
             ok = false;
             break;
@@ -474,15 +477,15 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
             if (s == n - 1) {
                 if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
                 __syncthreads();
-                coop_cols<NY, NX, COL_T_P, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
+                coop_cols<NY, NX, COL_T_P, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q, a.psi);
             } else {
-                coop_cols<NY, NX, COL_T, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
+                coop_cols<NY, NX, COL_T, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q, a.psi);
                 ok = coop_sync(a, &s_ok, &s_k);
             }
         } else if (!imag) {
             if (threadIdx.x == 0) s_rd = red_dev(a, te);
             __syncthreads();
-            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q, a.psi);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
         } else if (!cav) {
             if (threadIdx.x == 0) {
@@ -490,12 +493,12 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
                 s_rd = red_dev(a, te);
             }
             __syncthreads();
-            coop_cols<NY, NX, COL_T_PR, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_PR, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q, a.psi);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
         } else {                                   // imaginary time with a cavity: a third, pointwise pass
             if (threadIdx.x == 0) s_rd = red_dev(a, te);
             __syncthreads();
-            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q);
+            coop_cols<NY, NX, COL_T_R, CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::E>(a, s_P, s_ph, loc, slots, q, a.psi);
             ok = coop_reduce(a, q, s_rd, a.T.part_col, &loc, red, &s_ok, &s_k);
             if (!ok) break;
             if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
@@ -516,30 +519,319 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS) coo
     }
 }
 
+// ------------------------------------------------------------------ states of a segment
+// Real-time steps s0 .. s1 - 1 of a context without a cavity, each a whole
+// V/2 - T - V/2 step (Eq. 3) as one gpe_step call of one step runs it, with
+// every state kept: the row pass reads psi_s from st[s - s0] and writes into
+// st[s - s0 + 1], where the column pass finishes psi_{s+1} in place (T_y and
+// the closing half phase).  A fused run of several steps never holds
+// psi_{s+1}: its closing half phase is merged into the next opening one.
+// Step s opens at t0 + s dt and closes at that time plus dt, the times the
+// adjoint passes of the same step take.  The checkpointed adjoint runs its
+// forward sweep and each segment's recomputation through this kernel, so
+// the states it recomputes are bit for bit the ones of the forward sweep.
+template <int NX, int NY>
+__global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
+    coop_states_kernel(const __grid_constant__ CoopArgs a)
+{
+    using C = CoopCfg<NX, NY>;
+    extern __shared__ unsigned char smraw[];
+    __shared__ DevScalars loc;                     // c = 1, alpha = 0: no reduction on this path
+    __shared__ PhaseArgs s_ph;
+    __shared__ CoopPtrs s_P;
+    __shared__ int s_ok;
+    __shared__ unsigned int s_k;
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *slots = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    if (threadIdx.x == 0) {
+        memset(&loc, 0, sizeof(loc));
+        loc.c = 1.0;
+        s_k = 0;
+        s_P.T = a.T;
+        s_P.V = a.V;
+        s_ok = check_index((long long)((unsigned char *)slots + C::SLOT_BYTES - smraw) - 1, dyn_smem_bytes(), a.T.sc);
+        if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const double hh = __dmul_rn(0.5, a.dt);
+    float q[3] = {0.f, 0.f, 0.f};
+    for (int s = a.s0; s < a.s1; ++s) {
+        const double ts = __dadd_rn(a.t0, __dmul_rn((double)s, a.dt));
+        const double te = __dadd_rn(ts, a.dt);
+        const float2 *from = a.st + (size_t)(s - a.s0) * a.P;
+        float2 *to = a.st + (size_t)(s + 1 - a.s0) * a.P;
+        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, hh);
+        __syncthreads();
+        coop_rows_pt<NX, C::CT, C::E>(a, s_P, s_ph, 0, loc, slots, from, to);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
+        __syncthreads();
+        coop_cols<NY, NX, COL_T_P, C::CT, C::E>(a, s_P, s_ph, loc, slots, q, to);
+        if (s + 1 < a.s1 && !coop_sync(a, &s_ok, &s_k)) return;
+    }
+}
+
+// ------------------------------------------------------------------ adjoint segment
+// The reverse sweep of one segment of the checkpointed adjoint (the
+// discrete adjoint of the real-time step, Sec. 3.1, for a lattice-depth
+// control, Eq. 9): for s = s1 - 1 down to s0, the adjoint row pass with the
+// step's end state and the adjoint column pass with its start state, as
+// row_kernel<ROW_ADJ> and col_kernel<COL_ADJ> compute them, on pencil pairs,
+// separated by grid barriers.  Each pass's CTAs store their FP64 partials
+// of its dJ/dv; the sums are taken in CTA order after a grid barrier every
+// few hundred steps and at the end of the segment, off the passes' critical
+// path (the per-pass kernels finish each sum in the CTA that ends last).  No
+// cavity on this path.
+
+// Row pass of step s on the row pairs of lambda: the adjoint of the closing
+// half phase (its output psi2 = psi_{s+1} has the phase's density; its input
+// is exp(+i theta) psi2), then T_x^H.  gq: sum of Im(conj(mu) in) L(r).
+template <int N, int CT, int EE>
+__device__ __noinline__ void coop_adj_rows(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph,
+                                           const float2 *psi2, float4 *slots, float &gq)
+{
+    const Tables &T = P.T;
+    using A = CoopAxis<N, CT, EE>;
+    constexpr int E = A::E, TP = A::TP;
+    const int units = a.ny / 2;
+    const CoopUnits<N, CT, EE> U;
+    float4 *sb = slots + U.g * A::SLOTS;
+    const GroupSync gs{1 + U.g, TP};
+    float acx2, acxcy;
+    alpha_amps(ph, 0.0, 0.0, acx2, acxcy);
+    for (int u = U.gg; u < units; u += U.G) {
+        const bool act = check_index((long long)2 * u + 1, a.ny, T.sc);
+        const int y0 = act ? 2 * u : 0;
+        float2 *ra = a.lam + (size_t)y0 * N, *rb = ra + N;
+        const float2 *oa = psi2 + (size_t)y0 * N, *ob = oa + N;
+        const float4 ya = __ldg(&T.ytab[y0]), yb = __ldg(&T.ytab[y0 + 1]);
+        const PotCoefs pa = row_coefs_from(ph, acx2, acxcy, ya), pb = row_coefs_from(ph, acx2, acxcy, yb);
+        const float *Va = P.V ? P.V + (size_t)y0 * N : nullptr;
+        float2 X[E], Y[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int xi = U.j + r * TP;
+            const float4 xt = __ldg(&T.xtab[xi]);
+            float2 la = act ? __ldcg(ra + xi) : make_float2(0.f, 0.f);
+            float2 lb = act ? __ldcg(rb + xi) : make_float2(0.f, 0.f);
+            const float2 o_a = act ? __ldcg(oa + xi) : make_float2(0.f, 0.f);
+            const float2 o_b = act ? __ldcg(ob + xi) : make_float2(0.f, 0.f);
+            float Vxa = pot_at(pa, xt), Vxb = pot_at(pb, xt);
+            if (Va) {
+                Vxa += a.V_scale * __ldg(&Va[xi]);
+                Vxb += a.V_scale * __ldg(&Va[N + xi]);
+            }
+            const float tha = (Vxa + a.g * (o_a.x * o_a.x + o_a.y * o_a.y)) * ph.h;
+            const float thb = (Vxb + a.g * (o_b.x * o_b.x + o_b.y * o_b.y)) * ph.h;
+            gq += phase_adjoint(la, phase_rot(o_a, -tha), Vxa, a.g, ph.h) * (a.L0x * xt.y + a.L0y * ya.y);
+            gq += phase_adjoint(lb, phase_rot(o_b, -thb), Vxb, a.g, ph.h) * (a.L0x * xt.y + a.L0y * yb.y);
+            X[r] = make_float2(la.x, lb.x);
+            Y[r] = make_float2(la.y, lb.y);
+        }
+        transform_pair<N, E, TP, GroupSync, true>(X, Y, sb, U.j, E == 8 ? T.tw8x : T.twx, T.kinx, a.sx, 0, gs);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int xi = U.j + r * TP;
+                __stcg(ra + xi, make_float2(X[r].x, Y[r].x));
+                __stcg(rb + xi, make_float2(X[r].y, Y[r].y));
+            }
+        }
+    }
+}
+
+// Column pass of step s on the column pairs of lambda: T_y^H, then the
+// adjoint of the opening half phase, whose input psi2 = psi_s is the step's
+// start state.  gq as in the row pass.
+template <int N, int NX, int CT, int EE>
+__device__ __noinline__ void coop_adj_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph,
+                                           const float2 *psi2, float4 *slots, float &gq)
+{
+    const Tables &T = P.T;
+    using A = CoopAxis<N, CT, EE>;
+    constexpr int E = A::E, TP = A::TP;
+    constexpr int units = NX / 2, w4 = NX / 2;
+    const CoopUnits<N, CT, EE> U;
+    float4 *sb = slots + U.g * A::SLOTS;
+    const GroupSync gs{1 + U.g, TP};
+    float acx2, acxcy;
+    alpha_amps(ph, 0.0, 0.0, acx2, acxcy);
+    for (int u = U.gg; u < units; u += U.G) {
+        const bool act = check_index((long long)2 * u + 1, NX, T.sc);
+        const int x0 = act ? 2 * u : 0;
+        float4 *cb = reinterpret_cast<float4 *>(a.lam + x0) + (size_t)U.j * w4;
+        const float4 *ib = reinterpret_cast<const float4 *>(psi2 + x0) + (size_t)U.j * w4;
+        float2 X[E], Y[E];
+        // psi_s loaded before the transform rather than after it, where the
+        // registers allow (8 elements per thread; 16 would spill)
+        constexpr bool EARLY = E == 8;
+        float4 in[EARLY ? E : 1];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float4 t = act ? __ldcg(cb + r * TP * w4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (EARLY) in[r] = act ? __ldcg(ib + r * TP * w4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            X[r] = make_float2(t.x, t.z);
+            Y[r] = make_float2(t.y, t.w);
+        }
+        transform_pair<N, E, TP, GroupSync, true>(X, Y, sb, U.j, E == 8 ? T.tw8y : T.twy, T.kiny, a.sy, 0, gs);
+        const float4 xa = __ldg(&T.xtab[x0]), xb = __ldg(&T.xtab[x0 + 1]);
+        const PotCoefs pa = col_coefs_from(ph, acx2, acxcy, xa), pb = col_coefs_from(ph, acx2, acxcy, xb);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int y = U.j + r * TP;
+            const float4 yt = __ldg(&T.ytab[y]);
+            float Vya = pot_at(pa, yt), Vyb = pot_at(pb, yt);
+            if (P.V) {
+                Vya += a.V_scale * __ldg(&P.V[(size_t)y * NX + x0]);
+                Vyb += a.V_scale * __ldg(&P.V[(size_t)y * NX + x0 + 1]);
+            }
+            float4 pin;
+            if constexpr (EARLY) pin = in[r];
+            else pin = act ? __ldcg(ib + r * TP * w4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 la = make_float2(X[r].x, Y[r].x), lb = make_float2(X[r].y, Y[r].y);
+            gq += phase_adjoint(la, make_float2(pin.x, pin.y), Vya, a.g, ph.h) * (a.L0x * xa.y + a.L0y * yt.y);
+            gq += phase_adjoint(lb, make_float2(pin.z, pin.w), Vyb, a.g, ph.h) * (a.L0x * xb.y + a.L0y * yt.y);
+            X[r] = make_float2(la.x, lb.x);
+            Y[r] = make_float2(la.y, lb.y);
+        }
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) __stcg(cb + r * TP * w4, make_float4(X[r].x, Y[r].x, X[r].y, Y[r].y));
+        }
+    }
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
+    coop_adj_kernel(const __grid_constant__ CoopArgs a)
+{
+    using C = CoopCfg<NX, NY>;
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32 * NQ];
+    __shared__ PhaseArgs s_ph;
+    __shared__ CoopPtrs s_P;
+    __shared__ int s_ok;
+    __shared__ unsigned int s_k;
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *slots = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    if (threadIdx.x == 0) {
+        s_k = 0;
+        s_P.T = a.T;
+        s_P.V = a.V;
+        s_ok = check_index((long long)((unsigned char *)slots + C::SLOT_BYTES - smraw) - 1, dyn_smem_bytes(), a.T.sc);
+        if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const double hh = __dmul_rn(0.5, a.dt);
+    // dJ/dv partials: step s's row-pass partial of CTA b at part_row[j G + b]
+    // and its column-pass partial at part_col[j G + b], j = hi - s counting
+    // the steps since the last flush (hi); every R steps, and at the end, the
+    // 2 R sums are taken after a grid barrier, so no pass waits on them
+    const int G = (int)gridDim.x, R = NQ * MAX_BLOCKS / G;
+    int hi = a.s1 - 1;
+    for (int s = a.s1 - 1; s >= a.s0; --s) {
+        // the times of the step's closing and opening half phases, as the
+        // host computes them (t0 + s dt + dt, t0 + s dt)
+        const double ts = __dadd_rn(a.t0, __dmul_rn((double)s, a.dt));
+        const double te = __dadd_rn(ts, a.dt);
+        const size_t slot = (size_t)(hi - s) * G + blockIdx.x;
+        // psi_s, which the column pass reads, into L2 during the row pass:
+        // the segment's states outgrow L2 (65 x 2 MB at 512^2), and the
+        // column pass would otherwise wait on DRAM after its transform
+        prefetch_l2_share(a.st + (size_t)(s - a.s0) * a.P, sizeof(float2) * (size_t)NX * NY);
+        if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
+        __syncthreads();
+        float gq = 0.f;
+        coop_adj_rows<NX, C::CT, C::E>(a, s_P, s_ph, a.st + (size_t)(s + 1 - a.s0) * a.P, slots, gq);
+        float q1[1] = {2.f * s_ph.h * gq};
+        block_sum<1>(q1, a.T.part_row + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, hh);
+        __syncthreads();
+        gq = 0.f;
+        coop_adj_cols<NY, NX, C::CT, C::E>(a, s_P, s_ph, a.st + (size_t)(s - a.s0) * a.P, slots, gq);
+        q1[0] = 2.f * s_ph.h * gq;
+        block_sum<1>(q1, a.T.part_col + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (hi - s + 1 == R || s == a.s0) {
+            // flush: sum m = hi - s + 1 steps' partials, one warp per sum, in
+            // CTA order (the same in every run); a barrier before the slots
+            // are written again
+            const int m = hi - s + 1, W = (int)(blockDim.x >> 5), lane = threadIdx.x & 31;
+            for (int i = blockIdx.x * W + (int)(threadIdx.x >> 5); i < 2 * m; i += G * W) {
+                const double *src = ((i & 1) ? a.T.part_row : a.T.part_col) + (size_t)(i >> 1) * G;
+                double acc = 0.0;
+                for (int b = lane; b < G; b += 32) acc += __ldcg(&src[b]);
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+                if (lane == 0) a.gout[2 * (hi - (i >> 1)) + (i & 1)] = acc;
+            }
+            hi = s - 1;
+            if (s > a.s0 && !coop_sync(a, &s_ok, &s_k)) return;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launch
 bool coop_ok(int nx, int ny) { return (nx == 512 || nx == 1024) && (ny == 512 || ny == 1024); }
 
-template <int NX, int NY> static cudaError_t coop_launch(const CoopArgs &a, cudaStream_t s)
+// One cooperative launch of kernel K<NX, NY>: every CTA resident (CPS per
+// SM), or cudaErrorCooperativeLaunchTooLarge without launching.  `attr`
+// remembers the devices whose shared-memory limit was raised for K.
+template <int NX, int NY>
+static cudaError_t coop_go(void (*K)(CoopArgs), std::atomic<unsigned long long> &attr, const CoopArgs &a,
+                           cudaStream_t s)
 {
     using C = CoopCfg<NX, NY>;
-    static std::atomic<unsigned long long> attr{0};
-    const cudaError_t e = smem_opt_in(coop_kernel<NX, NY>, (int)C::SMEM, attr);
+    const cudaError_t e = smem_opt_in(K, (int)C::SMEM, attr);
     if (e != cudaSuccess) return e;
     int per = 0;
-    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coop_kernel<NX, NY>, C::CT, C::SMEM);
+    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, C::CT, C::SMEM);
     if (r != cudaSuccess) return r;
     if (per < C::CPS) return cudaErrorCooperativeLaunchTooLarge;
     const int grid = C::CPS * sm_count();          // all resident
     if (grid < 1) return cudaErrorInvalidValue;
     void *args[] = {const_cast<CoopArgs *>(&a)};
-    return cudaLaunchCooperativeKernel((const void *)coop_kernel<NX, NY>, dim3(grid), dim3(C::CT), args, C::SMEM, s);
+    return cudaLaunchCooperativeKernel((const void *)K, dim3(grid), dim3(C::CT), args, C::SMEM, s);
+}
+
+enum { COOP_STEPS, COOP_STATES, COOP_ADJ };
+
+template <int NX, int NY> static cudaError_t coop_launch(int which, const CoopArgs &a, cudaStream_t s)
+{
+    static std::atomic<unsigned long long> attr[3];
+    if (which == COOP_STATES) return coop_go<NX, NY>(coop_states_kernel<NX, NY>, attr[1], a, s);
+    if (which == COOP_ADJ) return coop_go<NX, NY>(coop_adj_kernel<NX, NY>, attr[2], a, s);
+    return coop_go<NX, NY>(coop_kernel<NX, NY>, attr[0], a, s);
+}
+
+static cudaError_t coop_dispatch(int which, const CoopArgs &a, cudaStream_t s)
+{
+    if (a.nx == 512) return a.ny == 512 ? coop_launch<512, 512>(which, a, s) : coop_launch<512, 1024>(which, a, s);
+    return a.ny == 512 ? coop_launch<1024, 512>(which, a, s) : coop_launch<1024, 1024>(which, a, s);
+}
+
+cudaError_t launch_coop_adj(const CoopArgs &a, cudaStream_t s)
+{
+    if (!coop_ok(a.nx, a.ny) || a.cavity || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL || a.s1 <= a.s0)
+        return cudaErrorInvalidValue;
+    return coop_dispatch(COOP_ADJ, a, s);
+}
+
+cudaError_t launch_coop_states(const CoopArgs &a, cudaStream_t s)
+{
+    if (!coop_ok(a.nx, a.ny) || a.cavity || a.imag || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL || a.s1 <= a.s0)
+        return cudaErrorInvalidValue;
+    return coop_dispatch(COOP_STATES, a, s);
 }
 
 cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s)
 {
     if (!coop_ok(a.nx, a.ny) || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL) return cudaErrorInvalidValue;
-    if (a.nx == 512) return a.ny == 512 ? coop_launch<512, 512>(a, s) : coop_launch<512, 1024>(a, s);
-    return a.ny == 512 ? coop_launch<1024, 512>(a, s) : coop_launch<1024, 1024>(a, s);
+    return coop_dispatch(COOP_STEPS, a, s);
 }
 
 }  // namespace gpe

@@ -447,6 +447,21 @@ __device__ __forceinline__ void stage_twiddles_async(float4 *__restrict__ dst, c
     bulk_load_1d(dst, src, twiddle_bytes<N>(), bar);
 }
 
+// Ask L2 to fetch this CTA's share of a `bytes`-long buffer (bytes and the
+// buffer's address multiples of 16): CTA b of G takes the b-th 16-byte-aligned
+// slice, in 4 KB bulk prefetches issued by the lanes of warp 0.  A hint
+// only: nothing waits for it, and it never reads outside the buffer.
+__device__ __forceinline__ void prefetch_l2_share(const void *buf, size_t bytes)
+{
+    if (threadIdx.x >= 32) return;
+    const size_t G = gridDim.x, chunk = ((bytes + G - 1) / G + 15) & ~(size_t)15;
+    const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < bytes ? lo + chunk : bytes;
+    for (size_t o = lo + (size_t)threadIdx.x * 4096; o < hi; o += 32 * 4096) {
+        const unsigned n = (unsigned)(hi - o < 4096 ? hi - o : 4096);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char *)buf + o), "r"(n) : "memory");
+    }
+}
+
 // Opt func in to `bytes` of dynamic shared memory once per device (function
 // attributes belong to the device's context), safe from several host threads.
 template <class F> [[maybe_unused]] static cudaError_t smem_opt_in(F *func, int bytes,

@@ -166,9 +166,26 @@ struct CoopArgs {
     double lat_V0x, lat_V0y, eta, U0, dc, kappa, N, dxdy, probe_omega, probe_delta, probe_phi;
     int cavity, pump_lattice, ctrl_target, nctrl;
     double ctrl_t[COOP_MAX_CTRL], ctrl_v[COOP_MAX_CTRL];
+    // one checkpointed-adjoint segment, steps s0 .. s1 - 1: the segment's
+    // states psi_{s0} .. psi_{s1}, P elements apart (written by
+    // launch_coop_states from psi_{s0}, read by launch_coop_adj); lambda,
+    // updated in place; dJ/dv of each half phase (gout[2 s], gout[2 s + 1]);
+    // the base lattice depths L0x, L0y (Eq. 9).  t0 is the time of step 0.
+    float2 *lam;
+    float2 *st;
+    size_t P;
+    double *gout;
+    float L0x, L0y;
+    int s0, s1;
 };
-bool coop_ok(int nx, int ny);              // grid sizes the cooperative kernel is built for
+bool coop_ok(int nx, int ny);              // grid sizes the cooperative kernels are built for
 cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s);
+// the adjoint passes of steps s1 - 1 down to s0 (ROW_ADJ, COL_ADJ of each) in
+// one cooperative launch, for a context without a cavity
+cudaError_t launch_coop_adj(const CoopArgs &a, cudaStream_t s);
+// real-time steps s0 .. s1 - 1 of a context without a cavity, unfused, from
+// st[0] = psi_{s0}, every state kept in st (one cooperative launch)
+cudaError_t launch_coop_states(const CoopArgs &a, cudaStream_t s);
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
 // tile_shift: the one-shot row pass takes 2^-tile_shift of its default rows

@@ -80,8 +80,9 @@ __device__ __forceinline__ void phase_all2(float2 (&X)[E], float2 (&Y)[E], float
 
 // T's kinetic factor on the pair, conjugated: (X, Y) <- conj(K (X, Y)) with
 // K = (1 + d) s in real time (the 1 + D form of the table) and e^{-k^2
-// dt/2m} s in imaginary time, s the 1/N of the inverse transform
-template <int E, int TP>
+// dt/2m} s in imaginary time, s the 1/N of the inverse transform.  KCONJ:
+// the adjoint propagator's factor, d -> conj(d) (real time).
+template <int E, int TP, bool KCONJ = false>
 __device__ __forceinline__ void kinetic_conj_pair(float2 (&X)[E], float2 (&Y)[E], const float2 *__restrict__ D,
                                                   int j, float s, int imag)
 {
@@ -95,7 +96,8 @@ __device__ __forceinline__ void kinetic_conj_pair(float2 (&X)[E], float2 (&Y)[E]
     } else {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            const float2 d = __ldg(&D[j + r * TP]);
+            float2 d = __ldg(&D[j + r * TP]);
+            if constexpr (KCONJ) d.y = -d.y;
             const float2 pdx = fma2(X[r], bc2(d.x), mul2(Y[r], bc2(-d.y)));
             const float2 pdy = fma2(X[r], bc2(d.y), mul2(Y[r], bc2(d.x)));
             X[r] = mul2(add2(X[r], pdx), bc2(s));
@@ -111,7 +113,7 @@ __device__ __forceinline__ void kinetic_conj_pair(float2 (&X)[E], float2 (&Y)[E]
 // directions: the row pass at 2048 points ran 34.0 -> 33.6 us per pass (its
 // instruction-cache hit rate 74 -> 85%), 4096 133 -> 125 us and 8192 918 ->
 // 814 us; the column pass at 8192 points 886 -> 798 us.
-template <int N, int E, int TP, class Sync = CtaSync>
+template <int N, int E, int TP, class Sync = CtaSync, bool KCONJ = false>
 __device__ __forceinline__ void transform_pair(float2 (&X)[E], float2 (&Y)[E], float4 *__restrict__ sb, int j,
                                                const float4 *__restrict__ tw, const float2 *__restrict__ D, float s,
                                                int imag, const Sync &sync = Sync())
@@ -119,7 +121,7 @@ __device__ __forceinline__ void transform_pair(float2 (&X)[E], float2 (&Y)[E], f
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
         fft_pair<N, E, false, 0, Sync>(X, Y, sb, j, tw, sync);
-        if (pass == 0) kinetic_conj_pair<E, TP>(X, Y, D, j, s, imag);
+        if (pass == 0) kinetic_conj_pair<E, TP, KCONJ>(X, Y, D, j, s, imag);
     }
 #pragma unroll
     for (int r = 0; r < E; ++r) Y[r] = mul2(Y[r], bc2(-1.f));      // the second conjugation

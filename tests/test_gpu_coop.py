@@ -217,3 +217,68 @@ def test_coop_defaults_and_fallbacks():
     Simulation.step_many([s, s2], 4, 5e-4)
     assert s.launches - l0 > 1
     assert s.sync() == 0 and s2.sync() == 0
+
+
+# ------------------------------------------------------------------ adjoint segments
+def adjoint_run(p, psi0, phi, steps, dt, coop):
+    """J, dJ/dv, the launches of the call, and the state and time the call
+    leaves the context at (psi_T, t_T)."""
+    s = sim_for(p, coop)
+    s.set_psi(c64(psi0))
+    l0 = s.launches
+    J, grad = s.adjoint_lattice(phi, steps, dt)
+    assert s.sync() == 0
+    return J, np.array(grad), s.launches - l0, s.get_psi(), s.t
+
+
+def segments(steps):
+    S = 1
+    while S * S < steps:
+        S += 1
+    return (steps + S - 1) // S
+
+
+@pytest.mark.parametrize("steps", [7, 16])
+def test_coop_adjoint_segments_match_per_pass_and_oracle(steps):
+    """The checkpointed adjoint on a 512^2 grid (the adjoint-control workload's
+    grid and potential, a few steps): the forward sweep, each segment's
+    recomputation and each segment's reverse sweep as one cooperative launch
+    each (segments 3 + 3 + 1 and 4 x 4), against the per-pass sweep and the
+    FP64 oracle adjoint (J to 1e-6, each dJ/dv_i to 1e-5 of the largest, the
+    tolerances of test_gpu_adjoint).  The state the call leaves the context
+    at, psi_T, agrees with the per-pass path's to the 3e-6 bound of two FP32
+    schedules (test_coop_agrees_with_per_pass_path)."""
+    w = gi.adjoint_control(n=512, L=20.0, steps=steps, npts=6, seed=15)
+    p, dt = w["params"], w["dt"]
+    psi0 = gi.gaussian_state(512, 512, 20.0, 20.0, 1.2, 1e-2, seed=16, x0=0.3, kx0=1.0)
+    phi = w["phi"]()
+    J, g, calls, psiT, tT = adjoint_run(p, psi0, phi, steps, dt, True)
+    Jq, gq, callsq, psiTq, tTq = adjoint_run(p, psi0, phi, steps, dt, False)
+    K = segments(steps)
+    # 3 K cooperative launches, the kinetic tables, and the terminal
+    # condition's passes (observables, overlap, two FFTs, kinetic product)
+    assert 3 * K <= calls <= 3 * K + 12 < callsq, (calls, callsq)
+    assert abs(tT - steps * dt) < 1e-12 and abs(tTq - steps * dt) < 1e-12
+    assert rel_l2(psiT, psiTq) < 3e-6
+    assert abs(J - Jq) < 1e-6 * abs(Jq)
+    assert np.max(np.abs(g - gq)) < 1e-5 * np.max(np.abs(gq))
+    Jr, gr = oracle.adjoint(p, c64(psi0).astype(np.complex128), phi, steps, dt)
+    assert abs(J - Jr) < 1e-6 * abs(Jr), (J, Jr)
+    assert np.max(np.abs(g - gr)) < 1e-5 * np.max(np.abs(gr))
+
+
+def test_coop_adjoint_rectangular_grid_with_potential_array():
+    """512 x 1024 with a static potential array beside the lattice control:
+    the segment kernels against the per-pass sweep."""
+    nx, ny, steps = 512, 1024, 9
+    w = gi.adjoint_control(n=512, L=10.24, steps=steps, npts=5, seed=17)
+    Varr = (0.3 * gi.normal(18, nx * ny).reshape(ny, nx)).astype(np.float32).astype(np.float64)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=10.24, Ly=20.48, Varr=Varr, V_scale=0.5)
+    psi0 = gi.gaussian_state(nx, ny, 10.24, 20.48, 1.2, 1e-2, seed=19)
+    phi = gi.target_gaussian(nx, ny, 10.24, 20.48)
+    J, g, calls, psiT, _ = adjoint_run(p, psi0, phi, steps, w["dt"], True)
+    Jq, gq, callsq, psiTq, _ = adjoint_run(p, psi0, phi, steps, w["dt"], False)
+    assert calls <= 3 * segments(steps) + 12 < callsq, (calls, callsq)
+    assert rel_l2(psiT, psiTq) < 3e-6
+    assert abs(J - Jq) < 1e-6 * abs(Jq)
+    assert np.max(np.abs(g - gq)) < 1e-5 * np.max(np.abs(gq))
