@@ -609,26 +609,81 @@ __device__ __noinline__ void coop_adj_rows(const CoopArgs &a, const CoopPtrs &P,
         const float4 ya = __ldg(&T.ytab[y0]), yb = __ldg(&T.ytab[y0 + 1]);
         const PotCoefs pa = row_coefs_from(ph, acx2, acxcy, ya), pb = row_coefs_from(ph, acx2, acxcy, yb);
         const float *Va = P.V ? P.V + (size_t)y0 * N : nullptr;
+        // 8 elements per thread: the pointwise adjoint on the packed pair; 16
+        // (1024-point rows): per row, which keeps the pass within 255 registers
         float2 X[E], Y[E];
+        if constexpr (E == 8) {
+            // lambda and psi_{s+1} of the two rows packed (row a, row b); V, then theta
+            float2 OX[E], OY[E], V[E];
+            bool small = true;
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int xi = U.j + r * TP;
-            const float4 xt = __ldg(&T.xtab[xi]);
-            float2 la = act ? __ldcg(ra + xi) : make_float2(0.f, 0.f);
-            float2 lb = act ? __ldcg(rb + xi) : make_float2(0.f, 0.f);
-            const float2 o_a = act ? __ldcg(oa + xi) : make_float2(0.f, 0.f);
-            const float2 o_b = act ? __ldcg(ob + xi) : make_float2(0.f, 0.f);
-            float Vxa = pot_at(pa, xt), Vxb = pot_at(pb, xt);
-            if (Va) {
-                Vxa += a.V_scale * __ldg(&Va[xi]);
-                Vxb += a.V_scale * __ldg(&Va[N + xi]);
+            for (int r = 0; r < E; ++r) {
+                const int xi = U.j + r * TP;
+                const float2 la = act ? __ldcg(ra + xi) : make_float2(0.f, 0.f);
+                const float2 lb = act ? __ldcg(rb + xi) : make_float2(0.f, 0.f);
+                const float2 o_a = act ? __ldcg(oa + xi) : make_float2(0.f, 0.f);
+                const float2 o_b = act ? __ldcg(ob + xi) : make_float2(0.f, 0.f);
+                X[r] = make_float2(la.x, lb.x);
+                Y[r] = make_float2(la.y, lb.y);
+                OX[r] = make_float2(o_a.x, o_b.x);
+                OY[r] = make_float2(o_a.y, o_b.y);
+                V[r] = pot_at2(pa, pb, __ldg(&T.xtab[xi]));
+                if (Va) V[r] = fma2(bc2(a.V_scale), make_float2(__ldg(&Va[xi]), __ldg(&Va[N + xi])), V[r]);
+                const float2 th = mul2(fma2(bc2(a.g), fma2(OX[r], OX[r], mul2(OY[r], OY[r])), V[r]), bc2(ph.h));
+                small = small && fabsf(th.x) <= 1.f && fabsf(th.y) <= 1.f;
             }
-            const float tha = (Vxa + a.g * (o_a.x * o_a.x + o_a.y * o_a.y)) * ph.h;
-            const float thb = (Vxb + a.g * (o_b.x * o_b.x + o_b.y * o_b.y)) * ph.h;
-            gq += phase_adjoint(la, phase_rot(o_a, -tha), Vxa, a.g, ph.h) * (a.L0x * xt.y + a.L0y * ya.y);
-            gq += phase_adjoint(lb, phase_rot(o_b, -thb), Vxb, a.g, ph.h) * (a.L0x * xt.y + a.L0y * yb.y);
-            X[r] = make_float2(la.x, lb.x);
-            Y[r] = make_float2(la.y, lb.y);
+            float2 g2 = make_float2(0.f, 0.f);
+            if (small) {
+                // the phase's input exp(+i theta) psi_{s+1}, then the adjoint of the
+                // phase on it, both rotations in the packed Taylor form
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int xi = U.j + r * TP;
+                    const float2 th = mul2(fma2(bc2(a.g), fma2(OX[r], OX[r], mul2(OY[r], OY[r])), V[r]), bc2(ph.h));
+                    float2 IX = OX[r], IY = OY[r];
+                    rot2_taylor(IX, IY, make_float2(-th.x, -th.y));
+                    const float2 thi = mul2(fma2(bc2(a.g), fma2(IX, IX, mul2(IY, IY)), V[r]), bc2(ph.h));
+                    const float2 q = adjoint2_taylor(X[r], Y[r], IX, IY, thi, a.g, ph.h);
+                    const float lx = a.L0x * __ldg(&T.xtab[xi]).y;
+                    g2 = fma2(q, fma2(bc2(a.L0y), make_float2(ya.y, yb.y), bc2(lx)), g2);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int xi = U.j + r * TP;
+                    const float4 xt = __ldg(&T.xtab[xi]);
+                    float2 la = make_float2(X[r].x, Y[r].x), lb = make_float2(X[r].y, Y[r].y);
+                    const float2 o_a = make_float2(OX[r].x, OY[r].x), o_b = make_float2(OX[r].y, OY[r].y);
+                    const float tha = (V[r].x + a.g * (o_a.x * o_a.x + o_a.y * o_a.y)) * ph.h;
+                    const float thb = (V[r].y + a.g * (o_b.x * o_b.x + o_b.y * o_b.y)) * ph.h;
+                    g2.x += phase_adjoint(la, phase_rot(o_a, -tha), V[r].x, a.g, ph.h) * (a.L0x * xt.y + a.L0y * ya.y);
+                    g2.y += phase_adjoint(lb, phase_rot(o_b, -thb), V[r].y, a.g, ph.h) * (a.L0x * xt.y + a.L0y * yb.y);
+                    X[r] = make_float2(la.x, lb.x);
+                    Y[r] = make_float2(la.y, lb.y);
+                }
+            }
+            gq += g2.x + g2.y;
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int xi = U.j + r * TP;
+                const float4 xt = __ldg(&T.xtab[xi]);
+                float2 la = act ? __ldcg(ra + xi) : make_float2(0.f, 0.f);
+                float2 lb = act ? __ldcg(rb + xi) : make_float2(0.f, 0.f);
+                const float2 o_a = act ? __ldcg(oa + xi) : make_float2(0.f, 0.f);
+                const float2 o_b = act ? __ldcg(ob + xi) : make_float2(0.f, 0.f);
+                float Vxa = pot_at(pa, xt), Vxb = pot_at(pb, xt);
+                if (Va) {
+                    Vxa += a.V_scale * __ldg(&Va[xi]);
+                    Vxb += a.V_scale * __ldg(&Va[N + xi]);
+                }
+                const float tha = (Vxa + a.g * (o_a.x * o_a.x + o_a.y * o_a.y)) * ph.h;
+                const float thb = (Vxb + a.g * (o_b.x * o_b.x + o_b.y * o_b.y)) * ph.h;
+                gq += phase_adjoint(la, phase_rot(o_a, -tha), Vxa, a.g, ph.h) * (a.L0x * xt.y + a.L0y * ya.y);
+                gq += phase_adjoint(lb, phase_rot(o_b, -thb), Vxb, a.g, ph.h) * (a.L0x * xt.y + a.L0y * yb.y);
+                X[r] = make_float2(la.x, lb.x);
+                Y[r] = make_float2(la.y, lb.y);
+            }
         }
         transform_pair<N, E, TP, GroupSync, true>(X, Y, sb, U.j, E == 8 ? T.tw8x : T.twx, T.kinx, a.sx, 0, gs);
         if (act) {
@@ -678,23 +733,64 @@ __device__ __noinline__ void coop_adj_cols(const CoopArgs &a, const CoopPtrs &P,
         transform_pair<N, E, TP, GroupSync, true>(X, Y, sb, U.j, E == 8 ? T.tw8y : T.twy, T.kiny, a.sy, 0, gs);
         const float4 xa = __ldg(&T.xtab[x0]), xb = __ldg(&T.xtab[x0 + 1]);
         const PotCoefs pa = col_coefs_from(ph, acx2, acxcy, xa), pb = col_coefs_from(ph, acx2, acxcy, xb);
+        if constexpr (E == 8) {
+            // psi_s of the two columns packed (column a, column b); V, then theta
+            float2 PX[E], PY[E], V[E];
+            bool small = true;
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int y = U.j + r * TP;
-            const float4 yt = __ldg(&T.ytab[y]);
-            float Vya = pot_at(pa, yt), Vyb = pot_at(pb, yt);
-            if (P.V) {
-                Vya += a.V_scale * __ldg(&P.V[(size_t)y * NX + x0]);
-                Vyb += a.V_scale * __ldg(&P.V[(size_t)y * NX + x0 + 1]);
+            for (int r = 0; r < E; ++r) {
+                const int y = U.j + r * TP;
+                const float4 pin = in[r];
+                PX[r] = make_float2(pin.x, pin.z);
+                PY[r] = make_float2(pin.y, pin.w);
+                V[r] = pot_at2(pa, pb, __ldg(&T.ytab[y]));
+                if (P.V)
+                    V[r] = fma2(bc2(a.V_scale),
+                                make_float2(__ldg(&P.V[(size_t)y * NX + x0]), __ldg(&P.V[(size_t)y * NX + x0 + 1])),
+                                V[r]);
+                const float2 th = mul2(fma2(bc2(a.g), fma2(PX[r], PX[r], mul2(PY[r], PY[r])), V[r]), bc2(ph.h));
+                small = small && fabsf(th.x) <= 1.f && fabsf(th.y) <= 1.f;
             }
-            float4 pin;
-            if constexpr (EARLY) pin = in[r];
-            else pin = act ? __ldcg(ib + r * TP * w4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 la = make_float2(X[r].x, Y[r].x), lb = make_float2(X[r].y, Y[r].y);
-            gq += phase_adjoint(la, make_float2(pin.x, pin.y), Vya, a.g, ph.h) * (a.L0x * xa.y + a.L0y * yt.y);
-            gq += phase_adjoint(lb, make_float2(pin.z, pin.w), Vyb, a.g, ph.h) * (a.L0x * xb.y + a.L0y * yt.y);
-            X[r] = make_float2(la.x, lb.x);
-            Y[r] = make_float2(la.y, lb.y);
+            float2 g2 = make_float2(0.f, 0.f);
+            if (small) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const float2 th = mul2(fma2(bc2(a.g), fma2(PX[r], PX[r], mul2(PY[r], PY[r])), V[r]), bc2(ph.h));
+                    const float2 q = adjoint2_taylor(X[r], Y[r], PX[r], PY[r], th, a.g, ph.h);
+                    const float ly = a.L0y * __ldg(&T.ytab[U.j + r * TP]).y;
+                    g2 = fma2(q, fma2(bc2(a.L0x), make_float2(xa.y, xb.y), bc2(ly)), g2);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const float4 yt = __ldg(&T.ytab[U.j + r * TP]);
+                    float2 la = make_float2(X[r].x, Y[r].x), lb = make_float2(X[r].y, Y[r].y);
+                    g2.x += phase_adjoint(la, make_float2(PX[r].x, PY[r].x), V[r].x, a.g, ph.h) *
+                            (a.L0x * xa.y + a.L0y * yt.y);
+                    g2.y += phase_adjoint(lb, make_float2(PX[r].y, PY[r].y), V[r].y, a.g, ph.h) *
+                            (a.L0x * xb.y + a.L0y * yt.y);
+                    X[r] = make_float2(la.x, lb.x);
+                    Y[r] = make_float2(la.y, lb.y);
+                }
+            }
+            gq += g2.x + g2.y;
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int y = U.j + r * TP;
+                const float4 yt = __ldg(&T.ytab[y]);
+                float Vya = pot_at(pa, yt), Vyb = pot_at(pb, yt);
+                if (P.V) {
+                    Vya += a.V_scale * __ldg(&P.V[(size_t)y * NX + x0]);
+                    Vyb += a.V_scale * __ldg(&P.V[(size_t)y * NX + x0 + 1]);
+                }
+                const float4 pin = act ? __ldcg(ib + r * TP * w4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 la = make_float2(X[r].x, Y[r].x), lb = make_float2(X[r].y, Y[r].y);
+                gq += phase_adjoint(la, make_float2(pin.x, pin.y), Vya, a.g, ph.h) * (a.L0x * xa.y + a.L0y * yt.y);
+                gq += phase_adjoint(lb, make_float2(pin.z, pin.w), Vyb, a.g, ph.h) * (a.L0x * xb.y + a.L0y * yt.y);
+                X[r] = make_float2(la.x, lb.x);
+                Y[r] = make_float2(la.y, lb.y);
+            }
         }
         if (act) {
 #pragma unroll

@@ -24,6 +24,43 @@ __device__ __forceinline__ float2 pot_at2(const PotCoefs &pa, const PotCoefs &pb
     return fma2(w, bc2(t.z), u);
 }
 
+// (X, Y) <- exp(-i theta) (X, Y) on a packed pair, in phase_mul's 1 + d form
+// with the Taylor series of sin and cos of theta/2 (|theta| <= 1)
+__device__ __forceinline__ void rot2_taylor(float2 &X, float2 &Y, float2 th)
+{
+    const float2 w = mul2(bc2(0.5f), th);
+    const float2 v = mul2(w, w);
+    float2 ps = fma2(v, bc2(1.f / 362880.f), bc2(-1.f / 5040.f));
+    ps = fma2(v, ps, bc2(1.f / 120.f));
+    ps = fma2(v, ps, bc2(-1.f / 6.f));
+    const float2 s = fma2(mul2(w, v), ps, w);
+    float2 pc = fma2(v, bc2(1.f / 40320.f), bc2(-1.f / 720.f));
+    pc = fma2(v, pc, bc2(1.f / 24.f));
+    pc = fma2(v, pc, bc2(-0.5f));
+    const float2 c = fma2(v, pc, bc2(1.f));
+    const float2 m2s = mul2(bc2(-2.f), s);
+    const float2 dr = mul2(m2s, s), di = mul2(m2s, c);
+    const float2 nx = add2(X, fma2(X, dr, mul2(Y, make_float2(-di.x, -di.y))));
+    Y = add2(Y, fma2(X, di, mul2(Y, dr)));
+    X = nx;
+}
+
+// phase_adjoint on a packed pair: lambda (LX, LY) <- mu + 2 h g Im(conj(mu)
+// psi) psi with mu = exp(+i theta) lambda, theta = (V + g |psi|^2) h given;
+// (PX, PY) is the phase's input psi.  Returns Im(conj(mu) psi) per lane.
+// The rotation in rot2_taylor's form (|theta| <= 1).
+__device__ __forceinline__ float2 adjoint2_taylor(float2 &LX, float2 &LY, float2 PX, float2 PY, float2 th, float g,
+                                                  float h)
+{
+    float2 MX = LX, MY = LY;
+    rot2_taylor(MX, MY, make_float2(-th.x, -th.y));
+    const float2 q = fma2(MX, PY, mul2(make_float2(-MY.x, -MY.y), PX));
+    const float2 f = mul2(bc2(2.f * h * g), q);
+    LX = fma2(f, PX, MX);
+    LY = fma2(f, PY, MY);
+    return q;
+}
+
 // phase_mul (exp(-i theta) in the 1 + d form with the Taylor series of sin
 // and cos of theta/2, or exp(-theta) in imaginary time; theta = (V + g
 // |psi|^2) h) on all E packed pairs of a thread: every theta first, then one
@@ -50,23 +87,7 @@ __device__ __forceinline__ void phase_all2(float2 (&X)[E], float2 (&Y)[E], float
         }
     } else if (small) {
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const float2 w = mul2(bc2(0.5f), V[r]);
-            const float2 v = mul2(w, w);
-            float2 ps = fma2(v, bc2(1.f / 362880.f), bc2(-1.f / 5040.f));
-            ps = fma2(v, ps, bc2(1.f / 120.f));
-            ps = fma2(v, ps, bc2(-1.f / 6.f));
-            const float2 s = fma2(mul2(w, v), ps, w);
-            float2 pc = fma2(v, bc2(1.f / 40320.f), bc2(-1.f / 720.f));
-            pc = fma2(v, pc, bc2(1.f / 24.f));
-            pc = fma2(v, pc, bc2(-0.5f));
-            const float2 c = fma2(v, pc, bc2(1.f));
-            const float2 m2s = mul2(bc2(-2.f), s);
-            const float2 dr = mul2(m2s, s), di = mul2(m2s, c);
-            const float2 nx = add2(X[r], fma2(X[r], dr, mul2(Y[r], make_float2(-di.x, -di.y))));
-            Y[r] = add2(Y[r], fma2(X[r], di, mul2(Y[r], dr)));
-            X[r] = nx;
-        }
+        for (int r = 0; r < E; ++r) rot2_taylor(X[r], Y[r], V[r]);
     } else {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
