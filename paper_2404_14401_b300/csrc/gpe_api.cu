@@ -662,9 +662,10 @@ std::unique_ptr<CoopArgs> coop_args(const gpe_ctx *c, int n, double dt, int imag
 // launch arguments carry, or its stream is being captured into a graph.
 bool coop_applies(gpe_ctx *c, int n)
 {
-    // at most 3 barriers per step: the 32-bit arrival count of one launch
-    // stays below 2^32 for n <= 2^22 on any GPU of up to 256 SMs
-    if (!c->coop || c->prof || !coop_ok(c->nx, c->ny) || c->ctrl_t.size() > (size_t)COOP_MAX_CTRL || n > (1 << 22))
+    // at most 3 grid barriers per step (callers pass twice their steps for a
+    // kernel with up to 6): the 32-bit arrival count of one launch stays
+    // below 2^32 for n <= 2^21 with up to 512 CTAs (256 SMs, 2 CTAs per SM)
+    if (!c->coop || c->prof || !coop_ok(c->nx, c->ny) || c->ctrl_t.size() > (size_t)COOP_MAX_CTRL || n > (1 << 21))
         return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -812,10 +813,12 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
 
     // The cooperative kernels take the forward sweep, each segment's
     // recomputation and its adjoint passes, one launch each, where they apply
-    // (a checkpointed run without a cavity on a grid they are built for).
-    // The forward sweep and the recomputation both run the unfused steps of
-    // launch_coop_states, so the recomputed states are the forward sweep's.
-    bool coop = !reverse && !c->pot.cavity && coop_applies(c, L.S);
+    // (no cavity, a grid they are built for).  The forward sweep and the
+    // recomputation both run the unfused steps of launch_coop_states, so the
+    // recomputed states are the forward sweep's.  With the reverse sweep by
+    // time reversal: the forward sweep in place in one launch, then the whole
+    // reverse sweep in one more (four barriers per step).
+    bool coop = !c->pot.cavity && coop_applies(c, reverse ? 2 * n : 2 * L.S);
     std::unique_ptr<CoopArgs> ca;
     if (coop) {
         if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)GPE_REAL) {
@@ -836,15 +839,19 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         ca->L0y = (float)c->pot.lat_V0y;
     }
     // steps s0 .. s1 - 1 in one cooperative launch: their states into st
-    // (adj = false) or their adjoint passes (adj = true).  *ran is false if
-    // the device refused the launch (nothing of it ran); the context keeps to
-    // the per-pass path from then on.
-    auto coop_run = [&](bool adj, int s0, int s1, bool *ran) -> gpe_status {
+    // (COOP_FWD), their adjoint passes (COOP_BWD), or the reverse sweep by
+    // time reversal (COOP_REV).  *ran is false if the device refused the
+    // launch (nothing of it ran); the context keeps to the per-pass path from
+    // then on.
+    enum { COOP_FWD, COOP_BWD, COOP_REV };
+    auto coop_run = [&](int which, int s0, int s1, bool *ran) -> gpe_status {
         *ran = false;
         ca->s0 = s0;
         ca->s1 = s1;
         TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
-        const cudaError_t e = adj ? launch_coop_adj(*ca, c->stream) : launch_coop_states(*ca, c->stream);
+        const cudaError_t e = which == COOP_BWD   ? launch_coop_adj(*ca, c->stream)
+                              : which == COOP_REV ? launch_coop_rev(*ca, c->stream)
+                                                  : launch_coop_states(*ca, c->stream);
         if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
             cudaGetLastError();
             c->coop = 0;
@@ -852,7 +859,7 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
             return fail(c, GPE_OK, "cooperative launch refused (%s): the per-pass path from now on",
                         cudaGetErrorString(e));
         }
-        TRY(cuda_check(c, e, adj ? "cooperative adjoint kernel" : "cooperative states kernel"));
+        TRY(cuda_check(c, e, "cooperative adjoint-sweep kernel"));
         c->launches++;
         *ran = true;
         return GPE_OK;
@@ -864,11 +871,18 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     if (!reverse) TRY(copy_d2d(c, ck, c->psi));
     float2 *psiT = ck + (size_t)L.K * P;
     int sf = 0;                                    // forward steps done
-    for (int k = 0; k < L.K && coop; ++k) {
+    if (reverse && coop) {                         // in place: st = psi, no stride
+        ca->st = c->psi;
+        ca->P = 0;
+        bool ran = false;
+        TRY(coop_run(COOP_FWD, 0, n, &ran));
+        if (ran) sf = n;
+    }
+    for (int k = 0; k < L.K && coop && !reverse; ++k) {
         const int s0 = k * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
         TRY(copy_d2d(c, st, ck + (size_t)k * P));
         bool ran = false;
-        TRY(coop_run(false, s0, s1, &ran));
+        TRY(coop_run(COOP_FWD, s0, s1, &ran));
         if (!ran) break;
         TRY(copy_d2d(c, ck + (size_t)(k + 1) * P, st + (size_t)(s1 - s0) * P));
         sf = s1;
@@ -882,12 +896,11 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         if (!reverse && (s + 1) % L.S == 0 && s + 1 < n)
             TRY(copy_d2d(c, ck + (size_t)((s + 1) / L.S) * P, c->psi));
     }
-    if (sf < n) {
-        TRY(copy_d2d(c, psiT, c->psi));
-    } else {                                       // the context at psi_T, as gpe_step leaves it
-        TRY(copy_d2d(c, c->psi, psiT));
-        c->t = tT;
-    }
+    // psi_T is in the context's psi after per-pass steps or the in-place
+    // launch, in the last checkpoint after the segments
+    if (sf < n || reverse) TRY(copy_d2d(c, psiT, c->psi));
+    else TRY(copy_d2d(c, c->psi, psiT));
+    if (sf == n) c->t = tT;                        // as gpe_step leaves it
 
     // J = E(psi_T) + |<phi|psi_T>|^2
     gpe_obs o;
@@ -961,7 +974,14 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         }, "kinetic tables"));
         // the row pass reads psi_{s+1} before the step back overwrites it, so
         // the context's psi is the only state buffer
-        for (int s = n - 1; s >= 0; --s) {
+        bool done = false;
+        if (coop) {
+            ca->kxb = kx;
+            ca->kyb = ky;
+            TRY(coop_run(COOP_REV, 0, n, &done));
+            if (done) c->t = t0;
+        }
+        for (int s = n - 1; s >= 0 && !done; --s) {
             TRY(adjoint_row(s, c->psi));                          // with psi_{s+1}
             TRY(step_backward(c, dt, kx, ky));                    // psi <- psi_s, t <- t_s
             TRY(adjoint_col(s, c->psi));                          // with psi_s
@@ -975,7 +995,7 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         bool rec = false, done = false;
         if (coop) {
             TRY(copy_d2d(c, st, ck + (size_t)k * P));
-            TRY(coop_run(false, s0, s1, &rec));
+            TRY(coop_run(COOP_FWD, s0, s1, &rec));
         }
         if (!rec) {
             TRY(copy_d2d(c, c->psi, ck + (size_t)k * P));
@@ -986,7 +1006,7 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
                 TRY(copy_d2d(c, st + (size_t)i * P, c->psi));
             }
         }
-        if (coop) TRY(coop_run(true, s0, s1, &done));
+        if (coop) TRY(coop_run(COOP_BWD, s0, s1, &done));
         for (int s = s1 - 1; s >= s0 && !done; --s) {
             TRY(adjoint_row(s, st + (size_t)(s + 1 - s0) * P));
             TRY(adjoint_col(s, st + (size_t)(s - s0) * P));

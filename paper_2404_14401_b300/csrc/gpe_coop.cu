@@ -799,6 +799,24 @@ __device__ __noinline__ void coop_adj_cols(const CoopArgs &a, const CoopPtrs &P,
     }
 }
 
+// The dJ/dv partials of an adjoint sweep (coop_adj_kernel, coop_rev_kernel):
+// step s's row-pass partial of CTA b sits at part_row[(hi - s) G + b] and its
+// column-pass partial at part_col[(hi - s) G + b], hi the latest step since
+// the last flush.  Called by every thread after a grid barrier: sums the m =
+// hi - lo + 1 steps' partials, one warp per sum, in CTA order (the same in
+// every run), into gout[2 s + 1] (row) and gout[2 s] (column).
+__device__ void coop_flush_grad(const CoopArgs &a, int hi, int lo)
+{
+    const int G = (int)gridDim.x, m = hi - lo + 1, W = (int)(blockDim.x >> 5), lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * W + (int)(threadIdx.x >> 5); i < 2 * m; i += G * W) {
+        const double *src = ((i & 1) ? a.T.part_row : a.T.part_col) + (size_t)(i >> 1) * G;
+        double acc = 0.0;
+        for (int b = lane; b < G; b += 32) acc += __ldcg(&src[b]);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) a.gout[2 * (hi - (i >> 1)) + (i & 1)] = acc;
+    }
+}
+
 template <int NX, int NY>
 __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
     coop_adj_kernel(const __grid_constant__ CoopArgs a)
@@ -853,18 +871,86 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
         q1[0] = 2.f * s_ph.h * gq;
         block_sum<1>(q1, a.T.part_col + slot, red);
         if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (hi - s + 1 == R || s == a.s0) {         // a barrier before the slots are written again
+            coop_flush_grad(a, hi, s);
+            hi = s - 1;
+            if (s > a.s0 && !coop_sync(a, &s_ok, &s_k)) return;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reverse sweep by time reversal
+// The reverse sweep without checkpoints (GPE_ADJ_REVERSE) in one launch: for
+// s = s1 - 1 down to s0, the adjoint row pass on psi_{s+1} (the context's
+// psi), one real-time step of -dt from t_{s+1} that turns psi into psi_s (the
+// conjugate opening half phase at t_{s+1}, T(-dt) from the kinetic tables
+// kxb / kyb, the conjugate closing half phase at t_s), then the adjoint
+// column pass on psi_s.  Four passes and four grid barriers per step; the
+// dJ/dv partials as in coop_adj_kernel.
+template <int NX, int NY>
+__global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
+    coop_rev_kernel(const __grid_constant__ CoopArgs a)
+{
+    using C = CoopCfg<NX, NY>;
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32 * NQ];
+    __shared__ DevScalars loc;                     // c = 1, alpha = 0 for the step back
+    __shared__ PhaseArgs s_ph;
+    __shared__ CoopPtrs s_P, s_Pb;                 // kinetic tables of +dt (adjoint) and -dt (step back)
+    __shared__ int s_ok;
+    __shared__ unsigned int s_k;
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *slots = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    if (threadIdx.x == 0) {
+        memset(&loc, 0, sizeof(loc));
+        loc.c = 1.0;
+        s_k = 0;
+        s_P.T = a.T;
+        s_P.V = a.V;
+        s_Pb = s_P;
+        s_Pb.T.kinx = const_cast<float2 *>(a.kxb);
+        s_Pb.T.kiny = const_cast<float2 *>(a.kyb);
+        s_ok = check_index((long long)((unsigned char *)slots + C::SLOT_BYTES - smraw) - 1, dyn_smem_bytes(), a.T.sc);
+        if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const double hh = __dmul_rn(0.5, a.dt), mh = -hh;
+    const int G = (int)gridDim.x, R = NQ * MAX_BLOCKS / G;
+    float q[3] = {0.f, 0.f, 0.f};
+    int hi = a.s1 - 1;
+    for (int s = a.s1 - 1; s >= a.s0; --s) {
+        const double ts = __dadd_rn(a.t0, __dmul_rn((double)s, a.dt));
+        const double te = __dadd_rn(ts, a.dt);
+        const size_t slot = (size_t)(hi - s) * G + blockIdx.x;
+        // adjoint row pass with psi_{s+1}
+        if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
+        __syncthreads();
+        float gq = 0.f;
+        coop_adj_rows<NX, C::CT, C::E>(a, s_P, s_ph, a.psi, slots, gq);
+        float q1[1] = {2.f * s_ph.h * gq};
+        block_sum<1>(q1, a.T.part_row + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        // psi_{s+1} -> psi_s: the step of -dt
+        if (threadIdx.x == 0) s_ph = phase_dev(a, te, mh);
+        __syncthreads();
+        coop_rows_pt<NX, C::CT, C::E>(a, s_Pb, s_ph, 0, loc, slots, a.psi, a.psi);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, mh);
+        __syncthreads();
+        coop_cols<NY, NX, COL_T_P, C::CT, C::E>(a, s_Pb, s_ph, loc, slots, q, a.psi);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        // adjoint column pass with psi_s
+        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, hh);
+        __syncthreads();
+        gq = 0.f;
+        coop_adj_cols<NY, NX, C::CT, C::E>(a, s_P, s_ph, a.psi, slots, gq);
+        q1[0] = 2.f * s_ph.h * gq;
+        block_sum<1>(q1, a.T.part_col + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
         if (hi - s + 1 == R || s == a.s0) {
-            // flush: sum m = hi - s + 1 steps' partials, one warp per sum, in
-            // CTA order (the same in every run); a barrier before the slots
-            // are written again
-            const int m = hi - s + 1, W = (int)(blockDim.x >> 5), lane = threadIdx.x & 31;
-            for (int i = blockIdx.x * W + (int)(threadIdx.x >> 5); i < 2 * m; i += G * W) {
-                const double *src = ((i & 1) ? a.T.part_row : a.T.part_col) + (size_t)(i >> 1) * G;
-                double acc = 0.0;
-                for (int b = lane; b < G; b += 32) acc += __ldcg(&src[b]);
-                for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-                if (lane == 0) a.gout[2 * (hi - (i >> 1)) + (i & 1)] = acc;
-            }
+            coop_flush_grad(a, hi, s);
             hi = s - 1;
             if (s > a.s0 && !coop_sync(a, &s_ok, &s_k)) return;
         }
@@ -894,13 +980,14 @@ static cudaError_t coop_go(void (*K)(CoopArgs), std::atomic<unsigned long long> 
     return cudaLaunchCooperativeKernel((const void *)K, dim3(grid), dim3(C::CT), args, C::SMEM, s);
 }
 
-enum { COOP_STEPS, COOP_STATES, COOP_ADJ };
+enum { COOP_STEPS, COOP_STATES, COOP_ADJ, COOP_REV };
 
 template <int NX, int NY> static cudaError_t coop_launch(int which, const CoopArgs &a, cudaStream_t s)
 {
-    static std::atomic<unsigned long long> attr[3];
+    static std::atomic<unsigned long long> attr[4];
     if (which == COOP_STATES) return coop_go<NX, NY>(coop_states_kernel<NX, NY>, attr[1], a, s);
     if (which == COOP_ADJ) return coop_go<NX, NY>(coop_adj_kernel<NX, NY>, attr[2], a, s);
+    if (which == COOP_REV) return coop_go<NX, NY>(coop_rev_kernel<NX, NY>, attr[3], a, s);
     return coop_go<NX, NY>(coop_kernel<NX, NY>, attr[0], a, s);
 }
 
@@ -915,6 +1002,14 @@ cudaError_t launch_coop_adj(const CoopArgs &a, cudaStream_t s)
     if (!coop_ok(a.nx, a.ny) || a.cavity || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL || a.s1 <= a.s0)
         return cudaErrorInvalidValue;
     return coop_dispatch(COOP_ADJ, a, s);
+}
+
+cudaError_t launch_coop_rev(const CoopArgs &a, cudaStream_t s)
+{
+    if (!coop_ok(a.nx, a.ny) || a.cavity || a.imag || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL || a.s1 <= a.s0 ||
+        !a.kxb || !a.kyb)
+        return cudaErrorInvalidValue;
+    return coop_dispatch(COOP_REV, a, s);
 }
 
 cudaError_t launch_coop_states(const CoopArgs &a, cudaStream_t s)

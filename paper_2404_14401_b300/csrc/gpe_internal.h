@@ -177,6 +177,9 @@ struct CoopArgs {
     double *gout;
     float L0x, L0y;
     int s0, s1;
+    // the reverse sweep by time reversal (launch_coop_rev): kinetic factors
+    // of -dt for the steps back, nx and ny entries
+    const float2 *kxb, *kyb;
 };
 bool coop_ok(int nx, int ny);              // grid sizes the cooperative kernels are built for
 cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s);
@@ -186,6 +189,9 @@ cudaError_t launch_coop_adj(const CoopArgs &a, cudaStream_t s);
 // real-time steps s0 .. s1 - 1 of a context without a cavity, unfused, from
 // st[0] = psi_{s0}, every state kept in st (one cooperative launch)
 cudaError_t launch_coop_states(const CoopArgs &a, cudaStream_t s);
+// the reverse sweep of GPE_ADJ_REVERSE over steps s1 - 1 down to s0 in one
+// cooperative launch: psi holds psi_{s1} on entry and psi_{s0} on return
+cudaError_t launch_coop_rev(const CoopArgs &a, cudaStream_t s);
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
 // tile_shift: the one-shot row pass takes 2^-tile_shift of its default rows

@@ -220,13 +220,13 @@ def test_coop_defaults_and_fallbacks():
 
 
 # ------------------------------------------------------------------ adjoint segments
-def adjoint_run(p, psi0, phi, steps, dt, coop):
+def adjoint_run(p, psi0, phi, steps, dt, coop, reverse=False):
     """J, dJ/dv, the launches of the call, and the state and time the call
     leaves the context at (psi_T, t_T)."""
     s = sim_for(p, coop)
     s.set_psi(c64(psi0))
     l0 = s.launches
-    J, grad = s.adjoint_lattice(phi, steps, dt)
+    J, grad = s.adjoint_lattice(phi, steps, dt, reverse=reverse)
     assert s.sync() == 0
     return J, np.array(grad), s.launches - l0, s.get_psi(), s.t
 
@@ -282,3 +282,35 @@ def test_coop_adjoint_rectangular_grid_with_potential_array():
     assert rel_l2(psiT, psiTq) < 3e-6
     assert abs(J - Jq) < 1e-6 * abs(Jq)
     assert np.max(np.abs(g - gq)) < 1e-5 * np.max(np.abs(gq))
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(512, 512, 16), (512, 1024, 9)])
+def test_coop_reverse_sweep_matches_per_pass_and_oracle(nx, ny, steps):
+    """The reverse sweep by time reversal on the cooperative kernels: the
+    forward sweep in place in one launch, the whole reverse sweep (adjoint row
+    pass, the step of -dt, adjoint column pass) in one more.  Against the
+    per-pass reverse sweep (J to 1e-6, dJ/dv to 1e-5 of its maximum, psi_T
+    to 3e-6), the FP64 oracle adjoint, and the checkpointed call on the
+    cooperative kernels, whose J is the same bit for bit (the two forward
+    sweeps run the same unfused steps)."""
+    w = gi.adjoint_control(n=512, L=20.0, steps=steps, npts=6, seed=21)
+    p = dict(w["params"], nx=nx, ny=ny, Lx=20.0, Ly=20.0 * ny / nx)
+    dt = w["dt"]
+    psi0 = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.2, 1e-2, seed=22, x0=0.3, kx0=1.0)
+    phi = gi.target_gaussian(nx, ny, p["Lx"], p["Ly"])
+    J, g, calls, psiT, tT = adjoint_run(p, psi0, phi, steps, dt, True, reverse=True)
+    Jq, gq, callsq, psiTq, _ = adjoint_run(p, psi0, phi, steps, dt, False, reverse=True)
+    # two cooperative launches, the kinetic tables of +dt and -dt, and the
+    # terminal condition's passes
+    assert calls <= 16 < callsq, (calls, callsq)
+    assert abs(tT - steps * dt) < 1e-12
+    assert rel_l2(psiT, psiTq) < 3e-6
+    assert abs(J - Jq) < 1e-6 * abs(Jq)
+    assert np.max(np.abs(g - gq)) < 1e-5 * np.max(np.abs(gq))
+    Jr, gr = oracle.adjoint(p, c64(psi0).astype(np.complex128), phi, steps, dt)
+    assert abs(J - Jr) < 1e-6 * abs(Jr), (J, Jr)
+    assert np.max(np.abs(g - gr)) < 1e-5 * np.max(np.abs(gr))
+    Jc, gc, _, psiTc, _ = adjoint_run(p, psi0, phi, steps, dt, True)
+    assert J == Jc
+    assert np.array_equal(psiT, psiTc)
+    assert np.max(np.abs(g - gc)) < 1e-5 * np.max(np.abs(gc))
