@@ -53,7 +53,7 @@ def parse():
                     help="only run `--steps` real-time steps of the lattice workload on one NX x NY grid (psi built "
                          "on the device, no relaxation) and exit: a small case for ncu captures of the passes; "
                          "`adjoint`: one checkpointed adjoint call of `--steps` steps of the adjoint-control "
-                         "workload (512^2)")
+                         "workload (512^2); `adjoint-reverse`: the same call by time reversal")
     ap.add_argument("--ncu-sweep", type=int, default=0, metavar="K",
                     help="only run `--steps` persistent-batch steps of the first K sweep instances of each size and "
                          "exit: a small case for ncu captures of the batch kernel")
@@ -936,14 +936,16 @@ def ncu_case(args):
 
     import gpe_inputs as gi
     from paper_2404_14401_b300 import Batch, Simulation
-    if args.ncu_case == "adjoint":
-        # one checkpointed adjoint call of the adjoint-control workload (512^2)
+    if args.ncu_case in ("adjoint", "adjoint-reverse"):
+        # one adjoint call of the adjoint-control workload (512^2), checkpointed
+        # or with the reverse sweep by time reversal
         w = gi.adjoint_control()
         p = w["params"]
         s = Simulation(p["nx"], p["ny"], p["Lx"], p["Ly"], p["m"], p["g"])
         s.set_potential(p)
         s.set_psi(w["psi0"]().astype(np.complex64))
-        s.adjoint_lattice(torch.from_numpy(w["phi"]().astype(np.complex64)).cuda(), args.steps, w["dt"])
+        s.adjoint_lattice(torch.from_numpy(w["phi"]().astype(np.complex64)).cuda(), args.steps, w["dt"],
+                          reverse=args.ncu_case == "adjoint-reverse")
         status = s.sync()
     elif args.ncu_case:
         nx, ny = (int(v) for v in (args.ncu_case + "x" + args.ncu_case).split("x")[:2])

@@ -7,9 +7,9 @@ loads that library (GPE_LIBRARY=debug) and runs cases through every pass
 kernel family -- the one-shot row and column passes on short pencils (the
 32 x 256 and 64 x 64 grids among them), the grouped, streaming, adjoint and
 readout passes, the pencil-pair column passes (2048-point columns by
-default, 512 by choice), the persistent batch and the cooperative step
-kernel -- each checked against the FP64 oracle and for a clean device
-status.
+default, 512 by choice), the persistent batch, the cooperative step kernel
+and the cooperative adjoint kernels -- each checked against the FP64 oracle
+and for a clean device status.
 """
 import os
 import subprocess
@@ -91,6 +91,23 @@ s.step(20, 5e-4)
 assert s.launches - l0 <= 2 and s.sync() == 0
 ref, _ = oracle.evolve(p, x.astype(np.complex128), 20, 5e-4, False)
 assert rel(s.get_psi(), ref) < 1e-5, rel(s.get_psi(), ref)
+# the cooperative adjoint kernels, checkpointed (states and segment kernels)
+# and by time reversal (in-place states kernel, reverse-sweep kernel): 512^2
+# (8 elements per thread, the packed pointwise adjoint) and 1024 x 512 (16)
+a = gi.adjoint_control(n=512, L=20.0, steps=9, npts=5, seed=3)
+for nx, ny, rev in ((512, 512, False), (512, 512, True), (1024, 512, False), (1024, 512, True)):
+    p = dict(a["params"], nx=nx, ny=ny, Lx=20.0 * nx / 512, Ly=20.0 * ny / 512)
+    x = gi.gaussian_state(nx, ny, p["Lx"], p["Ly"], 1.2, 1e-2, seed=8, x0=0.3, kx0=1.0).astype(np.complex64)
+    f = gi.target_gaussian(nx, ny, p["Lx"], p["Ly"])
+    s = sim(p)
+    s.variants = s.variants | abi.GPE_VARIANT_COOP
+    s.set_psi(x)
+    l0 = s.launches
+    J, g = s.adjoint_lattice(f.astype(np.complex64), 9, a["dt"], reverse=rev)
+    assert s.sync() == 0 and s.launches - l0 < 30, (nx, ny, rev, s.launches - l0)
+    Jr, gr = oracle.adjoint(p, x.astype(np.complex128), f, 9, a["dt"])
+    assert abs(J - Jr) < 1e-6 * abs(Jr), (nx, ny, rev, J, Jr)
+    assert np.max(np.abs(np.array(g) - gr)) < 1e-5 * np.max(np.abs(gr)), (nx, ny, rev)
 print("debug bounds build: all cases clean")
 '''
 
