@@ -396,7 +396,7 @@ gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, s
  * are launched one by one.  (512^2, 4000 steps: 0.175 s against 0.350 s.)
  * GPE_ADJ_REVERSE on those grids: the forward sweep in place in one launch
  * (the same unfused steps, so J is the checkpointed call's bit for bit) and
- * the whole reverse sweep in one more (0.179 s against 0.305 s).
+ * the whole reverse sweep in one more (0.166 s against 0.305 s).
  *
  * phi_dev: target state, complex64 [ny][nx] on the device (borrowed, 16-byte
  * aligned).  adj_ws: device scratch of at least

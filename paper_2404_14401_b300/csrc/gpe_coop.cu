@@ -885,8 +885,16 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
 // psi), one real-time step of -dt from t_{s+1} that turns psi into psi_s (the
 // conjugate opening half phase at t_{s+1}, T(-dt) from the kinetic tables
 // kxb / kyb, the conjugate closing half phase at t_s), then the adjoint
-// column pass on psi_s.  Four passes and four grid barriers per step; the
-// dJ/dv partials as in coop_adj_kernel.
+// column pass on psi_s.  Two phases and two grid barriers per step: the
+// adjoint row pass and the step back's row pass run on the same row pairs
+// one after the other, as do the step back's column pass and the adjoint
+// column pass on the same column pairs.  Within a pair every thread reads and
+// writes its own elements only (the same ones in every pass), so each
+// element of psi is read by the adjoint row pass before the step back
+// overwrites it, and the adjoint column pass reads psi_s that the same
+// thread has just stored; consecutive transforms of a group are ordered by
+// the barriers inside each exchange.  The dJ/dv partials as in
+// coop_adj_kernel.
 template <int NX, int NY>
 __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
     coop_rev_kernel(const __grid_constant__ CoopArgs a)
@@ -895,7 +903,7 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
     extern __shared__ unsigned char smraw[];
     __shared__ double red[32 * NQ];
     __shared__ DevScalars loc;                     // c = 1, alpha = 0 for the step back
-    __shared__ PhaseArgs s_ph;
+    __shared__ PhaseArgs s_ph, s_ph2;
     __shared__ CoopPtrs s_P, s_Pb;                 // kinetic tables of +dt (adjoint) and -dt (step back)
     __shared__ int s_ok;
     __shared__ unsigned int s_k;
@@ -924,29 +932,30 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
         const double ts = __dadd_rn(a.t0, __dmul_rn((double)s, a.dt));
         const double te = __dadd_rn(ts, a.dt);
         const size_t slot = (size_t)(hi - s) * G + blockIdx.x;
-        // adjoint row pass with psi_{s+1}
-        if (threadIdx.x == 0) s_ph = phase_dev(a, te, hh);
+        // rows: the adjoint row pass with psi_{s+1}, then psi's opening phase
+        // and T_x of the step of -dt
+        if (threadIdx.x == 0) {
+            s_ph = phase_dev(a, te, hh);
+            s_ph2 = phase_dev(a, te, mh);
+        }
         __syncthreads();
         float gq = 0.f;
         coop_adj_rows<NX, C::CT, C::E>(a, s_P, s_ph, a.psi, slots, gq);
+        coop_rows_pt<NX, C::CT, C::E>(a, s_Pb, s_ph2, 0, loc, slots, a.psi, a.psi);
         float q1[1] = {2.f * s_ph.h * gq};
         block_sum<1>(q1, a.T.part_row + slot, red);
         if (!coop_sync(a, &s_ok, &s_k)) return;
-        // psi_{s+1} -> psi_s: the step of -dt
-        if (threadIdx.x == 0) s_ph = phase_dev(a, te, mh);
-        __syncthreads();
-        coop_rows_pt<NX, C::CT, C::E>(a, s_Pb, s_ph, 0, loc, slots, a.psi, a.psi);
-        if (!coop_sync(a, &s_ok, &s_k)) return;
-        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, mh);
+        // columns: T_y and the closing phase of the step of -dt (psi <- psi_s),
+        // then the adjoint column pass with psi_s
+        if (threadIdx.x == 0) {
+            s_ph = phase_dev(a, ts, mh);
+            s_ph2 = phase_dev(a, ts, hh);
+        }
         __syncthreads();
         coop_cols<NY, NX, COL_T_P, C::CT, C::E>(a, s_Pb, s_ph, loc, slots, q, a.psi);
-        if (!coop_sync(a, &s_ok, &s_k)) return;
-        // adjoint column pass with psi_s
-        if (threadIdx.x == 0) s_ph = phase_dev(a, ts, hh);
-        __syncthreads();
         gq = 0.f;
-        coop_adj_cols<NY, NX, C::CT, C::E>(a, s_P, s_ph, a.psi, slots, gq);
-        q1[0] = 2.f * s_ph.h * gq;
+        coop_adj_cols<NY, NX, C::CT, C::E>(a, s_P, s_ph2, a.psi, slots, gq);
+        q1[0] = 2.f * s_ph2.h * gq;
         block_sum<1>(q1, a.T.part_col + slot, red);
         if (!coop_sync(a, &s_ok, &s_k)) return;
         if (hi - s + 1 == R || s == a.s0) {
