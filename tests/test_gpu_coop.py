@@ -238,12 +238,12 @@ def segments(steps):
     return (steps + S - 1) // S
 
 
-@pytest.mark.parametrize("steps", [7, 16])
+@pytest.mark.parametrize("steps", [1, 2, 7, 16])
 def test_coop_adjoint_segments_match_per_pass_and_oracle(steps):
     """The checkpointed adjoint on a 512^2 grid (the adjoint-control workload's
     grid and potential, a few steps): the forward sweep, each segment's
     recomputation and each segment's reverse sweep as one cooperative launch
-    each (segments 3 + 3 + 1 and 4 x 4), against the per-pass sweep and the
+    each (segments 1, 2, 3 + 3 + 1 and 4 x 4), against the per-pass sweep and the
     FP64 oracle adjoint (J to 1e-6, each dJ/dv_i to 1e-5 of the largest, the
     tolerances of test_gpu_adjoint).  The state the call leaves the context
     at, psi_T, agrees with the per-pass path's to the 3e-6 bound of two FP32
@@ -257,7 +257,7 @@ def test_coop_adjoint_segments_match_per_pass_and_oracle(steps):
     K = segments(steps)
     # 3 K cooperative launches, the kinetic tables, and the terminal
     # condition's passes (observables, overlap, two FFTs, kinetic product)
-    assert 3 * K <= calls <= 3 * K + 12 < callsq, (calls, callsq)
+    assert 3 * K <= calls <= 3 * K + 12 and calls < callsq, (calls, callsq)
     assert abs(tT - steps * dt) < 1e-12 and abs(tTq - steps * dt) < 1e-12
     assert rel_l2(psiT, psiTq) < 3e-6
     assert abs(J - Jq) < 1e-6 * abs(Jq)
@@ -284,7 +284,7 @@ def test_coop_adjoint_rectangular_grid_with_potential_array():
     assert np.max(np.abs(g - gq)) < 1e-5 * np.max(np.abs(gq))
 
 
-@pytest.mark.parametrize("nx,ny,steps", [(512, 512, 16), (512, 1024, 9)])
+@pytest.mark.parametrize("nx,ny,steps", [(512, 512, 1), (512, 512, 16), (512, 1024, 9)])
 def test_coop_reverse_sweep_matches_per_pass_and_oracle(nx, ny, steps):
     """The reverse sweep by time reversal on the cooperative kernels: the
     forward sweep in place in one launch, the whole reverse sweep (adjoint row
@@ -302,7 +302,7 @@ def test_coop_reverse_sweep_matches_per_pass_and_oracle(nx, ny, steps):
     Jq, gq, callsq, psiTq, _ = adjoint_run(p, psi0, phi, steps, dt, False, reverse=True)
     # two cooperative launches, the kinetic tables of +dt and -dt, and the
     # terminal condition's passes
-    assert calls <= 16 < callsq, (calls, callsq)
+    assert calls <= 16 and calls < callsq, (calls, callsq)
     assert abs(tT - steps * dt) < 1e-12
     assert rel_l2(psiT, psiTq) < 3e-6
     assert abs(J - Jq) < 1e-6 * abs(Jq)
