@@ -543,19 +543,26 @@ gpe_status step_check(gpe_ctx *c, int n, double dt, gpe_mode mode)
     return GPE_OK;
 }
 
+// The context's kinetic tables for steps of dt in `mode`, remade only when
+// dt or the mode changed since they were made.
+static gpe_status kinetic_for(gpe_ctx *c, double dt, gpe_mode mode)
+{
+    if (c->kin_valid && c->kin_dt == dt && c->kin_mode == (int)mode) return GPE_OK;
+    TRY(timed_launch(c, 2, [&] {
+        return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, mode == GPE_IMAG, c->stream);
+    }, "kinetic tables"));
+    c->kin_valid = true;
+    c->kin_dt = dt;
+    c->kin_mode = (int)mode;
+    return GPE_OK;
+}
+
 // Passes before step 0: kinetic factors for (dt, mode) and, with a cavity,
 // alpha of the initial density (Eq. 14).
 gpe_status step_prologue(gpe_ctx *c, double dt, gpe_mode mode)
 {
     const int imag = mode == GPE_IMAG;
-    if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
-        TRY(timed_launch(c, 2, [&] {
-            return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
-        }, "kinetic tables"));
-        c->kin_valid = true;
-        c->kin_dt = dt;
-        c->kin_mode = (int)mode;
-    }
+    TRY(kinetic_for(c, dt, mode));
     PhaseArgs none;
     memset(&none, 0, sizeof(none));
     if (c->pot.cavity) TRY(run_row(c, ROW_REDUCE_R, none, red_at(c, c->t), imag, 0));
@@ -685,14 +692,7 @@ gpe_status step_coop(gpe_ctx *c, int n, double dt, gpe_mode mode, bool *ran)
 {
     *ran = false;
     const int imag = mode == GPE_IMAG;
-    if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
-        TRY(timed_launch(c, 2, [&] {
-            return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
-        }, "kinetic tables"));
-        c->kin_valid = true;
-        c->kin_dt = dt;
-        c->kin_mode = (int)mode;
-    }
+    TRY(kinetic_for(c, dt, mode));
     std::unique_ptr<CoopArgs> a = coop_args(c, n, dt, imag);
     // the barrier's counter and abort flag start at zero
     TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
@@ -817,18 +817,11 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     // recomputation both run the unfused steps of launch_coop_states, so the
     // recomputed states are the forward sweep's.  With the reverse sweep by
     // time reversal: the forward sweep in place in one launch, then the whole
-    // reverse sweep in one more (four barriers per step).
+    // reverse sweep in one more (two grid barriers per step).
     bool coop = !c->pot.cavity && coop_applies(c, reverse ? 2 * n : 2 * L.S);
     std::unique_ptr<CoopArgs> ca;
     if (coop) {
-        if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)GPE_REAL) {
-            TRY(timed_launch(c, 2, [&] {
-                return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, 0, c->stream);
-            }, "kinetic tables"));
-            c->kin_valid = true;
-            c->kin_dt = dt;
-            c->kin_mode = (int)GPE_REAL;
-        }
+        TRY(kinetic_for(c, dt, GPE_REAL));
         ca = coop_args(c, 0, dt, 0);
         ca->t0 = t0;
         ca->lam = lam;
@@ -1839,19 +1832,9 @@ gpe_status gpe_batch_step(gpe_batch *b, int n, double dt, gpe_mode mode)
     bool stale = false;
     for (int i = 0; i < count; ++i) stale = stale || b->key[2 * i + 1] != b->ctxs[i]->version;
     if (stale) TRY(batch_upload(b));
-    // kinetic factors of (dt, mode) on each context's stream
     const int imag = mode == GPE_IMAG;
-    for (int i = 0; i < count; ++i) {
-        gpe_ctx *c = b->ctxs[i];
-        if (!c->kin_valid || c->kin_dt != dt || c->kin_mode != (int)mode) {
-            TRY(timed_launch(c, 2, [&] {
-                return launch_kinetic_tables(c->T, c->nx, c->ny, c->Lx, c->Ly, c->m, dt, imag, c->stream);
-            }, "kinetic tables"));
-            c->kin_valid = true;
-            c->kin_dt = dt;
-            c->kin_mode = (int)mode;
-        }
-    }
+    // kinetic factors of (dt, mode) on each context's stream
+    for (int i = 0; i < count; ++i) TRY(kinetic_for(b->ctxs[i], dt, mode));
     // the launch runs on the first context's stream, after the others' work
     const cudaStream_t s = c0->stream;
     for (cudaStream_t t : b->streams) {
