@@ -547,7 +547,7 @@ def adjoint_leg(dev, with_oracle):
     """The adjoint-control workload (512^2, 4000 real-time steps, 200 lattice
     control points): one gpe_adjoint_lattice call (checkpointed forward and
     reverse sweep) timed end to end on the default path (at 512^2 the
-    cooperative kernels: three launches per segment of 64 steps), the same
+    cooperative kernels: two launches per segment of 64 steps), the same
     call on the per-pass path beside it, the per-pass adjoint kernels timed
     with events over the first 256 steps, and the FP64 oracle adjoint on a
     bounded sample of steps."""

@@ -389,11 +389,13 @@ gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, s
  * starting from lambda_T = dx dy (H psi_T + <phi|psi_T> phi).  On grids the
  * cooperative kernels are built for (512 and 1024 points per axis; by default
  * those whose context has GPE_VARIANT_COOP, i.e. 512^2), unless the context
- * profiles its passes, each segment is three cooperative launches: the
+ * profiles its passes, each segment takes cooperative launches: the
  * forward sweep and the recomputation run the steps unfused with every state
  * kept, so the recomputed states are the forward sweep's bit for bit, and
  * the segment's adjoint passes follow in one launch.  Elsewhere the passes
- * are launched one by one.  (512^2, 4000 steps: 0.175 s against 0.350 s.)
+ * are launched one by one.  On 512^2 one segment's adjoint passes run beside
+ * the previous segment's recomputation in one launch.  (512^2, 4000 steps:
+ * 0.157 s against 0.350 s.)
  * GPE_ADJ_REVERSE on those grids: the forward sweep in place in one launch
  * (the same unfused steps, so J is the checkpointed call's bit for bit) and
  * the whole reverse sweep in one more (0.166 s against 0.305 s).
@@ -401,8 +403,10 @@ gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, s
  * phi_dev: target state, complex64 [ny][nx] on the device (borrowed, 16-byte
  * aligned).  adj_ws: device scratch of at least
  * gpe_adjoint_workspace_size(nx, ny, nsteps) bytes (256-byte aligned,
- * borrowed): (ceil(nsteps/S) + S + 3) copies of psi plus 2 nsteps + 1
- * doubles.  grad_out: host array of nctrl doubles.  The call synchronises the
+ * borrowed): (ceil(nsteps/S) + S + 3) copies of psi (S + 1 more on 512^2
+ * grids, where one segment is recomputed while the adjoint passes of the
+ * next run) plus 2 nsteps + 1 doubles.  grad_out: host array of nctrl
+ * doubles.  The call synchronises the
  * context's stream.  On return psi is the final state and the context's time
  * has advanced by nsteps dt, as after gpe_step.  Errors: GPE_EINVAL (no
  * lattice control table, a cavity, bad sizes or pointers), GPE_ENOMEM

@@ -725,12 +725,14 @@ gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
 // ---------------------------------------------------------------- adjoint
 // Layout of the adjoint workspace for n steps: S = ceil(sqrt(n)) steps per
 // segment, K = ceil(n / S) segments.  Checkpoints psi_{kS} (k < K) and psi_n,
-// the S + 1 states of one segment, lambda, and the 2n + 1 per-phase dJ/dv.
+// the S + 1 states of one segment (two such buffers on the grids of
+// launch_coop_adjrec, which recomputes one segment while the adjoint passes
+// of the next run), lambda, and the 2n + 1 per-phase dJ/dv.
 // GPE_ADJ_REVERSE keeps no checkpoints: ck holds psi_T only, and kx / ky the
 // kinetic factors of -dt for the backward steps (st is not used).
 struct AdjLayout {
     int S, K, variant;
-    size_t P, ck, st, lam, g, kx, ky, total;
+    size_t P, ck, st, st2, lam, g, kx, ky, total;      // st2: 0 when there is no second segment buffer
 };
 static AdjLayout adj_layout(int nx, int ny, int n, int variant = GPE_ADJ_CHECKPOINT)
 {
@@ -741,7 +743,7 @@ static AdjLayout adj_layout(int nx, int ny, int n, int variant = GPE_ADJ_CHECKPO
     if (variant == GPE_ADJ_REVERSE) {
         L.S = n;
         L.K = 0;
-        L.st = 0;
+        L.st = L.st2 = 0;
         L.lam = L.ck + L.P;
         L.kx = L.lam + L.P;
         L.ky = L.kx + align256(sizeof(float2) * (size_t)nx);
@@ -751,7 +753,8 @@ static AdjLayout adj_layout(int nx, int ny, int n, int variant = GPE_ADJ_CHECKPO
         while ((long long)L.S * L.S < n) ++L.S;
         L.K = (n + L.S - 1) / L.S;
         L.st = L.ck + (size_t)(L.K + 1) * L.P;
-        L.lam = L.st + (size_t)(L.S + 1) * L.P;
+        L.st2 = coop_adjrec_ok(nx, ny) ? L.st + (size_t)(L.S + 1) * L.P : 0;
+        L.lam = (L.st2 ? L.st2 : L.st) + (size_t)(L.S + 1) * L.P;
         L.kx = L.ky = 0;
         L.g = L.lam + L.P;
     }
@@ -832,19 +835,21 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         ca->L0y = (float)c->pot.lat_V0y;
     }
     // steps s0 .. s1 - 1 in one cooperative launch: their states into st
-    // (COOP_FWD), their adjoint passes (COOP_BWD), or the reverse sweep by
-    // time reversal (COOP_REV).  *ran is false if the device refused the
+    // (COOP_FWD), their adjoint passes (COOP_BWD), those beside the
+    // recomputation of steps r0 .. r1 - 1 into st2 (COOP_BOTH), or the
+    // reverse sweep by time reversal (COOP_REV).  *ran is false if the device refused the
     // launch (nothing of it ran); the context keeps to the per-pass path from
     // then on.
-    enum { COOP_FWD, COOP_BWD, COOP_REV };
+    enum { COOP_FWD, COOP_BWD, COOP_REV, COOP_BOTH };
     auto coop_run = [&](int which, int s0, int s1, bool *ran) -> gpe_status {
         *ran = false;
         ca->s0 = s0;
         ca->s1 = s1;
         TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
-        const cudaError_t e = which == COOP_BWD   ? launch_coop_adj(*ca, c->stream)
-                              : which == COOP_REV ? launch_coop_rev(*ca, c->stream)
-                                                  : launch_coop_states(*ca, c->stream);
+        const cudaError_t e = which == COOP_BWD    ? launch_coop_adj(*ca, c->stream)
+                              : which == COOP_REV  ? launch_coop_rev(*ca, c->stream)
+                              : which == COOP_BOTH ? launch_coop_adjrec(*ca, c->stream)
+                                                   : launch_coop_states(*ca, c->stream);
         if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
             cudaGetLastError();
             c->coop = 0;
@@ -982,8 +987,35 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     }
 
     // reverse sweep, segment by segment: recompute the segment's states from
-    // its checkpoint, then the two adjoint passes of each step
-    for (int k = L.K - 1; k >= 0 && !reverse; --k) {
+    // its checkpoint, then the two adjoint passes of each step.  On the grids
+    // of launch_coop_adjrec, once the forward sweep ran on the cooperative
+    // kernels: segment K - 1's states are still in st, and each launch runs
+    // segment k's adjoint passes beside segment k - 1's recomputation into
+    // the other buffer; segment 0's adjoint passes run alone.
+    int kr = L.K - 1;                              // segments left for the loop below
+    if (!reverse && coop && L.st2 && sf == n) {
+        float2 *cur = st, *nxt = (float2 *)(ws + L.st2);
+        for (; kr >= 1; --kr) {
+            const int s0 = kr * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
+            TRY(copy_d2d(c, nxt, ck + (size_t)(kr - 1) * P));
+            ca->st = cur;
+            ca->st2 = nxt;
+            ca->r0 = s0 - L.S;
+            ca->r1 = s0;
+            bool ran = false;
+            TRY(coop_run(COOP_BOTH, s0, s1, &ran));
+            if (!ran) break;
+            std::swap(cur, nxt);
+        }
+        if (kr == 0) {                             // segment 0: its states are in cur
+            ca->st = cur;
+            bool ran = false;
+            TRY(coop_run(COOP_BWD, 0, (L.S < n) ? L.S : n, &ran));
+            if (ran) kr = -1;
+        }
+        ca->st = st;
+    }
+    for (int k = kr; k >= 0 && !reverse; --k) {
         const int s0 = k * L.S, s1 = (s0 + L.S < n) ? s0 + L.S : n;
         bool rec = false, done = false;
         if (coop) {

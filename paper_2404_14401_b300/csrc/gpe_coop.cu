@@ -246,16 +246,22 @@ __device__ __forceinline__ int cta_fresh()
     return b;
 }
 
+// A pass's view of the CTA: its CT threads start at thread `base` (0, or CT
+// for the second role of coop_adjrec_kernel); g is the thread's group among
+// them, j its thread in the group, gg its first unit, G the units' stride,
+// bid the group's named barrier (unique in the CTA: 1 + the group's index
+// among all the CTA's groups).
 template <int N, int CT, int E> struct CoopUnits {
-    int g, j, gg, G;
-    __device__ CoopUnits()
+    int g, j, gg, G, bid;
+    __device__ explicit CoopUnits(int base = 0)
     {
         using A = CoopAxis<N, CT, E>;
         const int t = tid_fresh();
-        g = t / A::TP;
-        j = t % A::TP;
+        g = (t - base) / A::TP;
+        j = (t - base) % A::TP;
         gg = cta_fresh() + gridDim.x * g;
         G = gridDim.x * A::GPB;
+        bid = 1 + t / A::TP;
     }
 };
 
@@ -264,15 +270,16 @@ template <int N, int CT, int E> struct CoopUnits {
 // when the step is in place).
 template <int N, int CT, int EE>
 __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, int use_c,
-                             const DevScalars &loc, float4 *slots, const float2 *src, float2 *dst)
+                             const DevScalars &loc, float4 *slots, const float2 *src, float2 *dst,
+                             int base = 0)
 {
     const Tables &T = P.T;
     using A = CoopAxis<N, CT, EE>;
     constexpr int E = A::E, TP = A::TP;
     const int units = a.ny / 2;
-    const CoopUnits<N, CT, EE> U;
+    const CoopUnits<N, CT, EE> U(base);
     float4 *sb = slots + U.g * A::SLOTS;
-    const GroupSync gs{1 + U.g, TP};
+    const GroupSync gs{U.bid, TP};
     const float cs = use_c ? (float)loc.c : 1.f;
     float acx2, acxcy;
     alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
@@ -319,7 +326,7 @@ __device__ __noinline__ void coop_rows_pt(const CoopArgs &a, const CoopPtrs &P, 
 // thread's strided elements are immediate offsets from one address.
 template <int N, int NX, int MODE, int CT, int EE>
 __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph, const DevScalars &loc,
-                          float4 *slots, float (&q)[3], float2 *psi)
+                          float4 *slots, float (&q)[3], float2 *psi, int base = 0)
 {
     const Tables &T = P.T;
     using A = CoopAxis<N, CT, EE>;
@@ -327,9 +334,9 @@ __device__ __noinline__ void coop_cols(const CoopArgs &a, const CoopPtrs &P, con
     constexpr bool PHASE = (MODE == COL_T_P || MODE == COL_T_PR);
     constexpr bool REDUCE = (MODE == COL_T_R || MODE == COL_T_PR);
     constexpr int units = NX / 2, w4 = NX / 2;                 // float4 per grid row
-    const CoopUnits<N, CT, EE> U;
+    const CoopUnits<N, CT, EE> U(base);
     float4 *sb = slots + U.g * A::SLOTS;
-    const GroupSync gs{1 + U.g, TP};
+    const GroupSync gs{U.bid, TP};
     float acx2, acxcy;
     alpha_amps(ph, loc.alpha_re, loc.alpha_im, acx2, acxcy);
     for (int u = U.gg; u < units; u += U.G) {
@@ -590,15 +597,15 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
 // is exp(+i theta) psi2), then T_x^H.  gq: sum of Im(conj(mu) in) L(r).
 template <int N, int CT, int EE>
 __device__ __noinline__ void coop_adj_rows(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph,
-                                           const float2 *psi2, float4 *slots, float &gq)
+                                           const float2 *psi2, float4 *slots, float &gq, int base = 0)
 {
     const Tables &T = P.T;
     using A = CoopAxis<N, CT, EE>;
     constexpr int E = A::E, TP = A::TP;
     const int units = a.ny / 2;
-    const CoopUnits<N, CT, EE> U;
+    const CoopUnits<N, CT, EE> U(base);
     float4 *sb = slots + U.g * A::SLOTS;
-    const GroupSync gs{1 + U.g, TP};
+    const GroupSync gs{U.bid, TP};
     float acx2, acxcy;
     alpha_amps(ph, 0.0, 0.0, acx2, acxcy);
     for (int u = U.gg; u < units; u += U.G) {
@@ -702,15 +709,15 @@ __device__ __noinline__ void coop_adj_rows(const CoopArgs &a, const CoopPtrs &P,
 // start state.  gq as in the row pass.
 template <int N, int NX, int CT, int EE>
 __device__ __noinline__ void coop_adj_cols(const CoopArgs &a, const CoopPtrs &P, const PhaseArgs &ph,
-                                           const float2 *psi2, float4 *slots, float &gq)
+                                           const float2 *psi2, float4 *slots, float &gq, int base = 0)
 {
     const Tables &T = P.T;
     using A = CoopAxis<N, CT, EE>;
     constexpr int E = A::E, TP = A::TP;
     constexpr int units = NX / 2, w4 = NX / 2;
-    const CoopUnits<N, CT, EE> U;
+    const CoopUnits<N, CT, EE> U(base);
     float4 *sb = slots + U.g * A::SLOTS;
-    const GroupSync gs{1 + U.g, TP};
+    const GroupSync gs{U.bid, TP};
     float acx2, acxcy;
     alpha_amps(ph, 0.0, 0.0, acx2, acxcy);
     for (int u = U.gg; u < units; u += U.G) {
@@ -879,6 +886,100 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
     }
 }
 
+// ------------------------------------------------------------------ adjoint and recomputation side by side
+// One epoch per step: the adjoint passes of segment k (steps s1 - 1 down to
+// s0, on st) on threads [0, CT) of each CTA, and the recomputation of segment
+// k - 1 (steps r0 .. r1 - 1, into st2) on threads [CT, 2 CT), with the pass
+// functions of coop_adj_kernel and coop_states_kernel, each role with its own
+// groups, exchange slots and named barriers.  Both programs take two grid
+// barriers per step, so they share them: epoch i runs adjoint step s1 - 1 - i
+// and recomputation step r0 + i (either only while it has steps left).  The
+// two roles touch different buffers (lambda and st; st2).  Every pass on
+// one CTA runs as one warp per scheduler and waits on its own latency, so two
+// roles per SM take little longer than one.  The recomputation role adds
+// exact zeros to the CTA's dJ/dv partial, so the gradient is bit for bit that
+// of coop_adj_kernel; the recomputed states are bit for bit coop_states_kernel's.
+template <int NX, int NY>
+__global__ void __launch_bounds__(2 * CoopCfg<NX, NY>::CT, 1) coop_adjrec_kernel(const __grid_constant__ CoopArgs a)
+{
+    using C = CoopCfg<NX, NY>;
+    static_assert(C::CPS == 1, "one CTA of both roles per SM");
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32 * NQ];
+    __shared__ DevScalars loc;                     // c = 1, alpha = 0 for the recomputation
+    __shared__ PhaseArgs s_ph, s_phr;
+    __shared__ CoopPtrs s_P;
+    __shared__ int s_ok;
+    __shared__ unsigned int s_k;
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *slots = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    if (threadIdx.x == 0) {
+        memset(&loc, 0, sizeof(loc));
+        loc.c = 1.0;
+        s_k = 0;
+        s_P.T = a.T;
+        s_P.V = a.V;
+        s_ok = check_index((long long)((unsigned char *)slots + 2 * C::SLOT_BYTES - smraw) - 1, dyn_smem_bytes(),
+                           a.T.sc);
+        if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const bool rec = threadIdx.x >= C::CT;         // whole warps: CT is a multiple of 32
+    float4 *my = slots + (rec ? C::SLOT_BYTES / sizeof(float4) : 0);
+    const double hh = __dmul_rn(0.5, a.dt);
+    const int G = (int)gridDim.x, R = NQ * MAX_BLOCKS / G;
+    const int m = a.s1 - a.s0, mr = a.r1 - a.r0, epochs = m > mr ? m : mr;
+    float q[3] = {0.f, 0.f, 0.f};
+    int hi = a.s1 - 1;
+    for (int i = 0; i < epochs; ++i) {
+        const bool adj = i < m, rc = i < mr;
+        const int s = a.s1 - 1 - i, sr = a.r0 + i;
+        const double ts = __dadd_rn(a.t0, __dmul_rn((double)s, a.dt)), te = __dadd_rn(ts, a.dt);
+        const double tr = __dadd_rn(a.t0, __dmul_rn((double)sr, a.dt)), tre = __dadd_rn(tr, a.dt);
+        const size_t slot = (size_t)(hi - s) * G + blockIdx.x;
+        if (adj) prefetch_l2_share(a.st + (size_t)(s - a.s0) * a.P, sizeof(float2) * (size_t)NX * NY);
+        if (threadIdx.x == 0) {
+            if (adj) s_ph = phase_dev(a, te, hh);
+            if (rc) s_phr = phase_dev(a, tr, hh);
+        }
+        __syncthreads();
+        float gq = 0.f;
+        if (!rec) {
+            if (adj) coop_adj_rows<NX, C::CT, C::E>(a, s_P, s_ph, a.st + (size_t)(s + 1 - a.s0) * a.P, my, gq, 0);
+        } else if (rc) {
+            coop_rows_pt<NX, C::CT, C::E>(a, s_P, s_phr, 0, loc, my, a.st2 + (size_t)(sr - a.r0) * a.P,
+                                          a.st2 + (size_t)(sr + 1 - a.r0) * a.P, C::CT);
+        }
+        float q1[1] = {adj ? 2.f * s_ph.h * gq : 0.f};
+        if (adj) block_sum<1>(q1, a.T.part_row + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (threadIdx.x == 0) {
+            if (adj) s_ph = phase_dev(a, ts, hh);
+            if (rc) s_phr = phase_dev(a, tre, hh);
+        }
+        __syncthreads();
+        gq = 0.f;
+        if (!rec) {
+            if (adj) coop_adj_cols<NY, NX, C::CT, C::E>(a, s_P, s_ph, a.st + (size_t)(s - a.s0) * a.P, my, gq, 0);
+        } else if (rc) {
+            coop_cols<NY, NX, COL_T_P, C::CT, C::E>(a, s_P, s_phr, loc, my, q, a.st2 + (size_t)(sr + 1 - a.r0) * a.P,
+                                                    C::CT);
+        }
+        q1[0] = adj ? 2.f * s_ph.h * gq : 0.f;
+        if (adj) block_sum<1>(q1, a.T.part_col + slot, red);
+        if (i + 1 < epochs || adj) {
+            if (!coop_sync(a, &s_ok, &s_k)) return;
+        }
+        if (adj && (hi - s + 1 == R || s == a.s0)) {
+            coop_flush_grad(a, hi, s);
+            hi = s - 1;
+            if (s > a.s0 && !coop_sync(a, &s_ok, &s_k)) return;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ reverse sweep by time reversal
 // The reverse sweep without checkpoints (GPE_ADJ_REVERSE) in one launch: for
 // s = s1 - 1 down to s0, the adjoint row pass on psi_{s+1} (the context's
@@ -974,19 +1075,21 @@ bool coop_ok(int nx, int ny) { return (nx == 512 || nx == 1024) && (ny == 512 ||
 // remembers the devices whose shared-memory limit was raised for K.
 template <int NX, int NY>
 static cudaError_t coop_go(void (*K)(CoopArgs), std::atomic<unsigned long long> &attr, const CoopArgs &a,
-                           cudaStream_t s)
+                           cudaStream_t s, int roles = 1)
 {
     using C = CoopCfg<NX, NY>;
-    const cudaError_t e = smem_opt_in(K, (int)C::SMEM, attr);
+    const int threads = roles * C::CT;
+    const size_t smem = roles * C::SLOT_BYTES + 128;
+    const cudaError_t e = smem_opt_in(K, (int)smem, attr);
     if (e != cudaSuccess) return e;
     int per = 0;
-    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, C::CT, C::SMEM);
+    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, threads, smem);
     if (r != cudaSuccess) return r;
     if (per < C::CPS) return cudaErrorCooperativeLaunchTooLarge;
     const int grid = C::CPS * sm_count();          // all resident
     if (grid < 1) return cudaErrorInvalidValue;
     void *args[] = {const_cast<CoopArgs *>(&a)};
-    return cudaLaunchCooperativeKernel((const void *)K, dim3(grid), dim3(C::CT), args, C::SMEM, s);
+    return cudaLaunchCooperativeKernel((const void *)K, dim3(grid), dim3(threads), args, smem, s);
 }
 
 enum { COOP_STEPS, COOP_STATES, COOP_ADJ, COOP_REV };
@@ -1011,6 +1114,17 @@ cudaError_t launch_coop_adj(const CoopArgs &a, cudaStream_t s)
     if (!coop_ok(a.nx, a.ny) || a.cavity || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL || a.s1 <= a.s0)
         return cudaErrorInvalidValue;
     return coop_dispatch(COOP_ADJ, a, s);
+}
+
+bool coop_adjrec_ok(int nx, int ny) { return nx == 512 && ny == 512; }
+
+cudaError_t launch_coop_adjrec(const CoopArgs &a, cudaStream_t s)
+{
+    if (!coop_adjrec_ok(a.nx, a.ny) || a.cavity || a.imag || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL ||
+        a.s1 <= a.s0 || a.r1 < a.r0 || !a.st2)
+        return cudaErrorInvalidValue;
+    static std::atomic<unsigned long long> attr{0};
+    return coop_go<512, 512>(coop_adjrec_kernel<512, 512>, attr, a, s, 2);
 }
 
 cudaError_t launch_coop_rev(const CoopArgs &a, cudaStream_t s)

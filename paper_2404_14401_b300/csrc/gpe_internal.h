@@ -180,6 +180,11 @@ struct CoopArgs {
     // the reverse sweep by time reversal (launch_coop_rev): kinetic factors
     // of -dt for the steps back, nx and ny entries
     const float2 *kxb, *kyb;
+    // launch_coop_adjrec: the previous segment's steps r0 .. r1 - 1,
+    // recomputed from st2[0] = psi_{r0} into st2 (P elements apart) while
+    // the adjoint passes of steps s1 - 1 .. s0 run on st
+    float2 *st2;
+    int r0, r1;
 };
 bool coop_ok(int nx, int ny);              // grid sizes the cooperative kernels are built for
 cudaError_t launch_coop(const CoopArgs &a, cudaStream_t s);
@@ -192,6 +197,12 @@ cudaError_t launch_coop_states(const CoopArgs &a, cudaStream_t s);
 // the reverse sweep of GPE_ADJ_REVERSE over steps s1 - 1 down to s0 in one
 // cooperative launch: psi holds psi_{s1} on entry and psi_{s0} on return
 cudaError_t launch_coop_rev(const CoopArgs &a, cudaStream_t s);
+// grids launch_coop_adjrec is built for (512^2)
+bool coop_adjrec_ok(int nx, int ny);
+// the adjoint passes of one checkpointed segment (as launch_coop_adj) and
+// the recomputation of the segment before it (as launch_coop_states, into
+// st2) side by side in one cooperative launch
+cudaError_t launch_coop_adjrec(const CoopArgs &a, cudaStream_t s);
 
 // Launchers (gpe_kernels.cu).  Return cudaGetLastError() of the launch.
 // tile_shift: the one-shot row pass takes 2^-tile_shift of its default rows
