@@ -85,3 +85,31 @@ def test_bounds_check_build_compiles_and_exports_the_same_entry_points():
     lib.gpe_status_string.restype = ctypes.c_char_p
     assert lib.gpe_status_string(abi.GPE_EBOUNDS) == b"GPE_EBOUNDS"
     assert abi.status_string(abi.GPE_EBOUNDS) == "GPE_EBOUNDS"
+
+
+def test_adjoint_workspace_layout():
+    """The adjoint workspace sizes include/gpe.h states, without a GPU:
+    checkpointed, ceil(n/S) + S + 3 copies of psi (S + 1 more on 512^2 grids,
+    the second segment buffer) plus 2n + 1 doubles, S = ceil(sqrt(n)); by time
+    reversal, 2 copies (psi_T, lambda), the kinetic factors of -dt along each
+    axis and the doubles.  Every region starts on a 256-byte boundary."""
+    from paper_2404_14401_b300 import gpe as abi
+
+    def a256(x):
+        return (x + 255) // 256 * 256
+
+    for nx, ny, n in ((512, 512, 4000), (256, 256, 4000), (512, 1024, 100), (512, 512, 1), (512, 512, 7),
+                      (1024, 1024, 10), (64, 2048, 3)):
+        P = a256(8 * nx * ny)
+        S = 1
+        while S * S < n:
+            S += 1
+        K = -(-n // S)
+        copies = K + S + 3 + (S + 1 if (nx, ny) == (512, 512) else 0)
+        g = a256(8 * (2 * n + 1))
+        assert abi.gpe_adjoint_workspace_size_ex(nx, ny, n, abi.GPE_ADJ_CHECKPOINT) == copies * P + g, (nx, ny, n)
+        assert abi.gpe_adjoint_workspace_size(nx, ny, n) == copies * P + g
+        rev = 2 * P + a256(8 * nx) + a256(8 * ny) + g
+        assert abi.gpe_adjoint_workspace_size_ex(nx, ny, n, abi.GPE_ADJ_REVERSE) == rev, (nx, ny, n)
+    assert abi.gpe_adjoint_workspace_size_ex(512, 512, 0, abi.GPE_ADJ_CHECKPOINT) == 0
+    assert abi.gpe_adjoint_workspace_size_ex(500, 512, 10, abi.GPE_ADJ_CHECKPOINT) == 0
