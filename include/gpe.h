@@ -398,7 +398,8 @@ gpe_status gpe_tune(gpe_ctx *ctx, double dt, gpe_mode mode, void *scratch_dev, s
  * 0.157 s against 0.350 s.)
  * GPE_ADJ_REVERSE on those grids: the forward sweep in place in one launch
  * (the same unfused steps, so J is the checkpointed call's bit for bit) and
- * the whole reverse sweep in one more (0.166 s against 0.305 s).
+ * the whole reverse sweep in one more, on 512^2 with the step back one
+ * step ahead beside the adjoint passes (0.152 s against 0.305 s).
  *
  * phi_dev: target state, complex64 [ny][nx] on the device (borrowed, 16-byte
  * aligned).  adj_ws: device scratch of at least
@@ -425,9 +426,12 @@ gpe_status gpe_adjoint_lattice(gpe_ctx *ctx, int nsteps, double dt, const void *
  * gradient differs from the checkpointed one by about that much (the
  * reverse sweep costs the same passes as the recomputation it replaces).
  * Workspace (gpe_adjoint_workspace_size_ex): 2 copies of psi (psi_T and
- * lambda), the kinetic factors of -dt and 2 nsteps + 1 doubles, independent
- * of the number of steps apart from those doubles; the step back overwrites
- * the context's psi after the row adjoint pass of that step has read it.  Returns 0 / GPE_EINVAL for an unknown
+ * lambda; 2 more on 512^2 grids, where the step back runs one step ahead of
+ * the adjoint passes through three state buffers), the kinetic factors of
+ * -dt and 2 nsteps + 1 doubles, independent of the number of steps apart
+ * from those doubles; elsewhere the step back overwrites the context's psi
+ * after the row adjoint pass of that step has read it.  Returns 0 /
+ * GPE_EINVAL for an unknown
  * variant; otherwise as gpe_adjoint_workspace_size / gpe_adjoint_lattice. */
 typedef enum { GPE_ADJ_CHECKPOINT = 0, GPE_ADJ_REVERSE = 1 } gpe_adjoint_variant;
 size_t gpe_adjoint_workspace_size_ex(int nx, int ny, int nsteps, int variant);

@@ -729,7 +729,9 @@ gpe_status gpe_step(gpe_ctx *c, int n, double dt, gpe_mode mode)
 // launch_coop_adjrec, which recomputes one segment while the adjoint passes
 // of the next run), lambda, and the 2n + 1 per-phase dJ/dv.
 // GPE_ADJ_REVERSE keeps no checkpoints: ck holds psi_T only, and kx / ky the
-// kinetic factors of -dt for the backward steps (st is not used).
+// kinetic factors of -dt for the backward steps; on the grids of
+// launch_coop_rev2, st and st2 are two more state buffers (the step back runs
+// one step ahead of the adjoint passes, through three buffers).
 struct AdjLayout {
     int S, K, variant;
     size_t P, ck, st, st2, lam, g, kx, ky, total;      // st2: 0 when there is no second segment buffer
@@ -743,11 +745,17 @@ static AdjLayout adj_layout(int nx, int ny, int n, int variant = GPE_ADJ_CHECKPO
     if (variant == GPE_ADJ_REVERSE) {
         L.S = n;
         L.K = 0;
-        L.st = L.st2 = 0;
         L.lam = L.ck + L.P;
         L.kx = L.lam + L.P;
         L.ky = L.kx + align256(sizeof(float2) * (size_t)nx);
-        L.g = L.ky + align256(sizeof(float2) * (size_t)ny);
+        size_t o = L.ky + align256(sizeof(float2) * (size_t)ny);
+        L.st = L.st2 = 0;
+        if (coop_adjrec_ok(nx, ny)) {              // two more state buffers for launch_coop_rev2
+            L.st = o;
+            L.st2 = o + L.P;
+            o += 2 * L.P;
+        }
+        L.g = o;
     } else {
         L.S = 1;
         while ((long long)L.S * L.S < n) ++L.S;
@@ -837,10 +845,11 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
     // steps s0 .. s1 - 1 in one cooperative launch: their states into st
     // (COOP_FWD), their adjoint passes (COOP_BWD), those beside the
     // recomputation of steps r0 .. r1 - 1 into st2 (COOP_BOTH), or the
-    // reverse sweep by time reversal (COOP_REV).  *ran is false if the device refused the
+    // reverse sweep by time reversal (COOP_REV; COOP_REV2 with the step back
+    // beside the adjoint passes, through psi, st and st2).  *ran is false if the device refused the
     // launch (nothing of it ran); the context keeps to the per-pass path from
     // then on.
-    enum { COOP_FWD, COOP_BWD, COOP_REV, COOP_BOTH };
+    enum { COOP_FWD, COOP_BWD, COOP_REV, COOP_REV2, COOP_BOTH };
     auto coop_run = [&](int which, int s0, int s1, bool *ran) -> gpe_status {
         *ran = false;
         ca->s0 = s0;
@@ -848,6 +857,7 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         TRY(cuda_check(c, cudaMemsetAsync(&c->T.sc->bar_count, 0, 2 * sizeof(unsigned int), c->stream), "memset"));
         const cudaError_t e = which == COOP_BWD    ? launch_coop_adj(*ca, c->stream)
                               : which == COOP_REV  ? launch_coop_rev(*ca, c->stream)
+                              : which == COOP_REV2 ? launch_coop_rev2(*ca, c->stream)
                               : which == COOP_BOTH ? launch_coop_adjrec(*ca, c->stream)
                                                    : launch_coop_states(*ca, c->stream);
         if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
@@ -976,7 +986,12 @@ static gpe_status adjoint_run(gpe_ctx *c, int n, double dt, const float2 *phi, u
         if (coop) {
             ca->kxb = kx;
             ca->kyb = ky;
-            TRY(coop_run(COOP_REV, 0, n, &done));
+            if (L.st2) {                           // on 512^2: the step back beside the adjoint passes
+                ca->st = (float2 *)(ws + L.st);
+                ca->st2 = (float2 *)(ws + L.st2);
+                TRY(coop_run(COOP_REV2, 0, n, &done));
+            }
+            if (!done && coop) TRY(coop_run(COOP_REV, 0, n, &done));
             if (done) c->t = t0;
         }
         for (int s = n - 1; s >= 0 && !done; --s) {

@@ -1067,6 +1067,113 @@ __global__ void __launch_bounds__(CoopCfg<NX, NY>::CT, CoopCfg<NX, NY>::CPS)
     }
 }
 
+// ------------------------------------------------------------------ reverse sweep, two roles
+// The reverse sweep by time reversal on 512^2 in 256-thread CTAs: threads
+// [0, CT) run the adjoint passes of step s (row pass with psi_{s+1}, column
+// pass with psi_s) while threads [CT, 2 CT) run the step of -dt one step
+// ahead, psi_s -> psi_{s-1} (row pass from psi_s into the next buffer, column
+// pass there in place), with the pass functions and times of
+// coop_rev_kernel.  psi_k lives in buffer (s1 - k) mod 3 of {psi, st, st2}:
+// in each epoch the step back writes only psi_{s-1}'s buffer, which the
+// adjoint role does not read before the next step.  A prologue takes the
+// step back of step s1 - 1 alone.  Both roles share the two grid barriers of
+// each step; the step-back role adds exact zeros to the dJ/dv partials, so
+// gradient and states are coop_rev_kernel's bit for bit.  On return psi_{s0}
+// is in buffer (s1 - s0) mod 3.
+template <int NX, int NY>
+__global__ void __launch_bounds__(2 * CoopCfg<NX, NY>::CT, 1) coop_rev2_kernel(const __grid_constant__ CoopArgs a)
+{
+    using C = CoopCfg<NX, NY>;
+    static_assert(C::CPS == 1, "one CTA of both roles per SM");
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32 * NQ];
+    __shared__ DevScalars loc;                     // c = 1, alpha = 0 for the step back
+    __shared__ PhaseArgs s_ph, s_phb;
+    __shared__ CoopPtrs s_P, s_Pb;                 // kinetic tables of +dt (adjoint) and -dt (step back)
+    __shared__ int s_ok;
+    __shared__ unsigned int s_k;
+
+    const uint32_t s0 = smem_u32(smraw);
+    float4 *slots = reinterpret_cast<float4 *>(smraw + ((128u - (s0 & 127u)) & 127u));
+    if (threadIdx.x == 0) {
+        memset(&loc, 0, sizeof(loc));
+        loc.c = 1.0;
+        s_k = 0;
+        s_P.T = a.T;
+        s_P.V = a.V;
+        s_Pb = s_P;
+        s_Pb.T.kinx = const_cast<float2 *>(a.kxb);
+        s_Pb.T.kiny = const_cast<float2 *>(a.kyb);
+        s_ok = check_index((long long)((unsigned char *)slots + 2 * C::SLOT_BYTES - smraw) - 1, dyn_smem_bytes(),
+                           a.T.sc);
+        if (!s_ok) atomicExch(&a.T.sc->bar_abort, 1u);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const bool back = threadIdx.x >= C::CT;        // whole warps: CT is a multiple of 32
+    float4 *my = slots + (back ? C::SLOT_BYTES / sizeof(float4) : 0);
+    float2 *const buf[3] = {a.psi, a.st, a.st2};
+    auto state = [&](int k) { return buf[(a.s1 - k) % 3]; };
+    const double hh = __dmul_rn(0.5, a.dt), mh = -hh;
+    const int G = (int)gridDim.x, R = NQ * MAX_BLOCKS / G;
+    float q[3] = {0.f, 0.f, 0.f};
+    // the step back of step r: the conjugate opening phase at t_{r+1}, T(-dt),
+    // the conjugate closing phase at t_r, psi_{r+1} -> psi_r; row half
+    // (phase 0) or column half (phase 1), run by the step-back role
+    auto step_back = [&](int r, int half) {
+        if (!back) return;
+        if (half == 0)
+            coop_rows_pt<NX, C::CT, C::E>(a, s_Pb, s_phb, 0, loc, my, state(r + 1), state(r), C::CT);
+        else
+            coop_cols<NY, NX, COL_T_P, C::CT, C::E>(a, s_Pb, s_phb, loc, my, q, state(r), C::CT);
+    };
+    auto back_phase = [&](int r, int half) {
+        const double tr = __dadd_rn(a.t0, __dmul_rn((double)r, a.dt));
+        return half == 0 ? phase_dev(a, __dadd_rn(tr, a.dt), mh) : phase_dev(a, tr, mh);
+    };
+    // prologue: psi_{s1 - 1}
+    for (int half = 0; half < 2; ++half) {
+        if (threadIdx.x == 0) s_phb = back_phase(a.s1 - 1, half);
+        __syncthreads();
+        step_back(a.s1 - 1, half);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+    }
+    int hi = a.s1 - 1;
+    for (int s = a.s1 - 1; s >= a.s0; --s) {
+        const bool ahead = s - 1 >= a.s0;          // the step back of step s - 1 runs beside this step
+        const double ts = __dadd_rn(a.t0, __dmul_rn((double)s, a.dt));
+        const double te = __dadd_rn(ts, a.dt);
+        const size_t slot = (size_t)(hi - s) * G + blockIdx.x;
+        if (threadIdx.x == 0) {
+            s_ph = phase_dev(a, te, hh);
+            if (ahead) s_phb = back_phase(s - 1, 0);
+        }
+        __syncthreads();
+        float gq = 0.f;
+        if (!back) coop_adj_rows<NX, C::CT, C::E>(a, s_P, s_ph, state(s + 1), my, gq, 0);
+        else if (ahead) step_back(s - 1, 0);
+        float q1[1] = {back ? 0.f : 2.f * s_ph.h * gq};
+        block_sum<1>(q1, a.T.part_row + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (threadIdx.x == 0) {
+            s_ph = phase_dev(a, ts, hh);
+            if (ahead) s_phb = back_phase(s - 1, 1);
+        }
+        __syncthreads();
+        gq = 0.f;
+        if (!back) coop_adj_cols<NY, NX, C::CT, C::E>(a, s_P, s_ph, state(s), my, gq, 0);
+        else if (ahead) step_back(s - 1, 1);
+        q1[0] = back ? 0.f : 2.f * s_ph.h * gq;
+        block_sum<1>(q1, a.T.part_col + slot, red);
+        if (!coop_sync(a, &s_ok, &s_k)) return;
+        if (hi - s + 1 == R || s == a.s0) {
+            coop_flush_grad(a, hi, s);
+            hi = s - 1;
+            if (s > a.s0 && !coop_sync(a, &s_ok, &s_k)) return;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launch
 bool coop_ok(int nx, int ny) { return (nx == 512 || nx == 1024) && (ny == 512 || ny == 1024); }
 
@@ -1125,6 +1232,15 @@ cudaError_t launch_coop_adjrec(const CoopArgs &a, cudaStream_t s)
         return cudaErrorInvalidValue;
     static std::atomic<unsigned long long> attr{0};
     return coop_go<512, 512>(coop_adjrec_kernel<512, 512>, attr, a, s, 2);
+}
+
+cudaError_t launch_coop_rev2(const CoopArgs &a, cudaStream_t s)
+{
+    if (!coop_adjrec_ok(a.nx, a.ny) || a.cavity || a.imag || a.nctrl < 0 || a.nctrl > COOP_MAX_CTRL ||
+        a.s1 <= a.s0 || !a.kxb || !a.kyb || !a.st || !a.st2)
+        return cudaErrorInvalidValue;
+    static std::atomic<unsigned long long> attr{0};
+    return coop_go<512, 512>(coop_rev2_kernel<512, 512>, attr, a, s, 2);
 }
 
 cudaError_t launch_coop_rev(const CoopArgs &a, cudaStream_t s)

@@ -197,6 +197,10 @@ cudaError_t launch_coop_states(const CoopArgs &a, cudaStream_t s);
 // the reverse sweep of GPE_ADJ_REVERSE over steps s1 - 1 down to s0 in one
 // cooperative launch: psi holds psi_{s1} on entry and psi_{s0} on return
 cudaError_t launch_coop_rev(const CoopArgs &a, cudaStream_t s);
+// the same on the grids of launch_coop_adjrec, with the step back one step
+// ahead beside the adjoint passes; psi_k in buffer (s1 - k) mod 3 of
+// {psi, st, st2}
+cudaError_t launch_coop_rev2(const CoopArgs &a, cudaStream_t s);
 // grids launch_coop_adjrec is built for (512^2)
 bool coop_adjrec_ok(int nx, int ny);
 // the adjoint passes of one checkpointed segment (as launch_coop_adj) and
